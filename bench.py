@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark: Zernike basis values per second on the 2601-mode radial workload.
+
+Workload (radial_n100): all (n, m) with 0 <= m <= n <= 100, n - m even (2601 modes), 100000
+Chebyshev-Gauss points in [0, 1], radial derivative orders k = 0..3.  One step = one call of
+the library's radial walk over the whole batch (plan built once, outside the timed region),
+writing 4 x 2601 x 100000 float64 values (8.32 GB).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas; the
+path has no exchange step) and rank 0 prints the aggregate.  Prints ONE JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Zernike basis values/s (FP64, points x modes x derivs)"
+UNIT = "values/s"
+WORKLOAD = "radial_n100"
+# Float64 issue roofline: GB300 issues 2 float64 lanes per SM per clock (1.25 TFLOP/s
+# nominal = 152 SMs x 2 lanes x 2 flop x 2.07 GHz); one FMA or MUL = one op.
+SMS, DP_LANES_PER_SM, SM_MAX_MHZ = 152, 2, 2070.0
+DP_OPS_PEAK = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
+# float64 operations per (point, mode) of the k <= 3 walk: 1 (g) + 1 (g') + 1 + 2 + 3 + 3
+# (Taylor lanes 0..3) + 4 (stores scaled by k! w_N).
+DP_OPS_PER_VALUE_TUPLE = 15
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-points", type=int, default=256)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2409_19156_gb300 import inputs
+
+    ns, ms = inputs.radial_modes(100)
+    r = inputs.chebyshev_gauss_points(100_000)
+    return ns, ms, r
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.tmp.read())) if len(r) >= 9]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: power above the midpoint between idle and peak draw
+        thr = min(power) + 0.5 * (max(power) - min(power))
+        loaded = [s for s, p in zip(sm, power) if p >= thr] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def _oracle_chunk(args):
+    ns, ms, rs = args
+    from oracle import radial as oradial
+
+    tab = oradial.radial_table(ns, ms, rs, 3)
+    return len(ns) * len(rs) * 4 + 0 * len(tab)
+
+
+def time_oracle(n_points: int, cores: int | None = None) -> dict:
+    """The exact CPU oracle on a sample of the workload's points (all modes, k = 0..3), on a
+    spawn-started process pool over the host's cores."""
+    import multiprocessing as mp
+
+    ns, ms, r = workload()
+    cores = cores or os.cpu_count() or 1
+    idx = [int(i) for i in (len(r) - 1) * (0.5 + 0.5 * __import__("numpy").cos(
+        math.pi * (__import__("numpy").arange(n_points) + 0.5) / n_points))]
+    pts = [float(r[i]) for i in idx]
+    chunks = [pts[i::cores] for i in range(cores)]
+    chunks = [c for c in chunks if c]
+    nsl, msl = [int(v) for v in ns], [int(v) for v in ms]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(chunks)) as pool:
+        pool.map(_oracle_chunk, [(nsl[:3], msl[:3], c[:1]) for c in chunks])  # start-up outside timing
+        t0 = time.perf_counter()
+        vals = sum(pool.map(_oracle_chunk, [(nsl, msl, c) for c in chunks]))
+        dt = time.perf_counter() - t0
+    return {"value": vals / dt, "unit": UNIT, "cores": len(chunks), "kind": "oracle",
+            "sample": f"{len(pts)} of the 100000 points x all 2601 modes x k=0..3 "
+                      f"({vals} exact-rational values in {dt:.2f} s)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ns, ms, r = workload()
+    J, P, K = len(ns), len(r), 4
+    dev = torch.device("cuda", local)
+    plan = zp.Plan(ns, ms, device=dev)
+    rt = torch.as_tensor(r, device=dev)
+    out = torch.empty((K, J, P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 2x L2
+    lib = _lib.load()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step():
+        st = lib.zp_radial_plan(plan.handle, rt.data_ptr(), P, 3, out.data_ptr(), sp)
+        if st:
+            _lib.check("zp_radial_plan", st)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(ms_steps)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    values_per_step = P * J * K
+    value = world * values_per_step / (ms_per_step * 1e-3)
+
+    # Roofline: the walk kernel is the only launch of a step (float64-issue bound).
+    dp_ops = DP_OPS_PER_VALUE_TUPLE * P * J
+    kernel_ms = statistics.mean(ms_steps)
+    achieved = dp_ops / (kernel_ms * 1e-3)
+    out_bytes = values_per_step * 8
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # End to end through the C ABI with host buffers: r from pinned host memory in, the
+    # whole result back to pinned host memory, every step.
+    e2e = None
+    if args.e2e_steps > 0:
+        r_host = torch.as_tensor(r).pin_memory()
+        out_host = torch.empty((K, J, P), dtype=torch.float64, pin_memory=True)
+        rt2 = torch.empty_like(rt)
+
+        def e2e_step():
+            rt2.copy_(r_host, non_blocking=True)
+            st = lib.zp_radial_plan(plan.handle, rt2.data_ptr(), P, 3, out.data_ptr(), sp)
+            if st:
+                _lib.check("zp_radial_plan", st)
+            out_host.copy_(out, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        te = torch.tensor([e0.elapsed_time(e1) / args.e2e_steps], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        assert float(out_host[0, 0, 0]) == float(out[0, 0, 0].item())
+        e2e = {"value": world * values_per_step / (float(te.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": out_bytes, "ms_per_step": float(te.item())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(args.cpu_sample_points)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "modes": J, "n_max": 100, "points": P, "derivs": K,
+                       "points_dist": "Chebyshev-Gauss nodes mapped to [0,1]", "parallelism": f"replicas{world}",
+                       "l2": "256 MB write between steps, outside the per-step CUDA events; each step writes 8.3 GB"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": DP_OPS_PEAK / 1e9,
+                         "unit": "G float64 ops/s", "frac": achieved / DP_OPS_PEAK, "traffic": None,
+                         "kernel": "walk_kernel<3,false,true>", "ops_per_launch": dp_ops,
+                         "peak_source": "2 float64 lanes/SM/clk x 152 SMs x 2070 MHz (probe measured 1.91)",
+                         "hbm_write_gbs": out_bytes / (kernel_ms * 1e-3) / 1e9,
+                         "hbm_frac_of_measured_copy": out_bytes / (kernel_ms * 1e-3) / 1e9 / hbm_peak},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": args.steps,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args) -> None:
+    """The oracle as it stands on the host cores: each step is a bounded sample of the same
+    workload (all modes, k = 0..3, a fixed set of points)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    n_pts = max(os.cpu_count() or 1, 16)
+    for _ in range(args.warmup):
+        time_oracle(n_pts)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(time_oracle(n_pts))
+    value = statistics.mean(v["value"] for v in vals)
+    ms_per_step = statistics.mean(1e3 * n_pts * 2601 * 4 / v["value"] for v in vals)
+    cpu = dict(vals[0])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "exact rational (rounded to f64)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "modes": 2601, "n_max": 100, "points": 100_000, "derivs": 4,
+                       "parallelism": "host cores", "sample_points_per_step": n_pts},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * zernike_gb300.h -- C ABI of the GB300 (sm_103a) Zernike basis / series library.
+ *
+ * The library evaluates the radial Zernike polynomials R_n^m(rho), their rho-derivatives
+ * of order 0..3, the Zernike functions Z_n^m(rho, theta) = R_n^{|m|}(rho) cos(m theta)
+ * (m >= 0) or R_n^{|m|}(rho) sin(|m| theta) (m < 0), and series of them, through the
+ * Jacobi form R_n^m(rho) = (-1)^((n-m)/2) rho^m P_{(n-m)/2}^{(m,0)}(1 - 2 rho^2) and the
+ * three-term Jacobi recursion in n for each m (Sec. 2: the Jacobi relation, the beta = 0
+ * recursion; Sec. 3: Algorithm 1's per-m column walk).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Mode lists n[], m[] are HOST int32 arrays of length n_modes.  A mode is valid when
+ *    n >= 0, |m| <= n and n - |m| is even (Sec. 2).  Duplicated modes are allowed (the
+ *    duplicated-modes variant of Sec. 3); each occurrence gets its own output column.
+ *    Output columns follow the caller's mode order.  Radial entry points use |m|.
+ *  - Point arrays r[] (and theta[]) are DEVICE float64 arrays of length n_points.  r is
+ *    evaluated as the polynomial it is: values outside [0, 1] are not clamped.
+ *  - Outputs are DEVICE arrays owned and allocated by the caller; the library never keeps a
+ *    pointer to them after the call returns.  Layouts are row-major with the point index
+ *    fastest unless stated.
+ *  - Arguments are validated on the host before anything is launched.  On any error the
+ *    call returns a non-zero zp_status, launches nothing and leaves outputs untouched;
+ *    zp_last_error() then holds a one-line description (per host thread).
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) on the CURRENT device.  n_points == 0 or n_modes == 0 returns
+ *    ZP_OK without launching.
+ *  - The mode-list entry points build (and cache, keyed by the exact mode list and device)
+ *    a plan on first use; that first call copies small tables to the device synchronously.
+ *    Inside CUDA-graph capture use the *_plan variants with a plan created beforehand.
+ */
+#ifndef ZERNIKE_GB300_H
+#define ZERNIKE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ZP_API __attribute__((visibility("default")))
+#else
+#define ZP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ZP_OK = 0,
+  ZP_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad enum, misaligned pointer */
+  ZP_ERR_INVALID_MODE = 2,  /* a mode breaks n >= 0, |m| <= n, n - |m| even, or n > ZP_MAX_N */
+  ZP_ERR_DERIV_ORDER = 3,   /* derivative order outside 0..3 */
+  ZP_ERR_CUDA = 4,          /* a CUDA runtime or cuBLAS call failed */
+  ZP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  ZP_ERR_UNSUPPORTED = 6,   /* valid request this build does not support (e.g. wrong GPU) */
+  ZP_ERR_NO_MEMORY = 7      /* a device allocation failed */
+} zp_status;
+
+typedef enum {
+  ZP_PREC_FP64 = 0,   /* float64 throughout; outputs float64 */
+  ZP_PREC_BF16X3 = 1, /* float64 basis, contraction on tensor cores as hi*hi + hi*lo + lo*hi
+                         with bfloat16 halves and float32 accumulation; outputs float32 */
+  ZP_PREC_TF32 = 2    /* float64 basis rounded to TF32, tensor-core contraction with float32
+                         accumulation; outputs float32 */
+} zp_precision;
+
+/* Largest radial order accepted (recursion tables live in shared memory). */
+#define ZP_MAX_N 1000
+
+typedef struct zp_plan zp_plan;
+
+/* One-line text for a status code (static storage). */
+ZP_API const char* zp_status_string(zp_status status);
+
+/* Description of the last error raised on the calling host thread ("" if none). */
+ZP_API const char* zp_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+ZP_API int32_t zp_version(void);
+
+/*
+ * Plans.  A plan holds everything derived from a mode list: validation, the grouping of
+ * modes into |m| columns ordered by recursion length (Algorithm 1's outer loop over
+ * alpha = m), the Jacobi-degree N = (n - |m|)/2 of every output column, and the recursion
+ * coefficient tables of the beta = 0 Jacobi recursion (Sec. 2), uploaded to the current
+ * device.  zp_plan_create copies tables synchronously (call it outside stream capture).
+ * A plan may be used from any stream of the device it was created on; it is read-only
+ * after creation and may be shared by concurrent calls.  zp_plan_destroy frees it
+ * (synchronising the device first).  *out is written only on success.
+ */
+ZP_API zp_status zp_plan_create(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out);
+ZP_API zp_status zp_plan_destroy(zp_plan* plan);
+/* n_modes, largest n, number of distinct |m| columns of a plan (any pointer may be NULL). */
+ZP_API zp_status zp_plan_info(const zp_plan* plan, int64_t* n_modes, int32_t* n_max, int32_t* n_columns);
+
+/*
+ * Radial polynomials and rho-derivatives (Sec. 2 Jacobi relation and recursion; derivative
+ * orders as in the accuracy study of Sec. 4, Fig. 1).
+ *   out: DEVICE float64 [max_deriv+1][n_modes][n_points];
+ *        out[(k*n_modes + j)*n_points + p] = d^k/drho^k R_{n_j}^{|m_j|}(r_p).
+ *   max_deriv in 0..3.
+ */
+ZP_API zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes,
+                    const double* r, int64_t n_points, int32_t max_deriv,
+                    double* out, void* stream);
+ZP_API zp_status zp_radial_plan(const zp_plan* plan, const double* r, int64_t n_points,
+                         int32_t max_deriv, double* out, void* stream);
+
+/*
+ * Zernike functions (Sec. 2 definition of Z) and their derivatives.
+ *   out:        DEVICE float64 [max_deriv+1][n_modes][n_points],
+ *               out[(k*n_modes + j)*n_points + p] = d^k/drho^k Z_{n_j}^{m_j}(r_p, theta_p).
+ *   out_dtheta: DEVICE float64 [n_modes][n_points] = d/dtheta Z_{n_j}^{m_j}, or NULL.
+ */
+ZP_API zp_status zp_basis(const int32_t* n, const int32_t* m, int64_t n_modes,
+                   const double* r, const double* theta, int64_t n_points, int32_t max_deriv,
+                   double* out, double* out_dtheta, void* stream);
+ZP_API zp_status zp_basis_plan(const zp_plan* plan, const double* r, const double* theta,
+                        int64_t n_points, int32_t max_deriv, double* out, double* out_dtheta,
+                        void* stream);
+
+/*
+ * Algorithm 2 of Sec. 3 (the paper's per-mode GPU variant): every (point, mode) runs its
+ * own recursion from P_0, P_1 up to its own degree and stores only the last value.  Kept
+ * as the comparison kernel for the per-column walk; same output layout as zp_radial with
+ * max_deriv = 0.
+ */
+ZP_API zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_t n_points,
+                             double* out, void* stream);
+
+/*
+ * Series of Zernike functions (the spectral expansion motivated in Sec. 3's footnote):
+ *   F[p, s] = sum_j Z_j(r_p, theta_p) * coeffs[j, s].
+ *   coeffs: DEVICE float64 [n_modes][n_sets] row-major.
+ *   out:    DEVICE [n_points][n_sets] row-major; float64 for ZP_PREC_FP64, float32 for
+ *           ZP_PREC_BF16X3 / ZP_PREC_TF32.
+ * The float64 form writes the basis to scratch device memory (allocated stream-ordered on
+ * `stream` and released before return) and contracts with cuBLAS DGEMM.  The split forms
+ * run the float64 recursion into tensor-core tiles (tcgen05) with float32 accumulation.
+ */
+ZP_API zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes,
+                         const double* r, const double* theta, int64_t n_points,
+                         const double* coeffs, int64_t n_sets, zp_precision prec,
+                         void* out, void* stream);
+ZP_API zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double* theta,
+                              int64_t n_points, const double* coeffs, int64_t n_sets,
+                              zp_precision prec, void* out, void* stream);
+
+/*
+ * Adjoint of the series (the reverse-mode derivative that Sec. 3 provides by a custom
+ * rule), float64 throughout.  With G = grad_out (DEVICE float64 [n_points][n_sets]):
+ *   grad_coeffs[j, s] = sum_p Z_j(p) G[p, s]                         ([n_modes][n_sets])
+ *   grad_r[p]         = sum_j dZ_j/drho(p)   sum_s coeffs[j, s] G[p, s]      ([n_points])
+ *   grad_theta[p]     = sum_j dZ_j/dtheta(p) sum_s coeffs[j, s] G[p, s]      ([n_points])
+ * Any of the three outputs may be NULL (not computed).  The basis is recomputed, never
+ * read from a previous forward call.  Reductions are deterministic (no float atomics).
+ */
+ZP_API zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes,
+                            const double* r, const double* theta, int64_t n_points,
+                            const double* coeffs, int64_t n_sets, const double* grad_out,
+                            double* grad_coeffs, double* grad_r, double* grad_theta,
+                            void* stream);
+ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const double* theta,
+                                 int64_t n_points, const double* coeffs, int64_t n_sets,
+                                 const double* grad_out, double* grad_coeffs, double* grad_r,
+                                 double* grad_theta, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZERNIKE_GB300_H */

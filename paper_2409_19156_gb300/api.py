@@ -1,0 +1,185 @@
+"""Python front end: torch tensors in, torch tensors out, every step in the CUDA library.
+
+Functions mirror the C ABI (include/zernike_gb300.h):
+    radial(n, m, r, max_deriv)            -> [K][J][P] float64
+    basis(n, m, r, theta, max_deriv)      -> ([K][J][P], dtheta [J][P] or None)
+    radial_per_mode(plan, r)              -> [J][P] (Algorithm 2 comparison kernel)
+    series_eval(n, m, r, theta, C, prec)  -> [P][S] (float64, or float32 for split precision)
+    series_adjoint(n, m, r, theta, C, G)  -> (grad_C, grad_r, grad_theta)
+`n`, `m` are host integer sequences; r, theta, C, G are CUDA float64 tensors.  Work is
+enqueued on torch's current stream of the tensors' device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+PREC = {"fp64": 0, "bf16x3": 1, "tf32": 2}
+
+
+def _stream(device: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    return t.contiguous()
+
+
+class Plan:
+    """A mode list prepared once (validated, grouped by |m|, tables on the device)."""
+
+    def __init__(self, n, m, device=None):
+        self.n = _lib.modes_i32(n)
+        self.m = _lib.modes_i32(m)
+        if self.n.shape != self.m.shape or self.n.ndim != 1:
+            raise ValueError("n and m must be 1-D sequences of equal length")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _lib.call("zp_plan_create", _lib.i32_ptr(self.n), _lib.i32_ptr(self.m), len(self.n), ctypes.byref(handle))
+        self.handle = handle
+
+    @property
+    def n_modes(self) -> int:
+        return len(self.n)
+
+    def info(self) -> dict:
+        nm, nmax, ncol = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.call("zp_plan_info", self.handle, ctypes.byref(nm), ctypes.byref(nmax), ctypes.byref(ncol))
+        return {"n_modes": nm.value, "n_max": nmax.value, "n_columns": ncol.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.call("zp_plan_destroy", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def radial(n, m, r: torch.Tensor, max_deriv: int = 0, plan: Plan | None = None, out=None) -> torch.Tensor:
+    r = _dev_f64(r, "r")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P = len(nn), r.numel()
+    if out is None:
+        out = torch.empty((max_deriv + 1, J, P), dtype=torch.float64, device=r.device)
+    st = _stream(r.device)
+    with torch.cuda.device(r.device):
+        if plan is not None:
+            _lib.call("zp_radial_plan", plan.handle, r.data_ptr(), P, max_deriv, out.data_ptr(), st)
+        else:
+            _lib.call("zp_radial", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), P, max_deriv,
+                      out.data_ptr(), st)
+    return out
+
+
+def basis(n, m, r: torch.Tensor, theta: torch.Tensor, max_deriv: int = 0, dtheta: bool = False,
+          plan: Plan | None = None):
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    if theta.numel() != r.numel():
+        raise ValueError("r and theta must have the same length")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P = len(nn), r.numel()
+    out = torch.empty((max_deriv + 1, J, P), dtype=torch.float64, device=r.device)
+    dt = torch.empty((J, P), dtype=torch.float64, device=r.device) if dtheta else None
+    st = _stream(r.device)
+    with torch.cuda.device(r.device):
+        if plan is not None:
+            _lib.call("zp_basis_plan", plan.handle, r.data_ptr(), theta.data_ptr(), P, max_deriv, out.data_ptr(),
+                      _lib.ptr(dt), st)
+        else:
+            _lib.call("zp_basis", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(), P, max_deriv,
+                      out.data_ptr(), _lib.ptr(dt), st)
+    return out, dt
+
+
+def radial_per_mode(plan: Plan, r: torch.Tensor) -> torch.Tensor:
+    r = _dev_f64(r, "r")
+    out = torch.empty((plan.n_modes, r.numel()), dtype=torch.float64, device=r.device)
+    with torch.cuda.device(r.device):
+        _lib.call("zp_radial_per_mode", plan.handle, r.data_ptr(), r.numel(), out.data_ptr(), _stream(r.device))
+    return out
+
+
+def series_eval(n, m, r, theta, coeffs, prec: str = "fp64", plan: Plan | None = None) -> torch.Tensor:
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    coeffs = _dev_f64(coeffs, "coeffs")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P = len(nn), r.numel()
+    if coeffs.dim() != 2 or coeffs.shape[0] != J:
+        raise ValueError("coeffs must be [n_modes, n_sets]")
+    S = coeffs.shape[1]
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    out = torch.empty((P, S), dtype=dtype, device=r.device)
+    st = _stream(r.device)
+    with torch.cuda.device(r.device):
+        if plan is not None:
+            _lib.call("zp_series_eval_plan", plan.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(), S,
+                      PREC[prec], out.data_ptr(), st)
+        else:
+            _lib.call("zp_series_eval", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(), P,
+                      coeffs.data_ptr(), S, PREC[prec], out.data_ptr(), st)
+    return out
+
+
+def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), plan: Plan | None = None):
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    coeffs = _dev_f64(coeffs, "coeffs")
+    grad_out = _dev_f64(grad_out, "grad_out")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P = len(nn), r.numel()
+    S = coeffs.shape[1]
+    if grad_out.shape != (P, S):
+        raise ValueError("grad_out must be [n_points, n_sets]")
+    dev = r.device
+    gC = torch.empty((J, S), dtype=torch.float64, device=dev) if need[0] else None
+    gr = torch.empty(P, dtype=torch.float64, device=dev) if need[1] else None
+    gt = torch.empty(P, dtype=torch.float64, device=dev) if need[2] else None
+    st = _stream(dev)
+    with torch.cuda.device(dev):
+        if plan is not None:
+            _lib.call("zp_series_adjoint_plan", plan.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(), S,
+                      grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), st)
+        else:
+            _lib.call("zp_series_adjoint", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(), P,
+                      coeffs.data_ptr(), S, grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), st)
+    return gC, gr, gt
+
+
+class ZernikeSeries(torch.autograd.Function):
+    """F = Z(r, theta) C with gradients for C, r and theta from the library's adjoint
+    (basis recomputed in the backward pass, never stored).  float64 throughout."""
+
+    @staticmethod
+    def forward(ctx, r, theta, coeffs, plan: Plan):
+        ctx.plan = plan
+        ctx.save_for_backward(r, theta, coeffs)
+        return series_eval(None, None, r, theta, coeffs, "fp64", plan=plan)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        r, theta, coeffs = ctx.saved_tensors
+        need = (ctx.needs_input_grad[2], ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        if not any(need):
+            return None, None, None, None
+        gC, gr, gt = series_adjoint(None, None, r, theta, coeffs, grad_out.contiguous(), need=need, plan=ctx.plan)
+        return gr, gt, gC, None
+
+
+def zernike_series(r, theta, coeffs, plan: Plan) -> torch.Tensor:
+    """Differentiable float64 series F[p, s] = sum_j Z_j(r_p, theta_p) coeffs[j, s]."""
+    return ZernikeSeries.apply(r, theta, coeffs, plan)

@@ -1,0 +1,76 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "zernike_gb300.h"
+
+namespace zp {
+
+// Doubles per row of a column's recursion table.  Row layout (index N = Jacobi degree):
+//   N >= 2: {A_N, B_N, 2 A_N, W0_N, W1_N, W2_N, W3_N, 0}
+//   N = 0, 1: {0, 0, 0, W0, W1, W2, W3, 0} with W_k = k!
+// Two header rows precede row N = 0 and hold the seed constants:
+//   header[k]     = binom(m, k)                 (k = 0..3)  -> Taylor coefficients of rho^m
+//   header[4 + k] = (m+2) binom(m+2, k)                      -> of (m+2) rho^(m+2)
+//   header[8 + k] = (m+1) binom(m, k)                        -> of (m+1) rho^m
+constexpr int kRow = 8;
+constexpr int kHeaderRows = 2;
+
+// One |m| column of a plan: the recursion walks N = 0 .. n_steps-1.
+struct Column {
+  int32_t m;          // |m| (the Jacobi alpha)
+  int32_t n_steps;    // N_max + 1
+  int32_t table_row;  // first header row of this column in the table (rows of kRow doubles)
+  int32_t slot_base;  // index of (column, N = 0) in slot_ptr
+};
+
+struct DevicePlanTables {
+  Column* cols = nullptr;
+  double* table = nullptr;
+  int32_t* slot_ptr = nullptr;  // [total_steps + n_columns]: CSR offsets per (column, N)
+  int32_t* slot_idx = nullptr;  // output column j, bit 31 set for the sin (m < 0) factor
+  int32_t* mode_col = nullptr;  // [n_modes]: column index of every mode
+  int32_t* mode_N = nullptr;    // [n_modes]: Jacobi degree of every mode
+};
+
+}  // namespace zp
+
+struct zp_plan {
+  int device = 0;
+  int64_t n_modes = 0;
+  int32_t n_max = 0;
+  int32_t max_steps = 0;
+  std::vector<int32_t> n, m;
+  std::vector<zp::Column> cols;      // ordered by n_steps, longest first
+  std::vector<double> table;         // rows of kRow doubles
+  std::vector<int32_t> slot_ptr, slot_idx, mode_col, mode_N;
+  zp::DevicePlanTables dev;
+  size_t device_bytes = 0;
+  void* dev_block = nullptr;  // single allocation backing dev.*
+};
+
+namespace zp {
+
+// Error plumbing: set_error stores a message for zp_last_error and returns the status.
+zp_status set_error(zp_status s, const std::string& msg);
+zp_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+// Host-side plan construction (validation, grouping, tables, upload).
+zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out);
+// Cached plan for a mode list on the current device (created on first use).
+zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const zp_plan** out);
+zp_status check_plan_device(const zp_plan* plan);
+
+// Kernel launchers (zp_walk.cu).
+zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                      int max_deriv, double* out, double* out_dtheta, cudaStream_t stream);
+zp_status launch_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out,
+                          cudaStream_t stream);
+
+}  // namespace zp

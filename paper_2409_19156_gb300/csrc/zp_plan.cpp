@@ -1,0 +1,327 @@
+// Plan construction: validation, grouping of modes into |m| columns, recursion tables.
+//
+// The per-column walk is Algorithm 1 of Sec. 3 (outer loop over alpha = |m|, inner loop
+// over the Jacobi degree N, store every requested (n, m) on the way).  The coefficients
+// come from the beta = 0 Jacobi recursion of Sec. 2,
+//   P_N = [(2N+a-1)((2N+a)(2N+a-2) x + a^2) / D] P_{N-1} - [2(N+a-1)(N-1)(2N+a) / D] P_{N-2},
+//   D = 2N(N+a)(2N+a-2),  a = |m|,
+// rewritten for R_N = (-1)^N rho^m P_N(1 - 2 rho^2) (the Jacobi relation):
+//   R_N = (2 a_N rho^2 - a_N - b_N) R_{N-1} - c_N R_{N-2}
+// with a_N, b_N, c_N the three printed ratios.  The library carries Q_N = R_N / w_N with
+// w_0 = w_1 = 1 and w_N = c_N w_{N-2}, which turns the recursion into
+//   Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2},  A_N = 2 a_N w_{N-1}/w_N, B_N = (a_N+b_N) w_{N-1}/w_N
+// and saves one multiply per derivative lane per step; stores multiply by W_k = k! w_N.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+
+#include "zp_internal.h"
+
+namespace zp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+zp_status set_error(zp_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+zp_status cuda_error(cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_error(e == cudaErrorMemoryAllocation ? ZP_ERR_NO_MEMORY : ZP_ERR_CUDA, msg);
+}
+
+void clear_error() { g_last_error.clear(); }
+
+static long double binom_ld(int n, int k) {
+  if (k < 0 || k > n) return 0.0L;
+  long double v = 1.0L;
+  for (int i = 1; i <= k; ++i) v = v * (long double)(n - k + i) / (long double)i;
+  return v;
+}
+
+static void fill_column_table(int m, int n_steps, double* rows) {
+  // Header rows: seed constants (Taylor coefficients of rho^m and of R_{m+2}^m).
+  double* h = rows;
+  for (int k = 0; k < 4; ++k) {
+    h[k] = (double)binom_ld(m, k);
+    h[4 + k] = (double)((long double)(m + 2) * binom_ld(m + 2, k));
+    h[8 + k] = (double)((long double)(m + 1) * binom_ld(m, k));
+  }
+  for (int k = 12; k < 16; ++k) h[k] = 0.0;
+  double* t = rows + kHeaderRows * kRow;
+  std::vector<long double> w(std::max(n_steps, 2), 1.0L);
+  for (int N = 0; N < n_steps; ++N) {
+    double* row = t + (size_t)N * kRow;
+    long double A = 0.0L, B = 0.0L;
+    if (N >= 2) {
+      const long double a = m;
+      const long double D = 2.0L * N * (N + a) * (2.0L * N + a - 2.0L);
+      const long double aN = (2.0L * N + a - 1.0L) * (2.0L * N + a) * (2.0L * N + a - 2.0L) / D;
+      const long double bN = (2.0L * N + a - 1.0L) * a * a / D;
+      const long double cN = 2.0L * (N + a - 1.0L) * (N - 1.0L) * (2.0L * N + a) / D;
+      w[N] = cN * w[N - 2];
+      A = 2.0L * aN * w[N - 1] / w[N];
+      B = (aN + bN) * w[N - 1] / w[N];
+    }
+    row[0] = (double)A;
+    row[1] = (double)B;
+    row[2] = (double)(2.0L * A);
+    row[3] = (double)w[N];
+    row[4] = (double)w[N];
+    row[5] = (double)(2.0L * w[N]);
+    row[6] = (double)(6.0L * w[N]);
+    row[7] = 0.0;
+  }
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out) {
+  if (!out) return set_error(ZP_ERR_INVALID_ARG, "plan output pointer is NULL");
+  if (n_modes < 0) return set_error(ZP_ERR_INVALID_ARG, "n_modes < 0");
+  if (n_modes > 0 && (!n || !m)) return set_error(ZP_ERR_INVALID_ARG, "mode arrays are NULL");
+  if (n_modes >= (int64_t(1) << 31)) return set_error(ZP_ERR_INVALID_ARG, "n_modes >= 2^31");
+  int32_t n_max = 0;
+  for (int64_t j = 0; j < n_modes; ++j) {
+    const int32_t nj = n[j], mj = m[j];
+    const int64_t am = mj < 0 ? -(int64_t)mj : (int64_t)mj;
+    if (nj < 0 || am > nj || (((int64_t)nj - am) & 1)) {
+      return set_error(ZP_ERR_INVALID_MODE, "invalid mode at index " + std::to_string(j) + ": (n=" +
+                                                std::to_string(nj) + ", m=" + std::to_string(mj) +
+                                                ") needs n >= 0, |m| <= n, n - |m| even");
+    }
+    if (nj > ZP_MAX_N) {
+      return set_error(ZP_ERR_INVALID_MODE, "mode n=" + std::to_string(nj) + " above ZP_MAX_N");
+    }
+    n_max = std::max(n_max, nj);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+
+  std::unique_ptr<zp_plan> p(new zp_plan());
+  p->device = dev;
+  p->n_modes = n_modes;
+  p->n_max = n_max;
+  p->n.assign(n, n + n_modes);
+  p->m.assign(m, m + n_modes);
+
+  // Steps per |m| column = 1 + largest requested Jacobi degree of that column.
+  std::vector<int32_t> steps_of_m(n_max + 1, 0);
+  for (int64_t j = 0; j < n_modes; ++j) {
+    const int32_t am = std::abs(m[j]);
+    steps_of_m[am] = std::max(steps_of_m[am], (n[j] - am) / 2 + 1);
+  }
+  for (int32_t am = 0; am <= n_max; ++am) {
+    if (steps_of_m[am] > 0) p->cols.push_back(zp::Column{am, steps_of_m[am], 0, 0});
+  }
+  // Longest recursion first: better tail behaviour when blocks are scheduled in order.
+  std::stable_sort(p->cols.begin(), p->cols.end(),
+                   [](const Column& a, const Column& b) { return a.n_steps > b.n_steps; });
+  std::vector<int32_t> col_of_m(n_max + 1, -1);
+  int32_t row = 0, slot = 0;
+  for (size_t c = 0; c < p->cols.size(); ++c) {
+    Column& col = p->cols[c];
+    col.table_row = row;
+    col.slot_base = slot;
+    row += kHeaderRows + col.n_steps;
+    slot += col.n_steps + 1;
+    col_of_m[col.m] = (int32_t)c;
+    p->max_steps = std::max(p->max_steps, col.n_steps);
+  }
+  p->table.assign((size_t)row * kRow, 0.0);
+  for (const Column& col : p->cols) fill_column_table(col.m, col.n_steps, p->table.data() + (size_t)col.table_row * kRow);
+
+  // CSR of output columns per (column, N), in the caller's mode order.
+  std::vector<int32_t> count((size_t)slot, 0);
+  p->mode_col.resize(n_modes);
+  p->mode_N.resize(n_modes);
+  for (int64_t j = 0; j < n_modes; ++j) {
+    const int32_t am = std::abs(m[j]);
+    const int32_t c = col_of_m[am];
+    const int32_t N = (n[j] - am) / 2;
+    p->mode_col[j] = c;
+    p->mode_N[j] = N;
+    count[(size_t)p->cols[c].slot_base + N]++;
+  }
+  p->slot_ptr.assign((size_t)slot, 0);
+  {
+    int32_t acc = 0;
+    for (size_t c = 0; c < p->cols.size(); ++c) {
+      const Column& col = p->cols[c];
+      for (int32_t N = 0; N <= col.n_steps; ++N) {
+        const size_t s = (size_t)col.slot_base + N;
+        p->slot_ptr[s] = acc;
+        if (N < col.n_steps) acc += count[s];
+      }
+    }
+    p->slot_idx.assign((size_t)acc, 0);
+  }
+  std::vector<int32_t> fill((size_t)slot, 0);
+  for (int64_t j = 0; j < n_modes; ++j) {
+    const size_t s = (size_t)p->cols[p->mode_col[j]].slot_base + p->mode_N[j];
+    const int32_t pos = p->slot_ptr[s] + fill[s]++;
+    p->slot_idx[pos] = (int32_t)((uint32_t)j | (m[j] < 0 ? 0x80000000u : 0u));
+  }
+
+  // Upload: one device block holding every table.
+  const size_t b_cols = align_up(p->cols.size() * sizeof(Column), 256);
+  const size_t b_table = align_up(p->table.size() * sizeof(double), 256);
+  const size_t b_sptr = align_up(p->slot_ptr.size() * sizeof(int32_t), 256);
+  const size_t b_sidx = align_up(std::max<size_t>(p->slot_idx.size(), 1) * sizeof(int32_t), 256);
+  const size_t b_mode = align_up(std::max<int64_t>(n_modes, 1) * sizeof(int32_t), 256);
+  const size_t total = b_cols + b_table + b_sptr + b_sidx + 2 * b_mode;
+  if (total > 0) {
+    e = cudaMalloc(&p->dev_block, total);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(plan tables)");
+    p->device_bytes = total;
+    char* base = (char*)p->dev_block;
+    p->dev.cols = (Column*)base;
+    p->dev.table = (double*)(base + b_cols);
+    p->dev.slot_ptr = (int32_t*)(base + b_cols + b_table);
+    p->dev.slot_idx = (int32_t*)(base + b_cols + b_table + b_sptr);
+    p->dev.mode_col = (int32_t*)(base + b_cols + b_table + b_sptr + b_sidx);
+    p->dev.mode_N = (int32_t*)(base + b_cols + b_table + b_sptr + b_sidx + b_mode);
+    struct Part { void* dst; const void* src; size_t bytes; } parts[] = {
+        {p->dev.cols, p->cols.data(), p->cols.size() * sizeof(Column)},
+        {p->dev.table, p->table.data(), p->table.size() * sizeof(double)},
+        {p->dev.slot_ptr, p->slot_ptr.data(), p->slot_ptr.size() * sizeof(int32_t)},
+        {p->dev.slot_idx, p->slot_idx.data(), p->slot_idx.size() * sizeof(int32_t)},
+        {p->dev.mode_col, p->mode_col.data(), p->mode_col.size() * sizeof(int32_t)},
+        {p->dev.mode_N, p->mode_N.data(), p->mode_N.size() * sizeof(int32_t)},
+    };
+    for (const Part& part : parts) {
+      if (part.bytes == 0) continue;
+      e = cudaMemcpy(part.dst, part.src, part.bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(p->dev_block);
+        return cuda_error(e, "cudaMemcpy(plan tables)");
+      }
+    }
+  }
+  *out = p.release();
+  return ZP_OK;
+}
+
+static void free_plan(zp_plan* p) {
+  if (!p) return;
+  if (p->dev_block) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->dev_block);
+    cudaSetDevice(cur);
+  }
+  delete p;
+}
+
+zp_status check_plan_device(const zp_plan* plan) {
+  if (!plan) return set_error(ZP_ERR_INVALID_ARG, "plan is NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev != plan->device) {
+    return set_error(ZP_ERR_INVALID_ARG, "plan was created on device " + std::to_string(plan->device) +
+                                             " but the current device is " + std::to_string(dev));
+  }
+  return ZP_OK;
+}
+
+namespace {
+struct PlanKey {
+  int device;
+  std::vector<int32_t> n, m;
+  bool operator==(const PlanKey& o) const { return device == o.device && n == o.n && m == o.m; }
+};
+struct PlanKeyHash {
+  size_t operator()(const PlanKey& k) const {
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)k.device;
+    for (size_t i = 0; i < k.n.size(); ++i) {
+      h = (h ^ (uint32_t)k.n[i]) * 1099511628211ull;
+      h = (h ^ (uint32_t)k.m[i]) * 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+std::mutex g_cache_mu;
+std::unordered_map<PlanKey, zp_plan*, PlanKeyHash> g_cache;
+constexpr size_t kCacheMax = 64;
+}  // namespace
+
+zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const zp_plan** out) {
+  if (n_modes < 0) return set_error(ZP_ERR_INVALID_ARG, "n_modes < 0");
+  if (n_modes > 0 && (!n || !m)) return set_error(ZP_ERR_INVALID_ARG, "mode arrays are NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  PlanKey key{dev, std::vector<int32_t>(n, n + n_modes), std::vector<int32_t>(m, m + n_modes)};
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    *out = it->second;
+    return ZP_OK;
+  }
+  zp_plan* p = nullptr;
+  zp_status s = build_plan(n, m, n_modes, &p);
+  if (s != ZP_OK) return s;
+  if (g_cache.size() >= kCacheMax) {
+    // Plans handed out earlier may still be referenced by work in flight: freeing
+    // synchronises the device first.
+    for (auto& kv : g_cache) free_plan(kv.second);
+    g_cache.clear();
+  }
+  g_cache.emplace(std::move(key), p);
+  *out = p;
+  return ZP_OK;
+}
+
+}  // namespace zp
+
+extern "C" {
+
+const char* zp_status_string(zp_status s) {
+  switch (s) {
+    case ZP_OK: return "ok";
+    case ZP_ERR_INVALID_ARG: return "invalid argument";
+    case ZP_ERR_INVALID_MODE: return "invalid Zernike mode";
+    case ZP_ERR_DERIV_ORDER: return "derivative order outside 0..3";
+    case ZP_ERR_CUDA: return "CUDA error";
+    case ZP_ERR_TIMEOUT: return "device wait timed out";
+    case ZP_ERR_UNSUPPORTED: return "unsupported";
+    case ZP_ERR_NO_MEMORY: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* zp_last_error(void) { return zp::g_last_error.c_str(); }
+
+int32_t zp_version(void) { return 100; }
+
+zp_status zp_plan_create(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out) {
+  zp::clear_error();
+  return zp::build_plan(n, m, n_modes, out);
+}
+
+zp_status zp_plan_destroy(zp_plan* plan) {
+  zp::clear_error();
+  if (!plan) return zp::set_error(ZP_ERR_INVALID_ARG, "plan is NULL");
+  zp::free_plan(plan);
+  return ZP_OK;
+}
+
+zp_status zp_plan_info(const zp_plan* plan, int64_t* n_modes, int32_t* n_max, int32_t* n_columns) {
+  zp::clear_error();
+  if (!plan) return zp::set_error(ZP_ERR_INVALID_ARG, "plan is NULL");
+  if (n_modes) *n_modes = plan->n_modes;
+  if (n_max) *n_max = plan->n_max;
+  if (n_columns) *n_columns = (int32_t)plan->cols.size();
+  return ZP_OK;
+}
+
+}  // extern "C"

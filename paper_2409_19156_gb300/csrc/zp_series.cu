@@ -1,0 +1,294 @@
+// Series of Zernike functions and its adjoint, float64 ("plain basis-then-GEMM" form).
+//
+//   F = Z^T C                     (Z: basis [J][P] written by the walk kernel to scratch)
+//   grad_C = Z G                  (cuBLAS DGEMM)
+//   H = C G^T  -> [J][P]          (cuBLAS DGEMM, point-fastest so the next kernel coalesces)
+//   grad_r[p]     = sum_j dZ_j/drho(p)   H[j][p]
+//   grad_theta[p] = sum_j dZ_j/dtheta(p) H[j][p]
+// The last two are one kernel that regenerates the basis derivatives in registers (the
+// per-column recursion of zp_walk.cu with one rho-derivative lane) and reduces over all
+// modes inside one thread per point: no partial buffers, no atomics, deterministic.
+// Scratch is allocated stream-ordered (cudaMallocAsync) and released on the same stream.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "zp_api_common.h"
+#include "zp_series_internal.h"
+
+namespace zp {
+namespace {
+
+constexpr int kRedThreads = 128;
+
+__device__ __forceinline__ double pow_uint_r(double x, int e) {
+  double result = 1.0, base = x;
+  while (e) {
+    if (e & 1) result *= base;
+    base *= base;
+    e >>= 1;
+  }
+  return result;
+}
+
+// One thread per point: walks every |m| column (k <= 1 Taylor lanes) and accumulates
+// sum_j dZ_j/drho * H[j][p] and sum_j dZ_j/dtheta * H[j][p].
+__global__ void __launch_bounds__(kRedThreads)
+adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* __restrict__ table,
+                     const int32_t* __restrict__ slot_ptr, const int32_t* __restrict__ slot_idx,
+                     const double* __restrict__ r, const double* __restrict__ theta, int64_t P,
+                     const double* __restrict__ H, double* grad_r, double* grad_theta) {
+  const int64_t p = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  if (p >= P) return;
+  const double rho = r[p], u = rho * rho, th = theta[p];
+  double acc_r = 0.0, acc_t = 0.0;
+  for (int c = 0; c < n_cols; ++c) {
+    const Column col = cols[c];
+    const int m = col.m;
+    const double* h = table + (size_t)col.table_row * kRow;
+    const int32_t* sp = slot_ptr + col.slot_base;
+    double cs = 1.0, sn = 0.0;
+    if (m != 0) sincos((double)m * th, &sn, &cs);
+    // Seeds (Taylor lanes k = 0, 1): N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
+    const double pm1 = m >= 1 ? pow_uint_r(rho, m - 1) : 0.0;
+    const double pm = m >= 1 ? pm1 * rho : 1.0;
+    double T0 = pm, T1 = h[1] * pm1;
+    double S0 = fma(h[4], pm * u, -(h[8] * pm));
+    double S1 = fma(h[5], pm * rho, -(h[9] * pm1));
+    const double md = (double)m;
+    auto accumulate = [&](int N, double v0, double v1) {
+      const int sb = sp[N], se = sp[N + 1];
+      if (sb == se) return;
+      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
+      const double R0 = row[3] * v0, R1 = row[4] * v1;
+      for (int s = sb; s < se; ++s) {
+        const uint32_t code = (uint32_t)__ldg(slot_idx + s);
+        const int64_t j = (int64_t)(code & 0x7fffffffu);
+        const bool is_sin = (code >> 31) != 0;
+        const double hv = H[j * P + p];
+        const double f = is_sin ? sn : cs;
+        const double dt = is_sin ? md * cs : -md * sn;
+        acc_r = fma(R1 * f, hv, acc_r);
+        acc_t = fma(R0 * dt, hv, acc_t);
+      }
+    };
+    accumulate(0, T0, T1);
+    if (col.n_steps < 2) continue;
+    accumulate(1, S0, S1);
+    for (int N = 2; N < col.n_steps; ++N) {
+      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
+      const double A = row[0], B = row[1], A2 = row[2];
+      const double g = fma(A, u, -B);
+      const double n0 = fma(g, S0, -T0);
+      const double n1 = fma(g, S1, fma(A2 * rho, S0, -T1));
+      T0 = S0;
+      T1 = S1;
+      S0 = n0;
+      S1 = n1;
+      accumulate(N, S0, S1);
+    }
+  }
+  if (grad_r) grad_r[p] = acc_r;
+  if (grad_theta) grad_theta[p] = acc_t;
+}
+
+struct CublasHandles {
+  std::mutex mu;
+  std::vector<cublasHandle_t> per_device;
+};
+
+CublasHandles& handles() {
+  static CublasHandles h;
+  return h;
+}
+
+const char* cublas_name(cublasStatus_t s) {
+  switch (s) {
+    case CUBLAS_STATUS_SUCCESS: return "CUBLAS_STATUS_SUCCESS";
+    case CUBLAS_STATUS_NOT_INITIALIZED: return "CUBLAS_STATUS_NOT_INITIALIZED";
+    case CUBLAS_STATUS_ALLOC_FAILED: return "CUBLAS_STATUS_ALLOC_FAILED";
+    case CUBLAS_STATUS_INVALID_VALUE: return "CUBLAS_STATUS_INVALID_VALUE";
+    case CUBLAS_STATUS_ARCH_MISMATCH: return "CUBLAS_STATUS_ARCH_MISMATCH";
+    case CUBLAS_STATUS_EXECUTION_FAILED: return "CUBLAS_STATUS_EXECUTION_FAILED";
+    case CUBLAS_STATUS_NOT_SUPPORTED: return "CUBLAS_STATUS_NOT_SUPPORTED";
+    default: return "CUBLAS_STATUS_OTHER";
+  }
+}
+
+}  // namespace
+
+// Thread-safe: one handle per device, serialised by the lock for the duration of a call
+// sequence (set-stream + gemm) through the Lock object.
+struct CublasLock {
+  std::unique_lock<std::mutex> lock;
+  cublasHandle_t h = nullptr;
+};
+
+static zp_status get_cublas(CublasLock& out, cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  CublasHandles& hs = handles();
+  out.lock = std::unique_lock<std::mutex>(hs.mu);
+  if ((int)hs.per_device.size() <= dev) hs.per_device.resize(dev + 1, nullptr);
+  if (!hs.per_device[dev]) {
+    cublasStatus_t s = cublasCreate(&hs.per_device[dev]);
+    if (s != CUBLAS_STATUS_SUCCESS) return set_error(ZP_ERR_CUDA, std::string("cublasCreate: ") + cublas_name(s));
+  }
+  out.h = hs.per_device[dev];
+  cublasStatus_t s = cublasSetStream(out.h, stream);
+  if (s != CUBLAS_STATUS_SUCCESS) return set_error(ZP_ERR_CUDA, std::string("cublasSetStream: ") + cublas_name(s));
+  return ZP_OK;
+}
+
+// Column-major DGEMM wrapper: C = op(A) op(B).
+static zp_status dgemm(cublasHandle_t h, bool ta, bool tb, int64_t m, int64_t n, int64_t k, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc) {
+  const double one = 1.0, zero = 0.0;
+  cublasStatus_t s = cublasDgemm_64(h, ta ? CUBLAS_OP_T : CUBLAS_OP_N, tb ? CUBLAS_OP_T : CUBLAS_OP_N, m, n, k, &one,
+                                    A, lda, B, ldb, &zero, C, ldc);
+  if (s != CUBLAS_STATUS_SUCCESS) return set_error(ZP_ERR_CUDA, std::string("cublasDgemm: ") + cublas_name(s));
+  return ZP_OK;
+}
+
+ScratchBuffer::~ScratchBuffer() {
+  if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+zp_status ScratchBuffer::alloc(size_t bytes, cudaStream_t s) {
+  stream = s;
+  if (bytes == 0) return ZP_OK;
+  cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    return cuda_error(e, "cudaMallocAsync(scratch)");
+  }
+  return ZP_OK;
+}
+
+zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                           const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
+  const int64_t J = plan->n_modes;
+  ScratchBuffer z;
+  ZP_TRY(z.alloc((size_t)J * P * sizeof(double), stream));
+  ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream));
+  CublasLock cl;
+  ZP_TRY(get_cublas(cl, stream));
+  // F (row-major [P][S]) = column-major S x P = C^T(S x J) * Z(J x P):
+  //   C row-major [J][S] is column-major S x J (ld S); Z row-major [J][P] is column-major P x J -> op T.
+  return dgemm(cl.h, false, true, S, P, J, coeffs, S, (const double*)z.ptr, P, out, S);
+}
+
+zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                              const double* coeffs, int64_t S, const double* G, double* grad_coeffs, double* grad_r,
+                              double* grad_theta, cudaStream_t stream) {
+  const int64_t J = plan->n_modes;
+  const bool need_h = grad_r || grad_theta;
+  ScratchBuffer z, hbuf;
+  CublasLock cl;
+  if (grad_coeffs) {
+    ZP_TRY(z.alloc((size_t)J * P * sizeof(double), stream));
+    ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream));
+    ZP_TRY(get_cublas(cl, stream));
+    // grad_C row-major [J][S] = column-major S x J = G^T (S x P) * Z^T (P x J):
+    //   G row-major [P][S] is column-major S x P; Z row-major [J][P] is column-major P x J.
+    ZP_TRY(dgemm(cl.h, false, false, S, J, P, G, S, (const double*)z.ptr, P, grad_coeffs, S));
+  }
+  if (need_h) {
+    ZP_TRY(hbuf.alloc((size_t)J * P * sizeof(double), stream));
+    if (!cl.h) ZP_TRY(get_cublas(cl, stream));
+    // H row-major [J][P] = column-major P x J = G (P x S) * C^T (S x J):
+    //   G column-major S x P -> op T; C column-major S x J -> op N.
+    ZP_TRY(dgemm(cl.h, true, false, P, J, S, G, S, coeffs, S, (double*)hbuf.ptr, P));
+    const int64_t blocks = (P + kRedThreads - 1) / kRedThreads;
+    adjoint_point_kernel<<<(unsigned)blocks, kRedThreads, 0, stream>>>(
+        plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
+        (const double*)hbuf.ptr, grad_r, grad_theta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "adjoint_point_kernel launch");
+  }
+  return ZP_OK;
+}
+
+}  // namespace zp
+
+using namespace zp;
+
+static zp_status series_args(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                             const double* coeffs, int64_t S) {
+  ZP_TRY(check_plan_device(plan));
+  if (P < 0) return set_error(ZP_ERR_INVALID_ARG, "n_points < 0");
+  if (S < 0) return set_error(ZP_ERR_INVALID_ARG, "n_sets < 0");
+  if (P == 0 || plan->n_modes == 0 || S == 0) return ZP_OK;
+  ZP_TRY(check_device_array(r, "r", 8));
+  ZP_TRY(check_device_array(theta, "theta", 8));
+  ZP_TRY(check_device_array(coeffs, "coeffs", 8));
+  return ZP_OK;
+}
+
+extern "C" {
+
+zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                              const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream) {
+  clear_error();
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32)
+    return set_error(ZP_ERR_INVALID_ARG, "unknown precision");
+  ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
+  if (n_points == 0 || n_sets == 0) return ZP_OK;
+  ZP_TRY(check_device_array(out, "out", prec == ZP_PREC_FP64 ? 8 : 16));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->n_modes == 0) {
+    const size_t bytes = (size_t)n_points * n_sets * (prec == ZP_PREC_FP64 ? 8 : 4);
+    cudaError_t e = cudaMemsetAsync(out, 0, bytes, st);
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
+  }
+  if (prec == ZP_PREC_FP64) return series_eval_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
+  return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, st);
+}
+
+zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+                         int64_t n_points, const double* coeffs, int64_t n_sets, zp_precision prec, void* out,
+                         void* stream) {
+  clear_error();
+  const zp_plan* plan = nullptr;
+  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  return zp_series_eval_plan(plan, r, theta, n_points, coeffs, n_sets, prec, out, stream);
+}
+
+zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                 const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_coeffs,
+                                 double* grad_r, double* grad_theta, void* stream) {
+  clear_error();
+  ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
+  if (grad_coeffs) ZP_TRY(check_device_array(grad_coeffs, "grad_coeffs", 8));
+  if (grad_r) ZP_TRY(check_device_array(grad_r, "grad_r", 8));
+  if (grad_theta) ZP_TRY(check_device_array(grad_theta, "grad_theta", 8));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t J = plan->n_modes, P = n_points, S = n_sets;
+  if (P == 0 || J == 0 || S == 0) {
+    // Empty sums: zero whatever gradient exists.
+    cudaError_t e = cudaSuccess;
+    if (grad_coeffs && J * S > 0) e = cudaMemsetAsync(grad_coeffs, 0, (size_t)J * S * 8, st);
+    if (e == cudaSuccess && grad_r && P > 0) e = cudaMemsetAsync(grad_r, 0, (size_t)P * 8, st);
+    if (e == cudaSuccess && grad_theta && P > 0) e = cudaMemsetAsync(grad_theta, 0, (size_t)P * 8, st);
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
+  }
+  ZP_TRY(check_device_array(grad_out, "grad_out", 8));
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st);
+}
+
+zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+                            const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
+                            const double* grad_out, double* grad_coeffs, double* grad_r, double* grad_theta,
+                            void* stream) {
+  clear_error();
+  const zp_plan* plan = nullptr;
+  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  return zp_series_adjoint_plan(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta,
+                                stream);
+}
+
+}  // extern "C"

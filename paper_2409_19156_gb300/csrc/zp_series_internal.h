@@ -1,0 +1,30 @@
+// Declarations shared by the series translation units.
+#pragma once
+
+#include "zp_internal.h"
+
+namespace zp {
+
+// Stream-ordered scratch: cudaMallocAsync on `stream`, cudaFreeAsync on the same stream
+// when the object goes out of scope (after the work that uses it has been enqueued).
+struct ScratchBuffer {
+  void* ptr = nullptr;
+  cudaStream_t stream = nullptr;
+  ScratchBuffer() = default;
+  ScratchBuffer(const ScratchBuffer&) = delete;
+  ScratchBuffer& operator=(const ScratchBuffer&) = delete;
+  ~ScratchBuffer();
+  zp_status alloc(size_t bytes, cudaStream_t s);
+};
+
+zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                           const double* coeffs, int64_t S, double* out, cudaStream_t stream);
+zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                              const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
+                              double* grad_r, double* grad_theta, cudaStream_t stream);
+// Split-precision tensor-core series (BF16x3 or TF32, float32 output).
+zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                            const double* coeffs, int64_t S, zp_precision prec, float* out,
+                            cudaStream_t stream);
+
+}  // namespace zp

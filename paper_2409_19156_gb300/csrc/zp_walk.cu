@@ -1,0 +1,278 @@
+// The per-(point, |m|-column) recursion walk: radial polynomials, rho-derivatives, Z.
+//
+// Work decomposition (Algorithm 1 of Sec. 3, mapped to the GPU): one thread owns
+// kPPT consecutive points of one |m| column and walks the Jacobi degree N = 0 .. N_max in
+// registers, storing every requested (n, m) of that column as it passes (the store list
+// comes from the plan; the duplicated-modes variant of Sec. 3 is several entries per N).
+// The recursion is the beta = 0 Jacobi recursion of Sec. 2 in the rescaled form built by
+// the plan (see zp_plan.cpp):
+//   Q_N = g_N Q_{N-1} - Q_{N-2},   g_N(rho) = A_N rho^2 - B_N,   R_N = w_N Q_N.
+// Derivatives carry Taylor lanes S_k = Q^(k) / k!; by Leibniz,
+//   S_k,N = g S_k,N-1 + g' S_{k-1},N-1 + (g''/2) S_{k-2},N-1 - S_k,N-2,
+// with g' = 2 A_N rho, g''/2 = A_N and g''' = 0, and d^k R / drho^k = (k! w_N) S_k.
+// Per step and point that is 3 (k = 0), 7 (k <= 1), 11 (k <= 2) or 15 (k <= 3) float64
+// operations, which on GB300 (two float64 lanes per SM per clock) makes this kernel
+// float64-issue bound; the stores (point-fastest rows, 16-byte vectors) are coalesced.
+//
+// Seeds (Sec. 2 explicit Jacobi sum for P_0, P_1 through the Jacobi relation):
+//   R_{m}^{m} = rho^m,   R_{m+2}^{m} = (m+2) rho^(m+2) - (m+1) rho^m.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "zp_internal.h"
+
+namespace zp {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kPPT = 2;
+constexpr int kPointsPerBlock = kThreads * kPPT;
+
+struct WalkArgs {
+  const Column* cols;
+  const double* table;
+  const int32_t* slot_ptr;
+  const int32_t* slot_idx;
+  const double* r;
+  const double* theta;
+  int64_t P;
+  int64_t J;
+  double* out;
+  double* out_dtheta;
+};
+
+__device__ __forceinline__ double pow_uint(double x, int e) {
+  double result = 1.0;
+  double base = x;
+  while (e) {
+    if (e & 1) result *= base;
+    base *= base;
+    e >>= 1;
+  }
+  return result;
+}
+
+__device__ __forceinline__ void store_pair(double* dst, int64_t p, double v0, double v1, bool two, bool vec) {
+  if (vec) {
+    __stcs(reinterpret_cast<double2*>(dst + p), make_double2(v0, v1));
+  } else {
+    __stcs(dst + p, v0);
+    if (two) __stcs(dst + p + 1, v1);
+  }
+}
+
+// KMAX: highest rho-derivative; ANG: multiply by cos/sin(|m| theta) (Z instead of R);
+// VEC: 16-byte stores (P even and outputs 16-byte aligned).
+template <int KMAX, bool ANG, bool VEC>
+__global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
+  extern __shared__ double smem[];
+  const Column col = a.cols[blockIdx.y];
+  const int n_rows = kHeaderRows + col.n_steps;
+  double* tab = smem;
+  int32_t* sptr = reinterpret_cast<int32_t*>(smem + (size_t)n_rows * kRow);
+  {
+    const double* src = a.table + (size_t)col.table_row * kRow;
+    for (int i = threadIdx.x; i < n_rows * kRow; i += kThreads) tab[i] = src[i];
+    const int32_t* s2 = a.slot_ptr + col.slot_base;
+    for (int i = threadIdx.x; i <= col.n_steps; i += kThreads) sptr[i] = s2[i];
+  }
+  __syncthreads();
+
+  const int64_t p0 = (int64_t)blockIdx.x * kPointsPerBlock + (int64_t)threadIdx.x * kPPT;
+  if (p0 >= a.P) return;
+  const bool two = p0 + 1 < a.P;
+  const int m = col.m;
+
+  double rho[kPPT], u[kPPT];
+  rho[0] = a.r[p0];
+  rho[1] = two ? a.r[p0 + 1] : 0.0;
+#pragma unroll
+  for (int i = 0; i < kPPT; ++i) u[i] = rho[i] * rho[i];
+
+  double cs[kPPT], sn[kPPT];
+  if constexpr (ANG) {
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+      cs[i] = 1.0;
+      sn[i] = 0.0;
+    }
+    if (m != 0) {
+      const double th0 = a.theta[p0];
+      const double th1 = two ? a.theta[p0 + 1] : 0.0;
+      sincos((double)m * th0, &sn[0], &cs[0]);
+      sincos((double)m * th1, &sn[1], &cs[1]);
+    }
+  }
+
+  // Seeds.  pw[i] = rho^(m - KMAX + i) for i = 0 .. KMAX+2 (0 for negative exponents, whose
+  // coefficients vanish).
+  double S[kPPT][KMAX + 1], T[kPPT][KMAX + 1];
+  {
+    const double* h = tab;
+    const int e0 = m - KMAX;
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+      double pw[KMAX + 3];
+      double cur = e0 >= 0 ? pow_uint(rho[i], e0) : 0.0;
+#pragma unroll
+      for (int t = 0; t < KMAX + 3; ++t) {
+        if (t > 0) cur = (e0 + t == 0) ? 1.0 : cur * rho[i];
+        pw[t] = cur;
+      }
+#pragma unroll
+      for (int k = 0; k <= KMAX; ++k) {
+        T[i][k] = h[k] * pw[KMAX - k];                                      // N = 0: rho^m
+        S[i][k] = fma(h[4 + k], pw[KMAX - k + 2], -(h[8 + k] * pw[KMAX - k]));  // N = 1
+      }
+    }
+  }
+
+  auto store_step = [&](int N, const double (&V)[kPPT][KMAX + 1]) {
+    const int s_begin = sptr[N], s_end = sptr[N + 1];
+    if (s_begin == s_end) return;
+    const double* row = tab + (size_t)(kHeaderRows + N) * kRow;
+    double R[kPPT][KMAX + 1];
+#pragma unroll
+    for (int k = 0; k <= KMAX; ++k) {
+      const double W = row[3 + k];
+#pragma unroll
+      for (int i = 0; i < kPPT; ++i) R[i][k] = W * V[i][k];
+    }
+    for (int s = s_begin; s < s_end; ++s) {
+      const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+      const int64_t j = (int64_t)(code & 0x7fffffffu);
+      if constexpr (ANG) {
+        const bool is_sin = (code >> 31) != 0;
+        double f[kPPT];
+#pragma unroll
+        for (int i = 0; i < kPPT; ++i) f[i] = is_sin ? sn[i] : cs[i];
+#pragma unroll
+        for (int k = 0; k <= KMAX; ++k)
+          store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, R[0][k] * f[0], R[1][k] * f[1], two, VEC);
+        if (a.out_dtheta) {
+          const double md = (double)m;
+          double dt[kPPT];
+#pragma unroll
+          for (int i = 0; i < kPPT; ++i) dt[i] = is_sin ? md * cs[i] : -md * sn[i];
+          store_pair(a.out_dtheta + j * a.P, p0, R[0][0] * dt[0], R[1][0] * dt[1], two, VEC);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k <= KMAX; ++k)
+          store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, R[0][k], R[1][k], two, VEC);
+      }
+    }
+  };
+
+  store_step(0, T);
+  if (col.n_steps < 2) return;
+  store_step(1, S);
+  for (int N = 2; N < col.n_steps; ++N) {
+    const double* row = tab + (size_t)(kHeaderRows + N) * kRow;
+    const double A = row[0], B = row[1], A2 = row[2];
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+      const double g = fma(A, u[i], -B);
+      double nw[KMAX + 1];
+      nw[0] = fma(g, S[i][0], -T[i][0]);
+      if constexpr (KMAX >= 1) {
+        const double hg = A2 * rho[i];
+        nw[1] = fma(g, S[i][1], fma(hg, S[i][0], -T[i][1]));
+        if constexpr (KMAX >= 2) nw[2] = fma(g, S[i][2], fma(hg, S[i][1], fma(A, S[i][0], -T[i][2])));
+        if constexpr (KMAX >= 3) nw[3] = fma(g, S[i][3], fma(hg, S[i][2], fma(A, S[i][1], -T[i][3])));
+      }
+#pragma unroll
+      for (int k = 0; k <= KMAX; ++k) {
+        T[i][k] = S[i][k];
+        S[i][k] = nw[k];
+      }
+    }
+    store_step(N, S);
+  }
+}
+
+// Algorithm 2 of Sec. 3: one thread per (point, mode), each running its own recursion to
+// its own degree and storing only the last value (k = 0).  Comparison kernel.
+__global__ void __launch_bounds__(kThreads) per_mode_kernel(const Column* cols, const double* table,
+                                                            const int32_t* mode_col, const int32_t* mode_N,
+                                                            const double* r, int64_t P, int64_t J, double* out) {
+  const int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= P) return;
+  const double rho = r[p], u = rho * rho;
+  for (int64_t j = blockIdx.y; j < J; j += gridDim.y) {
+    const Column col = cols[mode_col[j]];
+    const int N = mode_N[j];
+    const double* h = table + (size_t)col.table_row * kRow;
+    const double rm = pow_uint(rho, col.m);
+    double q0 = rm;                                  // Q_0
+    double q1 = fma(h[4], rm * u, -(h[8] * rm));      // Q_1 = (m+2) rho^(m+2) - (m+1) rho^m
+    double q = N == 0 ? q0 : q1;
+    for (int s = 2; s <= N; ++s) {
+      const double* row = h + (size_t)(kHeaderRows + s) * kRow;
+      q = fma(fma(row[0], u, -row[1]), q1, -q0);
+      q0 = q1;
+      q1 = q;
+    }
+    __stcs(out + j * P + p, q * h[(size_t)(kHeaderRows + N) * kRow + 3]);
+  }
+}
+
+template <int KMAX, bool ANG>
+cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, size_t smem, bool vec, cudaStream_t st) {
+  if (vec)
+    walk_kernel<KMAX, ANG, true><<<grid, kThreads, smem, st>>>(a);
+  else
+    walk_kernel<KMAX, ANG, false><<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points, int max_deriv,
+                      double* out, double* out_dtheta, cudaStream_t stream) {
+  if (n_points == 0 || plan->n_modes == 0) return ZP_OK;
+  WalkArgs a;
+  a.cols = plan->dev.cols;
+  a.table = plan->dev.table;
+  a.slot_ptr = plan->dev.slot_ptr;
+  a.slot_idx = plan->dev.slot_idx;
+  a.r = r;
+  a.theta = theta;
+  a.P = n_points;
+  a.J = plan->n_modes;
+  a.out = out;
+  a.out_dtheta = out_dtheta;
+  const int64_t blocks_x = (n_points + kPointsPerBlock - 1) / kPointsPerBlock;
+  if (blocks_x > 0x7fffffffLL) return set_error(ZP_ERR_INVALID_ARG, "n_points too large for one launch");
+  dim3 grid((unsigned)blocks_x, (unsigned)plan->cols.size());
+  const size_t smem = (size_t)(kHeaderRows + plan->max_steps) * kRow * sizeof(double) +
+                      (size_t)(plan->max_steps + 1) * sizeof(int32_t);
+  const bool vec = (n_points % 2 == 0) && ((uintptr_t)out % 16 == 0) &&
+                   (out_dtheta == nullptr || (uintptr_t)out_dtheta % 16 == 0);
+  const bool ang = theta != nullptr;
+  cudaError_t e;
+  switch (max_deriv) {
+    case 0: e = ang ? launch_walk_t<0, true>(a, grid, smem, vec, stream) : launch_walk_t<0, false>(a, grid, smem, vec, stream); break;
+    case 1: e = ang ? launch_walk_t<1, true>(a, grid, smem, vec, stream) : launch_walk_t<1, false>(a, grid, smem, vec, stream); break;
+    case 2: e = ang ? launch_walk_t<2, true>(a, grid, smem, vec, stream) : launch_walk_t<2, false>(a, grid, smem, vec, stream); break;
+    case 3: e = ang ? launch_walk_t<3, true>(a, grid, smem, vec, stream) : launch_walk_t<3, false>(a, grid, smem, vec, stream); break;
+    default: return set_error(ZP_ERR_DERIV_ORDER, "max_deriv outside 0..3");
+  }
+  if (e != cudaSuccess) return cuda_error(e, "walk_kernel launch");
+  return ZP_OK;
+}
+
+zp_status launch_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out, cudaStream_t stream) {
+  if (n_points == 0 || plan->n_modes == 0) return ZP_OK;
+  const int64_t blocks_x = (n_points + kThreads - 1) / kThreads;
+  if (blocks_x > 0x7fffffffLL) return set_error(ZP_ERR_INVALID_ARG, "n_points too large for one launch");
+  dim3 grid((unsigned)blocks_x, (unsigned)(plan->n_modes < 65535 ? plan->n_modes : 65535));
+  per_mode_kernel<<<grid, kThreads, 0, stream>>>(plan->dev.cols, plan->dev.table, plan->dev.mode_col, plan->dev.mode_N,
+                                                 r, n_points, plan->n_modes, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "per_mode_kernel launch");
+  return ZP_OK;
+}
+
+}  // namespace zp
