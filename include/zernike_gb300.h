@@ -165,6 +165,14 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  const double* grad_out, double* grad_coeffs, double* grad_r,
                                  double* grad_theta, void* stream);
 
+/*
+ * Reads (and optionally clears) the library's device-side wait-status word on the current
+ * device, synchronously.  Returns ZP_ERR_TIMEOUT if a bounded wait inside a tensor-core
+ * kernel gave up since the last reset (the kernel then skipped its remaining work and its
+ * outputs are incomplete), ZP_OK otherwise.
+ */
+ZP_API zp_status zp_device_wait_status(int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

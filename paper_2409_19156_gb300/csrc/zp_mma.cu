@@ -1,11 +1,482 @@
-// Split-precision tensor-core series evaluation (placeholder until the tcgen05 path lands).
+// Split-precision Zernike series on the fifth-generation tensor cores (tcgen05 + TMEM).
+//
+//   F[p, s] = sum_j Z_j(p) C[j, s],   Z from the float64 per-column recursion (zp_walk.cu),
+// contracted as BF16x3 (Z = Zh + Zl, C = Ch + Cl in bfloat16, F ~ Zh Ch + Zh Cl + Zl Ch with
+// float32 accumulation) or TF32 (one product of TF32-rounded operands).
+//
+// Two kernels per slab of point tiles:
+//  (A) split_basis_kernel: one thread per point walks every |m| column (the recursion of
+//      Sec. 2 in float64, Algorithm 1's order), rotates cos/sin(m theta) by angle addition
+//      from column to column, splits each Z into bfloat16 hi/lo (or TF32) and writes it into
+//      a shared-memory K-chunk already in the tensor core's 128-byte-swizzled K-major layout;
+//      complete chunks leave with bulk async copies (cp.async.bulk) into a scratch buffer.
+//      The K order of the contraction is the plan's slot order (column by column), so a
+//      thread's outputs are consecutive in K; the coefficient rows are permuted to match.
+//  (B) split_gemm_kernel: persistent, warp-specialised tcgen05 GEMM.  Warp 0 streams A
+//      (points x K) and B (sets x K) chunks into a shared-memory ring with bulk copies and
+//      mbarrier transaction counts; warp 1 issues tcgen05.mma (M = 128 points, N = 256 sets,
+//      K = 16 per instruction) into one of two TMEM accumulators; warps 2-5 drain the other
+//      accumulator (tcgen05.ld) to float32 rows of F while the next tile accumulates.
+// The coefficients are split/permuted once per call by split_coeff_kernel.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "zp_api_common.h"
+#include "zp_ptx.cuh"
 #include "zp_series_internal.h"
 
 namespace zp {
+namespace {
 
-zp_status series_eval_split(const zp_plan*, const double*, const double*, int64_t, const double*, int64_t,
-                            zp_precision, float*, cudaStream_t) {
-  return set_error(ZP_ERR_UNSUPPORTED, "split-precision series not built yet");
+constexpr int BM = 128;  // points per tile (TMEM lanes)
+constexpr int BN = 256;  // coefficient sets per tile (TMEM columns per accumulator)
+constexpr uint32_t kRowBytes = 128;
+constexpr uint32_t kAPart = BM * kRowBytes;  // 16 KB: one 128 x 128-byte K-chunk
+constexpr uint32_t kBPart = BN * kRowBytes;  // 32 KB
+constexpr int kGemmThreads = 192;            // 6 warps: producer, MMA, 4 x epilogue
+constexpr int kBasisThreads = BM;
+constexpr int kCoeffThreads = BN;
+
+template <bool TF32>
+struct Cfg {
+  static constexpr int BK = TF32 ? 32 : 64;  // K elements per 128-byte row
+  static constexpr int PARTS = TF32 ? 1 : 2;  // hi (+ lo)
+  static constexpr uint32_t A_CHUNK = kAPart * PARTS;
+  static constexpr uint32_t B_CHUNK = kBPart * PARTS;
+  static constexpr int STAGES = TF32 ? 4 : 2;
+  static constexpr uint32_t STAGE = A_CHUNK + B_CHUNK;
+  static constexpr int KSTEPS = 4;  // MMA K-steps per chunk (16 bf16 or 8 tf32 = 32 bytes each)
+  static constexpr uint32_t SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+__device__ unsigned int g_split_error = 0;  // set when a bounded wait gives up
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void put_elem(uint8_t* chunk, uint32_t row, uint32_t kk, float z) {
+  if constexpr (TF32) {
+    *reinterpret_cast<float*>(chunk + ptx::sw128_offset_b32(row, kk)) = to_tf32(z);
+  } else {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(z);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(z - __bfloat162float(hi));
+    const uint32_t off = ptx::sw128_offset_b16(row, kk);
+    *reinterpret_cast<__nv_bfloat16*>(chunk + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(chunk + kAPart + off) = lo;
+  }
+}
+
+__device__ __forceinline__ double pow_uint_m(double x, int e) {
+  double result = 1.0, base = x;
+  while (e) {
+    if (e & 1) result *= base;
+    base *= base;
+    e >>= 1;
+  }
+  return result;
+}
+
+struct BasisArgs {
+  const Column* cols;
+  int n_cols;
+  const double* table;
+  const int32_t* slot_ptr;
+  const int32_t* slot_idx;
+  const double* r;
+  const double* theta;
+  int64_t P;
+  int64_t mt_base;  // first point tile of this slab
+  int KC;           // K chunks
+  uint8_t* A;       // slab scratch: [tiles][KC][A_CHUNK]
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a) {
+  using C = Cfg<TF32>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const uint32_t t = threadIdx.x;
+  const int64_t p = (a.mt_base + blockIdx.x) * BM + t;
+  const bool valid = p < a.P;
+  const double rho = valid ? a.r[p] : 0.0;
+  const double th = valid ? a.theta[p] : 0.0;
+  const double u = rho * rho;
+  double s1, c1;
+  sincos(th, &s1, &c1);
+  double cm = 1.0, sm = 0.0, pm = 1.0;
+  int m_prev = 0;
+  uint8_t* gA = a.A + (size_t)blockIdx.x * a.KC * C::A_CHUNK;
+  int k = 0, buf = 0, kc = 0;
+
+  auto flush = [&]() {
+    ptx::fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      ptx::bulk_s2g(gA + (size_t)kc * C::A_CHUNK, smem + buf * C::A_CHUNK, C::A_CHUNK);
+      ptx::bulk_commit();
+      ptx::bulk_wait_read<1>();
+    }
+    __syncthreads();
+    buf ^= 1;
+    ++kc;
+  };
+
+  for (int c = 0; c < a.n_cols; ++c) {
+    const Column col = a.cols[c];
+    const int m = col.m;
+    if (m == m_prev + 1) {
+      const double cn = fma(cm, c1, -sm * s1);
+      const double sn = fma(sm, c1, cm * s1);
+      cm = cn;
+      sm = sn;
+      pm *= rho;
+    } else if (m != m_prev) {
+      sincos((double)m * th, &sm, &cm);
+      pm = pow_uint_m(rho, m);
+    }
+    m_prev = m;
+    const float cf = (float)cm, sf = (float)sm;
+    const double* h = a.table + (size_t)col.table_row * kRow;
+    const int32_t* sp = a.slot_ptr + col.slot_base;
+    double T = pm;
+    double S = fma(h[4], pm * u, -(h[8] * pm));
+    for (int N = 0; N < col.n_steps; ++N) {
+      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
+      double q;
+      if (N == 0) {
+        q = T;
+      } else if (N == 1) {
+        q = S;
+      } else {
+        const double g = fma(row[0], u, -row[1]);
+        q = fma(g, S, -T);
+        T = S;
+        S = q;
+      }
+      const int sb = sp[N], se = sp[N + 1];
+      if (sb == se) continue;
+      const float Rf = (float)(row[3] * q);
+      for (int s = sb; s < se; ++s) {
+        const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+        const float z = Rf * ((code >> 31) ? sf : cf);
+        put_elem<TF32>(smem + buf * C::A_CHUNK, t, (uint32_t)(k % C::BK), z);
+        if (++k % C::BK == 0) flush();
+      }
+    }
+  }
+  if (k % C::BK != 0) {
+    while (k % C::BK != 0) {
+      put_elem<TF32>(smem + buf * C::A_CHUNK, t, (uint32_t)(k % C::BK), 0.0f);
+      ++k;
+    }
+    flush();
+  }
+  if (t == 0) ptx::bulk_wait<0>();
+}
+
+struct CoeffArgs {
+  const double* coeffs;  // [J][S]
+  const int32_t* slot_idx;
+  int64_t J, S;
+  int KC;
+  uint8_t* B;  // [NT][KC][B_CHUNK]
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(kCoeffThreads) split_coeff_kernel(CoeffArgs a) {
+  using C = Cfg<TF32>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const int nt = blockIdx.x / a.KC, kc = blockIdx.x % a.KC;
+  const uint32_t t = threadIdx.x;
+  const int64_t s = (int64_t)nt * BN + t;
+  for (int kk = 0; kk < C::BK; ++kk) {
+    const int64_t kg = (int64_t)kc * C::BK + kk;
+    double v = 0.0;
+    if (kg < a.J && s < a.S) {
+      const int64_t j = (int64_t)((uint32_t)__ldg(a.slot_idx + kg) & 0x7fffffffu);
+      v = a.coeffs[j * a.S + s];
+    }
+    const float f = (float)v;
+    if constexpr (TF32) {
+      *reinterpret_cast<float*>(smem + ptx::sw128_offset_b32(t, kk)) = to_tf32(f);
+    } else {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+      const uint32_t off = ptx::sw128_offset_b16(t, kk);
+      *reinterpret_cast<__nv_bfloat16*>(smem + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(smem + kBPart + off) = lo;
+    }
+  }
+  __syncthreads();
+  uint4* dst = reinterpret_cast<uint4*>(a.B + ((size_t)nt * a.KC + kc) * C::B_CHUNK);
+  const uint4* src = reinterpret_cast<const uint4*>(smem);
+  for (uint32_t i = t; i < C::B_CHUNK / 16; i += kCoeffThreads) dst[i] = src[i];
+}
+
+struct GemmArgs {
+  const uint8_t* A;  // slab: [tiles][KC][A_CHUNK]
+  const uint8_t* B;  // [NT][KC][B_CHUNK]
+  float* F;          // [P][S]
+  int64_t P, S;
+  int64_t mt_base;
+  int64_t m_tiles;  // tiles in this slab
+  int n_tiles;      // NT
+  int KC;
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a) {
+  using C = Cfg<TF32>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* tmem_full = empty + C::STAGES;
+  uint64_t* tmem_empty = tmem_full + 2;
+  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(tmem_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::STAGES; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&tmem_full[i], 1);
+      ptx::mbar_init(&tmem_empty[i], 128);
+    }
+    *abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_base_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_slot;
+
+  const int64_t total_tiles = a.m_tiles * a.n_tiles;
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicOr(&g_split_error, 1u);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
+        const int64_t mt = tile / a.n_tiles;
+        const int nt = (int)(tile % a.n_tiles);
+        const uint8_t* gA = a.A + (size_t)mt * a.KC * C::A_CHUNK;
+        const uint8_t* gB = a.B + (size_t)nt * a.KC * C::B_CHUNK;
+        for (int kc = 0; kc < a.KC; ++kc) {
+          if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+            fail();
+            break;
+          }
+          uint8_t* sA = smem + stage * C::STAGE;
+          ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
+          ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
+          ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = TF32 ? ptx::idesc_tf32_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t local = 0;
+      for (int64_t tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x, ++local) {
+        const uint32_t acc = (uint32_t)(local & 1);
+        const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+        if (!ptx::mbar_wait(&tmem_empty[acc], acc_phase ^ 1u, abort_flag)) {
+          fail();
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        bool ok = true;
+        for (int kc = 0; kc < a.KC; ++kc) {
+          if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sA = ptx::smem_u32(smem + stage * C::STAGE);
+          const uint32_t sB = sA + C::A_CHUNK;
+#pragma unroll
+          for (int ks = 0; ks < C::KSTEPS; ++ks) {
+            const uint32_t koff = ks * 32;
+            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+            if constexpr (TF32) {
+              ptx::mma_tf32(d_tmem, ptx::sw128_kmajor_desc(sA + koff), ptx::sw128_kmajor_desc(sB + koff), idesc,
+                            first);
+            } else {
+              const uint64_t ah = ptx::sw128_kmajor_desc(sA + koff);
+              const uint64_t al = ptx::sw128_kmajor_desc(sA + kAPart + koff);
+              const uint64_t bh = ptx::sw128_kmajor_desc(sB + koff);
+              const uint64_t bl = ptx::sw128_kmajor_desc(sB + kBPart + koff);
+              ptx::mma_bf16(d_tmem, ah, bh, idesc, first);
+              ptx::mma_bf16(d_tmem, ah, bl, idesc, 1u);
+              ptx::mma_bf16(d_tmem, al, bh, idesc, 1u);
+            }
+          }
+          ptx::mma_commit(&empty[stage]);
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&tmem_full[acc]);
+      }
+    }
+  } else {
+    // Epilogue: warp (2..5) & 3 selects the TMEM lane quadrant it may access.
+    const uint32_t q = (uint32_t)(warp & 3);
+    const uint32_t row = q * 32 + lane;
+    int64_t local = 0;
+    for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++local) {
+      const uint32_t acc = (uint32_t)(local & 1);
+      const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
+      if (!ptx::mbar_wait(&tmem_full[acc], acc_phase, abort_flag)) {
+        fail();
+        break;
+      }
+      ptx::tc_fence_after();
+      const int64_t mt = a.mt_base + tile / a.n_tiles;
+      const int nt = (int)(tile % a.n_tiles);
+      const int64_t p = mt * BM + row;
+      const int64_t col0 = (int64_t)nt * BN;
+      float* frow = a.F + p * a.S;
+      const bool vec = (a.S % 4) == 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        ptx::tmem_ld_32x32b_x32(tmem_base + ((q * 32u) << 16) + acc * BN + (uint32_t)c0, v);
+        ptx::tmem_ld_wait();
+        if (p < a.P) {
+          const int64_t cbase = col0 + c0;
+          if (vec && cbase + 32 <= a.S) {
+            float4* dst = reinterpret_cast<float4*>(frow + cbase);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              __stcs(dst + i, make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
+                                          __uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])));
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (cbase + i < a.S) frow[cbase + i] = __uint_as_float(v[i]);
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(&tmem_empty[acc]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 512);
+  }
+}
+
+template <bool TF32>
+zp_status run_split(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                    int64_t S, float* out, cudaStream_t stream) {
+  using C = Cfg<TF32>;
+  const int64_t J = plan->n_modes;
+  const int KC = (int)((J + C::BK - 1) / C::BK);
+  const int64_t MT = (P + BM - 1) / BM;
+  const int NT = (int)((S + BN - 1) / BN);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // Slab of point tiles whose split basis fits a 512 MB scratch buffer.
+  const size_t tile_bytes = (size_t)KC * C::A_CHUNK;
+  const int64_t slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
+  ScratchBuffer bbuf, abuf;
+  ZP_TRY(bbuf.alloc((size_t)NT * KC * C::B_CHUNK, stream));
+  ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
+
+  const uint32_t basis_smem = 2 * C::A_CHUNK + 1024;
+  const uint32_t coeff_smem = C::B_CHUNK + 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(split_basis_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, basis_smem)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+          cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
+
+  CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, (uint8_t*)bbuf.ptr};
+  split_coeff_kernel<TF32><<<(unsigned)(NT * KC), kCoeffThreads, coeff_smem, stream>>>(ca);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_coeff_kernel launch");
+
+  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
+    const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
+    BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
+                 r, theta, P, mt0, KC, (uint8_t*)abuf.ptr};
+    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, basis_smem, stream>>>(ba);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
+    GemmArgs ga{(const uint8_t*)abuf.ptr, (const uint8_t*)bbuf.ptr, out, P, S, mt0, tiles, NT, KC};
+    const int64_t total = tiles * NT;
+    const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
+    split_gemm_kernel<TF32><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
+  }
+  return ZP_OK;
+}
+
+}  // namespace
+
+zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                            const double* coeffs, int64_t S, zp_precision prec, float* out, cudaStream_t stream) {
+  if (prec == ZP_PREC_TF32) return run_split<true>(plan, r, theta, P, coeffs, S, out, stream);
+  return run_split<false>(plan, r, theta, P, coeffs, S, out, stream);
+}
+
+zp_status split_error_word(unsigned int* value, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_split_error, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyFromSymbol");
+  if (reset) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyToSymbol(g_split_error, &zero, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyToSymbol");
+  }
+  return ZP_OK;
 }
 
 }  // namespace zp
+
+extern "C" zp_status zp_device_wait_status(int32_t reset) {
+  zp::clear_error();
+  unsigned int v = 0;
+  ZP_TRY(zp::split_error_word(&v, reset != 0));
+  if (v) return zp::set_error(ZP_ERR_TIMEOUT, "a bounded device wait in the tensor-core series kernel gave up");
+  return ZP_OK;
+}
