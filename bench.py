@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-points", type=int, default=1536)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads (series, adjoint, basis latency)")
+    ap.add_argument("--series-only", action="store_true",
+                    help="run only the mixed_n32 series measurement (profiling captures)")
+    ap.add_argument("--series-points", type=int, default=1_000_000)
     ap.add_argument("--points", type=int, default=100_000,
                     help="point count (smaller values only for profiling captures; the bench line uses 100000)")
     return ap.parse_args()
@@ -274,6 +279,13 @@ def run_ours(args) -> None:
                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": out_bytes, "ms_per_step": best, "how": how,
                "ms_per_step_copy": t_copy, "ms_per_step_mapped": t_mapped}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        del out
+        torch.cuda.empty_cache()
+        extras = {"series": measure_series(dev, peaks), "adjoint": measure_adjoint(dev),
+                  "basis": measure_basis_latency(dev)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.cpu_sample_points)
@@ -297,10 +309,139 @@ def run_ours(args) -> None:
             "clocks": clk,
             "gpu_launches": args.steps,
             "wall_s_timed": wall,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- secondary workloads
+def _events_ms(stream, fn, steps):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_fp64: bool = True) -> dict:
+    """mixed_n32: 561 modes, 1e6 points r = sqrt(U), 4096 coefficient sets.  The split-precision
+    tensor-core series (per-phase CUDA-event times recorded by the library on the launching
+    stream) against the plain float64 basis-then-DGEMM form on the same inputs."""
+    import ctypes
+
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import _lib, inputs
+
+    cfg = inputs.WORKLOADS["mixed_n32"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.sqrt_uniform_points(cfg["n_points"], cfg["seed"])
+    r, th = r[:n_points], th[:n_points]
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    J, P, S = len(ns), len(r), C.shape[1]
+    plan = zp.Plan(ns, ms, device=dev)
+    rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
+    lib = _lib.load()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    out = {"workload": "mixed_n32", "modes": J, "points": P, "sets": S}
+    F = torch.empty((P, S), dtype=torch.float32, device=dev)
+    phase = (ctypes.c_float * 3)()
+    bf16_peak = peaks.get("bf16_tflops", 1906.3) * 1e12
+    for prec, code, parts, bk in (("bf16x3", 1, 3, 64), ("tf32", 2, 1, 32)):
+        kp = -(-J // bk) * bk
+        issued = parts * 2.0 * (-(-P // 128) * 128) * kp * (-(-S // 256) * 256)
+        runs = []
+        for i in range(steps + 1):
+            t = _events_ms(stream, lambda: _lib.check("zp_series_eval_timed", lib.zp_series_eval_timed(
+                plan.handle, rt.data_ptr(), tt.data_ptr(), P, Ct.data_ptr(), S, code, F.data_ptr(), sp, phase)), 1)
+            if i:
+                runs.append((t, list(phase)))
+        call_ms = statistics.mean(x[0] for x in runs)
+        ph = [statistics.mean(x[1][k] for x in runs) for k in range(3)]
+        _lib.check("zp_device_wait_status", lib.zp_device_wait_status(1))
+        peak = bf16_peak if prec == "bf16x3" else bf16_peak / 2  # TF32 dense rate = bf16 / 2 (nominal ratio)
+        out[prec] = {"ms_per_call": call_ms, "ms_coeff_split": ph[0], "ms_basis_split": ph[1], "ms_gemm": ph[2],
+                     "useful_tflops": 2.0 * P * J * S / (call_ms * 1e-3) / 1e12,
+                     "roofline": {"bound": "tensor", "kernel": f"split_gemm_kernel<{prec == 'tf32'}>",
+                                  "achieved": issued / (ph[2] * 1e-3) / 1e12, "peak": peak / 1e12,
+                                  "unit": "TFLOP/s", "frac": issued / (ph[2] * 1e-3) / peak,
+                                  "flops_per_call_issued": issued,
+                                  "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" +
+                                                 (" x 1/2 (nominal tf32:bf16)" if prec == "tf32" else "")}}
+        if prec == "bf16x3":
+            F_keep = F.clone()
+    if not with_fp64:
+        return out
+    # Plain float64 form: basis to HBM, then cuBLAS DGEMM.
+    zp.series_eval(None, None, rt[:1024].contiguous(), tt[:1024].contiguous(), Ct, "fp64", plan=plan)
+    torch.cuda.synchronize()
+    F64 = torch.empty((P, S), dtype=torch.float64, device=dev)
+    t64 = _events_ms(stream, lambda: _lib.check("zp_series_eval_plan", lib.zp_series_eval_plan(
+        plan.handle, rt.data_ptr(), tt.data_ptr(), P, Ct.data_ptr(), S, 0, F64.data_ptr(), sp)), 1)
+    num = den = 0.0
+    for i in range(0, P, 1 << 17):
+        d = F_keep[i:i + (1 << 17)].double() - F64[i:i + (1 << 17)]
+        num += float((d * d).sum())
+        den += float((F64[i:i + (1 << 17)] ** 2).sum())
+    out["fp64_basis_then_dgemm_ms"] = t64
+    out["speedup_bf16x3_vs_fp64"] = t64 / out["bf16x3"]["ms_per_call"]
+    out["bf16x3_rel_frobenius_vs_fp64"] = math.sqrt(num / den)
+    del F64, F_keep, F
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_adjoint(dev, steps: int = 5) -> dict:
+    """series_n24: 325 modes, 250 x 200 polar grid, 256 sets; float64 forward and adjoint."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import inputs
+
+    cfg = inputs.WORKLOADS["series_n24"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.polar_grid(cfg["n_r"], cfg["n_theta"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    G = torch.randn((len(r), C.shape[1]), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(2))
+    plan = zp.Plan(ns, ms, device=dev)
+    rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
+    stream = torch.cuda.current_stream(dev)
+    zp.series_eval(None, None, rt, tt, Ct, plan=plan)
+    zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
+    fwd = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, plan=plan), steps)
+    adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan), steps)
+    return {"workload": "series_n24", "modes": len(ns), "points": len(r), "sets": C.shape[1],
+            "fp64_forward_ms": fwd, "fp64_adjoint_ms": adj}
+
+
+def measure_basis_latency(dev, steps: int = 200) -> dict:
+    """basis_n20: 231 modes, 1000 points, R, R', R'' times the angular factor, plus d/dtheta Z."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import inputs
+
+    cfg = inputs.WORKLOADS["basis_n20"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.uniform_points(cfg["n_points"], cfg["seed"])
+    plan = zp.Plan(ns, ms, device=dev)
+    rt, tt = (torch.as_tensor(x, device=dev) for x in (r, th))
+    stream = torch.cuda.current_stream(dev)
+    fn = lambda: zp.basis(None, None, rt, tt, 2, dtheta=True, plan=plan)  # noqa: E731
+    fn()
+    ms_call = _events_ms(stream, fn, steps)
+    vals = len(ns) * len(r) * 4
+    return {"workload": "basis_n20", "modes": len(ns), "points": len(r), "us_per_call": ms_call * 1e3,
+            "values_per_s": vals / (ms_call * 1e-3)}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -333,6 +474,14 @@ def run_reference(args) -> None:
 
 def main():
     args = parse_args()
+    if args.series_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        res = measure_series(torch.device("cuda", 0), {}, steps=args.steps, n_points=args.series_points,
+                             with_fp64=False)
+        print(json.dumps({"series_only": res}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

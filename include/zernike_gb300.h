@@ -147,6 +147,16 @@ ZP_API zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const
                               zp_precision prec, void* out, void* stream);
 
 /*
+ * zp_series_eval_plan for ZP_PREC_BF16X3 / ZP_PREC_TF32 with per-phase timing: CUDA events
+ * are recorded on `stream` around each launch and phase_ms[0..2] receives the summed device
+ * time of the coefficient split, the basis split and the tensor-core GEMM launches.  The
+ * call synchronises `stream` before returning (instrumentation; not for graph capture).
+ */
+ZP_API zp_status zp_series_eval_timed(const zp_plan* plan, const double* r, const double* theta,
+                                      int64_t n_points, const double* coeffs, int64_t n_sets,
+                                      zp_precision prec, void* out, void* stream, float* phase_ms);
+
+/*
  * Adjoint of the series (the reverse-mode derivative that Sec. 3 provides by a custom
  * rule), float64 throughout.  With G = grad_out (DEVICE float64 [n_points][n_sets]):
  *   grad_coeffs[j, s] = sum_p Z_j(p) G[p, s]                         ([n_modes][n_sets])

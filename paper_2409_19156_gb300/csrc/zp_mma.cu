@@ -23,6 +23,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 #include "zp_api_common.h"
 #include "zp_ptx.cuh"
@@ -404,9 +406,51 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
 }
 
+// Optional per-phase timing: CUDA events recorded on the launching stream around every
+// launch, summed per phase after the stream is synchronised.
+struct PhaseTimer {
+  float* ms = nullptr;  // [3]: coefficient split, basis split, GEMM (NULL: no timing)
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
+  void begin(int phase, cudaEvent_t* start) {
+    *start = nullptr;
+    if (!ms) return;
+    cudaEventCreate(start);
+    cudaEventRecord(*start, stream);
+    (void)phase;
+  }
+  void end(int phase, cudaEvent_t start) {
+    if (!ms) return;
+    cudaEvent_t stop;
+    cudaEventCreate(&stop);
+    cudaEventRecord(stop, stream);
+    ev[phase].emplace_back(start, stop);
+  }
+  zp_status finish() {
+    if (!ms) return ZP_OK;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    for (int i = 0; i < 3; ++i) {
+      ms[i] = 0.0f;
+      for (auto& pr : ev[i]) {
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pr.first, pr.second);
+        ms[i] += t;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+      ev[i].clear();
+    }
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "phase timing");
+  }
+};
+
 template <bool TF32>
 zp_status run_split(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
-                    int64_t S, float* out, cudaStream_t stream) {
+                    int64_t S, float* out, cudaStream_t stream, float* phase_ms) {
+  PhaseTimer timer;
+  timer.ms = phase_ms;
+  timer.stream = stream;
+  cudaEvent_t ev0;
   using C = Cfg<TF32>;
   const int64_t J = plan->n_modes;
   const int KC = (int)((J + C::BK - 1) / C::BK);
@@ -434,30 +478,37 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, (uint8_t*)bbuf.ptr};
+  timer.begin(0, &ev0);
   split_coeff_kernel<TF32><<<(unsigned)(NT * KC), kCoeffThreads, coeff_smem, stream>>>(ca);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_coeff_kernel launch");
+  timer.end(0, ev0);
 
   for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
     const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
     BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
                  r, theta, P, mt0, KC, (uint8_t*)abuf.ptr};
+    timer.begin(1, &ev0);
     split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, basis_smem, stream>>>(ba);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
+    timer.end(1, ev0);
     GemmArgs ga{(const uint8_t*)abuf.ptr, (const uint8_t*)bbuf.ptr, out, P, S, mt0, tiles, NT, KC};
     const int64_t total = tiles * NT;
     const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
+    timer.begin(2, &ev0);
     split_gemm_kernel<TF32><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
+    timer.end(2, ev0);
   }
-  return ZP_OK;
+  return timer.finish();
 }
 
 }  // namespace
 
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
-                            const double* coeffs, int64_t S, zp_precision prec, float* out, cudaStream_t stream) {
-  if (prec == ZP_PREC_TF32) return run_split<true>(plan, r, theta, P, coeffs, S, out, stream);
-  return run_split<false>(plan, r, theta, P, coeffs, S, out, stream);
+                            const double* coeffs, int64_t S, zp_precision prec, float* out, cudaStream_t stream,
+                            float* phase_ms) {
+  if (prec == ZP_PREC_TF32) return run_split<true>(plan, r, theta, P, coeffs, S, out, stream, phase_ms);
+  return run_split<false>(plan, r, theta, P, coeffs, S, out, stream, phase_ms);
 }
 
 zp_status split_error_word(unsigned int* value, bool reset) {

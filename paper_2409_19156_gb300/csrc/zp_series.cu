@@ -249,6 +249,21 @@ zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double
   return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, st);
 }
 
+zp_status zp_series_eval_timed(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                               const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream,
+                               float* phase_ms) {
+  clear_error();
+  if (!phase_ms) return set_error(ZP_ERR_INVALID_ARG, "phase_ms is NULL");
+  if (prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32)
+    return set_error(ZP_ERR_INVALID_ARG, "timed series supports the split precisions only");
+  ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
+  phase_ms[0] = phase_ms[1] = phase_ms[2] = 0.0f;
+  if (n_points == 0 || n_sets == 0 || plan->n_modes == 0) return ZP_OK;
+  ZP_TRY(check_device_array(out, "out", 16));
+  return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, (cudaStream_t)stream,
+                           phase_ms);
+}
+
 zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
                          int64_t n_points, const double* coeffs, int64_t n_sets, zp_precision prec, void* out,
                          void* stream) {

@@ -23,8 +23,10 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
                               double* grad_r, double* grad_theta, cudaStream_t stream);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
+// phase_ms: NULL, or [3] receiving the summed CUDA-event times of the coefficient split,
+// the basis split and the GEMM launches (the call then synchronises the stream).
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                             const double* coeffs, int64_t S, zp_precision prec, float* out,
-                            cudaStream_t stream);
+                            cudaStream_t stream, float* phase_ms = nullptr);
 
 }  // namespace zp

@@ -1,0 +1,104 @@
+"""Parity of the tensor-core split-precision series (BF16x3 / TF32, tcgen05) with the exact oracle
+and with the float64 path.
+
+Tolerance (derived from the arithmetic): BF16x3 keeps Zh Ch + Zh Cl + Zl Ch of each product,
+whose relative error is at most about 3 * 2^-16 (the dropped Zl Cl term plus the rounding of
+the low halves), and the float32 accumulation adds about J * 2^-24; with Z and C first
+rounded to float32 this gives |F - F64| <= 1e-4 * sum_j |Z_j C_js| + 1e-6 elementwise.  TF32
+keeps 10 mantissa bits per operand (2 * 2^-11 per product): 2e-3 * sum_j |Z_j C_js| + 1e-6.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2409_19156_gb300 as zp  # noqa: E402
+from paper_2409_19156_gb300 import _lib, inputs  # noqa: E402
+from oracle import basis as obasis, series as oseries  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+REL = {"bf16x3": 1e-4, "tf32": 2e-3}
+
+
+def dev(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device=DEV)
+
+
+def abs_sum(ns, ms, r, th, C):
+    Z = np.abs(np.array(obasis.basis_table(ns, ms, r, th, 0)[0][0]))
+    return Z.T @ np.abs(C)
+
+
+def wait_ok():
+    assert _lib.load().zp_device_wait_status(1) == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("nmax,P,S", [(8, 128, 256), (8, 300, 5), (20, 77, 300), (3, 1, 1), (0, 5, 3)])
+def test_split_small_against_oracle(prec, nmax, P, S):
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.uniform_points(P, 31 + nmax)
+    C = inputs.scaled_normal_coeffs(ns, S, 31 + nmax)
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), prec).cpu().numpy()
+    wait_ok()
+    assert F.dtype == np.float32 and F.shape == (P, S)
+    want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
+    tol = REL[prec] * abs_sum(ns, ms, r, th, C) + 1e-6
+    assert (np.abs(F - want) <= tol).all()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_split_many_chunks_ragged_against_fp64(prec):
+    """n <= 32 (561 modes: 9 K-chunks), ragged point and set tails; the full output against
+    the float64 path (itself checked against the oracle) and sampled rows against the oracle."""
+    ns, ms = inputs.full_zernike_modes(32)
+    r, th = inputs.sqrt_uniform_points(1000, 5)
+    C = inputs.scaled_normal_coeffs(ns, 300, 5)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    F = zp.series_eval(ns, ms, rt, tt, Ct, prec).double()
+    wait_ok()
+    F64 = zp.series_eval(ns, ms, rt, tt, Ct, "fp64")
+    rel = float((F - F64).norm() / F64.norm())
+    assert rel < (2e-5 if prec == "bf16x3" else 1e-3), rel
+    rows = np.array([0, 127, 128, 999])
+    want = np.array(oseries.series_eval(ns, ms, r[rows], th[rows], C.tolist()))
+    tol = REL[prec] * abs_sum(ns, ms, r[rows], th[rows], C) + 1e-6
+    assert (np.abs(F[torch.as_tensor(rows, device=DEV)].cpu().numpy() - want) <= tol).all()
+
+
+def test_split_duplicates_and_scrambled_modes():
+    ns = [5, 12, 12, 0, 7, 5, 30, 30]
+    ms = [-3, 4, 4, 0, -7, 1, 0, -2]
+    r, th = inputs.uniform_points(200, 6)
+    C = inputs.scaled_normal_coeffs(np.array(ns), 40, 6)
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), "bf16x3").cpu().numpy()
+    wait_ok()
+    want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
+    tol = REL["bf16x3"] * abs_sum(ns, ms, r, th, C) + 1e-6
+    assert (np.abs(F - want) <= tol).all()
+
+
+def test_mixed_n32_full_size_sampled():
+    """The 561-mode, 1e6-point (r = sqrt(U)), 4096-set workload at full size in the
+    benchmark's configuration: sampled rows against the oracle, and the relative Frobenius
+    error against float64 on a 4096-point slice."""
+    cfg = inputs.WORKLOADS["mixed_n32"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.sqrt_uniform_points(cfg["n_points"], cfg["seed"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    plan = zp.Plan(ns, ms)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    F = zp.series_eval(None, None, rt, tt, Ct, "bf16x3", plan=plan)
+    torch.cuda.synchronize()
+    wait_ok()
+    rows = np.array([0, 1, 523_777, 999_999])
+    got = F[torch.as_tensor(rows, device=DEV)].double().cpu().numpy()[:, :512]
+    want = np.array(oseries.series_eval(ns, ms, r[rows], th[rows], C[:, :512].tolist()))
+    tol = REL["bf16x3"] * abs_sum(ns, ms, r[rows], th[rows], C[:, :512]) + 1e-6
+    assert (np.abs(got - want) <= tol).all()
+    sl = slice(500_000, 504_096)
+    F64 = zp.series_eval(None, None, rt[sl].contiguous(), tt[sl].contiguous(), Ct, "fp64", plan=plan)
+    rel = float((F[sl].double() - F64).norm() / F64.norm())
+    assert rel < 2e-5, rel
+    assert bool(torch.isfinite(F).all())
