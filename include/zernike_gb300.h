@@ -176,6 +176,35 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  double* grad_theta, void* stream);
 
 /*
+ * Allocation-free series evaluation.  (The paper has no counterpart: this is a library
+ * service for callers that cannot allocate device memory while they run, such as code in a
+ * host callback or an allocator hook, applications that reserve all device memory at
+ * start-up, or latency-critical loops where a cudaMalloc would stall other work.)
+ *
+ * Same arguments and result as zp_series_eval with ZP_PREC_BF16X3 or ZP_PREC_TF32 (out is
+ * float32 [n_points][n_sets], 16-byte aligned), but no device memory is allocated: the plan
+ * tables, the split coefficient tiles and the split basis live in one file-scope device array
+ * of ZP_STATIC_SCRATCH_BYTES, present on every GPU that loads the library until the process
+ * exits.  The array is shared by every call and keeps the last call's contents; each call
+ * rewrites everything it reads, so nothing needs clearing.  Calls that overlap on the GPU
+ * (different streams, or different host threads) race on the array: serialise them, for
+ * example by issuing them on one stream.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The tables travel by cudaMemcpyAsync from pageable host
+ * memory on `stream`.
+ * Limits: the plan tables, the coefficient tiles (ceil(n_sets/256) * ceil(n_modes/64) * 64 KiB
+ * for BF16X3, /32 and 32 KiB for TF32) and one 128-point basis tile (ceil(n_modes/64) * 32 KiB,
+ * TF32: ceil(n_modes/32) * 16 KiB) must fit in ZP_STATIC_SCRATCH_BYTES; larger problems are
+ * rejected with ZP_ERR_INVALID_ARG before anything is launched.  Points beyond one tile are
+ * processed in slabs, so n_points has no limit of its own.
+ */
+#define ZP_STATIC_SCRATCH_BYTES (64u << 20)
+ZP_API zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64_t n_modes,
+                                       const double* r, const double* theta, int64_t n_points,
+                                       const double* coeffs, int64_t n_sets, zp_precision prec,
+                                       float* out, void* stream);
+
+/*
  * Reads (and optionally clears) the library's device-side wait-status word on the current
  * device, synchronously.  Returns ZP_ERR_TIMEOUT if a bounded wait inside a tensor-core
  * kernel gave up since the last reset (the kernel then skipped its remaining work and its

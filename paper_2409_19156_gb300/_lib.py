@@ -39,6 +39,8 @@ SIGNATURES = {
     "zp_series_adjoint": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
                                          ctypes.c_int64, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_device_wait_status": (ctypes.c_int, [ctypes.c_int32]),
+    "zp_series_eval_static": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
+                                             ctypes.c_int64, ctypes.c_int, c_dp, c_dp]),
     "zp_series_eval_timed": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
                                             ctypes.c_int, c_dp, c_dp, ctypes.POINTER(ctypes.c_float)]),
     "zp_series_adjoint_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64, c_dp,

@@ -63,6 +63,14 @@ void clear_error();
 
 // Host-side plan construction (validation, grouping, tables, upload).
 zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out);
+// Host half only: validates and fills the host tables of *p (no device memory touched).
+zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan* p);
+// Byte size of the plan's device tables; offsets[0..5] of cols, table, slot_ptr, slot_idx,
+// mode_col, mode_N inside that block (256-byte aligned sections).
+size_t plan_device_layout(const zp_plan* p, size_t offsets[6]);
+// Points p->dev at `base` (laid out as plan_device_layout) and copies the host tables there,
+// with cudaMemcpyAsync on `stream` when async, else synchronously.
+zp_status plan_upload(zp_plan* p, void* base, cudaStream_t stream, bool async);
 // Cached plan for a mode list on the current device (created on first use).
 zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const zp_plan** out);
 zp_status check_plan_device(const zp_plan* plan);

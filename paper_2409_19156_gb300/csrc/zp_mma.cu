@@ -446,7 +446,7 @@ struct PhaseTimer {
 
 template <bool TF32>
 zp_status run_split(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
-                    int64_t S, float* out, cudaStream_t stream, float* phase_ms) {
+                    int64_t S, float* out, cudaStream_t stream, float* phase_ms, const SplitScratch* preset) {
   PhaseTimer timer;
   timer.ms = phase_ms;
   timer.stream = stream;
@@ -459,12 +459,27 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // Slab of point tiles whose split basis fits a 512 MB scratch buffer.
   const size_t tile_bytes = (size_t)KC * C::A_CHUNK;
-  const int64_t slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
+  const size_t b_bytes = (size_t)NT * KC * C::B_CHUNK;
   ScratchBuffer bbuf, abuf;
-  ZP_TRY(bbuf.alloc((size_t)NT * KC * C::B_CHUNK, stream));
-  ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
+  uint8_t* A = nullptr;
+  uint8_t* B = nullptr;
+  int64_t slab = 0;
+  if (preset) {
+    // Caller-provided scratch: the B tiles first, then as many point tiles as fit.
+    if (preset->b_bytes < b_bytes || preset->a_bytes < tile_bytes)
+      return set_error(ZP_ERR_INVALID_ARG, "split scratch too small for this problem");
+    A = preset->a;
+    B = preset->b;
+    slab = std::min<int64_t>(MT, (int64_t)(preset->a_bytes / tile_bytes));
+  } else {
+    // Slab of point tiles whose split basis fits a 512 MB scratch buffer.
+    slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
+    ZP_TRY(bbuf.alloc(b_bytes, stream));
+    ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
+    A = (uint8_t*)abuf.ptr;
+    B = (uint8_t*)bbuf.ptr;
+  }
 
   const uint32_t basis_smem = 2 * C::A_CHUNK + 1024;
   const uint32_t coeff_smem = C::B_CHUNK + 1024;
@@ -477,7 +492,7 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
           cudaSuccess)
     return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
 
-  CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, (uint8_t*)bbuf.ptr};
+  CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
   timer.begin(0, &ev0);
   split_coeff_kernel<TF32><<<(unsigned)(NT * KC), kCoeffThreads, coeff_smem, stream>>>(ca);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_coeff_kernel launch");
@@ -486,12 +501,12 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
     const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
     BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
-                 r, theta, P, mt0, KC, (uint8_t*)abuf.ptr};
+                 r, theta, P, mt0, KC, A};
     timer.begin(1, &ev0);
     split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, basis_smem, stream>>>(ba);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
     timer.end(1, ev0);
-    GemmArgs ga{(const uint8_t*)abuf.ptr, (const uint8_t*)bbuf.ptr, out, P, S, mt0, tiles, NT, KC};
+    GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
     const int64_t total = tiles * NT;
     const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
     timer.begin(2, &ev0);
@@ -506,9 +521,21 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                             const double* coeffs, int64_t S, zp_precision prec, float* out, cudaStream_t stream,
-                            float* phase_ms) {
-  if (prec == ZP_PREC_TF32) return run_split<true>(plan, r, theta, P, coeffs, S, out, stream, phase_ms);
-  return run_split<false>(plan, r, theta, P, coeffs, S, out, stream, phase_ms);
+                            float* phase_ms, const SplitScratch* preset) {
+  if (prec == ZP_PREC_TF32) return run_split<true>(plan, r, theta, P, coeffs, S, out, stream, phase_ms, preset);
+  return run_split<false>(plan, r, theta, P, coeffs, S, out, stream, phase_ms, preset);
+}
+
+size_t split_scratch_bytes(zp_precision prec, int64_t n_modes, int64_t n_sets, size_t* b_bytes, size_t* tile_bytes) {
+  const bool tf32 = prec == ZP_PREC_TF32;
+  const int64_t bk = tf32 ? Cfg<true>::BK : Cfg<false>::BK;
+  const size_t a_chunk = tf32 ? Cfg<true>::A_CHUNK : Cfg<false>::A_CHUNK;
+  const size_t b_chunk = tf32 ? Cfg<true>::B_CHUNK : Cfg<false>::B_CHUNK;
+  const int64_t KC = (n_modes + bk - 1) / bk;
+  const int64_t NT = (n_sets + BN - 1) / BN;
+  *b_bytes = (size_t)NT * KC * b_chunk;
+  *tile_bytes = (size_t)KC * a_chunk;
+  return *b_bytes + *tile_bytes;
 }
 
 zp_status split_error_word(unsigned int* value, bool reset) {

@@ -81,8 +81,7 @@ static void fill_column_table(int m, int n_steps, double* rows) {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out) {
-  if (!out) return set_error(ZP_ERR_INVALID_ARG, "plan output pointer is NULL");
+zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan* p) {
   if (n_modes < 0) return set_error(ZP_ERR_INVALID_ARG, "n_modes < 0");
   if (n_modes > 0 && (!n || !m)) return set_error(ZP_ERR_INVALID_ARG, "mode arrays are NULL");
   if (n_modes >= (int64_t(1) << 31)) return set_error(ZP_ERR_INVALID_ARG, "n_modes >= 2^31");
@@ -104,7 +103,6 @@ zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_pla
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
 
-  std::unique_ptr<zp_plan> p(new zp_plan());
   p->device = dev;
   p->n_modes = n_modes;
   p->n_max = n_max;
@@ -168,41 +166,69 @@ zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_pla
     const int32_t pos = p->slot_ptr[s] + fill[s]++;
     p->slot_idx[pos] = (int32_t)((uint32_t)j | (m[j] < 0 ? 0x80000000u : 0u));
   }
+  return ZP_OK;
+}
 
-  // Upload: one device block holding every table.
+size_t plan_device_layout(const zp_plan* p, size_t offsets[6]) {
   const size_t b_cols = align_up(p->cols.size() * sizeof(Column), 256);
   const size_t b_table = align_up(p->table.size() * sizeof(double), 256);
   const size_t b_sptr = align_up(p->slot_ptr.size() * sizeof(int32_t), 256);
   const size_t b_sidx = align_up(std::max<size_t>(p->slot_idx.size(), 1) * sizeof(int32_t), 256);
-  const size_t b_mode = align_up(std::max<int64_t>(n_modes, 1) * sizeof(int32_t), 256);
-  const size_t total = b_cols + b_table + b_sptr + b_sidx + 2 * b_mode;
-  if (total > 0) {
-    e = cudaMalloc(&p->dev_block, total);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(plan tables)");
-    p->device_bytes = total;
-    char* base = (char*)p->dev_block;
-    p->dev.cols = (Column*)base;
-    p->dev.table = (double*)(base + b_cols);
-    p->dev.slot_ptr = (int32_t*)(base + b_cols + b_table);
-    p->dev.slot_idx = (int32_t*)(base + b_cols + b_table + b_sptr);
-    p->dev.mode_col = (int32_t*)(base + b_cols + b_table + b_sptr + b_sidx);
-    p->dev.mode_N = (int32_t*)(base + b_cols + b_table + b_sptr + b_sidx + b_mode);
-    struct Part { void* dst; const void* src; size_t bytes; } parts[] = {
-        {p->dev.cols, p->cols.data(), p->cols.size() * sizeof(Column)},
-        {p->dev.table, p->table.data(), p->table.size() * sizeof(double)},
-        {p->dev.slot_ptr, p->slot_ptr.data(), p->slot_ptr.size() * sizeof(int32_t)},
-        {p->dev.slot_idx, p->slot_idx.data(), p->slot_idx.size() * sizeof(int32_t)},
-        {p->dev.mode_col, p->mode_col.data(), p->mode_col.size() * sizeof(int32_t)},
-        {p->dev.mode_N, p->mode_N.data(), p->mode_N.size() * sizeof(int32_t)},
-    };
-    for (const Part& part : parts) {
-      if (part.bytes == 0) continue;
-      e = cudaMemcpy(part.dst, part.src, part.bytes, cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) {
-        cudaFree(p->dev_block);
-        return cuda_error(e, "cudaMemcpy(plan tables)");
-      }
-    }
+  const size_t b_mode = align_up(std::max<int64_t>(p->n_modes, 1) * sizeof(int32_t), 256);
+  offsets[0] = 0;
+  offsets[1] = b_cols;
+  offsets[2] = b_cols + b_table;
+  offsets[3] = b_cols + b_table + b_sptr;
+  offsets[4] = b_cols + b_table + b_sptr + b_sidx;
+  offsets[5] = b_cols + b_table + b_sptr + b_sidx + b_mode;
+  return offsets[5] + b_mode;
+}
+
+zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool async) {
+  size_t off[6];
+  plan_device_layout(p, off);
+  char* base = (char*)base_ptr;
+  p->dev.cols = (Column*)(base + off[0]);
+  p->dev.table = (double*)(base + off[1]);
+  p->dev.slot_ptr = (int32_t*)(base + off[2]);
+  p->dev.slot_idx = (int32_t*)(base + off[3]);
+  p->dev.mode_col = (int32_t*)(base + off[4]);
+  p->dev.mode_N = (int32_t*)(base + off[5]);
+  struct Part {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } parts[] = {
+      {p->dev.cols, p->cols.data(), p->cols.size() * sizeof(Column)},
+      {p->dev.table, p->table.data(), p->table.size() * sizeof(double)},
+      {p->dev.slot_ptr, p->slot_ptr.data(), p->slot_ptr.size() * sizeof(int32_t)},
+      {p->dev.slot_idx, p->slot_idx.data(), p->slot_idx.size() * sizeof(int32_t)},
+      {p->dev.mode_col, p->mode_col.data(), p->mode_col.size() * sizeof(int32_t)},
+      {p->dev.mode_N, p->mode_N.data(), p->mode_N.size() * sizeof(int32_t)},
+  };
+  for (const Part& part : parts) {
+    if (part.bytes == 0) continue;
+    cudaError_t e = async ? cudaMemcpyAsync(part.dst, part.src, part.bytes, cudaMemcpyHostToDevice, stream)
+                          : cudaMemcpy(part.dst, part.src, part.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "copy of plan tables");
+  }
+  return ZP_OK;
+}
+
+zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out) {
+  if (!out) return set_error(ZP_ERR_INVALID_ARG, "plan output pointer is NULL");
+  std::unique_ptr<zp_plan> p(new zp_plan());
+  zp_status st = build_plan_host(n, m, n_modes, p.get());
+  if (st != ZP_OK) return st;
+  size_t off[6];
+  const size_t total = plan_device_layout(p.get(), off);
+  cudaError_t e = cudaMalloc(&p->dev_block, total);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(plan tables)");
+  p->device_bytes = total;
+  st = plan_upload(p.get(), p->dev_block, nullptr, false);
+  if (st != ZP_OK) {
+    cudaFree(p->dev_block);
+    return st;
   }
   *out = p.release();
   return ZP_OK;

@@ -23,10 +23,23 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
                               double* grad_r, double* grad_theta, cudaStream_t stream);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
+// Caller-provided scratch for the split path: `b` holds the split coefficient tiles,
+// `a` the split basis of as many point tiles as fit (at least one).
+struct SplitScratch {
+  uint8_t* a = nullptr;
+  size_t a_bytes = 0;
+  uint8_t* b = nullptr;
+  size_t b_bytes = 0;
+};
+// Bytes of coefficient tiles (*b_bytes) and of one point tile of split basis (*tile_bytes);
+// returns their sum (the least scratch the split path can run in).
+size_t split_scratch_bytes(zp_precision prec, int64_t n_modes, int64_t n_sets, size_t* b_bytes, size_t* tile_bytes);
+
 // phase_ms: NULL, or [3] receiving the summed CUDA-event times of the coefficient split,
 // the basis split and the GEMM launches (the call then synchronises the stream).
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                             const double* coeffs, int64_t S, zp_precision prec, float* out,
-                            cudaStream_t stream, float* phase_ms = nullptr);
+                            cudaStream_t stream, float* phase_ms = nullptr,
+                            const SplitScratch* preset = nullptr);
 
 }  // namespace zp
