@@ -60,8 +60,10 @@ typedef enum {
   ZP_PREC_FP64 = 0,   /* float64 throughout; outputs float64 */
   ZP_PREC_BF16X3 = 1, /* float64 basis, contraction on tensor cores as hi*hi + hi*lo + lo*hi
                          with bfloat16 halves and float32 accumulation; outputs float32 */
-  ZP_PREC_TF32 = 2    /* float64 basis rounded to TF32, tensor-core contraction with float32
+  ZP_PREC_TF32 = 2,   /* float64 basis rounded to TF32, tensor-core contraction with float32
                          accumulation; outputs float32 */
+  ZP_PREC_FP32 = 3    /* float64 basis rounded to float32, float32 contraction on the CUDA
+                         cores; outputs float32 (batched forward only) */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */
@@ -174,6 +176,61 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  int64_t n_points, const double* coeffs, int64_t n_sets,
                                  const double* grad_out, double* grad_coeffs, double* grad_r,
                                  double* grad_theta, void* stream);
+
+/*
+ * Batched series over many instances of uneven size (different mode lists, point counts)
+ * in one persistent launch per pass; the launches are stream-ordered and contain no host
+ * synchronisation, so zp_batch_forward / zp_batch_adjoint can be captured in a CUDA graph.
+ * The paper evaluates one mode set at a time (Sec. 3, Algorithm 1); this is the throughput
+ * form of the same per-column recursion for many independent problems.
+ *
+ * zp_instance: HOST mode list n[], m[] (n_modes entries); DEVICE arrays r, theta
+ * [n_points], coeffs [n_modes][n_sets] (float64); out [n_points][n_sets] (float64 for
+ * ZP_PREC_FP64, float32 for ZP_PREC_FP32); for the adjoint grad_out [n_points][n_sets]
+ * (float64) and optional outputs grad_coeffs [n_modes][n_sets], grad_r, grad_theta
+ * [n_points] (float64, NULL = not computed).  All sets share one n_sets.
+ * zp_batch_create validates every instance, builds one plan per distinct mode list, copies
+ * tables and descriptors to the device (synchronously) and keeps the device pointers: the
+ * arrays must stay allocated, and may change contents, between calls.
+ */
+typedef struct {
+  const int32_t* n;
+  const int32_t* m;
+  int64_t n_modes;
+  const double* r;
+  const double* theta;
+  int64_t n_points;
+  const double* coeffs;
+  void* out;
+  const double* grad_out;
+  double* grad_coeffs;
+  double* grad_r;
+  double* grad_theta;
+} zp_instance;
+
+typedef struct zp_batch zp_batch;
+
+ZP_API zp_status zp_batch_create(const zp_instance* instances, int64_t n_instances, int64_t n_sets,
+                                 zp_batch** out);
+ZP_API zp_status zp_batch_destroy(zp_batch* batch);
+/* F for every instance: one launch (plus a float32 copy of C for ZP_PREC_FP32). */
+ZP_API zp_status zp_batch_forward(zp_batch* batch, zp_precision prec, void* stream);
+/* The same float64 forward as one launch per instance (comparison path). */
+ZP_API zp_status zp_batch_forward_per_instance(zp_batch* batch, zp_precision prec, void* stream);
+/* grad_r, grad_theta (one launch) and grad_coeffs (one launch), float64, deterministic. */
+ZP_API zp_status zp_batch_adjoint(zp_batch* batch, void* stream);
+/* Launch configuration: point-tile size (threads per CTA of the point kernel, multiple of 32),
+ * persistent CTAs per SM, points per thread (1, 2, 4) and threads per CTA of the grad_coeffs
+ * kernel.  cfg[4] receives the current values. */
+ZP_API zp_status zp_batch_set_config(zp_batch* batch, int32_t tile_points, int32_t ctas_per_sm,
+                                     int32_t col_ppt, int32_t col_threads);
+ZP_API zp_status zp_batch_get_config(const zp_batch* batch, int32_t* cfg);
+/* Autotuner: times each candidate configuration on this batch (which = 0: forward with
+ * `prec`, 1: adjoint), one warm-up then `reps` timed runs with CUDA events on `stream`, and
+ * keeps the fastest; cfg[4] (may be NULL) and *best_ms receive the result.  Synchronises
+ * `stream`; outputs hold the result of the last candidate run. */
+ZP_API zp_status zp_batch_tune(zp_batch* batch, int32_t which, zp_precision prec, int32_t reps,
+                               void* stream, int32_t* cfg, float* best_ms);
 
 /*
  * Allocation-free series evaluation.  (The paper has no counterpart: this is a library

@@ -3,6 +3,6 @@
 The compute lives in a C-ABI CUDA library (include/zernike_gb300.h, sources in csrc/);
 this package is its build step and a thin torch-facing binding.
 """
-from .api import (PREC, Plan, ZernikeSeries, basis, radial, radial_per_mode, series_adjoint,  # noqa: F401
+from .api import (PREC, Batch, Plan, ZernikeSeries, basis, radial, radial_per_mode, series_adjoint,  # noqa: F401
                   series_eval, zernike_series)
 from ._lib import ZernikeError, library_path, load  # noqa: F401

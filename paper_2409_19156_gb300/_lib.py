@@ -39,6 +39,16 @@ SIGNATURES = {
     "zp_series_adjoint": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
                                          ctypes.c_int64, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_device_wait_status": (ctypes.c_int, [ctypes.c_int32]),
+    "zp_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
+    "zp_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "zp_batch_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_dp]),
+    "zp_batch_forward_per_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_dp]),
+    "zp_batch_adjoint": (ctypes.c_int, [ctypes.c_void_p, c_dp]),
+    "zp_batch_set_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32]),
+    "zp_batch_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "zp_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, c_dp,
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "zp_series_eval_static": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
                                              ctypes.c_int64, ctypes.c_int, c_dp, c_dp]),
     "zp_series_eval_timed": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
@@ -104,6 +114,15 @@ def modes_i32(x) -> np.ndarray:
 
 def i32_ptr(a: np.ndarray):
     return a.ctypes.data_as(c_i32p)
+
+
+class ZpInstance(ctypes.Structure):
+    """Mirror of zp_instance (include/zernike_gb300.h)."""
+
+    _fields_ = [("n", c_i32p), ("m", c_i32p), ("n_modes", ctypes.c_int64), ("r", ctypes.c_void_p),
+                ("theta", ctypes.c_void_p), ("n_points", ctypes.c_int64), ("coeffs", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("grad_out", ctypes.c_void_p), ("grad_coeffs", ctypes.c_void_p),
+                ("grad_r", ctypes.c_void_p), ("grad_theta", ctypes.c_void_p)]
 
 
 def ptr(t) -> int | None:

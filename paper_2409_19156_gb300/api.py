@@ -183,3 +183,87 @@ class ZernikeSeries(torch.autograd.Function):
 def zernike_series(r, theta, coeffs, plan: Plan) -> torch.Tensor:
     """Differentiable float64 series F[p, s] = sum_j Z_j(r_p, theta_p) coeffs[j, s]."""
     return ZernikeSeries.apply(r, theta, coeffs, plan)
+
+
+class Batch:
+    """Many independent series (uneven mode lists and point counts) evaluated together:
+    forward in one persistent launch, adjoint in two (capturable in a CUDA graph).
+
+    instances: list of dicts with keys n, m (host sequences), r, theta (CUDA float64 [P]),
+    coeffs (CUDA float64 [J][S]); optional out, grad_out, grad_coeffs, grad_r, grad_theta
+    tensors (allocated here when missing).  All instances share n_sets = S."""
+
+    def __init__(self, instances, n_sets: int, out_dtype=torch.float64, with_adjoint: bool = True):
+        self._keep = []
+        arr = (_lib.ZpInstance * len(instances))()
+        self.instances = []
+        for i, d in enumerate(instances):
+            n = _lib.modes_i32(d["n"])
+            m = _lib.modes_i32(d["m"])
+            r = _dev_f64(d["r"], "r")
+            th = _dev_f64(d["theta"], "theta")
+            C = _dev_f64(d["coeffs"], "coeffs")
+            P, dev = r.numel(), r.device
+            out = d.get("out")
+            if out is None:
+                out = torch.empty((P, n_sets), dtype=out_dtype, device=dev)
+            rec = {"n": n, "m": m, "r": r, "theta": th, "coeffs": C, "out": out}
+            if with_adjoint:
+                rec["grad_out"] = d.get("grad_out") if d.get("grad_out") is not None else \
+                    torch.zeros((P, n_sets), dtype=torch.float64, device=dev)
+                for key, shape in (("grad_coeffs", (len(n), n_sets)), ("grad_r", (P,)), ("grad_theta", (P,))):
+                    rec[key] = d.get(key) if d.get(key) is not None else \
+                        torch.empty(shape, dtype=torch.float64, device=dev)
+            self.instances.append(rec)
+            a = arr[i]
+            a.n, a.m, a.n_modes = _lib.i32_ptr(n), _lib.i32_ptr(m), len(n)
+            a.r, a.theta, a.n_points = r.data_ptr(), th.data_ptr(), P
+            a.coeffs, a.out = C.data_ptr(), out.data_ptr()
+            if with_adjoint:
+                a.grad_out = rec["grad_out"].data_ptr()
+                a.grad_coeffs = rec["grad_coeffs"].data_ptr()
+                a.grad_r = rec["grad_r"].data_ptr()
+                a.grad_theta = rec["grad_theta"].data_ptr()
+        self.out_dtype = out_dtype
+        handle = ctypes.c_void_p()
+        _lib.call("zp_batch_create", ctypes.cast(arr, ctypes.c_void_p), len(instances), n_sets, ctypes.byref(handle))
+        self.handle = handle
+        self._arr = arr
+
+    def forward(self, prec: str = "fp64"):
+        code = {"fp64": 0, "fp32": 3}[prec]
+        _lib.call("zp_batch_forward", self.handle, code, _stream(torch.device("cuda", torch.cuda.current_device())))
+
+    def forward_per_instance(self):
+        _lib.call("zp_batch_forward_per_instance", self.handle, 0,
+                  _stream(torch.device("cuda", torch.cuda.current_device())))
+
+    def adjoint(self):
+        _lib.call("zp_batch_adjoint", self.handle, _stream(torch.device("cuda", torch.cuda.current_device())))
+
+    def set_config(self, tile_points=128, ctas_per_sm=4, col_ppt=2, col_threads=128):
+        _lib.call("zp_batch_set_config", self.handle, tile_points, ctas_per_sm, col_ppt, col_threads)
+
+    def config(self) -> tuple:
+        cfg = (ctypes.c_int32 * 4)()
+        _lib.call("zp_batch_get_config", self.handle, cfg)
+        return tuple(cfg)
+
+    def tune(self, which: str = "forward", prec: str = "fp64", reps: int = 2):
+        cfg = (ctypes.c_int32 * 4)()
+        best = ctypes.c_float()
+        code = {"fp64": 0, "fp32": 3}[prec]
+        _lib.call("zp_batch_tune", self.handle, 0 if which == "forward" else 1, code, reps,
+                  _stream(torch.device("cuda", torch.cuda.current_device())), cfg, ctypes.byref(best))
+        return tuple(cfg), best.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.call("zp_batch_destroy", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -32,7 +32,10 @@ zp_status set_error(zp_status s, const std::string& msg) {
 
 zp_status cuda_error(cudaError_t e, const char* what) {
   std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-  return set_error(e == cudaErrorMemoryAllocation ? ZP_ERR_NO_MEMORY : ZP_ERR_CUDA, msg);
+  if (e == cudaErrorMemoryAllocation) return set_error(ZP_ERR_NO_MEMORY, msg);
+  // A launch configuration the GPU cannot hold (registers, shared memory): not a device fault.
+  if (e == cudaErrorLaunchOutOfResources || e == cudaErrorInvalidConfiguration) return set_error(ZP_ERR_UNSUPPORTED, msg);
+  return set_error(ZP_ERR_CUDA, msg);
 }
 
 void clear_error() { g_last_error.clear(); }
