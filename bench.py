@@ -284,7 +284,7 @@ def run_ours(args) -> None:
         del out
         torch.cuda.empty_cache()
         extras = {"series": measure_series(dev, peaks), "adjoint": measure_adjoint(dev),
-                  "basis": measure_basis_latency(dev)}
+                  "basis": measure_basis_latency(dev), "batched": measure_batched(dev)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -442,6 +442,61 @@ def measure_basis_latency(dev, steps: int = 200) -> dict:
     vals = len(ns) * len(r) * 4
     return {"workload": "basis_n20", "modes": len(ns), "points": len(r), "us_per_call": ms_call * 1e3,
             "values_per_s": vals / (ms_call * 1e-3)}
+
+
+def measure_batched(dev, steps: int = 3) -> dict:
+    """batched_512: 512 instances, n_max ~ U{8..64} (full Z sets), points log-uniform in
+    [1e3, 2e5], 16 coefficient sets.  Persistent forward (float64 and float32 contraction) as a
+    CUDA-graph replay after autotuning, the same float64 forward as one launch per instance,
+    and the float64 adjoint (grad_r, grad_theta, grad_C)."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import inputs
+
+    cfg = inputs.WORKLOADS["batched_512"]
+    raw = inputs.batched_instances(cfg["n_instances"], cfg["n_sets"], cfg["seed"])
+    S = cfg["n_sets"]
+    inst = []
+    gen = torch.Generator(dev).manual_seed(5)
+    for x in raw:
+        inst.append({"n": x.n, "m": x.m, "r": torch.as_tensor(x.r, device=dev),
+                     "theta": torch.as_tensor(x.theta, device=dev), "coeffs": torch.as_tensor(x.coeffs, device=dev),
+                     "grad_out": torch.randn((len(x.r), S), dtype=torch.float64, device=dev, generator=gen)})
+    points = sum(len(x.r) for x in raw)
+    basis_values = sum(len(x.r) * len(x.n) for x in raw)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "batched_512", "instances": len(raw), "points": points, "sets": S,
+           "basis_values": basis_values}
+    b = zp.Batch(inst, S)
+    cfg64, _ = b.tune("forward", "fp64", reps=1)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            b.forward("fp64")
+    stream.wait_stream(side)
+    g.replay()
+    t_graph = _events_ms(stream, g.replay, steps)
+    t_per = _events_ms(stream, b.forward_per_instance, 1)
+    cfg_adj, _ = b.tune("adjoint", reps=1)
+    b.adjoint()
+    t_adj = _events_ms(stream, b.adjoint, 1)
+    out["fp64_forward_graph_ms"] = t_graph
+    out["fp64_forward_per_instance_launches_ms"] = t_per
+    out["fp64_adjoint_ms"] = t_adj
+    out["tuned_forward_cfg"] = list(cfg64)
+    out["tuned_adjoint_cfg"] = list(cfg_adj)
+    out["fp64_forward_basis_values_per_s"] = basis_values / (t_graph * 1e-3)
+    b.close()
+    b32 = zp.Batch(inst, S, out_dtype=torch.float32, with_adjoint=False)
+    cfg32, _ = b32.tune("forward", "fp32", reps=1)
+    b32.forward("fp32")
+    out["fp32_forward_ms"] = _events_ms(stream, lambda: b32.forward("fp32"), steps)
+    out["tuned_fp32_cfg"] = list(cfg32)
+    b32.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
