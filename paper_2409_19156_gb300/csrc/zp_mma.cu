@@ -4,7 +4,8 @@
 // contracted as BF16x3 (Z = Zh + Zl, C = Ch + Cl in bfloat16, F ~ Zh Ch + Zh Cl + Zl Ch with
 // float32 accumulation) or TF32 (one product of TF32-rounded operands).
 //
-// Two kernels per slab of point tiles:
+// Two kernels per slab of point tiles (the basis of slab i+1 runs on a second stream while the
+// GEMM of slab i runs, sharing the SMs: one uses the float64 pipe, the other the tensor pipe):
 //  (A) split_basis_kernel: one thread per point walks every |m| column (the recursion of
 //      Sec. 2 in float64, Algorithm 1's order), rotates cos/sin(m theta) by angle addition
 //      from column to column, splits each Z into bfloat16 hi/lo (or TF32) and writes it into
@@ -23,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -103,11 +105,35 @@ struct BasisArgs {
   uint8_t* A;       // slab scratch: [tiles][KC][A_CHUNK]
 };
 
+// Register packing of consecutive K values into one 16-byte unit of the swizzled layout:
+// each push shifts the 128-bit chain w[3]:w[2]:w[1]:w[0] right by one element and inserts
+// the new element at the top, so after a full unit w[0] holds the first element.
+struct Pack16 {
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  __device__ __forceinline__ void push16(uint32_t v) {
+    w[0] = (w[0] >> 16) | (w[1] << 16);
+    w[1] = (w[1] >> 16) | (w[2] << 16);
+    w[2] = (w[2] >> 16) | (w[3] << 16);
+    w[3] = (w[3] >> 16) | (v << 16);
+  }
+  __device__ __forceinline__ void push32(uint32_t v) {
+    w[0] = w[1];
+    w[1] = w[2];
+    w[2] = w[3];
+    w[3] = v;
+  }
+  __device__ __forceinline__ void store(uint8_t* dst) const {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+// No shared memory: each thread packs 8 bf16 (or 4 tf32) consecutive K values of its row in
+// registers and writes the 16-byte unit straight to its place in the swizzled chunk, so the
+// kernel can share SMs with the GEMM kernel of the previous slab.
 template <bool TF32>
 __global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a) {
   using C = Cfg<TF32>;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = align1024(smem_raw);
+  constexpr int UNIT = TF32 ? 4 : 8;  // K values per 16-byte unit
   const uint32_t t = threadIdx.x;
   const int64_t p = (a.mt_base + blockIdx.x) * BM + t;
   const bool valid = p < a.P;
@@ -119,19 +145,29 @@ __global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a)
   double cm = 1.0, sm = 0.0, pm = 1.0;
   int m_prev = 0;
   uint8_t* gA = a.A + (size_t)blockIdx.x * a.KC * C::A_CHUNK;
-  int k = 0, buf = 0, kc = 0;
+  int k = 0;
+  Pack16 hi, lo;
 
-  auto flush = [&]() {
-    ptx::fence_proxy_async_smem();
-    __syncthreads();
-    if (t == 0) {
-      ptx::bulk_s2g(gA + (size_t)kc * C::A_CHUNK, smem + buf * C::A_CHUNK, C::A_CHUNK);
-      ptx::bulk_commit();
-      ptx::bulk_wait_read<1>();
+  auto push = [&](float z) {
+    if constexpr (TF32) {
+      hi.push32(__float_as_uint(to_tf32(z)));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(z);
+      const __nv_bfloat16 l = __float2bfloat16_rn(z - __bfloat162float(h));
+      hi.push16((uint32_t)__bfloat16_as_ushort(h));
+      lo.push16((uint32_t)__bfloat16_as_ushort(l));
     }
-    __syncthreads();
-    buf ^= 1;
-    ++kc;
+    if (++k % UNIT == 0) {
+      const int k0 = k - UNIT;
+      uint8_t* chunk = gA + (size_t)(k0 / C::BK) * C::A_CHUNK;
+      if constexpr (TF32) {
+        hi.store(chunk + ptx::sw128_offset_b32(t, (uint32_t)(k0 % C::BK)));
+      } else {
+        const uint32_t off = ptx::sw128_offset_b16(t, (uint32_t)(k0 % C::BK));
+        hi.store(chunk + off);
+        lo.store(chunk + kAPart + off);
+      }
+    }
   };
 
   for (int c = 0; c < a.n_cols; ++c) {
@@ -171,20 +207,11 @@ __global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a)
       const float Rf = (float)(row[3] * q);
       for (int s = sb; s < se; ++s) {
         const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
-        const float z = Rf * ((code >> 31) ? sf : cf);
-        put_elem<TF32>(smem + buf * C::A_CHUNK, t, (uint32_t)(k % C::BK), z);
-        if (++k % C::BK == 0) flush();
+        push(Rf * ((code >> 31) ? sf : cf));
       }
     }
   }
-  if (k % C::BK != 0) {
-    while (k % C::BK != 0) {
-      put_elem<TF32>(smem + buf * C::A_CHUNK, t, (uint32_t)(k % C::BK), 0.0f);
-      ++k;
-    }
-    flush();
-  }
-  if (t == 0) ptx::bulk_wait<0>();
+  while (k % C::BK != 0) push(0.0f);
 }
 
 struct CoeffArgs {
@@ -406,24 +433,59 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
 }
 
+// A non-blocking library stream per device for the basis kernels of the slab pipeline.
+zp_status side_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> per_device;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)per_device.size() <= dev) per_device.resize(dev + 1, nullptr);
+  if (!per_device[dev]) {
+    e = cudaStreamCreateWithFlags(&per_device[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreateWithFlags");
+  }
+  *out = per_device[dev];
+  return ZP_OK;
+}
+
+// Timing-free events owned by one call (destroyed at scope exit; pending records complete
+// normally).
+struct EventSet {
+  std::vector<cudaEvent_t> ev;
+  ~EventSet() {
+    for (cudaEvent_t x : ev) cudaEventDestroy(x);
+  }
+  zp_status create(int n) {
+    for (int k = 0; k < n; ++k) {
+      cudaEvent_t x;
+      cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_error(e, "cudaEventCreateWithFlags");
+      ev.push_back(x);
+    }
+    return ZP_OK;
+  }
+};
+
 // Optional per-phase timing: CUDA events recorded on the launching stream around every
 // launch, summed per phase after the stream is synchronised.
 struct PhaseTimer {
   float* ms = nullptr;  // [3]: coefficient split, basis split, GEMM (NULL: no timing)
   cudaStream_t stream = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
-  void begin(int phase, cudaEvent_t* start) {
+  void begin(int phase, cudaEvent_t* start, cudaStream_t on) {
     *start = nullptr;
     if (!ms) return;
     cudaEventCreate(start);
-    cudaEventRecord(*start, stream);
+    cudaEventRecord(*start, on);
     (void)phase;
   }
-  void end(int phase, cudaEvent_t start) {
+  void end(int phase, cudaEvent_t start, cudaStream_t on) {
     if (!ms) return;
     cudaEvent_t stop;
     cudaEventCreate(&stop);
-    cudaEventRecord(stop, stream);
+    cudaEventRecord(stop, on);
     ev[phase].emplace_back(start, stop);
   }
   zp_status finish() {
@@ -465,55 +527,82 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   uint8_t* A = nullptr;
   uint8_t* B = nullptr;
   int64_t slab = 0;
+  int nbuf = 1;  // slab buffers: 2 when the basis of slab i+1 overlaps the GEMM of slab i
   if (preset) {
-    // Caller-provided scratch: the B tiles first, then as many point tiles as fit.
+    // Caller-provided scratch: the B tiles first, then as many point tiles as fit (one
+    // buffer, slabs run back to back on the caller's stream).
     if (preset->b_bytes < b_bytes || preset->a_bytes < tile_bytes)
       return set_error(ZP_ERR_INVALID_ARG, "split scratch too small for this problem");
     A = preset->a;
     B = preset->b;
     slab = std::min<int64_t>(MT, (int64_t)(preset->a_bytes / tile_bytes));
   } else {
-    // Slab of point tiles whose split basis fits a 512 MB scratch buffer.
-    slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
+    // About a dozen slabs (at most 256 MB each) so that the float64 basis of slab i+1,
+    // computed on a second stream, runs on the same SMs as the tensor-core GEMM of slab i.
+    const int64_t cap = std::max<int64_t>(1, (int64_t)((256ull << 20) / tile_bytes));
+    slab = std::max<int64_t>(1, std::min<int64_t>(cap, (MT + 11) / 12));
+    if (MT < 48) slab = std::min<int64_t>(MT, cap);  // small problems: no pipeline
+    nbuf = (MT > slab) ? 2 : 1;
     ZP_TRY(bbuf.alloc(b_bytes, stream));
-    ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
+    ZP_TRY(abuf.alloc((size_t)nbuf * slab * tile_bytes, stream));
     A = (uint8_t*)abuf.ptr;
     B = (uint8_t*)bbuf.ptr;
   }
 
-  const uint32_t basis_smem = 2 * C::A_CHUNK + 1024;
   const uint32_t coeff_smem = C::B_CHUNK + 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(split_basis_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, basis_smem)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
+  if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
           cudaSuccess ||
       (e = cudaFuncSetAttribute(split_gemm_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
           cudaSuccess)
     return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
-  timer.begin(0, &ev0);
+  timer.begin(0, &ev0, stream);
   split_coeff_kernel<TF32><<<(unsigned)(NT * KC), kCoeffThreads, coeff_smem, stream>>>(ca);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_coeff_kernel launch");
-  timer.end(0, ev0);
+  timer.end(0, ev0, stream);
 
-  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
+  // Basis kernels go to `side` (a library stream joined to the caller's stream by events)
+  // when two slab buffers are in use; otherwise everything runs on the caller's stream.
+  cudaStream_t side = stream;
+  EventSet evs;
+  if (nbuf == 2) {
+    ZP_TRY(side_stream(&side));
+    ZP_TRY(evs.create(5));
+    // evs[0]: fork; evs[1+b]: basis of buffer b written; evs[3+b]: GEMM done reading buffer b.
+    if ((e = cudaEventRecord(evs.ev[0], stream)) != cudaSuccess || (e = cudaStreamWaitEvent(side, evs.ev[0], 0)) != cudaSuccess)
+      return cuda_error(e, "fork to the basis stream");
+  }
+  int64_t i = 0;
+  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab, ++i) {
     const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
+    const int buf = (int)(i % nbuf);
+    uint8_t* Ab = A + (size_t)buf * slab * tile_bytes;
+    if (nbuf == 2 && i >= 2 && (e = cudaStreamWaitEvent(side, evs.ev[3 + buf], 0)) != cudaSuccess)
+      return cuda_error(e, "cudaStreamWaitEvent");
     BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
-                 r, theta, P, mt0, KC, A};
-    timer.begin(1, &ev0);
-    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, basis_smem, stream>>>(ba);
+                 r, theta, P, mt0, KC, Ab};
+    timer.begin(1, &ev0, side);
+    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, 0, side>>>(ba);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
-    timer.end(1, ev0);
-    GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
+    timer.end(1, ev0, side);
+    if (nbuf == 2) {
+      if ((e = cudaEventRecord(evs.ev[1 + buf], side)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(stream, evs.ev[1 + buf], 0)) != cudaSuccess)
+        return cuda_error(e, "basis -> GEMM dependency");
+    }
+    GemmArgs ga{Ab, B, out, P, S, mt0, tiles, NT, KC};
     const int64_t total = tiles * NT;
     const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
-    timer.begin(2, &ev0);
+    timer.begin(2, &ev0, stream);
     split_gemm_kernel<TF32><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
-    timer.end(2, ev0);
+    timer.end(2, ev0, stream);
+    if (nbuf == 2 && (e = cudaEventRecord(evs.ev[3 + buf], stream)) != cudaSuccess)
+      return cuda_error(e, "cudaEventRecord");
   }
+  // The caller's stream already waited for the last basis launch, so `side` is joined.
   return timer.finish();
 }
 
