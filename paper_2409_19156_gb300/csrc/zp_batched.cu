@@ -790,16 +790,14 @@ zp_status zp_batch_tune(zp_batch* b, int32_t which, zp_precision prec, int32_t r
   int32_t best_cfg[4] = {b->tp, b->ctas_per_sm, b->col_ppt, b->col_threads};
   const int tps[] = {64, 128, 256};
   const int ctas[] = {2, 4, 8};
-  const int ppts[] = {1, 2, 4};
-  const int cths[] = {64, 128, 256};
   std::vector<std::array<int, 4>> cands;
   if (which == 0) {
     for (int tp : tps)
       for (int c : ctas) cands.push_back({tp, c, b->col_ppt, b->col_threads});
   } else {
-    for (int tp : tps)
-      for (int pp : ppts)
-        for (int ct : cths) cands.push_back({tp, b->ctas_per_sm, pp, ct});
+    for (int tp : {128, 256})
+      for (int pp : {2, 4})
+        for (int ct : {64, 128}) cands.push_back({tp, b->ctas_per_sm, pp, ct});
   }
   zp_status result = ZP_OK;
   for (auto& cnd : cands) {

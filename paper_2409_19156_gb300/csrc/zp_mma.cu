@@ -4,13 +4,12 @@
 // contracted as BF16x3 (Z = Zh + Zl, C = Ch + Cl in bfloat16, F ~ Zh Ch + Zh Cl + Zl Ch with
 // float32 accumulation) or TF32 (one product of TF32-rounded operands).
 //
-// Two kernels per slab of point tiles (the basis of slab i+1 runs on a second stream while the
-// GEMM of slab i runs, sharing the SMs: one uses the float64 pipe, the other the tensor pipe):
+// Two kernels per slab of point tiles, back to back on the caller's stream:
 //  (A) split_basis_kernel: one thread per point walks every |m| column (the recursion of
 //      Sec. 2 in float64, Algorithm 1's order), rotates cos/sin(m theta) by angle addition
-//      from column to column, splits each Z into bfloat16 hi/lo (or TF32) and writes it into
-//      a shared-memory K-chunk already in the tensor core's 128-byte-swizzled K-major layout;
-//      complete chunks leave with bulk async copies (cp.async.bulk) into a scratch buffer.
+//      from column to column, splits each Z into bfloat16 hi/lo (or TF32), packs 8 (4)
+//      consecutive K values in registers and writes each 16-byte unit straight to its place
+//      in the tensor core's 128-byte-swizzled K-major layout in a scratch buffer.
 //      The K order of the contraction is the plan's slot order (column by column), so a
 //      thread's outputs are consecutive in K; the coefficient rows are permuted to match.
 //  (B) split_gemm_kernel: persistent, warp-specialised tcgen05 GEMM.  Warp 0 streams A
@@ -24,7 +23,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -127,15 +125,24 @@ struct Pack16 {
   }
 };
 
-// No shared memory: each thread packs 8 bf16 (or 4 tf32) consecutive K values of its row in
-// registers and writes the 16-byte unit straight to its place in the swizzled chunk, so the
-// kernel can share SMs with the GEMM kernel of the previous slab.
+// No shared memory or barriers: each thread packs 8 bf16 (or 4 tf32) consecutive K values of
+// its row in registers and writes the 16-byte unit straight to its place in the swizzled
+// chunk (measured faster than staging whole chunks in shared memory for bulk stores).
 template <bool TF32>
-__global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a) {
+__device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t tile);
+
+// One CTA per point tile of the slab (grid-stride if the grid is smaller).
+template <bool TF32>
+__global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a, int64_t tiles) {
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) split_basis_tile<TF32>(a, tile);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t tile) {
   using C = Cfg<TF32>;
   constexpr int UNIT = TF32 ? 4 : 8;  // K values per 16-byte unit
   const uint32_t t = threadIdx.x;
-  const int64_t p = (a.mt_base + blockIdx.x) * BM + t;
+  const int64_t p = (a.mt_base + tile) * BM + t;
   const bool valid = p < a.P;
   const double rho = valid ? a.r[p] : 0.0;
   const double th = valid ? a.theta[p] : 0.0;
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a)
   sincos(th, &s1, &c1);
   double cm = 1.0, sm = 0.0, pm = 1.0;
   int m_prev = 0;
-  uint8_t* gA = a.A + (size_t)blockIdx.x * a.KC * C::A_CHUNK;
+  uint8_t* gA = a.A + (size_t)tile * a.KC * C::A_CHUNK;
   int k = 0;
   Pack16 hi, lo;
 
@@ -433,41 +440,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
 }
 
-// A non-blocking library stream per device for the basis kernels of the slab pipeline.
-zp_status side_stream(cudaStream_t* out) {
-  static std::mutex mu;
-  static std::vector<cudaStream_t> per_device;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lock(mu);
-  if ((int)per_device.size() <= dev) per_device.resize(dev + 1, nullptr);
-  if (!per_device[dev]) {
-    e = cudaStreamCreateWithFlags(&per_device[dev], cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreateWithFlags");
-  }
-  *out = per_device[dev];
-  return ZP_OK;
-}
-
-// Timing-free events owned by one call (destroyed at scope exit; pending records complete
-// normally).
-struct EventSet {
-  std::vector<cudaEvent_t> ev;
-  ~EventSet() {
-    for (cudaEvent_t x : ev) cudaEventDestroy(x);
-  }
-  zp_status create(int n) {
-    for (int k = 0; k < n; ++k) {
-      cudaEvent_t x;
-      cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-      if (e != cudaSuccess) return cuda_error(e, "cudaEventCreateWithFlags");
-      ev.push_back(x);
-    }
-    return ZP_OK;
-  }
-};
-
 // Optional per-phase timing: CUDA events recorded on the launching stream around every
 // launch, summed per phase after the stream is synchronised.
 struct PhaseTimer {
@@ -527,24 +499,20 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   uint8_t* A = nullptr;
   uint8_t* B = nullptr;
   int64_t slab = 0;
-  int nbuf = 1;  // slab buffers: 2 when the basis of slab i+1 overlaps the GEMM of slab i
   if (preset) {
-    // Caller-provided scratch: the B tiles first, then as many point tiles as fit (one
-    // buffer, slabs run back to back on the caller's stream).
+    // Caller-provided scratch: the B tiles first, then as many point tiles as fit.
     if (preset->b_bytes < b_bytes || preset->a_bytes < tile_bytes)
       return set_error(ZP_ERR_INVALID_ARG, "split scratch too small for this problem");
     A = preset->a;
     B = preset->b;
     slab = std::min<int64_t>(MT, (int64_t)(preset->a_bytes / tile_bytes));
   } else {
-    // About a dozen slabs (at most 256 MB each) so that the float64 basis of slab i+1,
-    // computed on a second stream, runs on the same SMs as the tensor-core GEMM of slab i.
-    const int64_t cap = std::max<int64_t>(1, (int64_t)((256ull << 20) / tile_bytes));
-    slab = std::max<int64_t>(1, std::min<int64_t>(cap, (MT + 11) / 12));
-    if (MT < 48) slab = std::min<int64_t>(MT, cap);  // small problems: no pipeline
-    nbuf = (MT > slab) ? 2 : 1;
+    // Slabs of at most 512 MB of split basis, run back to back on the caller's stream.  (Running
+    // the float64 basis of slab i+1 on a second stream beside the GEMM of slab i was measured
+    // slower on GB300: the GEMM is sensitive to the basis kernel's extra L2 write traffic.)
+    slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
     ZP_TRY(bbuf.alloc(b_bytes, stream));
-    ZP_TRY(abuf.alloc((size_t)nbuf * slab * tile_bytes, stream));
+    ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
     A = (uint8_t*)abuf.ptr;
     B = (uint8_t*)bbuf.ptr;
   }
@@ -563,46 +531,22 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_coeff_kernel launch");
   timer.end(0, ev0, stream);
 
-  // Basis kernels go to `side` (a library stream joined to the caller's stream by events)
-  // when two slab buffers are in use; otherwise everything runs on the caller's stream.
-  cudaStream_t side = stream;
-  EventSet evs;
-  if (nbuf == 2) {
-    ZP_TRY(side_stream(&side));
-    ZP_TRY(evs.create(5));
-    // evs[0]: fork; evs[1+b]: basis of buffer b written; evs[3+b]: GEMM done reading buffer b.
-    if ((e = cudaEventRecord(evs.ev[0], stream)) != cudaSuccess || (e = cudaStreamWaitEvent(side, evs.ev[0], 0)) != cudaSuccess)
-      return cuda_error(e, "fork to the basis stream");
-  }
-  int64_t i = 0;
-  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab, ++i) {
+  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
     const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
-    const int buf = (int)(i % nbuf);
-    uint8_t* Ab = A + (size_t)buf * slab * tile_bytes;
-    if (nbuf == 2 && i >= 2 && (e = cudaStreamWaitEvent(side, evs.ev[3 + buf], 0)) != cudaSuccess)
-      return cuda_error(e, "cudaStreamWaitEvent");
     BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
-                 r, theta, P, mt0, KC, Ab};
-    timer.begin(1, &ev0, side);
-    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, 0, side>>>(ba);
+                 r, theta, P, mt0, KC, A};
+    timer.begin(1, &ev0, stream);
+    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, 0, stream>>>(ba, tiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
-    timer.end(1, ev0, side);
-    if (nbuf == 2) {
-      if ((e = cudaEventRecord(evs.ev[1 + buf], side)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(stream, evs.ev[1 + buf], 0)) != cudaSuccess)
-        return cuda_error(e, "basis -> GEMM dependency");
-    }
-    GemmArgs ga{Ab, B, out, P, S, mt0, tiles, NT, KC};
+    timer.end(1, ev0, stream);
+    GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
     const int64_t total = tiles * NT;
     const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
     timer.begin(2, &ev0, stream);
     split_gemm_kernel<TF32><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
     timer.end(2, ev0, stream);
-    if (nbuf == 2 && (e = cudaEventRecord(evs.ev[3 + buf], stream)) != cudaSuccess)
-      return cuda_error(e, "cudaEventRecord");
   }
-  // The caller's stream already waited for the last basis launch, so `side` is joined.
   return timer.finish();
 }
 
