@@ -128,28 +128,58 @@ def _oracle_chunk(args):
     return len(ns) * len(rs) * 4 + 0 * len(tab)
 
 
-def time_oracle(n_points: int, cores: int | None = None) -> dict:
-    """The exact CPU oracle on a sample of the workload's points (all modes, k = 0..3), on a
-    spawn-started process pool over the host's cores."""
-    import multiprocessing as mp
+class OraclePool:
+    """A spawn-started process pool over the host cores that times the exact CPU oracle on a
+    sample of the workload's points (all modes, k = 0..3)."""
 
-    ns, ms, r = workload()
-    cores = cores or os.cpu_count() or 1
-    idx = [int(i) for i in (len(r) - 1) * (0.5 + 0.5 * __import__("numpy").cos(
-        math.pi * (__import__("numpy").arange(n_points) + 0.5) / n_points))]
-    pts = [float(r[i]) for i in idx]
-    chunks = [pts[i::cores] for i in range(cores)]
-    chunks = [c for c in chunks if c]
-    nsl, msl = [int(v) for v in ns], [int(v) for v in ms]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(len(chunks)) as pool:
-        pool.map(_oracle_chunk, [(nsl[:3], msl[:3], c[:1]) for c in chunks])  # start-up outside timing
+    def __init__(self, cores: int | None = None):
+        import multiprocessing as mp
+
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        ns, ms, self.r = workload()
+        self.ns, self.ms = [int(v) for v in ns], [int(v) for v in ms]
+        self.pool.map(_oracle_chunk, [(self.ns[:3], self.ms[:3], [0.5])] * self.cores)  # start-up
+
+    def time(self, n_points: int) -> dict:
+        import numpy as np
+
+        idx = ((len(self.r) - 1) * (0.5 + 0.5 * np.cos(np.pi * (np.arange(n_points) + 0.5) / n_points))).astype(int)
+        pts = [float(self.r[i]) for i in idx]
+        chunks = [c for c in (pts[i::self.cores] for i in range(self.cores)) if c]
         t0 = time.perf_counter()
-        vals = sum(pool.map(_oracle_chunk, [(nsl, msl, c) for c in chunks]))
+        vals = sum(self.pool.map(_oracle_chunk, [(self.ns, self.ms, c) for c in chunks]))
         dt = time.perf_counter() - t0
-    return {"value": vals / dt, "unit": UNIT, "cores": len(chunks), "kind": "oracle",
-            "sample": f"{len(pts)} of the 100000 points x all 2601 modes x k=0..3 "
-                      f"({vals} exact-rational values in {dt:.2f} s)"}
+        return {"value": vals / dt, "unit": UNIT, "cores": len(chunks), "kind": "oracle",
+                "sample": f"{len(pts)} of the 100000 points x all 2601 modes x k=0..3 "
+                          f"({vals} exact-rational values in {dt:.2f} s)"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def time_oracle(n_points: int, cores: int | None = None) -> dict:
+    pool = OraclePool(cores)
+    try:
+        return pool.time(n_points)
+    finally:
+        pool.close()
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's x (x itself when not distributed)."""
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank's units in one step over the slowest rank's step time."""
+    return world * units_per_rank_step / (ms_per_step * 1e-3)
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -209,14 +239,10 @@ def run_ours(args) -> None:
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(ms_steps)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms_steps), dist, dev)
     ms_per_step = total_ms / args.steps
     values_per_step = P * J * K
-    value = world * values_per_step / (ms_per_step * 1e-3)
+    value = aggregate_value(values_per_step, world, ms_per_step)
 
     # Roofline: the walk kernel is the only launch of a step (float64-issue bound).
     dp_ops = DP_OPS_PER_VALUE_TUPLE * P * J
@@ -264,10 +290,7 @@ def run_ours(args) -> None:
                 fn()
             e1.record(stream)
             barrier()
-            te = torch.tensor([e0.elapsed_time(e1) / args.e2e_steps], dtype=torch.float64, device=dev)
-            if dist is not None:
-                dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            return float(te.item())
+            return max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, dist, dev)
 
         t_copy = time_e2e(e2e_copy_step)
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
@@ -275,7 +298,7 @@ def run_ours(args) -> None:
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
         best, how = (t_copy, "device kernel + D2H copy") if t_copy <= t_mapped else \
             (t_mapped, "kernel writes pinned host memory directly")
-        e2e = {"value": world * values_per_step / (best * 1e-3), "unit": UNIT,
+        e2e = {"value": aggregate_value(values_per_step, world, best), "unit": UNIT,
                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": out_bytes, "ms_per_step": best, "how": how,
                "ms_per_step_copy": t_copy, "ms_per_step_mapped": t_mapped}
 
@@ -508,11 +531,13 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     n_pts = max(os.cpu_count() or 1, 16)
-    for _ in range(args.warmup):
-        time_oracle(n_pts)
-    vals = []
-    for _ in range(args.steps):
-        vals.append(time_oracle(n_pts))
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.time(n_pts)
+        vals = [pool.time(n_pts) for _ in range(args.steps)]
+    finally:
+        pool.close()
     value = statistics.mean(v["value"] for v in vals)
     ms_per_step = statistics.mean(1e3 * n_pts * 2601 * 4 / v["value"] for v in vals)
     cpu = dict(vals[0])
