@@ -211,7 +211,7 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
       }
       const int sb = sp[N], se = sp[N + 1];
       if (sb == se) continue;
-      const float Rf = (float)(row[3] * q);
+      const float Rf = (float)fma(row[3], q, row[7]);  // row[7] = 0: a DFMA issues faster than a DMUL
       for (int s = sb; s < se; ++s) {
         const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
         push(Rf * ((code >> 31) ? sf : cf));

@@ -63,7 +63,8 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
       const int sb = sp[N], se = sp[N + 1];
       if (sb == se) return;
       const double* row = h + (size_t)(kHeaderRows + N) * kRow;
-      const double R0 = row[3] * v0, R1 = row[4] * v1;
+      const double zero = row[7];  // 0.0: products issue as DFMA, faster than DMUL on GB300
+      const double R0 = fma(row[3], v0, zero), R1 = fma(row[4], v1, zero);
       for (int s = sb; s < se; ++s) {
         const uint32_t code = (uint32_t)__ldg(slot_idx + s);
         const int64_t j = (int64_t)(code & 0x7fffffffu);
@@ -71,8 +72,8 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
         const double hv = H[j * P + p];
         const double f = is_sin ? sn : cs;
         const double dt = is_sin ? md * cs : -md * sn;
-        acc_r = fma(R1 * f, hv, acc_r);
-        acc_t = fma(R0 * dt, hv, acc_t);
+        acc_r = fma(fma(R1, f, zero), hv, acc_r);
+        acc_t = fma(fma(R0, dt, zero), hv, acc_t);
       }
     };
     accumulate(0, T0, T1);
@@ -83,7 +84,7 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
       const double A = row[0], B = row[1], A2 = row[2];
       const double g = fma(A, u, -B);
       const double n0 = fma(g, S0, -T0);
-      const double n1 = fma(g, S1, fma(A2 * rho, S0, -T1));
+      const double n1 = fma(g, S1, fma(fma(A2, rho, row[7]), S0, -T1));
       T0 = S0;
       T1 = S1;
       S0 = n0;
