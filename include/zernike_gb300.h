@@ -269,6 +269,14 @@ ZP_API zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64
  */
 ZP_API zp_status zp_device_wait_status(int32_t reset);
 
+/*
+ * Failure-detection self-test: launches (asynchronously, on `stream`) one thread that waits on
+ * a device barrier nothing arrives on, with the same bounded wait the tensor-core kernels use,
+ * giving up after limit_ms (1..2000).  A following zp_device_wait_status then reports
+ * ZP_ERR_TIMEOUT, and the context stays usable.
+ */
+ZP_API zp_status zp_device_wait_selftest(int32_t limit_ms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

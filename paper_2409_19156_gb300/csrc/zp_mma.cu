@@ -272,7 +272,12 @@ struct GemmArgs {
   int KC;
 };
 
-template <bool TF32>
+// CL = 1: one CTA per tile.  CL = 2: CTA pairs (a cluster of two) work on two point tiles of
+// the same coefficient tile; each CTA loads its own A chunk and one half of the B chunk, which
+// a cluster-multicast bulk copy writes into both CTAs' shared memory, so B crosses L2 once per
+// pair.  A stage is refilled only after both CTAs' MMAs have released it (the MMA commit
+// arrives on the "empty" barrier of both CTAs).
+template <bool TF32, int CL>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a) {
   using C = Cfg<TF32>;
   extern __shared__ uint8_t smem_raw[];
@@ -285,10 +290,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = CL == 2 ? ptx::cluster_ctarank() : 0u;
+  const int64_t cid = blockIdx.x / CL, nclusters = gridDim.x / CL;
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::STAGES; ++i) {
       ptx::mbar_init(&full[i], 1);
-      ptx::mbar_init(&empty[i], 1);
+      ptx::mbar_init(&empty[i], CL);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tmem_full[i], 1);
@@ -303,10 +310,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) ptx::cluster_sync();  // peers' barriers exist before any multicast
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
 
-  const int64_t total_tiles = a.m_tiles * a.n_tiles;
+  // Tile t of this cluster: point-tile group t / n_tiles (CL point tiles), set tile t % n_tiles.
+  const int64_t groups = (a.m_tiles + CL - 1) / CL;
+  const int64_t total = groups * a.n_tiles;
   auto fail = [&]() {
     *abort_flag = 1;
     atomicOr(&g_split_error, 1u);
@@ -316,10 +326,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
-        const int64_t mt = tile / a.n_tiles;
-        const int nt = (int)(tile % a.n_tiles);
-        const uint8_t* gA = a.A + (size_t)mt * a.KC * C::A_CHUNK;
+      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters) {
+        const int64_t mt = (t / a.n_tiles) * CL + rank;
+        const int nt = (int)(t % a.n_tiles);
+        // A pair's second tile past the slab end reuses the last valid tile's data (its rows
+        // are never stored); it still takes part in the shared B loads.
+        const int64_t mt_src = mt < a.m_tiles ? mt : a.m_tiles - 1;
+        const uint8_t* gA = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
         const uint8_t* gB = a.B + (size_t)nt * a.KC * C::B_CHUNK;
         for (int kc = 0; kc < a.KC; ++kc) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
@@ -329,7 +342,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           uint8_t* sA = smem + stage * C::STAGE;
           ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
           ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
-          ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
+          if constexpr (CL == 1) {
+            ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
+          } else {
+            constexpr uint32_t HALF = C::B_CHUNK / 2;
+            ptx::bulk_g2s_multicast(sA + C::A_CHUNK + rank * HALF, gB + (size_t)kc * C::B_CHUNK + rank * HALF, HALF,
+                                    &full[stage], (uint16_t)0x3);
+          }
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -343,7 +362,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       int stage = 0;
       uint32_t phase = 0;
       int64_t local = 0;
-      for (int64_t tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x, ++local) {
+      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters, ++local) {
         const uint32_t acc = (uint32_t)(local & 1);
         const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
         if (!ptx::mbar_wait(&tmem_empty[acc], acc_phase ^ 1u, abort_flag)) {
@@ -379,7 +398,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
               ptx::mma_bf16(d_tmem, al, bh, idesc, 1u);
             }
           }
-          ptx::mma_commit(&empty[stage]);
+          if constexpr (CL == 1) {
+            ptx::mma_commit(&empty[stage]);
+          } else {
+            ptx::mma_commit_multicast(&empty[stage], (uint16_t)0x3);
+          }
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -394,7 +417,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     const uint32_t q = (uint32_t)(warp & 3);
     const uint32_t row = q * 32 + lane;
     int64_t local = 0;
-    for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++local) {
+    for (int64_t t = cid; t < total; t += nclusters, ++local) {
       const uint32_t acc = (uint32_t)(local & 1);
       const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
       if (!ptx::mbar_wait(&tmem_full[acc], acc_phase, abort_flag)) {
@@ -402,8 +425,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         break;
       }
       ptx::tc_fence_after();
-      const int64_t mt = a.mt_base + tile / a.n_tiles;
-      const int nt = (int)(tile % a.n_tiles);
+      const int64_t mt_local = (t / a.n_tiles) * CL + rank;
+      const bool valid_tile = mt_local < a.m_tiles;
+      const int64_t mt = a.mt_base + mt_local;
+      const int nt = (int)(t % a.n_tiles);
       const int64_t p = mt * BM + row;
       const int64_t col0 = (int64_t)nt * BN;
       float* frow = a.F + p * a.S;
@@ -413,7 +438,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         uint32_t v[32];
         ptx::tmem_ld_32x32b_x32(tmem_base + ((q * 32u) << 16) + acc * BN + (uint32_t)c0, v);
         ptx::tmem_ld_wait();
-        if (p < a.P) {
+        if (valid_tile && p < a.P) {
           const int64_t cbase = col0 + c0;
           if (vec && cbase + 32 <= a.S) {
             float4* dst = reinterpret_cast<float4*>(frow + cbase);
@@ -434,6 +459,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
+  // No CTA of a pair leaves while its peer may still multicast into it or arrive on its barriers.
+  if constexpr (CL == 2) ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, 512);
@@ -521,9 +548,30 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
           cudaSuccess)
     return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
+  // CTA pairs when the GPU can co-schedule them (the occupancy query says how many pairs fit).
+  int pairs = 0;
+  {
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(2 * (unsigned)sms);
+    q.blockDim = dim3(kGemmThreads);
+    q.dynamicSmemBytes = C::SMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    q.attrs = at;
+    q.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<TF32, 2>, &q) != cudaSuccess) {
+      cudaGetLastError();
+      pairs = 0;
+    }
+  }
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
   timer.begin(0, &ev0, stream);
@@ -540,11 +588,28 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
     timer.end(1, ev0, stream);
     GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
-    const int64_t total = tiles * NT;
-    const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
     timer.begin(2, &ev0, stream);
-    split_gemm_kernel<TF32><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
+    if (pairs > 0 && tiles >= 2) {
+      const int64_t groups = ((tiles + 1) / 2) * NT;
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(2 * (unsigned)std::min<int64_t>(groups, pairs));
+      lc.blockDim = dim3(kGemmThreads);
+      lc.dynamicSmemBytes = C::SMEM;
+      lc.stream = stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+      e = cudaLaunchKernelEx(&lc, split_gemm_kernel<TF32, 2>, ga);
+    } else {
+      const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT, sms);
+      split_gemm_kernel<TF32, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
     timer.end(2, ev0, stream);
   }
   return timer.finish();
@@ -571,6 +636,29 @@ size_t split_scratch_bytes(zp_precision prec, int64_t n_modes, int64_t n_sets, s
   return *b_bytes + *tile_bytes;
 }
 
+namespace {
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing ever arrives on;
+// the wait gives up after limit_ns and records the timeout in the status word, exactly as the
+// tensor-core kernels do.  No asynchronous copy or TMEM is involved, so giving up is safe.
+__global__ void wait_selftest_kernel(uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    abort_flag = 0;
+    ptx::fence_barrier_init();
+    if (!ptx::mbar_wait(&bar, 0u, &abort_flag, limit_ns)) atomicOr(&g_split_error, 2u);
+    ptx::mbar_arrive(&bar);  // complete the phase so the barrier is left in a finished state
+  }
+}
+}  // namespace
+
+zp_status wait_selftest(int32_t limit_ms, cudaStream_t stream) {
+  wait_selftest_kernel<<<1, 32, 0, stream>>>((uint64_t)limit_ms * 1000000ull);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "wait_selftest_kernel launch");
+}
+
 zp_status split_error_word(unsigned int* value, bool reset) {
   cudaError_t e = cudaMemcpyFromSymbol(value, g_split_error, sizeof(unsigned int));
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyFromSymbol");
@@ -583,6 +671,12 @@ zp_status split_error_word(unsigned int* value, bool reset) {
 }
 
 }  // namespace zp
+
+extern "C" zp_status zp_device_wait_selftest(int32_t limit_ms, void* stream) {
+  zp::clear_error();
+  if (limit_ms < 1 || limit_ms > 2000) return zp::set_error(ZP_ERR_INVALID_ARG, "limit_ms must be 1..2000");
+  return zp::wait_selftest(limit_ms, (cudaStream_t)stream);
+}
 
 extern "C" zp_status zp_device_wait_status(int32_t reset) {
   zp::clear_error();
