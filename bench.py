@@ -54,6 +54,10 @@ def parse_args():
     ap.add_argument("--series-only", action="store_true",
                     help="run only the mixed_n32 series measurement (profiling captures)")
     ap.add_argument("--series-points", type=int, default=1_000_000)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
+    ap.add_argument("--batched-instances", type=int, default=512)
+    ap.add_argument("--batched-point-scale", type=float, default=1.0)
     ap.add_argument("--points", type=int, default=100_000,
                     help="point count (smaller values only for profiling captures; the bench line uses 100000)")
     return ap.parse_args()
@@ -307,7 +311,8 @@ def run_ours(args) -> None:
         del out
         torch.cuda.empty_cache()
         extras = {"series": measure_series(dev, peaks), "adjoint": measure_adjoint(dev),
-                  "basis": measure_basis_latency(dev), "batched": measure_batched(dev)}
+                  "basis": measure_basis_latency(dev), "batched": measure_batched(dev),
+                  "paper_shapes": measure_paper_shapes(dev)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,6 +451,58 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
             "fp64_forward_ms": fwd, "fp64_adjoint_ms": adj}
 
 
+def measure_paper_shapes(dev, steps: int = 50) -> dict:
+    """The paper's own timing shapes.  (1) Algorithm 2 (one recursion per mode) against the
+    per-column walk (Algorithm 1's decomposition) on the 2601-mode radial set, k = 0, 100000
+    points.  (2) The Fig. 3 grid: full radial set k = 0 at 100 and 1000 linearly spaced points
+    for n_max = 10, 20, 50, 100, as single calls and as CUDA-graph replays."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import _lib, inputs
+
+    lib = _lib.load()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    ns, ms = inputs.radial_modes(100)
+    r = torch.as_tensor(inputs.chebyshev_gauss_points(100_000), device=dev)
+    plan = zp.Plan(ns, ms, device=dev)
+    out = torch.empty((len(ns), r.numel()), dtype=torch.float64, device=dev)
+    walk = lambda: _lib.check("zp_radial_plan", lib.zp_radial_plan(plan.handle, r.data_ptr(), r.numel(), 0,  # noqa: E731
+                                                                     out.data_ptr(), sp))
+    per_mode = lambda: _lib.check("zp_radial_per_mode", lib.zp_radial_per_mode(  # noqa: E731
+        plan.handle, r.data_ptr(), r.numel(), out.data_ptr(), sp))
+    walk()
+    per_mode()
+    res = {"alg1_column_walk_k0_ms": _events_ms(stream, walk, 5), "alg2_per_mode_k0_ms": _events_ms(stream, per_mode, 2)}
+    res["alg2_over_alg1"] = res["alg2_per_mode_k0_ms"] / res["alg1_column_walk_k0_ms"]
+    del out
+    fig3 = []
+    for P in (100, 1000):
+        rr = torch.as_tensor(inputs.linspace_points(P), device=dev)
+        for n_max in (10, 20, 50, 100):
+            n2, m2 = inputs.radial_modes(n_max)
+            pl = zp.Plan(n2, m2, device=dev)
+            o = torch.empty((len(n2), P), dtype=torch.float64, device=dev)
+            call = lambda: _lib.check("zp_radial_plan", lib.zp_radial_plan(  # noqa: E731
+                pl.handle, rr.data_ptr(), P, 0, o.data_ptr(), torch.cuda.current_stream(dev).cuda_stream))
+            call()
+            t_call = _events_ms(stream, call, steps)
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    call()
+            stream.wait_stream(side)
+            g.replay()
+            t_graph = _events_ms(stream, g.replay, steps)
+            fig3.append({"points": P, "n_max": n_max, "modes": len(n2), "us_per_call": t_call * 1e3,
+                         "us_per_graph_replay": t_graph * 1e3})
+    res["fig3_full_radial_set_k0"] = fig3
+    return res
+
+
 def measure_basis_latency(dev, steps: int = 200) -> dict:
     """basis_n20: 231 modes, 1000 points, R, R', R'' times the angular factor, plus d/dtheta Z."""
     import torch
@@ -462,12 +519,22 @@ def measure_basis_latency(dev, steps: int = 200) -> dict:
     fn = lambda: zp.basis(None, None, rt, tt, 2, dtheta=True, plan=plan)  # noqa: E731
     fn()
     ms_call = _events_ms(stream, fn, steps)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            fn()
+    stream.wait_stream(side)
+    g.replay()
+    ms_graph = _events_ms(stream, g.replay, steps)
     vals = len(ns) * len(r) * 4
     return {"workload": "basis_n20", "modes": len(ns), "points": len(r), "us_per_call": ms_call * 1e3,
-            "values_per_s": vals / (ms_call * 1e-3)}
+            "us_per_graph_replay": ms_graph * 1e3, "values_per_s_graph": vals / (ms_graph * 1e-3)}
 
 
-def measure_batched(dev, steps: int = 3) -> dict:
+def measure_batched(dev, steps: int = 3, n_instances: int = 512, point_scale: float = 1.0,
+                    tune: bool = True) -> dict:
     """batched_512: 512 instances, n_max ~ U{8..64} (full Z sets), points log-uniform in
     [1e3, 2e5], 16 coefficient sets.  Persistent forward (float64 and float32 contraction) as a
     CUDA-graph replay after autotuning, the same float64 forward as one launch per instance,
@@ -478,7 +545,7 @@ def measure_batched(dev, steps: int = 3) -> dict:
     from paper_2409_19156_gb300 import inputs
 
     cfg = inputs.WORKLOADS["batched_512"]
-    raw = inputs.batched_instances(cfg["n_instances"], cfg["n_sets"], cfg["seed"])
+    raw = inputs.batched_instances(n_instances, cfg["n_sets"], cfg["seed"], point_scale=point_scale)
     S = cfg["n_sets"]
     inst = []
     gen = torch.Generator(dev).manual_seed(5)
@@ -492,7 +559,7 @@ def measure_batched(dev, steps: int = 3) -> dict:
     out = {"workload": "batched_512", "instances": len(raw), "points": points, "sets": S,
            "basis_values": basis_values}
     b = zp.Batch(inst, S)
-    cfg64, _ = b.tune("forward", "fp64", reps=1)
+    cfg64 = b.tune("forward", "fp64", reps=1)[0] if tune else b.config()
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
@@ -503,7 +570,7 @@ def measure_batched(dev, steps: int = 3) -> dict:
     g.replay()
     t_graph = _events_ms(stream, g.replay, steps)
     t_per = _events_ms(stream, b.forward_per_instance, 1)
-    cfg_adj, _ = b.tune("adjoint", reps=1)
+    cfg_adj = b.tune("adjoint", reps=1)[0] if tune else b.config()
     b.adjoint()
     t_adj = _events_ms(stream, b.adjoint, 1)
     out["fp64_forward_graph_ms"] = t_graph
@@ -514,7 +581,7 @@ def measure_batched(dev, steps: int = 3) -> dict:
     out["fp64_forward_basis_values_per_s"] = basis_values / (t_graph * 1e-3)
     b.close()
     b32 = zp.Batch(inst, S, out_dtype=torch.float32, with_adjoint=False)
-    cfg32, _ = b32.tune("forward", "fp32", reps=1)
+    cfg32 = b32.tune("forward", "fp32", reps=1)[0] if tune else b32.config()
     b32.forward("fp32")
     out["fp32_forward_ms"] = _events_ms(stream, lambda: b32.forward("fp32"), steps)
     out["tuned_fp32_cfg"] = list(cfg32)
@@ -554,6 +621,14 @@ def run_reference(args) -> None:
 
 def main():
     args = parse_args()
+    if args.batched_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        res = measure_batched(torch.device("cuda", 0), steps=args.steps, n_instances=args.batched_instances,
+                              point_scale=args.batched_point_scale, tune=False)
+        print(json.dumps({"batched_only": res}), flush=True)
+        return
     if args.series_only:
         import torch
 
