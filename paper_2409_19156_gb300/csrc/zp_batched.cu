@@ -157,7 +157,7 @@ __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
           S0 = n0;
           q0 = n0;
           if constexpr (MODE == ADJ) {
-            const double n1 = fma(g, S1, fma(fma(row[2], rho, row[7]), T0, -T1));
+            const double n1 = fma(g, S1, fma(row[2] * rho, T0, -T1));
             T1 = S1;
             S1 = n1;
             q1 = n1;
@@ -165,13 +165,12 @@ __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
         }
         const int sb = sp[N], se = sp[N + 1];
         if (sb == se) continue;
-        const double zero = row[7];  // 0.0: products below issue as DFMA, faster than DMUL on GB300
-        const double R0 = fma(row[3], q0, zero);
+        const double R0 = row[3] * q0;
         if constexpr (MODE == FWD64) {
           for (int s = sb; s < se; ++s) {
             const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
             const int64_t j = (int64_t)(code & 0x7fffffffu);
-            const double z = fma(R0, (code >> 31) ? sm : cm, zero);
+            const double z = R0 * ((code >> 31) ? sm : cm);
             const double* cr = d.coeffs + j * S + s0;
 #pragma unroll
             for (int i = 0; i < kSC; ++i)
@@ -190,7 +189,7 @@ __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
               if (i < sc) accf[i] = fmaf(z, __ldg(cr + i), accf[i]);
           }
         } else {
-          const double R1 = fma(row[4], q1, zero);
+          const double R1 = row[4] * q1;
           for (int s = sb; s < se; ++s) {
             const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
             const int64_t j = (int64_t)(code & 0x7fffffffu);
@@ -202,8 +201,8 @@ __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
               if (i < sc) hv = fma(G[i], __ldg(cr + i), hv);
             const double f = is_sin ? sm : cm;
             const double dt = is_sin ? md * cm : -md * sm;
-            acc_r = fma(fma(R1, f, zero), hv, acc_r);
-            acc_t = fma(fma(R0, dt, zero), hv, acc_t);
+            acc_r = fma(R1 * f, hv, acc_r);
+            acc_t = fma(R0 * dt, hv, acc_t);
           }
         }
       }
@@ -356,7 +355,7 @@ __global__ void batched_column_kernel(BatchArgs a, int max_slots) {
             for (int i = 0; i < kSC; ++i) v[i] = 0.0;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              const double z = fma(fma(row[3], q[k], row[7]), is_sin ? sm[k] : cm[k], row[7]);
+              const double z = row[3] * q[k] * (is_sin ? sm[k] : cm[k]);
 #pragma unroll
               for (int i = 0; i < kSC; ++i) v[i] = fma(z, G[k][i], v[i]);
             }

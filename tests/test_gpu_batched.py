@@ -153,6 +153,12 @@ def test_batched_512_full_size_sampled():
         d, rec = inst[i], b.instances[i]
         want = zp.series_eval(d["n"], d["m"], d["r"], d["theta"], d["coeffs"])
         assert float((rec["out"] - want).abs().max()) <= 1e-12 * (1 + float(want.abs().max()))
+    # one instance's rows directly against the oracle
+    x = raw[17]
+    rows = [0, len(x.r) - 1]
+    want = np.array(oseries.series_eval(x.n, x.m, x.r[rows], x.theta[rows], x.coeffs.tolist()))
+    tol = 1e-13 * (1.0 + abs_bound(x.n, x.m, x.r[rows], x.theta[rows], x.coeffs))
+    assert (np.abs(b.instances[17]["out"][rows].cpu().numpy() - want) <= tol).all()
     keep = [rec["out"].clone() for rec in b.instances[:8]]
     b.forward_per_instance()
     torch.cuda.synchronize()

@@ -134,3 +134,15 @@ def test_error_paths_leave_output_untouched():
     assert torch.all(out == 7.0)
     with pytest.raises(zp.ZernikeError):
         zp.radial([5], [1], r, 4)
+
+
+def test_high_order_modes_n300():
+    """Modes well beyond the paper's n <= 100 (tables longer, more steps): values and all
+    derivatives against the oracle, and R_n^m(1) = 1."""
+    ns = [300, 300, 299, 250, 200, 300, 151]
+    ms = [0, 2, 1, 250, 100, 300, 3]
+    r = np.concatenate([[0.0, 1.0, 0.5], inputs.uniform_points(29, 77)[0]])
+    got = run_radial(ns, ms, r, 3)
+    want = np.array(oradial.radial_table(ns, ms, r, 3))
+    assert_radial_close(got, want, ns, "n<=300")
+    assert np.max(np.abs(got[0][:, 1] - 1.0)) < 1e-11

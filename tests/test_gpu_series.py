@@ -110,3 +110,48 @@ def test_series_empty_and_errors():
     assert F.shape == (5, 0)
     with pytest.raises(ValueError):
         zp.series_eval(ns, ms, dev(r), dev(th), dev(np.ones((3, 2))))
+
+
+def test_series_n24_full_size_autograd_against_central_differences():
+    """The 325-mode, 50000-point polar-grid, 256-set workload through the autograd wrapper:
+    sampled gradient entries (r, theta, C) against central differences with h = 1e-6."""
+    cfg = inputs.WORKLOADS["series_n24"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.polar_grid(cfg["n_r"], cfg["n_theta"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    plan = zp.Plan(ns, ms)
+    G = torch.randn((len(r), C.shape[1]), dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(DEV).manual_seed(3))
+    rt = dev(r).requires_grad_(True)
+    tt = dev(th).requires_grad_(True)
+    Ct = dev(C).requires_grad_(True)
+    (zp.zernike_series(rt, tt, Ct, plan) * G).sum().backward()
+    h = 1e-6
+    base = (dev(r), dev(th), dev(C))
+
+    # Perturbing r_p or theta_p changes only row p of F, and C[j, s] only column s, so the
+    # finite-difference loss sums just that row / column (summing all 1.28e7 products would
+    # put ~1e-9 of rounding noise into each loss value, 5e-4 after dividing by 2h).
+    def row_loss(p, rr, t2, cc):
+        F = zp.series_eval(None, None, rr, t2, cc, plan=plan)
+        return float((F[p] * G[p]).sum())
+
+    def col_loss(s, rr, t2, cc):
+        F = zp.series_eval(None, None, rr, t2, cc, plan=plan)
+        return float((F[:, s] * G[:, s]).sum())
+
+    for p in (0, 12_345, 49_999):
+        for which, grad in ((0, rt.grad), (1, tt.grad)):
+            e = torch.zeros(len(r), dtype=torch.float64, device=DEV)
+            e[p] = h
+            plus = list(base)
+            minus = list(base)
+            plus[which] = base[which] + e
+            minus[which] = base[which] - e
+            fd = (row_loss(p, *plus) - row_loss(p, *minus)) / (2 * h)
+            assert abs(fd - float(grad[p])) < 1e-6 * (1 + abs(fd)), (which, p, fd, float(grad[p]))
+    for j, s in ((0, 0), (200, 100), (324, 255)):
+        e = torch.zeros_like(base[2])
+        e[j, s] = h
+        fd = (col_loss(s, base[0], base[1], base[2] + e) - col_loss(s, base[0], base[1], base[2] - e)) / (2 * h)
+        assert abs(fd - float(Ct.grad[j, s])) < 1e-6 * (1 + abs(fd))
