@@ -178,6 +178,27 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  double* grad_theta, void* stream);
 
 /*
+ * Least-squares fit of series coefficients (the "fit" counterpart of zp_series_eval):
+ *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
+ * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 throughout (basis by
+ * the recursion walk, Gram matrix by DSYRK, right-hand side by DGEMM, Cholesky by cuSOLVER).
+ *   weights: DEVICE float64 [n_points] (w_p >= 0) or NULL (all 1).
+ *   samples: DEVICE float64 [n_points][n_sets] (Y, row-major).
+ *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
+ *   ridge >= 0 (Tikhonov term; 0 for plain least squares).
+ * Scratch is allocated stream-ordered on `stream`.  The call synchronises `stream` to read the
+ * factorisation status: a singular normal matrix (fewer independent points than modes, or a
+ * duplicated mode without ridge) returns ZP_ERR_INVALID_ARG.  At most 46340 modes.
+ */
+ZP_API zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes,
+                               const double* r, const double* theta, const double* weights,
+                               int64_t n_points, const double* samples, int64_t n_sets, double ridge,
+                               double* coeffs, void* stream);
+ZP_API zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta,
+                                    const double* weights, int64_t n_points, const double* samples,
+                                    int64_t n_sets, double ridge, double* coeffs, void* stream);
+
+/*
  * Batched series over many instances of uneven size (different mode lists, point counts)
  * in one persistent launch per pass; the launches are stream-ordered and contain no host
  * synchronisation, so zp_batch_forward / zp_batch_adjoint can be captured in a CUDA graph.

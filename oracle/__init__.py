@@ -12,5 +12,6 @@ Modules:
   trig    -- cos/sin(m*theta) in big-integer fixed point (no mpmath dependency)
   basis   -- Z_n^m and its rho / theta derivatives, rounded once to float64
   series  -- series F = Z C and its adjoint, exact sums over the rounded basis
+  fit     -- weighted least-squares coefficients (normal equations)
 """
-from . import radial, trig, basis, series  # noqa: F401
+from . import radial, trig, basis, series, fit  # noqa: F401

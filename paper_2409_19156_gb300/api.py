@@ -160,6 +160,30 @@ def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), pl
     return gC, gr, gt
 
 
+def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: Plan | None = None):
+    """Least-squares coefficients C [J][S] with sum_j Z_j(p) C[j, s] ~ samples[p, s] (weighted,
+    optional ridge); float64 throughout."""
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    Y = _dev_f64(samples, "samples")
+    w = None if weights is None else _dev_f64(weights, "weights")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P = len(nn), r.numel()
+    if Y.dim() != 2 or Y.shape[0] != P:
+        raise ValueError("samples must be [n_points, n_sets]")
+    S = Y.shape[1]
+    out = torch.empty((J, S), dtype=torch.float64, device=r.device)
+    st = _stream(r.device)
+    with torch.cuda.device(r.device):
+        if plan is not None:
+            _lib.call("zp_series_fit_plan", plan.handle, r.data_ptr(), theta.data_ptr(), _lib.ptr(w), P, Y.data_ptr(),
+                      S, float(ridge), out.data_ptr(), st)
+        else:
+            _lib.call("zp_series_fit", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(),
+                      _lib.ptr(w), P, Y.data_ptr(), S, float(ridge), out.data_ptr(), st)
+    return out
+
+
 class ZernikeSeries(torch.autograd.Function):
     """F = Z(r, theta) C with gradients for C, r and theta from the library's adjoint
     (basis recomputed in the backward pass, never stored).  float64 throughout."""
