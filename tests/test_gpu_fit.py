@@ -34,7 +34,7 @@ def test_weighted_fit_against_oracle():
 
 
 def test_unweighted_and_ridge_fit_against_oracle():
-    ns, ms = [5, 3, 3, 0, 8, 7]
+    ns = [5, 3, 3, 0, 8, 7]
     ms = [1, -3, 3, 0, -4, 7]
     r, th = inputs.uniform_points(200, 3)
     Y = np.random.default_rng(2).standard_normal((200, 3))
