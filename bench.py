@@ -447,8 +447,21 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
     fwd = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, plan=plan), steps)
     adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan), steps)
+    # Least-squares fit of the same coefficients back from the series values, with the
+    # grid's exact quadrature weights (Gauss-Legendre in r^2 x uniform theta).
+    import numpy as np
+
+    _, wgl = np.polynomial.legendre.leggauss(cfg["n_r"])
+    w = torch.as_tensor(np.repeat(0.25 * wgl, cfg["n_theta"]) * (2.0 * math.pi / cfg["n_theta"]), device=dev)
+    Y = zp.series_eval(None, None, rt, tt, Ct, plan=plan)
+    Cfit = zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
+    fit_ms = (time.perf_counter() - t0) * 1e3 / steps  # the fit synchronises its stream
     return {"workload": "series_n24", "modes": len(ns), "points": len(r), "sets": C.shape[1],
-            "fp64_forward_ms": fwd, "fp64_adjoint_ms": adj}
+            "fp64_forward_ms": fwd, "fp64_adjoint_ms": adj, "fp64_fit_ms": fit_ms,
+            "fit_roundtrip_max_abs_err": float((Cfit - Ct).abs().max())}
 
 
 def measure_paper_shapes(dev, steps: int = 50) -> dict:

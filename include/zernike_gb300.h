@@ -187,8 +187,9 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
  *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
  *   ridge >= 0 (Tikhonov term; 0 for plain least squares).
  * Scratch is allocated stream-ordered on `stream`.  The call synchronises `stream` to read the
- * factorisation status: a singular normal matrix (fewer independent points than modes, or a
- * duplicated mode without ridge) returns ZP_ERR_INVALID_ARG.  At most 46340 modes.
+ * factorisation status: a singular or numerically singular normal matrix (squared Cholesky
+ * pivot ratio below 1e-14: fewer independent points than modes, or a duplicated mode without
+ * ridge) returns ZP_ERR_INVALID_ARG after writing coeffs.  At most 46340 modes.
  */
 ZP_API zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes,
                                const double* r, const double* theta, const double* weights,

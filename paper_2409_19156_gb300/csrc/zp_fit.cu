@@ -13,6 +13,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -37,6 +38,32 @@ __global__ void scale_samples_kernel(const double* Y, double* Ys, int64_t P, int
 __global__ void add_ridge_kernel(double* G, int64_t J, double ridge) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J; i += (int64_t)gridDim.x * blockDim.x)
     G[i * J + i] += ridge;
+}
+
+// Smallest and largest squared pivot of the Cholesky factor (single block).
+__global__ void pivot_range_kernel(const double* L, int64_t J, double* out) {
+  __shared__ double smin[256], smax[256];
+  double lo = 1.0 / 0.0, hi = 0.0;
+  for (int64_t i = threadIdx.x; i < J; i += blockDim.x) {
+    const double d = L[i * J + i];
+    const double d2 = d * d;
+    lo = d2 < lo ? d2 : lo;
+    hi = d2 > hi ? d2 : hi;
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      smin[threadIdx.x] = smin[threadIdx.x + s] < smin[threadIdx.x] ? smin[threadIdx.x + s] : smin[threadIdx.x];
+      smax[threadIdx.x] = smax[threadIdx.x + s] > smax[threadIdx.x] ? smax[threadIdx.x + s] : smax[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smin[0];
+    out[1] = smax[0];
+  }
 }
 
 struct SolverHandles {
@@ -76,7 +103,7 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
   ZP_TRY(zbuf.alloc((size_t)J * P * sizeof(double), stream));
   ZP_TRY(gram.alloc((size_t)J * J * sizeof(double), stream));
   ZP_TRY(rhs.alloc((size_t)J * S * sizeof(double), stream));
-  ZP_TRY(info.alloc(sizeof(int), stream));
+  ZP_TRY(info.alloc(4 * sizeof(double), stream));  // [0]: potrf status (int), [2..3]: pivot range
   double* Z = (double*)zbuf.ptr;
   ZP_TRY(launch_walk(plan, r, theta, P, 0, Z, nullptr, stream));
   const double* Yuse = Y;
@@ -109,6 +136,8 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
   if (cusolverDnDpotrf(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, (double*)work.ptr, lwork,
                        (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
     return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf failed");
+  pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
   if (cusolverDnDpotrs(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (int)S, (double*)gram.ptr, (int)J, (double*)rhs.ptr,
                        (int)J, (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
     return set_error(ZP_ERR_CUDA, "cusolverDnDpotrs failed");
@@ -116,13 +145,17 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
   if (cublasDgeam(blas, CUBLAS_OP_T, CUBLAS_OP_N, (int)S, (int)J, &one, (double*)rhs.ptr, (int)J, &zero, coeffs,
                   (int)S, coeffs, (int)S) != CUBLAS_STATUS_SUCCESS)
     return set_error(ZP_ERR_CUDA, "cublasDgeam failed");
-  int h_info = 0;
-  if ((e = cudaMemcpyAsync(&h_info, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+  double h_info[4] = {0, 0, 0, 0};
+  if ((e = cudaMemcpyAsync(h_info, info.ptr, sizeof(h_info), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(stream)) != cudaSuccess)
     return cuda_error(e, "reading the factorisation status");
-  if (h_info != 0)
-    return set_error(ZP_ERR_INVALID_ARG, "normal matrix not positive definite (leading minor " +
-                                             std::to_string(h_info) +
+  int status = 0;
+  memcpy(&status, h_info, sizeof(int));
+  // A rank-deficient normal matrix can factor with tiny positive pivots in floating point;
+  // a squared-pivot ratio below 1e-14 (condition number above ~1e14) is reported as singular.
+  if (status != 0 || !(h_info[2] > 1e-14 * h_info[3]))
+    return set_error(ZP_ERR_INVALID_ARG, "normal matrix not positive definite (potrf status " + std::to_string(status) +
+                                             ", squared pivot ratio " + std::to_string(h_info[2] / h_info[3]) +
                                              "): fewer independent points than modes, or duplicated modes; add a "
                                              "ridge");
   return ZP_OK;
