@@ -39,7 +39,6 @@ constexpr uint32_t kRowBytes = 128;
 constexpr uint32_t kAPart = BM * kRowBytes;  // 16 KB: one 128 x 128-byte K-chunk
 constexpr uint32_t kBPart = BN * kRowBytes;  // 32 KB
 constexpr int kGemmThreads = 192;            // 6 warps: producer, MMA, 4 x epilogue
-constexpr int kBasisThreads = BM;
 constexpr int kCoeffThreads = BN;
 
 template <bool TF32>
@@ -125,15 +124,28 @@ struct Pack16 {
   }
 };
 
-// No shared memory or barriers: each thread packs 8 bf16 (or 4 tf32) consecutive K values of
-// its row in registers and writes the 16-byte unit straight to its place in the swizzled
-// chunk (measured faster than staging whole chunks in shared memory for bulk stores).
+// No shared memory or barriers: each thread owns two rows of the 128-point tile (rows t and
+// t + 64), packs 8 bf16 (or 4 tf32) consecutive K values of each row in registers and writes
+// every 16-byte unit straight to its place in the swizzled chunk (measured faster than
+// staging whole chunks in shared memory for bulk stores).  With two points per thread (TF32)
+// the table and slot loads are shared and the float64 pipe gets two independent recursions;
+// BF16x3 keeps one point per thread (measured faster: its hi/lo split and packing add
+// integer work per value that the second point does not amortise).
+template <bool TF32>
+__host__ __device__ constexpr int basis_ppt() {
+  return TF32 ? 2 : 1;
+}
+template <bool TF32>
+__host__ __device__ constexpr int basis_threads() {
+  return BM / basis_ppt<TF32>();
+}
+
 template <bool TF32>
 __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t tile);
 
 // One CTA per point tile of the slab (grid-stride if the grid is smaller).
 template <bool TF32>
-__global__ void __launch_bounds__(kBasisThreads) split_basis_kernel(BasisArgs a, int64_t tiles) {
+__global__ void __launch_bounds__(basis_threads<TF32>()) split_basis_kernel(BasisArgs a, int64_t tiles) {
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) split_basis_tile<TF32>(a, tile);
 }
 
@@ -141,38 +153,51 @@ template <bool TF32>
 __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t tile) {
   using C = Cfg<TF32>;
   constexpr int UNIT = TF32 ? 4 : 8;  // K values per 16-byte unit
-  const uint32_t t = threadIdx.x;
-  const int64_t p = (a.mt_base + tile) * BM + t;
-  const bool valid = p < a.P;
-  const double rho = valid ? a.r[p] : 0.0;
-  const double th = valid ? a.theta[p] : 0.0;
-  const double u = rho * rho;
-  double s1, c1;
-  sincos(th, &s1, &c1);
-  double cm = 1.0, sm = 0.0, pm = 1.0;
+  constexpr int Q = basis_ppt<TF32>();
+  uint32_t rowi[Q];
+  double rho[Q], u[Q], s1[Q], c1[Q], cm[Q], sm[Q], pm[Q], T[Q], S[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rowi[i] = threadIdx.x + (uint32_t)i * basis_threads<TF32>();
+    const int64_t p = (a.mt_base + tile) * BM + rowi[i];
+    const bool valid = p < a.P;
+    rho[i] = valid ? a.r[p] : 0.0;
+    const double th = valid ? a.theta[p] : 0.0;
+    u[i] = rho[i] * rho[i];
+    sincos(th, &s1[i], &c1[i]);
+    cm[i] = 1.0;
+    sm[i] = 0.0;
+    pm[i] = 1.0;
+  }
   int m_prev = 0;
   uint8_t* gA = a.A + (size_t)tile * a.KC * C::A_CHUNK;
   int k = 0;
-  Pack16 hi, lo;
+  Pack16 hi[Q], lo[Q];
 
-  auto push = [&](float z) {
-    if constexpr (TF32) {
-      hi.push32(__float_as_uint(to_tf32(z)));
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(z);
-      const __nv_bfloat16 l = __float2bfloat16_rn(z - __bfloat162float(h));
-      hi.push16((uint32_t)__bfloat16_as_ushort(h));
-      lo.push16((uint32_t)__bfloat16_as_ushort(l));
+  auto push = [&](const float (&z)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (TF32) {
+        hi[i].push32(__float_as_uint(to_tf32(z[i])));
+      } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(z[i]);
+        const __nv_bfloat16 l = __float2bfloat16_rn(z[i] - __bfloat162float(h));
+        hi[i].push16((uint32_t)__bfloat16_as_ushort(h));
+        lo[i].push16((uint32_t)__bfloat16_as_ushort(l));
+      }
     }
     if (++k % UNIT == 0) {
       const int k0 = k - UNIT;
       uint8_t* chunk = gA + (size_t)(k0 / C::BK) * C::A_CHUNK;
-      if constexpr (TF32) {
-        hi.store(chunk + ptx::sw128_offset_b32(t, (uint32_t)(k0 % C::BK)));
-      } else {
-        const uint32_t off = ptx::sw128_offset_b16(t, (uint32_t)(k0 % C::BK));
-        hi.store(chunk + off);
-        lo.store(chunk + kAPart + off);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if constexpr (TF32) {
+          hi[i].store(chunk + ptx::sw128_offset_b32(rowi[i], (uint32_t)(k0 % C::BK)));
+        } else {
+          const uint32_t off = ptx::sw128_offset_b16(rowi[i], (uint32_t)(k0 % C::BK));
+          hi[i].store(chunk + off);
+          lo[i].store(chunk + kAPart + off);
+        }
       }
     }
   };
@@ -180,45 +205,60 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
   for (int c = 0; c < a.n_cols; ++c) {
     const Column col = a.cols[c];
     const int m = col.m;
-    if (m == m_prev + 1) {
-      const double cn = fma(cm, c1, -sm * s1);
-      const double sn = fma(sm, c1, cm * s1);
-      cm = cn;
-      sm = sn;
-      pm *= rho;
-    } else if (m != m_prev) {
-      sincos((double)m * th, &sm, &cm);
-      pm = pow_uint_m(rho, m);
+    const double* h = a.table + (size_t)col.table_row * kRow;
+    float cf[Q], sf[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (m == m_prev + 1) {
+        const double cn = fma(cm[i], c1[i], -sm[i] * s1[i]);
+        const double sn = fma(sm[i], c1[i], cm[i] * s1[i]);
+        cm[i] = cn;
+        sm[i] = sn;
+        pm[i] *= rho[i];
+      } else if (m != m_prev) {
+        const int64_t p = (a.mt_base + tile) * BM + rowi[i];
+        const double th = p < a.P ? a.theta[p] : 0.0;
+        sincos((double)m * th, &sm[i], &cm[i]);
+        pm[i] = pow_uint_m(rho[i], m);
+      }
+      cf[i] = (float)cm[i];
+      sf[i] = (float)sm[i];
+      T[i] = pm[i];
+      S[i] = fma(h[4], pm[i] * u[i], -(h[8] * pm[i]));
     }
     m_prev = m;
-    const float cf = (float)cm, sf = (float)sm;
-    const double* h = a.table + (size_t)col.table_row * kRow;
     const int32_t* sp = a.slot_ptr + col.slot_base;
-    double T = pm;
-    double S = fma(h[4], pm * u, -(h[8] * pm));
     for (int N = 0; N < col.n_steps; ++N) {
       const double* row = h + (size_t)(kHeaderRows + N) * kRow;
-      double q;
-      if (N == 0) {
-        q = T;
-      } else if (N == 1) {
-        q = S;
-      } else {
-        const double g = fma(row[0], u, -row[1]);
-        q = fma(g, S, -T);
-        T = S;
-        S = q;
+      const double A = row[0], B = row[1], W = row[3], zero = row[7];
+      float Rf[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        double q;
+        if (N == 0) {
+          q = T[i];
+        } else if (N == 1) {
+          q = S[i];
+        } else {
+          const double g = fma(A, u[i], -B);
+          q = fma(g, S[i], -T[i]);
+          T[i] = S[i];
+          S[i] = q;
+        }
+        Rf[i] = (float)fma(W, q, zero);  // zero = row[7] = 0: a DFMA issues faster than a DMUL
       }
       const int sb = sp[N], se = sp[N + 1];
-      if (sb == se) continue;
-      const float Rf = (float)fma(row[3], q, row[7]);  // row[7] = 0: a DFMA issues faster than a DMUL
       for (int s = sb; s < se; ++s) {
         const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
-        push(Rf * ((code >> 31) ? sf : cf));
+        float z[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) z[i] = Rf[i] * ((code >> 31) ? sf[i] : cf[i]);
+        push(z);
       }
     }
   }
-  while (k % C::BK != 0) push(0.0f);
+  const float zeros[Q] = {};
+  while (k % C::BK != 0) push(zeros);
 }
 
 struct CoeffArgs {
@@ -584,7 +624,7 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
                  r, theta, P, mt0, KC, A};
     timer.begin(1, &ev0, stream);
-    split_basis_kernel<TF32><<<(unsigned)tiles, kBasisThreads, 0, stream>>>(ba, tiles);
+    split_basis_kernel<TF32><<<(unsigned)tiles, basis_threads<TF32>(), 0, stream>>>(ba, tiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "split_basis_kernel launch");
     timer.end(1, ev0, stream);
     GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
