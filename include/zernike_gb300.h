@@ -178,6 +178,28 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  double* grad_theta, void* stream);
 
 /*
+ * Second derivatives for Jacobian/Hessian work (Sec. 3 mentions Jacobian and Hessian
+ * calculations through automatic differentiation).  For the scalar L = sum_{p,s} F[p,s] G[p,s]
+ * the Hessian in the point coordinates is block diagonal (r_p, theta_p enter row p only);
+ * this returns each point's block and gradient, float64:
+ *   grad_r[p]  = dL/dr_p,        grad_theta[p] = dL/dtheta_p,
+ *   hess_rr[p] = d2L/dr_p^2,     hess_rt[p] = d2L/dr_p dtheta_p,     hess_tt[p] = d2L/dtheta_p^2.
+ * Any output may be NULL.  grad_out = G, DEVICE float64 [n_points][n_sets].  Same basis
+ * recomputation and reduction as zp_series_adjoint (one extra Taylor lane).
+ */
+ZP_API zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes,
+                                         const double* r, const double* theta, int64_t n_points,
+                                         const double* coeffs, int64_t n_sets, const double* grad_out,
+                                         double* grad_r, double* grad_theta, double* hess_rr,
+                                         double* hess_rt, double* hess_tt, void* stream);
+ZP_API zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r,
+                                              const double* theta, int64_t n_points,
+                                              const double* coeffs, int64_t n_sets,
+                                              const double* grad_out, double* grad_r,
+                                              double* grad_theta, double* hess_rr, double* hess_rt,
+                                              double* hess_tt, void* stream);
+
+/*
  * Least-squares fit of series coefficients (the "fit" counterpart of zp_series_eval):
  *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
  * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 throughout (basis by

@@ -46,6 +46,25 @@ def basis_dtheta(n: int, m: int, r: float, theta: float) -> float:
     return _round_product(f.numerator, f.denominator, _dtheta_fixed(m, theta))
 
 
+def _dtheta_k_fixed(m: int, theta: float, kt: int) -> int:
+    """d^kt/dtheta^kt of cos(|m| theta) (m >= 0) or sin(|m| theta) (m < 0), kt = 0..2, fixed point."""
+    c, s = _trig.cos_sin_multiple(abs(m), theta)
+    a = abs(m)
+    if kt == 0:
+        return c if m >= 0 else s
+    if kt == 1:
+        return -a * s if m >= 0 else a * c
+    if kt == 2:
+        return -a * a * (c if m >= 0 else s)
+    raise ValueError("kt must be 0..2")
+
+
+def basis_deriv(n: int, m: int, r: float, theta: float, kr: int, kt: int) -> float:
+    """d^kr/drho^kr d^kt/dtheta^kt Z_n^m(r, theta) = R^(kr)(r) * (trig)^(kt)(theta), rounded once."""
+    f = _radial.radial_fraction(n, m, kr, r)
+    return _round_product(f.numerator, f.denominator, _dtheta_k_fixed(m, theta, kt))
+
+
 def basis_table(ns, ms, rs, thetas, max_deriv: int = 0, with_dtheta: bool = False):
     """Returns (zk, zt): zk[k][j][p] = d^k/drho^k Z_{n_j}^{m_j}(r_p, theta_p), k = 0..max_deriv,
     and zt[j][p] = d/dtheta Z (or None).  Column order = the caller's mode order."""

@@ -64,3 +64,19 @@ def series_adjoint(ns, ms, rs, thetas, coeffs, grad_out):
     gt = [exact_sum_of_products((zt[j][p], coeffs[j][s], grad_out[p][s])
                                 for j in range(J) for s in range(S)) for p in range(P)]
     return gC, gr, gt
+
+
+def point_hessian(ns, ms, rs, thetas, coeffs, grad_out):
+    """Per point p, for L = sum_{p,s} F[p,s] G[p,s]: (dL/dr_p, dL/dtheta_p, d2L/dr_p^2,
+    d2L/dr_p dtheta_p, d2L/dtheta_p^2), each the exact sum over j, s of the corresponding
+    derivative of Z_j at p (oracle basis, rounded once) times C[j, s] G[p, s], rounded once."""
+    J, P = len(ns), len(rs)
+    S = len(coeffs[0]) if J else 0
+    out = []
+    for kr, kt in ((1, 0), (0, 1), (2, 0), (1, 1), (0, 2)):
+        vals = []
+        for p in range(P):
+            z = [_basis.basis_deriv(int(ns[j]), int(ms[j]), float(rs[p]), float(thetas[p]), kr, kt) for j in range(J)]
+            vals.append(exact_sum_of_products((z[j], coeffs[j][s], grad_out[p][s]) for j in range(J) for s in range(S)))
+        out.append(vals)
+    return tuple(out)

@@ -160,6 +160,37 @@ def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), pl
     return gC, gr, gt
 
 
+def series_point_hessian(n, m, r, theta, coeffs, grad_out, plan: Plan | None = None):
+    """Per-point gradient and 2x2 Hessian block of L = <grad_out, F>: returns
+    (grad_r, grad_theta, hess_rr, hess_rt, hess_tt), each [P] float64."""
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    coeffs = _dev_f64(coeffs, "coeffs")
+    G = _dev_f64(grad_out, "grad_out")
+    nn, mm = (plan.n, plan.m) if plan is not None else (_lib.modes_i32(n), _lib.modes_i32(m))
+    J, P, S = len(nn), r.numel(), coeffs.shape[1]
+    if G.shape != (P, S):
+        raise ValueError("grad_out must be [n_points, n_sets]")
+    outs = [torch.empty(P, dtype=torch.float64, device=r.device) for _ in range(5)]
+    ptrs = [o.data_ptr() for o in outs]
+    st = _stream(r.device)
+    with torch.cuda.device(r.device):
+        if plan is not None:
+            _lib.call("zp_series_point_hessian_plan", plan.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(),
+                      S, G.data_ptr(), *ptrs, st)
+        else:
+            _lib.call("zp_series_point_hessian", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(),
+                      P, coeffs.data_ptr(), S, G.data_ptr(), *ptrs, st)
+    return tuple(outs)
+
+
+def point_hvp(hess, v_r, v_theta):
+    """Hessian-vector product with the block-diagonal point Hessian from series_point_hessian:
+    returns (Hv)_r, (Hv)_theta for tangent vectors v_r, v_theta over the points."""
+    _, _, hrr, hrt, htt = hess
+    return hrr * v_r + hrt * v_theta, hrt * v_r + htt * v_theta
+
+
 def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: Plan | None = None):
     """Least-squares coefficients C [J][S] with sum_j Z_j(p) C[j, s] ~ samples[p, s] (weighted,
     optional ridge); float64 throughout."""

@@ -34,17 +34,23 @@ __device__ __forceinline__ double pow_uint_r(double x, int e) {
   return result;
 }
 
-// One thread per point: walks every |m| column (k <= 1 Taylor lanes) and accumulates
-// sum_j dZ_j/drho * H[j][p] and sum_j dZ_j/dtheta * H[j][p].
+// One thread per point: walks every |m| column (Taylor lanes k <= 1, or k <= 2 with HESS) and
+// accumulates, with H[j][p] = sum_s C[j, s] G[p, s],
+//   grad_r  = sum_j dZ_j/drho H,        grad_theta = sum_j dZ_j/dtheta H,
+//   and with HESS the point's 2x2 Hessian block of L = <G, F>:
+//   hess_rr = sum_j d2Z_j/drho2 H,  hess_rt = sum_j d2Z_j/drho dtheta H,  hess_tt = sum_j d2Z_j/dtheta2 H.
+// (The Hessian of L in the point coordinates is block diagonal: r_p and theta_p only enter row p.)
+template <bool HESS>
 __global__ void __launch_bounds__(kRedThreads)
 adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* __restrict__ table,
                      const int32_t* __restrict__ slot_ptr, const int32_t* __restrict__ slot_idx,
                      const double* __restrict__ r, const double* __restrict__ theta, int64_t P,
-                     const double* __restrict__ H, double* grad_r, double* grad_theta) {
+                     const double* __restrict__ H, double* grad_r, double* grad_theta, double* hess_rr,
+                     double* hess_rt, double* hess_tt) {
   const int64_t p = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
   if (p >= P) return;
   const double rho = r[p], u = rho * rho, th = theta[p];
-  double acc_r = 0.0, acc_t = 0.0;
+  double acc_r = 0.0, acc_t = 0.0, acc_rr = 0.0, acc_rt = 0.0, acc_tt = 0.0;
   for (int c = 0; c < n_cols; ++c) {
     const Column col = cols[c];
     const int m = col.m;
@@ -52,19 +58,22 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
     const int32_t* sp = slot_ptr + col.slot_base;
     double cs = 1.0, sn = 0.0;
     if (m != 0) sincos((double)m * th, &sn, &cs);
-    // Seeds (Taylor lanes k = 0, 1): N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
-    const double pm1 = m >= 1 ? pow_uint_r(rho, m - 1) : 0.0;
+    // Seeds of the Taylor lanes: N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
+    const double pm2 = m >= 2 ? pow_uint_r(rho, m - 2) : 0.0;
+    const double pm1 = m >= 2 ? pm2 * rho : (m == 1 ? 1.0 : 0.0);
     const double pm = m >= 1 ? pm1 * rho : 1.0;
-    double T0 = pm, T1 = h[1] * pm1;
+    double T0 = pm, T1 = h[1] * pm1, T2 = HESS ? h[2] * pm2 : 0.0;
     double S0 = fma(h[4], pm * u, -(h[8] * pm));
     double S1 = fma(h[5], pm * rho, -(h[9] * pm1));
+    double S2 = HESS ? fma(h[6], pm, -(h[10] * pm2)) : 0.0;
     const double md = (double)m;
-    auto accumulate = [&](int N, double v0, double v1) {
+    auto accumulate = [&](int N, double v0, double v1, double v2) {
       const int sb = sp[N], se = sp[N + 1];
       if (sb == se) return;
       const double* row = h + (size_t)(kHeaderRows + N) * kRow;
       const double zero = row[7];  // 0.0: products issue as DFMA, faster than DMUL on GB300
       const double R0 = fma(row[3], v0, zero), R1 = fma(row[4], v1, zero);
+      const double R2 = HESS ? fma(row[5], v2, zero) : 0.0;
       for (int s = sb; s < se; ++s) {
         const uint32_t code = (uint32_t)__ldg(slot_idx + s);
         const int64_t j = (int64_t)(code & 0x7fffffffu);
@@ -74,26 +83,42 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
         const double dt = is_sin ? md * cs : -md * sn;
         acc_r = fma(fma(R1, f, zero), hv, acc_r);
         acc_t = fma(fma(R0, dt, zero), hv, acc_t);
+        if constexpr (HESS) {
+          acc_rr = fma(fma(R2, f, zero), hv, acc_rr);
+          acc_rt = fma(fma(R1, dt, zero), hv, acc_rt);
+          acc_tt = fma(fma(R0, -md * md * f, zero), hv, acc_tt);
+        }
       }
     };
-    accumulate(0, T0, T1);
+    accumulate(0, T0, T1, T2);
     if (col.n_steps < 2) continue;
-    accumulate(1, S0, S1);
+    accumulate(1, S0, S1, S2);
     for (int N = 2; N < col.n_steps; ++N) {
       const double* row = h + (size_t)(kHeaderRows + N) * kRow;
       const double A = row[0], B = row[1], A2 = row[2];
       const double g = fma(A, u, -B);
+      const double hg = fma(A2, rho, row[7]);
       const double n0 = fma(g, S0, -T0);
-      const double n1 = fma(g, S1, fma(fma(A2, rho, row[7]), S0, -T1));
+      const double n1 = fma(g, S1, fma(hg, S0, -T1));
+      if constexpr (HESS) {
+        const double n2 = fma(g, S2, fma(hg, S1, fma(A, S0, -T2)));
+        T2 = S2;
+        S2 = n2;
+      }
       T0 = S0;
       T1 = S1;
       S0 = n0;
       S1 = n1;
-      accumulate(N, S0, S1);
+      accumulate(N, S0, S1, S2);
     }
   }
   if (grad_r) grad_r[p] = acc_r;
   if (grad_theta) grad_theta[p] = acc_t;
+  if constexpr (HESS) {
+    if (hess_rr) hess_rr[p] = acc_rr;
+    if (hess_rt) hess_rt[p] = acc_rt;
+    if (hess_tt) hess_tt[p] = acc_tt;
+  }
 }
 
 struct CublasHandles {
@@ -185,9 +210,10 @@ zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* t
 
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs, double* grad_r,
-                              double* grad_theta, cudaStream_t stream) {
+                              double* grad_theta, cudaStream_t stream, double* hess_rr, double* hess_rt,
+                              double* hess_tt) {
   const int64_t J = plan->n_modes;
-  const bool need_h = grad_r || grad_theta;
+  const bool need_h = grad_r || grad_theta || hess_rr || hess_rt || hess_tt;
   ScratchBuffer z, hbuf;
   CublasLock cl;
   if (grad_coeffs) {
@@ -205,9 +231,14 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
     //   G column-major S x P -> op T; C column-major S x J -> op N.
     ZP_TRY(dgemm(cl.h, true, false, P, J, S, G, S, coeffs, S, (double*)hbuf.ptr, P));
     const int64_t blocks = (P + kRedThreads - 1) / kRedThreads;
-    adjoint_point_kernel<<<(unsigned)blocks, kRedThreads, 0, stream>>>(
-        plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
-        (const double*)hbuf.ptr, grad_r, grad_theta);
+    if (hess_rr || hess_rt || hess_tt)
+      adjoint_point_kernel<true><<<(unsigned)blocks, kRedThreads, 0, stream>>>(
+          plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
+          (const double*)hbuf.ptr, grad_r, grad_theta, hess_rr, hess_rt, hess_tt);
+    else
+      adjoint_point_kernel<false><<<(unsigned)blocks, kRedThreads, 0, stream>>>(
+          plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
+          (const double*)hbuf.ptr, grad_r, grad_theta, nullptr, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "adjoint_point_kernel launch");
   }
@@ -294,6 +325,43 @@ zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const dou
   }
   ZP_TRY(check_device_array(grad_out, "grad_out", 8));
   return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st);
+}
+
+zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                       const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_r,
+                                       double* grad_theta, double* hess_rr, double* hess_rt, double* hess_tt,
+                                       void* stream) {
+  clear_error();
+  ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
+  double* outs[5] = {grad_r, grad_theta, hess_rr, hess_rt, hess_tt};
+  const char* names[5] = {"grad_r", "grad_theta", "hess_rr", "hess_rt", "hess_tt"};
+  for (int i = 0; i < 5; ++i)
+    if (outs[i]) ZP_TRY(check_device_array(outs[i], names[i], 8));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t J = plan->n_modes, P = n_points, S = n_sets;
+  if (P == 0) return ZP_OK;
+  if (J == 0 || S == 0) {
+    for (int i = 0; i < 5; ++i) {
+      if (!outs[i]) continue;
+      cudaError_t e = cudaMemsetAsync(outs[i], 0, (size_t)P * 8, st);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    }
+    return ZP_OK;
+  }
+  ZP_TRY(check_device_array(grad_out, "grad_out", 8));
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, nullptr, grad_r, grad_theta, st, hess_rr, hess_rt,
+                             hess_tt);
+}
+
+zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+                                  const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
+                                  const double* grad_out, double* grad_r, double* grad_theta, double* hess_rr,
+                                  double* hess_rt, double* hess_tt, void* stream) {
+  clear_error();
+  const zp_plan* plan = nullptr;
+  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  return zp_series_point_hessian_plan(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_r, grad_theta, hess_rr,
+                                      hess_rt, hess_tt, stream);
 }
 
 zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,

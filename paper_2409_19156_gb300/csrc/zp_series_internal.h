@@ -19,9 +19,11 @@ struct ScratchBuffer {
 
 zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                            const double* coeffs, int64_t S, double* out, cudaStream_t stream);
+// hess_*: NULL, or [P] outputs of the per-point Hessian blocks of L = <G, F>.
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
-                              double* grad_r, double* grad_theta, cudaStream_t stream);
+                              double* grad_r, double* grad_theta, cudaStream_t stream,
+                              double* hess_rr = nullptr, double* hess_rt = nullptr, double* hess_tt = nullptr);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
 // Caller-provided scratch for the split path: `b` holds the split coefficient tiles,
 // `a` the split basis of as many point tiles as fit (at least one).

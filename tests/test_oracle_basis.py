@@ -130,3 +130,46 @@ def test_adjoint_is_the_derivative_of_the_series():
         tp[p] += h
         tm[p] -= h
         assert abs(float((loss(r, tp) - loss(r, tm)) / (2 * h)) - gt[p]) < 1e-7
+
+
+def test_mixed_derivatives_against_exact_differences():
+    """basis_deriv(kr, kt) against exact central differences of lower derivatives."""
+    h = 2.0 ** -28
+    for n, m in [(7, 3), (7, -3), (10, 0), (12, -4)]:
+        r, th = 0.61, 1.7
+        # d2/dtheta2 from d/dtheta
+        fd = (Fraction(basis.basis_deriv(n, m, r, th + h, 0, 1)) - Fraction(basis.basis_deriv(n, m, r, th - h, 0, 1))) / (2 * h)
+        assert abs(float(fd) - basis.basis_deriv(n, m, r, th, 0, 2)) < 1e-6
+        # d2/drho dtheta from d/dtheta in rho
+        fd = (Fraction(basis.basis_deriv(n, m, r + h, th, 0, 1)) - Fraction(basis.basis_deriv(n, m, r - h, th, 0, 1))) / (2 * h)
+        assert abs(float(fd) - basis.basis_deriv(n, m, r, th, 1, 1)) < 1e-6
+        # consistency with the basis table and d/dtheta
+        assert basis.basis_deriv(n, m, r, th, 0, 1) == basis.basis_dtheta(n, m, r, th)
+        assert basis.basis_deriv(n, m, r, th, 2, 0) == basis.basis_value(n, m, r, th, 2)
+
+
+def test_point_hessian_is_the_derivative_of_the_gradient():
+    """The oracle's per-point Hessian against exact central differences of its gradient."""
+    ns, ms = inputs.full_zernike_modes(4)
+    r, th = inputs.uniform_points(3, 12)
+    C = inputs.scaled_normal_coeffs(ns, 2, 12).tolist()
+    G = np.random.default_rng(4).standard_normal((3, 2)).tolist()
+    gr, gt, hrr, hrt, htt = series.point_hessian(ns, ms, r, th, C, G)
+    _, gr0, gt0 = series.series_adjoint(ns, ms, r, th, C, G)
+    assert gr == gr0 and gt == gt0
+    h = 2.0 ** -26
+    for p in range(3):
+        rp, rm = r.copy(), r.copy()
+        rp[p] += h
+        rm[p] -= h
+        a = series.series_adjoint(ns, ms, rp, th, C, G)
+        b = series.series_adjoint(ns, ms, rm, th, C, G)
+        assert abs((a[1][p] - b[1][p]) / (2 * h) - hrr[p]) < 1e-6 * (1 + abs(hrr[p]))
+        assert abs((a[2][p] - b[2][p]) / (2 * h) - hrt[p]) < 1e-6 * (1 + abs(hrt[p]))
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        a = series.series_adjoint(ns, ms, r, tp, C, G)
+        b = series.series_adjoint(ns, ms, r, tm, C, G)
+        assert abs((a[2][p] - b[2][p]) / (2 * h) - htt[p]) < 1e-6 * (1 + abs(htt[p]))
+        assert abs((a[1][p] - b[1][p]) / (2 * h) - hrt[p]) < 1e-6 * (1 + abs(hrt[p]))  # symmetry
