@@ -420,10 +420,23 @@ def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_f
         d = F_keep[i:i + (1 << 17)].double() - F64[i:i + (1 << 17)]
         num += float((d * d).sum())
         den += float((F64[i:i + (1 << 17)] ** 2).sum())
+    # float64-accurate contraction emulated on the tensor cores (error-free slicing)
+    del F_keep
+    Fe = torch.empty((P, S), dtype=torch.float64, device=dev)
+    emu = lambda: _lib.check("zp_series_eval_plan", lib.zp_series_eval_plan(  # noqa: E731
+        plan.handle, rt.data_ptr(), tt.data_ptr(), P, Ct.data_ptr(), S, 4, Fe.data_ptr(), sp))
+    emu()
+    t_emu = _events_ms(stream, emu, 1)
+    out["fp64_emulated_ms"] = t_emu
+    out["fp64_emulated_max_abs_diff_vs_dgemm"] = max(float((Fe[i:i + (1 << 17)] - F64[i:i + (1 << 17)]).abs().max())
+                                                     for i in range(0, P, 1 << 17))
+    out["speedup_fp64_emulated_vs_dgemm"] = t64 / t_emu
+    del Fe
+    F_keep = None
     out["fp64_basis_then_dgemm_ms"] = t64
     out["speedup_bf16x3_vs_fp64"] = t64 / out["bf16x3"]["ms_per_call"]
     out["bf16x3_rel_frobenius_vs_fp64"] = math.sqrt(num / den)
-    del F64, F_keep, F
+    del F64, F
     torch.cuda.empty_cache()
     return out
 
@@ -446,6 +459,8 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     zp.series_eval(None, None, rt, tt, Ct, plan=plan)
     zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
     fwd = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, plan=plan), steps)
+    zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan)
+    fwd_emu = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan), steps)
     adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan), steps)
     # Least-squares fit of the same coefficients back from the series values, with the
     # grid's exact quadrature weights (Gauss-Legendre in r^2 x uniform theta).
@@ -460,7 +475,8 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
         zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
     fit_ms = (time.perf_counter() - t0) * 1e3 / steps  # the fit synchronises its stream
     return {"workload": "series_n24", "modes": len(ns), "points": len(r), "sets": C.shape[1],
-            "fp64_forward_ms": fwd, "fp64_adjoint_ms": adj, "fp64_fit_ms": fit_ms,
+            "fp64_forward_ms": fwd, "fp64_emulated_forward_ms": fwd_emu, "fp64_adjoint_ms": adj,
+            "fp64_fit_ms": fit_ms,
             "fit_roundtrip_max_abs_err": float((Cfit - Ct).abs().max())}
 
 

@@ -62,8 +62,12 @@ typedef enum {
                          with bfloat16 halves and float32 accumulation; outputs float32 */
   ZP_PREC_TF32 = 2,   /* float64 basis rounded to TF32, tensor-core contraction with float32
                          accumulation; outputs float32 */
-  ZP_PREC_FP32 = 3    /* float64 basis rounded to float32, float32 contraction on the CUDA
+  ZP_PREC_FP32 = 3,   /* float64 basis rounded to float32, float32 contraction on the CUDA
                          cores; outputs float32 (batched forward only) */
+  ZP_PREC_FP64_EMULATED = 4 /* float64-accurate contraction on the tensor cores: rows of Z and
+                         columns of C scaled by powers of two and cut into small-integer bf16
+                         slices (error-free), exact float32 sums per slice diagonal, float64
+                         recombination; outputs float64 (zp_series_eval only, <= 4672 modes) */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */

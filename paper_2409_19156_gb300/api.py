@@ -17,7 +17,7 @@ import torch
 
 from . import _lib
 
-PREC = {"fp64": 0, "bf16x3": 1, "tf32": 2}
+PREC = {"fp64": 0, "bf16x3": 1, "tf32": 2, "fp64emu": 4}
 
 
 def _stream(device: torch.device) -> ctypes.c_void_p:
@@ -122,7 +122,7 @@ def series_eval(n, m, r, theta, coeffs, prec: str = "fp64", plan: Plan | None = 
     if coeffs.dim() != 2 or coeffs.shape[0] != J:
         raise ValueError("coeffs must be [n_modes, n_sets]")
     S = coeffs.shape[1]
-    dtype = torch.float64 if prec == "fp64" else torch.float32
+    dtype = torch.float64 if prec in ("fp64", "fp64emu") else torch.float32
     out = torch.empty((P, S), dtype=dtype, device=r.device)
     st = _stream(r.device)
     with torch.cuda.device(r.device):

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <utility>
 #include <vector>
@@ -41,13 +42,17 @@ constexpr uint32_t kBPart = BN * kRowBytes;  // 32 KB
 constexpr int kGemmThreads = 192;            // 6 warps: producer, MMA, 4 x epilogue
 constexpr int kCoeffThreads = BN;
 
-template <bool TF32>
+// Operand kinds of the GEMM: BF16x3 (hi/lo halves, three products), TF32 (one product),
+// SLICE (one bf16 product of integer-valued slices, for the emulated-float64 contraction).
+constexpr int KIND_BF16X3 = 0, KIND_TF32 = 1, KIND_SLICE = 2;
+
+template <int KIND>
 struct Cfg {
-  static constexpr int BK = TF32 ? 32 : 64;  // K elements per 128-byte row
-  static constexpr int PARTS = TF32 ? 1 : 2;  // hi (+ lo)
+  static constexpr int BK = KIND == KIND_TF32 ? 32 : 64;  // K elements per 128-byte row
+  static constexpr int PARTS = KIND == KIND_BF16X3 ? 2 : 1;  // hi (+ lo)
   static constexpr uint32_t A_CHUNK = kAPart * PARTS;
   static constexpr uint32_t B_CHUNK = kBPart * PARTS;
-  static constexpr int STAGES = TF32 ? 4 : 2;
+  static constexpr int STAGES = PARTS == 2 ? 2 : 4;
   static constexpr uint32_t STAGE = A_CHUNK + B_CHUNK;
   static constexpr int KSTEPS = 4;  // MMA K-steps per chunk (16 bf16 or 8 tf32 = 32 bytes each)
   static constexpr uint32_t SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(basis_threads<TF32>()) split_basis_kernel(Basi
 
 template <bool TF32>
 __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t tile) {
-  using C = Cfg<TF32>;
+  using C = Cfg<TF32 ? KIND_TF32 : KIND_BF16X3>;
   constexpr int UNIT = TF32 ? 4 : 8;  // K values per 16-byte unit
   constexpr int Q = basis_ppt<TF32>();
   uint32_t rowi[Q];
@@ -271,7 +276,7 @@ struct CoeffArgs {
 
 template <bool TF32>
 __global__ void __launch_bounds__(kCoeffThreads) split_coeff_kernel(CoeffArgs a) {
-  using C = Cfg<TF32>;
+  using C = Cfg<TF32 ? KIND_TF32 : KIND_BF16X3>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   const int nt = blockIdx.x / a.KC, kc = blockIdx.x % a.KC;
@@ -302,14 +307,19 @@ __global__ void __launch_bounds__(kCoeffThreads) split_coeff_kernel(CoeffArgs a)
 }
 
 struct GemmArgs {
-  const uint8_t* A;  // slab: [tiles][KC][A_CHUNK]
-  const uint8_t* B;  // [NT][KC][B_CHUNK]
+  const uint8_t* A;  // slab: [tiles][KC][A_CHUNK] (slice 0 for KIND_SLICE)
+  const uint8_t* B;  // [NT][KC][B_CHUNK] (slice 0 for KIND_SLICE)
   float* F;          // [P][S]
   int64_t P, S;
   int64_t mt_base;
   int64_t m_tiles;  // tiles in this slab
   int n_tiles;      // NT
   int KC;
+  // KIND_SLICE: the tile's K runs over npairs slice pairs (t, u) with t + u = npairs - 1
+  // (0-based), KC chunks each; A slice t starts a_slice_stride bytes after slice t-1, B likewise.
+  int npairs = 1;
+  int64_t a_slice_stride = 0;
+  int64_t b_slice_stride = 0;
 };
 
 // CL = 1: one CTA per tile.  CL = 2: CTA pairs (a cluster of two) work on two point tiles of
@@ -317,9 +327,10 @@ struct GemmArgs {
 // a cluster-multicast bulk copy writes into both CTAs' shared memory, so B crosses L2 once per
 // pair.  A stage is refilled only after both CTAs' MMAs have released it (the MMA commit
 // arrives on the "empty" barrier of both CTAs).
-template <bool TF32, int CL>
+template <int KIND, int CL>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a) {
-  using C = Cfg<TF32>;
+  using C = Cfg<KIND>;
+  constexpr bool TF32 = KIND == KIND_TF32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
@@ -372,13 +383,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         // A pair's second tile past the slab end reuses the last valid tile's data (its rows
         // are never stored); it still takes part in the shared B loads.
         const int64_t mt_src = mt < a.m_tiles ? mt : a.m_tiles - 1;
-        const uint8_t* gA = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
-        const uint8_t* gB = a.B + (size_t)nt * a.KC * C::B_CHUNK;
-        for (int kc = 0; kc < a.KC; ++kc) {
+        const uint8_t* gA0 = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
+        const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
+        for (int kk = 0; kk < a.npairs * a.KC; ++kk) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
             break;
           }
+          const int t = kk / a.KC, kc = kk % a.KC;
+          const uint8_t* gA = gA0 + (size_t)t * a.a_slice_stride;
+          const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - t) * a.b_slice_stride;
           uint8_t* sA = smem + stage * C::STAGE;
           ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
           ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * BN;
         bool ok = true;
-        for (int kc = 0; kc < a.KC; ++kc) {
+        for (int kk = 0; kk < a.npairs * a.KC; ++kk) {
           if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
             fail();
             ok = false;
@@ -424,9 +438,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
 #pragma unroll
           for (int ks = 0; ks < C::KSTEPS; ++ks) {
             const uint32_t koff = ks * 32;
-            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+            const uint32_t first = (kk == 0 && ks == 0) ? 0u : 1u;
             if constexpr (TF32) {
               ptx::mma_tf32(d_tmem, ptx::sw128_kmajor_desc(sA + koff), ptx::sw128_kmajor_desc(sB + koff), idesc,
+                            first);
+            } else if constexpr (KIND == KIND_SLICE) {
+              ptx::mma_bf16(d_tmem, ptx::sw128_kmajor_desc(sA + koff), ptx::sw128_kmajor_desc(sB + koff), idesc,
                             first);
             } else {
               const uint64_t ah = ptx::sw128_kmajor_desc(sA + koff);
@@ -552,7 +569,7 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   timer.ms = phase_ms;
   timer.stream = stream;
   cudaEvent_t ev0;
-  using C = Cfg<TF32>;
+  using C = Cfg<TF32 ? KIND_TF32 : KIND_BF16X3>;
   const int64_t J = plan->n_modes;
   const int KC = (int)((J + C::BK - 1) / C::BK);
   const int64_t MT = (P + BM - 1) / BM;
@@ -588,9 +605,9 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
           cudaSuccess)
     return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
   // CTA pairs when the GPU can co-schedule them (the occupancy query says how many pairs fit).
@@ -607,7 +624,7 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     at[0].val.clusterDim.z = 1;
     q.attrs = at;
     q.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<TF32, 2>, &q) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, &q) != cudaSuccess) {
       cudaGetLastError();
       pairs = 0;
     }
@@ -643,10 +660,10 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
       at[0].val.clusterDim.z = 1;
       lc.attrs = at;
       lc.numAttrs = 1;
-      e = cudaLaunchKernelEx(&lc, split_gemm_kernel<TF32, 2>, ga);
+      e = cudaLaunchKernelEx(&lc, split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, ga);
     } else {
       const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT, sms);
-      split_gemm_kernel<TF32, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+      split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
@@ -655,7 +672,251 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   return timer.finish();
 }
 
+// ---------------------------------------------------------------------------------------
+// Float64-accurate contraction emulated on the tensor cores (Ozaki-style error-free slicing,
+// a published scheme): rows of Z and columns of C are scaled by powers of two into [-1, 1]
+// and cut into s slices of beta bits, x = sum_t a_t 2^(-beta t) with every a_t an integer of
+// at most beta bits (exact in bfloat16).  For each slice diagonal d = t + u the GEMM sums all
+// pairs (t, u) along a concatenated K into float32; every partial sum is an integer below
+// 2^24, so it is exact.  A float64 pass forms F = sigma_p sigma_s sum_d 2^(-beta d) T_d.
+// Pairs with t + u > s + 1 are dropped (their total is below 2^(-beta s) of the scale).
+
+struct SliceParams {
+  int beta = 6, s = 9;
+};
+
+// beta and the slice count for a padded K, so that npairs * K * 2^(2 beta) < 2^24 holds for
+// every diagonal (npairs <= s): exact float32 accumulation.
+bool choose_slices(int64_t k_pad, SliceParams* sp) {
+  const struct {
+    int beta, s;
+  } opts[] = {{6, 9}, {5, 11}, {4, 14}};
+  for (auto o : opts) {
+    if ((double)o.s * (double)k_pad * std::ldexp(1.0, 2 * o.beta) < 16777216.0) {
+      sp->beta = o.beta;
+      sp->s = o.s;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Power-of-two scale per point: 2^e >= max_j |Z[j][p]| (1 for an all-zero row).
+__global__ void row_scale_kernel(const double* __restrict__ Z, int64_t J, int64_t P, double* __restrict__ scale) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double mx = 0.0;
+  for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(Z[j * P + p]));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  scale[p] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+}
+
+// Power-of-two scale per coefficient set: 2^e >= max_j |C[j][s]|.
+__global__ void col_scale_kernel(const double* __restrict__ C, int64_t J, int64_t S, double* __restrict__ scale) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double mx = 0.0;
+  for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(C[j * S + s]));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  scale[s] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+}
+
+// Cuts 8 consecutive K values x[0..7] (already scaled into [-1, 1]) into `s` slices and writes
+// each slice's 16-byte unit at `dst + t * slice_stride` (bf16 integers of at most beta bits).
+__device__ __forceinline__ void cut_slices(double (&x)[8], int beta, int s, uint8_t* dst, int64_t slice_stride) {
+  const double up = ldexp(1.0, beta);
+  for (int t = 0; t < s; ++t) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double y0 = x[2 * i] * up, y1 = x[2 * i + 1] * up;
+      const double a0 = rint(y0), a1 = rint(y1);
+      x[2 * i] = y0 - a0;  // exact: y has at most 53 significant bits and a is its nearest integer
+      x[2 * i + 1] = y1 - a1;
+      const uint32_t h0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)a0));
+      const uint32_t h1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)a1));
+      w[i] = h0 | (h1 << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + (size_t)t * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// A slices of one slab: thread = (point row of the slab, group of 8 consecutive modes).
+__global__ void slice_a_kernel(const double* __restrict__ Z, const double* __restrict__ scale, int64_t J,
+                               int64_t Ps, int64_t tiles, int KC, SliceParams sp, uint8_t* A, int64_t slice_stride) {
+  const int64_t groups = (int64_t)KC * 8;  // 8-mode groups per row
+  const int64_t total = tiles * BM * groups;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % (tiles * BM);  // point fastest: coalesced reads of Z[j][p]
+    const int64_t g = i / (tiles * BM);
+    const int64_t j0 = g * 8;
+    const double inv = p < Ps ? 1.0 / scale[p] : 0.0;  // a power of two: exact
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (p < Ps && j0 + q < J) ? Z[(j0 + q) * Ps + p] * inv : 0.0;
+    const int64_t tile = p / BM;
+    const uint32_t row = (uint32_t)(p % BM);
+    const int kc = (int)(j0 / 64);
+    uint8_t* dst = A + ((size_t)tile * KC + kc) * kAPart + ptx::sw128_offset_b16(row, (uint32_t)(j0 % 64));
+    cut_slices(x, sp.beta, sp.s, dst, slice_stride);
+  }
+}
+
+// B slices: thread = (set, group of 8 consecutive modes).
+__global__ void slice_b_kernel(const double* __restrict__ C, const double* __restrict__ scale, int64_t J, int64_t S,
+                               int NT, int KC, SliceParams sp, uint8_t* B, int64_t slice_stride) {
+  const int64_t rows = (int64_t)NT * BN;
+  const int64_t total = rows * KC * 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sidx = i % rows;
+    const int64_t j0 = (i / rows) * 8;
+    const double inv = sidx < S ? 1.0 / scale[sidx] : 0.0;
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (sidx < S && j0 + q < J) ? C[(j0 + q) * S + sidx] * inv : 0.0;
+    const int64_t nt = sidx / BN;
+    const uint32_t row = (uint32_t)(sidx % BN);
+    const int kc = (int)(j0 / 64);
+    uint8_t* dst = B + ((size_t)nt * KC + kc) * kBPart + ptx::sw128_offset_b16(row, (uint32_t)(j0 % 64));
+    cut_slices(x, sp.beta, sp.s, dst, slice_stride);
+  }
+}
+
+// F[p][s] = sigma_p sigma_s sum_{d=2}^{s+1} 2^(-beta d) T_d[p][s], smallest terms first.
+__global__ void recombine_kernel(const float* __restrict__ T, int64_t diag_stride, int ndiag, int beta,
+                                 const double* __restrict__ rscale, const double* __restrict__ cscale, int64_t Ps,
+                                 int64_t S, double* __restrict__ F) {
+  const int64_t n = Ps * S;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = ndiag - 1; q >= 0; --q) acc = fma(ldexp(1.0, -beta * (q + 2)), (double)T[(size_t)q * diag_stride + i], acc);
+    F[i] = acc * rscale[i / S] * cscale[i % S];
+  }
+}
+
+template <int KIND>
+zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, int sms, int pairs, cudaStream_t stream) {
+  using C = Cfg<KIND>;
+  cudaError_t e;
+  if (pairs > 0 && tiles >= 2) {
+    const int64_t groups = ((tiles + 1) / 2) * NT;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(2 * (unsigned)std::min<int64_t>(groups, pairs));
+    lc.blockDim = dim3(kGemmThreads);
+    lc.dynamicSmemBytes = C::SMEM;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, 2>, ga);
+  } else {
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT, sms);
+    split_gemm_kernel<KIND, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "split_gemm_kernel launch");
+}
+
+template <int KIND>
+int gemm_pairs(int sms) {
+  using C = Cfg<KIND>;
+  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(split_gemm_kernel<KIND, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int pairs = 0;
+  cudaLaunchConfig_t q = {};
+  q.gridDim = dim3(2 * (unsigned)sms);
+  q.blockDim = dim3(kGemmThreads);
+  q.dynamicSmemBytes = C::SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  q.attrs = at;
+  q.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<KIND, 2>, &q) != cudaSuccess) {
+    cudaGetLastError();
+    pairs = 0;
+  }
+  return pairs;
+}
+
+zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                            const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
+  using C = Cfg<KIND_SLICE>;
+  const int64_t J = plan->n_modes;
+  const int KC = (int)((J + C::BK - 1) / C::BK);
+  const int64_t MT = (P + BM - 1) / BM;
+  const int NT = (int)((S + BN - 1) / BN);
+  SliceParams sp;
+  if (!choose_slices((int64_t)KC * C::BK, &sp))
+    return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 contraction supports at most 4672 modes");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int pairs = gemm_pairs<KIND_SLICE>(sms);
+  if (pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+  // Slab of point tiles: float32 diagonal sums (s x rows x S x 4 B) within about 4 GB.
+  const size_t tdiag_tile = (size_t)BM * S * sizeof(float);
+  const int64_t slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / (sp.s * tdiag_tile))));
+  const int64_t rows = slab * BM;
+  const int64_t a_stride = slab * KC * (int64_t)C::A_CHUNK;
+  const int64_t b_stride = (int64_t)NT * KC * C::B_CHUNK;
+  ScratchBuffer zbuf, rsc, csc, abuf, bbuf, tbuf;
+  ZP_TRY(zbuf.alloc((size_t)J * rows * sizeof(double), stream));
+  ZP_TRY(rsc.alloc((size_t)rows * sizeof(double), stream));
+  ZP_TRY(csc.alloc((size_t)S * sizeof(double), stream));
+  ZP_TRY(abuf.alloc((size_t)sp.s * a_stride, stream));
+  ZP_TRY(bbuf.alloc((size_t)sp.s * b_stride, stream));
+  ZP_TRY(tbuf.alloc((size_t)sp.s * rows * S * sizeof(float), stream));
+  cudaError_t e;
+  col_scale_kernel<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(coeffs, J, S, (double*)csc.ptr);
+  slice_b_kernel<<<1024, 256, 0, stream>>>(coeffs, (const double*)csc.ptr, J, S, NT, KC, sp, (uint8_t*)bbuf.ptr,
+                                           b_stride);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "coefficient slicing launch");
+  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
+    const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
+    const int64_t p0 = mt0 * BM;
+    const int64_t Ps = std::min<int64_t>(tiles * BM, P - p0);
+    ZP_TRY(launch_walk(plan, r + p0, theta + p0, Ps, 0, (double*)zbuf.ptr, nullptr, stream));
+    row_scale_kernel<<<(unsigned)((Ps + 127) / 128), 128, 0, stream>>>((const double*)zbuf.ptr, J, Ps,
+                                                                      (double*)rsc.ptr);
+    slice_a_kernel<<<2048, 256, 0, stream>>>((const double*)zbuf.ptr, (const double*)rsc.ptr, J, Ps, tiles, KC, sp,
+                                             (uint8_t*)abuf.ptr, slab * KC * (int64_t)C::A_CHUNK);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "basis slicing launch");
+    for (int d = 2; d <= sp.s + 1; ++d) {
+      GemmArgs ga{(const uint8_t*)abuf.ptr, (const uint8_t*)bbuf.ptr,
+                  (float*)tbuf.ptr + (size_t)(d - 2) * rows * S, Ps, S, 0, tiles, NT, KC};
+      ga.npairs = d - 1;
+      ga.a_slice_stride = a_stride;
+      ga.b_slice_stride = b_stride;
+      ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, NT, sms, pairs, stream));
+    }
+    recombine_kernel<<<2048, 256, 0, stream>>>((const float*)tbuf.ptr, rows * S, sp.s, sp.beta,
+                                               (const double*)rsc.ptr, (const double*)csc.ptr, Ps, S,
+                                               out + (size_t)p0 * S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "recombine_kernel launch");
+  }
+  return ZP_OK;
+}
+
 }  // namespace
+
+zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                                    const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
+  return run_emulated_fp64(plan, r, theta, P, coeffs, S, out, stream);
+}
 
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                             const double* coeffs, int64_t S, zp_precision prec, float* out, cudaStream_t stream,
@@ -666,9 +927,9 @@ zp_status series_eval_split(const zp_plan* plan, const double* r, const double* 
 
 size_t split_scratch_bytes(zp_precision prec, int64_t n_modes, int64_t n_sets, size_t* b_bytes, size_t* tile_bytes) {
   const bool tf32 = prec == ZP_PREC_TF32;
-  const int64_t bk = tf32 ? Cfg<true>::BK : Cfg<false>::BK;
-  const size_t a_chunk = tf32 ? Cfg<true>::A_CHUNK : Cfg<false>::A_CHUNK;
-  const size_t b_chunk = tf32 ? Cfg<true>::B_CHUNK : Cfg<false>::B_CHUNK;
+  const int64_t bk = tf32 ? Cfg<KIND_TF32>::BK : Cfg<KIND_BF16X3>::BK;
+  const size_t a_chunk = tf32 ? Cfg<KIND_TF32>::A_CHUNK : Cfg<KIND_BF16X3>::A_CHUNK;
+  const size_t b_chunk = tf32 ? Cfg<KIND_TF32>::B_CHUNK : Cfg<KIND_BF16X3>::B_CHUNK;
   const int64_t KC = (n_modes + bk - 1) / bk;
   const int64_t NT = (n_sets + BN - 1) / BN;
   *b_bytes = (size_t)NT * KC * b_chunk;

@@ -266,18 +266,21 @@ extern "C" {
 zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                               const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream) {
   clear_error();
-  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32)
-    return set_error(ZP_ERR_INVALID_ARG, "unknown precision");
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32 && prec != ZP_PREC_FP64_EMULATED)
+    return set_error(ZP_ERR_INVALID_ARG, "unknown precision for zp_series_eval");
+  const bool f64_out = prec == ZP_PREC_FP64 || prec == ZP_PREC_FP64_EMULATED;
   ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
   if (n_points == 0 || n_sets == 0) return ZP_OK;
-  ZP_TRY(check_device_array(out, "out", prec == ZP_PREC_FP64 ? 8 : 16));
+  ZP_TRY(check_device_array(out, "out", f64_out ? 8 : 16));
   cudaStream_t st = (cudaStream_t)stream;
   if (plan->n_modes == 0) {
-    const size_t bytes = (size_t)n_points * n_sets * (prec == ZP_PREC_FP64 ? 8 : 4);
+    const size_t bytes = (size_t)n_points * n_sets * (f64_out ? 8 : 4);
     cudaError_t e = cudaMemsetAsync(out, 0, bytes, st);
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
   }
   if (prec == ZP_PREC_FP64) return series_eval_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
+  if (prec == ZP_PREC_FP64_EMULATED)
+    return series_eval_emulated_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
   return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, st);
 }
 

@@ -25,6 +25,10 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
                               double* grad_r, double* grad_theta, cudaStream_t stream,
                               double* hess_rr = nullptr, double* hess_rt = nullptr, double* hess_tt = nullptr);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
+// Float64-accurate series by error-free slicing on the tensor cores (float64 output).
+zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                                    const double* coeffs, int64_t S, double* out, cudaStream_t stream);
+
 // Caller-provided scratch for the split path: `b` holds the split coefficient tiles,
 // `a` the split basis of as many point tiles as fit (at least one).
 struct SplitScratch {
