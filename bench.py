@@ -296,15 +296,36 @@ def run_ours(args) -> None:
             barrier()
             return max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, dist, dev)
 
+        streams = [torch.cuda.Stream(dev) for _ in range(4)]
+        flat_dev, flat_host = out.view(-1), out_host.view(-1)
+        chunk = (flat_dev.numel() + 3) // 4
+
+        def e2e_multi_copy_step():
+            # inputs H2D, kernel into device memory, result D2H split over four copy streams
+            rt2.copy_(r_host, non_blocking=True)
+            st = lib.zp_radial_plan(plan.handle, rt2.data_ptr(), P, 3, out.data_ptr(), sp)
+            if st:
+                _lib.check("zp_radial_plan", st)
+            done = torch.cuda.Event()
+            done.record(stream)
+            for i, cs in enumerate(streams):
+                cs.wait_event(done)
+                with torch.cuda.stream(cs):
+                    flat_host[i * chunk:(i + 1) * chunk].copy_(flat_dev[i * chunk:(i + 1) * chunk], non_blocking=True)
+            for cs in streams:
+                stream.wait_stream(cs)
+
         t_copy = time_e2e(e2e_copy_step)
+        t_multi = time_e2e(e2e_multi_copy_step)
+        assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
         t_mapped = time_e2e(e2e_mapped_step)
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
-        best, how = (t_copy, "device kernel + D2H copy") if t_copy <= t_mapped else \
-            (t_mapped, "kernel writes pinned host memory directly")
+        best, how = min((t_copy, "device kernel + D2H copy"), (t_multi, "device kernel + D2H on four copy streams"),
+                        (t_mapped, "kernel writes pinned host memory directly"))
         e2e = {"value": aggregate_value(values_per_step, world, best), "unit": UNIT,
                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": out_bytes, "ms_per_step": best, "how": how,
-               "ms_per_step_copy": t_copy, "ms_per_step_mapped": t_mapped}
+               "ms_per_step_copy": t_copy, "ms_per_step_copy4": t_multi, "ms_per_step_mapped": t_mapped}
 
     extras = None
     if rank == 0 and not args.no_extras:

@@ -67,7 +67,7 @@ typedef enum {
   ZP_PREC_FP64_EMULATED = 4 /* float64-accurate contraction on the tensor cores: rows of Z and
                          columns of C scaled by powers of two and cut into small-integer bf16
                          slices (error-free), exact float32 sums per slice diagonal, float64
-                         recombination; outputs float64 (zp_series_eval only, <= 4672 modes) */
+                         recombination; outputs float64 (zp_series_eval only, <= 16320 modes) */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */

@@ -685,14 +685,18 @@ struct SliceParams {
   int beta = 6, s = 9;
 };
 
-// beta and the slice count for a padded K, so that npairs * K * 2^(2 beta) < 2^24 holds for
-// every diagonal (npairs <= s): exact float32 accumulation.
+// beta and the slice count for a padded K such that every float32 partial sum stays an
+// integer below 2^24 (exact).  With |a_1| <= 2^beta and |a_t| <= 2^(beta-1) for t >= 2 (each
+// later slice cuts a remainder of at most 1/2), diagonal d sums K * (2 * 2^beta * 2^(beta-1) +
+// (d-3) * 2^(2 beta - 2)) at most, largest at d = s + 1: K * 2^(2 beta) * (1 + (s-2)/4).
+// Candidates in order of fewest slice pairs (s (s+1) / 2), all with beta * s >= 54 bits.
 bool choose_slices(int64_t k_pad, SliceParams* sp) {
   const struct {
     int beta, s;
-  } opts[] = {{6, 9}, {5, 11}, {4, 14}};
+  } opts[] = {{7, 8}, {6, 9}, {5, 11}, {4, 14}};
   for (auto o : opts) {
-    if ((double)o.s * (double)k_pad * std::ldexp(1.0, 2 * o.beta) < 16777216.0) {
+    const double worst = (double)k_pad * std::ldexp(1.0, 2 * o.beta) * (1.0 + (o.s - 2) / 4.0);
+    if (worst < 16777216.0) {
       sp->beta = o.beta;
       sp->s = o.s;
       return true;
@@ -701,26 +705,26 @@ bool choose_slices(int64_t k_pad, SliceParams* sp) {
   return false;
 }
 
-// Power-of-two scale per point: 2^e >= max_j |Z[j][p]| (1 for an all-zero row).
-__global__ void row_scale_kernel(const double* __restrict__ Z, int64_t J, int64_t P, double* __restrict__ scale) {
+// Power-of-two scale per point: exponent e with 2^e >= max_j |Z[j][p]| (0 for a zero row).
+__global__ void row_scale_kernel(const double* __restrict__ Z, int64_t J, int64_t P, int* __restrict__ expo) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double mx = 0.0;
   for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(Z[j * P + p]));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
-  scale[p] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+  expo[p] = e;
 }
 
-// Power-of-two scale per coefficient set: 2^e >= max_j |C[j][s]|.
-__global__ void col_scale_kernel(const double* __restrict__ C, int64_t J, int64_t S, double* __restrict__ scale) {
+// Power-of-two scale per coefficient set: exponent e with 2^e >= max_j |C[j][s]|.
+__global__ void col_scale_kernel(const double* __restrict__ C, int64_t J, int64_t S, int* __restrict__ expo) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   double mx = 0.0;
   for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(C[j * S + s]));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
-  scale[s] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+  expo[s] = e;
 }
 
 // Cuts 8 consecutive K values x[0..7] (already scaled into [-1, 1]) into `s` slices and writes
@@ -744,7 +748,7 @@ __device__ __forceinline__ void cut_slices(double (&x)[8], int beta, int s, uint
 }
 
 // A slices of one slab: thread = (point row of the slab, group of 8 consecutive modes).
-__global__ void slice_a_kernel(const double* __restrict__ Z, const double* __restrict__ scale, int64_t J,
+__global__ void slice_a_kernel(const double* __restrict__ Z, const int* __restrict__ expo, int64_t J,
                                int64_t Ps, int64_t tiles, int KC, SliceParams sp, uint8_t* A, int64_t slice_stride) {
   const int64_t groups = (int64_t)KC * 8;  // 8-mode groups per row
   const int64_t total = tiles * BM * groups;
@@ -752,7 +756,7 @@ __global__ void slice_a_kernel(const double* __restrict__ Z, const double* __res
     const int64_t p = i % (tiles * BM);  // point fastest: coalesced reads of Z[j][p]
     const int64_t g = i / (tiles * BM);
     const int64_t j0 = g * 8;
-    const double inv = p < Ps ? 1.0 / scale[p] : 0.0;  // a power of two: exact
+    const double inv = p < Ps ? ldexp(1.0, -expo[p]) : 0.0;  // a power of two: exact
     double x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = (p < Ps && j0 + q < J) ? Z[(j0 + q) * Ps + p] * inv : 0.0;
@@ -765,14 +769,14 @@ __global__ void slice_a_kernel(const double* __restrict__ Z, const double* __res
 }
 
 // B slices: thread = (set, group of 8 consecutive modes).
-__global__ void slice_b_kernel(const double* __restrict__ C, const double* __restrict__ scale, int64_t J, int64_t S,
+__global__ void slice_b_kernel(const double* __restrict__ C, const int* __restrict__ expo, int64_t J, int64_t S,
                                int NT, int KC, SliceParams sp, uint8_t* B, int64_t slice_stride) {
   const int64_t rows = (int64_t)NT * BN;
   const int64_t total = rows * KC * 8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sidx = i % rows;
     const int64_t j0 = (i / rows) * 8;
-    const double inv = sidx < S ? 1.0 / scale[sidx] : 0.0;
+    const double inv = sidx < S ? ldexp(1.0, -expo[sidx]) : 0.0;
     double x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = (sidx < S && j0 + q < J) ? C[(j0 + q) * S + sidx] * inv : 0.0;
@@ -784,15 +788,39 @@ __global__ void slice_b_kernel(const double* __restrict__ C, const double* __res
   }
 }
 
-// F[p][s] = sigma_p sigma_s sum_{d=2}^{s+1} 2^(-beta d) T_d[p][s], smallest terms first.
+// Exact float32 -> float64 of an integer-valued float by bit assembly (integer pipe; the
+// float64 pipe is the scarce one on GB300).  |v| < 2^24, so the value is normal or zero.
+__device__ __forceinline__ double int_float_to_double(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e8 = (b >> 23) & 0xffu;
+  const uint32_t hi = (b & 0x80000000u) | ((e8 + 896u) << 20) | ((b >> 3) & 0x000fffffu);
+  const uint32_t lo = b << 29;
+  return e8 ? __hiloint2double((int)hi, (int)lo) : 0.0;
+}
+
+// Multiplies a float64 by 2^e by adding e to its exponent field (integer pipe); x == 0 stays 0.
+// The scales keep |F| far inside the normal range, so no over- or underflow handling is needed.
+__device__ __forceinline__ double times_pow2(double x, int e) {
+  if (x == 0.0) return 0.0;
+  const int hi = __double2hiint(x) + (e << 20);
+  return __hiloint2double(hi, __double2loint(x));
+}
+
+// F[p][s] = sigma_p sigma_s sum_{d=2}^{s+1} 2^(-beta d) T_d[p][s], smallest terms first: one
+// float64 FMA per diagonal; conversions and the power-of-two scales on the integer pipe.
 __global__ void recombine_kernel(const float* __restrict__ T, int64_t diag_stride, int ndiag, int beta,
-                                 const double* __restrict__ rscale, const double* __restrict__ cscale, int64_t Ps,
-                                 int64_t S, double* __restrict__ F) {
+                                 const int* __restrict__ rexp, const int* __restrict__ cexp, int64_t Ps, int64_t S,
+                                 double* __restrict__ F) {
+  double c[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) c[q] = q < ndiag ? ldexp(1.0, -beta * (q + 2)) : 0.0;
   const int64_t n = Ps * S;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int q = ndiag - 1; q >= 0; --q) acc = fma(ldexp(1.0, -beta * (q + 2)), (double)T[(size_t)q * diag_stride + i], acc);
-    F[i] = acc * rscale[i / S] * cscale[i % S];
+#pragma unroll
+    for (int q = 15; q >= 0; --q)
+      if (q < ndiag) acc = fma(c[q], int_float_to_double(T[(size_t)q * diag_stride + i]), acc);
+    F[i] = times_pow2(acc, rexp[i / S] + cexp[i % S]);
   }
 }
 
@@ -861,7 +889,7 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
   const int NT = (int)((S + BN - 1) / BN);
   SliceParams sp;
   if (!choose_slices((int64_t)KC * C::BK, &sp))
-    return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 contraction supports at most 4672 modes");
+    return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 contraction supports at most 16320 modes");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -875,14 +903,14 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
   const int64_t b_stride = (int64_t)NT * KC * C::B_CHUNK;
   ScratchBuffer zbuf, rsc, csc, abuf, bbuf, tbuf;
   ZP_TRY(zbuf.alloc((size_t)J * rows * sizeof(double), stream));
-  ZP_TRY(rsc.alloc((size_t)rows * sizeof(double), stream));
-  ZP_TRY(csc.alloc((size_t)S * sizeof(double), stream));
+  ZP_TRY(rsc.alloc((size_t)rows * sizeof(int), stream));
+  ZP_TRY(csc.alloc((size_t)S * sizeof(int), stream));
   ZP_TRY(abuf.alloc((size_t)sp.s * a_stride, stream));
   ZP_TRY(bbuf.alloc((size_t)sp.s * b_stride, stream));
   ZP_TRY(tbuf.alloc((size_t)sp.s * rows * S * sizeof(float), stream));
   cudaError_t e;
-  col_scale_kernel<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(coeffs, J, S, (double*)csc.ptr);
-  slice_b_kernel<<<1024, 256, 0, stream>>>(coeffs, (const double*)csc.ptr, J, S, NT, KC, sp, (uint8_t*)bbuf.ptr,
+  col_scale_kernel<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(coeffs, J, S, (int*)csc.ptr);
+  slice_b_kernel<<<1024, 256, 0, stream>>>(coeffs, (const int*)csc.ptr, J, S, NT, KC, sp, (uint8_t*)bbuf.ptr,
                                            b_stride);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "coefficient slicing launch");
   for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
@@ -891,8 +919,8 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
     const int64_t Ps = std::min<int64_t>(tiles * BM, P - p0);
     ZP_TRY(launch_walk(plan, r + p0, theta + p0, Ps, 0, (double*)zbuf.ptr, nullptr, stream));
     row_scale_kernel<<<(unsigned)((Ps + 127) / 128), 128, 0, stream>>>((const double*)zbuf.ptr, J, Ps,
-                                                                      (double*)rsc.ptr);
-    slice_a_kernel<<<2048, 256, 0, stream>>>((const double*)zbuf.ptr, (const double*)rsc.ptr, J, Ps, tiles, KC, sp,
+                                                                      (int*)rsc.ptr);
+    slice_a_kernel<<<2048, 256, 0, stream>>>((const double*)zbuf.ptr, (const int*)rsc.ptr, J, Ps, tiles, KC, sp,
                                              (uint8_t*)abuf.ptr, slab * KC * (int64_t)C::A_CHUNK);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "basis slicing launch");
     for (int d = 2; d <= sp.s + 1; ++d) {
@@ -904,7 +932,7 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
       ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, NT, sms, pairs, stream));
     }
     recombine_kernel<<<2048, 256, 0, stream>>>((const float*)tbuf.ptr, rows * S, sp.s, sp.beta,
-                                               (const double*)rsc.ptr, (const double*)csc.ptr, Ps, S,
+                                               (const int*)rsc.ptr, (const int*)csc.ptr, Ps, S,
                                                out + (size_t)p0 * S);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "recombine_kernel launch");
   }

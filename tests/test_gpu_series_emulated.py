@@ -36,9 +36,11 @@ def test_emulated_fp64_against_oracle(nmax, P, S):
     assert (np.abs(F - want) <= tol).all(), float(np.max(np.abs(F - want) / tol))
 
 
-def test_emulated_fp64_five_bit_slices():
-    """861 modes (padded K 896) take the beta = 5, 11-slice variant."""
-    ns, ms = inputs.full_zernike_modes(40)
+@pytest.mark.parametrize("nmax", [40, 60, 100])
+def test_emulated_fp64_narrower_slices(nmax):
+    """861 / 1891 / 5151 modes (padded K 896 / 1920 / 5184) take the beta = 6, 5 and 4 slice
+    widths (9, 11 and 14 slices) that keep every float32 partial sum exact."""
+    ns, ms = inputs.full_zernike_modes(nmax)
     r, th = inputs.sqrt_uniform_points(200, 61)
     C = inputs.scaled_normal_coeffs(ns, 20, 61)
     F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), "fp64emu").cpu().numpy()
