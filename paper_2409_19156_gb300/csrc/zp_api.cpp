@@ -61,8 +61,9 @@ zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes, const d
   clear_error();
   if (max_deriv < 0 || max_deriv > 3) return set_error(ZP_ERR_DERIV_ORDER, "max_deriv must be 0..3");
   if (n_points < 0) return set_error(ZP_ERR_INVALID_ARG, "n_points < 0");
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false);
 }
 
@@ -77,8 +78,9 @@ zp_status zp_basis(const int32_t* n, const int32_t* m, int64_t n_modes, const do
   clear_error();
   if (max_deriv < 0 || max_deriv > 3) return set_error(ZP_ERR_DERIV_ORDER, "max_deriv must be 0..3");
   if (n_points < 0) return set_error(ZP_ERR_INVALID_ARG, "n_points < 0");
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return radial_common(plan, r, theta, n_points, max_deriv, out, out_dtheta, stream, true);
 }
 

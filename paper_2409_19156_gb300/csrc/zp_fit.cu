@@ -191,8 +191,9 @@ zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes, con
                         const double* weights, int64_t n_points, const double* samples, int64_t n_sets, double ridge,
                         double* coeffs, void* stream) {
   clear_error();
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return zp_series_fit_plan(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, stream);
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -71,8 +72,9 @@ size_t plan_device_layout(const zp_plan* p, size_t offsets[6]);
 // Points p->dev at `base` (laid out as plan_device_layout) and copies the host tables there,
 // with cudaMemcpyAsync on `stream` when async, else synchronously.
 zp_status plan_upload(zp_plan* p, void* base, cudaStream_t stream, bool async);
-// Cached plan for a mode list on the current device (created on first use).
-zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const zp_plan** out);
+// Cached plan for a mode list on the current device (created on first use).  The caller
+// keeps *out alive while it uses the plan; the cache may drop its own reference.
+zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, std::shared_ptr<const zp_plan>* out);
 zp_status check_plan_device(const zp_plan* plan);
 
 // Kernel launchers (zp_walk.cu).

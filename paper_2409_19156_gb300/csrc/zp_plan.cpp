@@ -279,11 +279,11 @@ struct PlanKeyHash {
   }
 };
 std::mutex g_cache_mu;
-std::unordered_map<PlanKey, zp_plan*, PlanKeyHash> g_cache;
+std::unordered_map<PlanKey, std::shared_ptr<const zp_plan>, PlanKeyHash> g_cache;
 constexpr size_t kCacheMax = 64;
 }  // namespace
 
-zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const zp_plan** out) {
+zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, std::shared_ptr<const zp_plan>* out) {
   if (n_modes < 0) return set_error(ZP_ERR_INVALID_ARG, "n_modes < 0");
   if (n_modes > 0 && (!n || !m)) return set_error(ZP_ERR_INVALID_ARG, "mode arrays are NULL");
   int dev = 0;
@@ -299,14 +299,13 @@ zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, const
   zp_plan* p = nullptr;
   zp_status s = build_plan(n, m, n_modes, &p);
   if (s != ZP_OK) return s;
-  if (g_cache.size() >= kCacheMax) {
-    // Plans handed out earlier may still be referenced by work in flight: freeing
-    // synchronises the device first.
-    for (auto& kv : g_cache) free_plan(kv.second);
-    g_cache.clear();
-  }
-  g_cache.emplace(std::move(key), p);
-  *out = p;
+  // Callers hold a reference for the duration of their call; an evicted plan is freed when
+  // the last reference drops (freeing synchronises the device first, so work already
+  // enqueued with it completes).
+  std::shared_ptr<const zp_plan> sp(p, [](const zp_plan* q) { free_plan(const_cast<zp_plan*>(q)); });
+  if (g_cache.size() >= kCacheMax) g_cache.clear();
+  g_cache.emplace(std::move(key), sp);
+  *out = sp;
   return ZP_OK;
 }
 

@@ -303,8 +303,9 @@ zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, co
                          int64_t n_points, const double* coeffs, int64_t n_sets, zp_precision prec, void* out,
                          void* stream) {
   clear_error();
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return zp_series_eval_plan(plan, r, theta, n_points, coeffs, n_sets, prec, out, stream);
 }
 
@@ -361,8 +362,9 @@ zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_
                                   const double* grad_out, double* grad_r, double* grad_theta, double* hess_rr,
                                   double* hess_rt, double* hess_tt, void* stream) {
   clear_error();
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return zp_series_point_hessian_plan(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_r, grad_theta, hess_rr,
                                       hess_rt, hess_tt, stream);
 }
@@ -372,8 +374,9 @@ zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes,
                             const double* grad_out, double* grad_coeffs, double* grad_r, double* grad_theta,
                             void* stream) {
   clear_error();
-  const zp_plan* plan = nullptr;
-  ZP_TRY(cached_plan(n, m, n_modes, &plan));
+  std::shared_ptr<const zp_plan> held;
+  ZP_TRY(cached_plan(n, m, n_modes, &held));
+  const zp_plan* plan = held.get();
   return zp_series_adjoint_plan(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta,
                                 stream);
 }

@@ -1,0 +1,84 @@
+"""Host-side library behaviour on the GPU: concurrent host threads, the plan cache's eviction,
+explicit plans on several streams, and CUDA-graph capture of the plan entry points."""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2409_19156_gb300 as zp  # noqa: E402
+from paper_2409_19156_gb300 import inputs  # noqa: E402
+from oracle import radial as oradial  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def test_concurrent_host_threads_with_different_mode_lists():
+    r = inputs.uniform_points(300, 5)[0]
+    rt = torch.as_tensor(r, device=DEV)
+    jobs = [inputs.radial_modes(n) for n in (4, 9, 15, 22)]
+    want = [np.array(oradial.radial_table(ns, ms, r, 1)) for ns, ms in jobs]
+    results, errors = {}, []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(0)
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    out = zp.radial(jobs[i][0], jobs[i][1], rt, 1)
+                s.synchronize()
+                results[i] = out.cpu().numpy()
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(jobs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i, w in enumerate(want):
+        assert np.max(np.abs(results[i] - w)) < 1e-9
+
+
+def test_plan_cache_eviction_keeps_results_correct():
+    """More distinct mode lists than the cache holds (64): every call still matches."""
+    r = inputs.uniform_points(64, 6)[0]
+    rt = torch.as_tensor(r, device=DEV)
+    for k in range(70):
+        ns = [k, k + 2]
+        ms = [k % 2, k % 2]
+        out = zp.radial(ns, ms, rt, 0).cpu().numpy()
+        if k % 17 == 0:
+            want = np.array(oradial.radial_table(ns, ms, r, 0))
+            assert np.max(np.abs(out - want)) < 1e-12
+
+
+def test_plan_entry_points_capture_in_a_cuda_graph():
+    ns, ms = inputs.full_zernike_modes(12)
+    r, th = inputs.uniform_points(1000, 7)
+    rt, tt = torch.as_tensor(r, device=DEV), torch.as_tensor(th, device=DEV)
+    plan = zp.Plan(ns, ms)
+    ref, _ = zp.basis(None, None, rt, tt, 2, plan=plan)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            out, _ = zp.basis(None, None, rt, tt, 2, plan=plan)
+    torch.cuda.current_stream().wait_stream(s)
+    rt.add_(0.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # new inputs in the same buffers, replay again
+    r2 = inputs.uniform_points(1000, 8)[0]
+    rt.copy_(torch.as_tensor(r2, device=DEV))
+    g.replay()
+    torch.cuda.synchronize()
+    ref2, _ = zp.basis(None, None, rt, tt, 2, plan=plan)
+    assert torch.equal(out, ref2)
