@@ -38,6 +38,10 @@ DP_OPS_PEAK = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
 # float64 operations per (point, mode) of the k <= 3 walk: 1 (g) + 1 (g') + 1 + 2 + 3 + 3
 # (Taylor lanes 0..3) + 4 (stores scaled by k! w_N).
 DP_OPS_PER_VALUE_TUPLE = 15
+# DRAM bytes (read + write) of one walk_kernel<3,false,true> launch, from the ncu capture in
+# profiles/walk_kernel_radial_n100.md (20000 points: 1.603771 GB written + 0.415 MB read),
+# scaled to 100000 points (the traffic is the output, proportional to the point count).
+WALK_TRAFFIC_20000 = 1.603771e9 + 0.414976e6
 
 
 def parse_args():
@@ -348,7 +352,9 @@ def run_ours(args) -> None:
                        "points_dist": "Chebyshev-Gauss nodes mapped to [0,1]", "parallelism": f"replicas{world}",
                        "l2": "256 MB write between steps, outside the per-step CUDA events; each step writes 8.3 GB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": DP_OPS_PEAK / 1e9,
-                         "unit": "G float64 ops/s", "frac": achieved / DP_OPS_PEAK, "traffic": None,
+                         "unit": "G float64 ops/s", "frac": achieved / DP_OPS_PEAK,
+                         "traffic": WALK_TRAFFIC_20000 * P / 20000,
+                         "traffic_note": "ncu dram__bytes_read+write of a 20000-point launch scaled by points",
                          "kernel": "walk_kernel<3,false,true>", "ops_per_launch": dp_ops,
                          "peak_source": "2 float64 lanes/SM/clk x 152 SMs x 2070 MHz (probe measured 1.91)",
                          "hbm_write_gbs": out_bytes / (kernel_ms * 1e-3) / 1e9,
