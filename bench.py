@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--series-only", action="store_true",
                     help="run only the mixed_n32 series measurement (profiling captures)")
     ap.add_argument("--series-points", type=int, default=1_000_000)
+    ap.add_argument("--series-emulated", action="store_true",
+                    help="with --series-only: also time the emulated float64 contraction")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
@@ -385,7 +387,8 @@ def _events_ms(stream, fn, steps):
     return e0.elapsed_time(e1) / steps
 
 
-def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_fp64: bool = True) -> dict:
+def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_fp64: bool = True,
+                   with_emulated_only: bool = False) -> dict:
     """mixed_n32: 561 modes, 1e6 points r = sqrt(U), 4096 coefficient sets.  The split-precision
     tensor-core series (per-phase CUDA-event times recorded by the library on the launching
     stream) against the plain float64 basis-then-DGEMM form on the same inputs."""
@@ -434,6 +437,13 @@ def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_f
                                                  (" x 1/2 (nominal tf32:bf16)" if prec == "tf32" else "")}}
         if prec == "bf16x3":
             F_keep = F.clone()
+    if with_emulated_only:
+        Fe = torch.empty((P, S), dtype=torch.float64, device=dev)
+        emu = lambda: _lib.check("zp_series_eval_plan", lib.zp_series_eval_plan(  # noqa: E731
+            plan.handle, rt.data_ptr(), tt.data_ptr(), P, Ct.data_ptr(), S, 4, Fe.data_ptr(), sp))
+        emu()
+        out["fp64_emulated_ms"] = _events_ms(stream, emu, steps)
+        del Fe
     if not with_fp64:
         return out
     # Plain float64 form: basis to HBM, then cuBLAS DGEMM.
@@ -690,7 +700,7 @@ def main():
 
         torch.cuda.set_device(0)
         res = measure_series(torch.device("cuda", 0), {}, steps=args.steps, n_points=args.series_points,
-                             with_fp64=False)
+                             with_fp64=False, with_emulated_only=args.series_emulated)
         print(json.dumps({"series_only": res}), flush=True)
         return
     if args.impl == "reference":
