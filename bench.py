@@ -164,9 +164,78 @@ class OraclePool:
                 "sample": f"{len(pts)} of the 100000 points x all 2601 modes x k=0..3 "
                           f"({vals} exact-rational values in {dt:.2f} s)"}
 
+    def time_alg1_numpy(self, chunk: int = 8192) -> dict:
+        """The numpy restatement of Algorithm 1 on the whole workload (all 100000 points, all
+        2601 modes, k = 0..3), the m-columns dealt round-robin over the pool's processes, each
+        process writing its columns' values chunk by chunk (not a timing of the oracle)."""
+        import numpy as np
+
+        r = np.asarray(self.r, dtype=np.float64)
+        cols = sorted(set(abs(m) for m in self.ms))
+        parts = [cols[i::self.cores] for i in range(self.cores)]
+        parts = [p for p in parts if p]
+        t0 = time.perf_counter()
+        vals = sum(self.pool.map(_alg1_numpy_chunk, [(r, 100, p, chunk) for p in parts]))
+        dt = time.perf_counter() - t0
+        return {"value": vals / dt, "unit": UNIT, "cores": len(parts), "kind": "numpy Algorithm 1",
+                "sample": f"whole workload: {vals} values in {dt:.2f} s, {chunk}-point chunks"}
+
     def close(self):
         self.pool.close()
         self.pool.join()
+
+
+def alg1_numpy_column(r, n_max: int, m: int):
+    """Algorithm 1 restated in numpy for one m-column, the CPU comparison program: R_n^m and
+    its first three rho-derivatives for n = m, m+2, ..., n_max at the points r, returned as a
+    [4][(n_max-m)//2 + 1][len(r)] float64 block.  Seeds rho^m and ((m+2) rho^2 - (m+1)) rho^m
+    (Sec. 3, the first two Jacobi polynomials times (-1)^N rho^m), then the Jacobi three-term
+    recursion of Sec. 3 in rho^2 form, R_N = (2 a_N rho^2 - a_N - b_N) R_{N-1} - c_N R_{N-2},
+    differentiated term by term in rho (Leibniz on the factor g = 2 a_N rho^2 - a_N - b_N)."""
+    import numpy as np
+
+    r = np.asarray(r, dtype=np.float64)
+    n_steps = (n_max - m) // 2
+    out = np.empty((4, n_steps + 1, r.size))
+
+    def falling(p, k):
+        v = 1
+        for i in range(k):
+            v *= p - i
+        return v
+
+    def power_deriv(p, k):  # d^k/drho^k rho^p
+        return falling(p, k) * r ** (p - k) if k <= p else np.zeros_like(r)
+
+    for k in range(4):
+        out[k, 0] = power_deriv(m, k)
+        if n_steps >= 1:
+            out[k, 1] = (m + 2) * power_deriv(m + 2, k) - (m + 1) * power_deriv(m, k)
+    u = r * r
+    for N in range(2, n_steps + 1):
+        D = 2.0 * N * (N + m) * (2 * N + m - 2)
+        a = (2 * N + m - 1) * (2 * N + m) * (2 * N + m - 2) / D
+        b = (2 * N + m - 1) * m * m / D
+        c = 2.0 * (N + m - 1) * (N - 1) * (2 * N + m) / D
+        g = 2.0 * a * u - (a + b)
+        g1 = 4.0 * a * r
+        g2 = 4.0 * a
+        p0, p1, p2, p3 = out[0, N - 1], out[1, N - 1], out[2, N - 1], out[3, N - 1]
+        out[0, N] = g * p0 - c * out[0, N - 2]
+        out[1, N] = g * p1 + g1 * p0 - c * out[1, N - 2]
+        out[2, N] = g * p2 + 2.0 * g1 * p1 + g2 * p0 - c * out[2, N - 2]
+        out[3, N] = g * p3 + 3.0 * g1 * p2 + 3.0 * g2 * p1 - c * out[3, N - 2]
+    return out
+
+
+def _alg1_numpy_chunk(args):
+    r, n_max, m_list, chunk = args
+    values = 0
+    for lo in range(0, len(r), chunk):
+        rr = r[lo:lo + chunk]
+        for m in m_list:
+            values += alg1_numpy_column(rr, n_max, m).size
+    return values
 
 
 def time_oracle(n_points: int, cores: int | None = None) -> dict:
@@ -341,9 +410,14 @@ def run_ours(args) -> None:
                   "basis": measure_basis_latency(dev), "batched": measure_batched(dev),
                   "paper_shapes": measure_paper_shapes(dev)}
 
-    cpu = None
+    cpu = cpu_alg1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(args.cpu_sample_points)
+        pool = OraclePool()
+        try:
+            cpu = pool.time(args.cpu_sample_points)
+            cpu_alg1 = pool.time_alg1_numpy()
+        finally:
+            pool.close()
 
     if rank == 0:
         line = {
@@ -363,6 +437,7 @@ def run_ours(args) -> None:
                          "hbm_frac_of_measured_copy": out_bytes / (kernel_ms * 1e-3) / 1e9 / hbm_peak},
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_alg1_numpy": cpu_alg1,
             "clocks": clk,
             "gpu_launches": args.steps,
             "wall_s_timed": wall,
@@ -521,7 +596,9 @@ def measure_paper_shapes(dev, steps: int = 50) -> dict:
     """The paper's own timing shapes.  (1) Algorithm 2 (one recursion per mode) against the
     per-column walk (Algorithm 1's decomposition) on the 2601-mode radial set, k = 0, 100000
     points.  (2) The Fig. 3 grid: full radial set k = 0 at 100 and 1000 linearly spaced points
-    for n_max = 10, 20, 50, 100, as single calls and as CUDA-graph replays."""
+    for n_max = 10, 20, 50, 100, as single calls and as CUDA-graph replays.  (3) Duplicated
+    modes, 16 copies of each mode of the n <= 24 set."""
+    import numpy as np
     import torch
 
     import paper_2409_19156_gb300 as zp
@@ -566,6 +643,24 @@ def measure_paper_shapes(dev, steps: int = 50) -> dict:
             fig3.append({"points": P, "n_max": n_max, "modes": len(n2), "us_per_call": t_call * 1e3,
                          "us_per_graph_replay": t_graph * 1e3})
     res["fig3_full_radial_set_k0"] = fig3
+    # Duplicated modes (the Zernike x Fourier footnote of Sec. 3): the full n <= 24 set, every
+    # mode repeated L = 16 times, Z at k = 0 on 100000 points.  One recursion per distinct
+    # column, 16 stores per value: the launch is bound by the HBM writes.
+    n24, m24 = inputs.full_zernike_modes(24)
+    L = 16
+    nd, md = np.repeat(n24, L), np.repeat(m24, L)
+    rd, td = (torch.as_tensor(a, device=dev) for a in inputs.uniform_points(100_000, 17))
+    pld = zp.Plan(nd, md, device=dev)
+    od = torch.empty((len(nd), rd.numel()), dtype=torch.float64, device=dev)
+    dup = lambda: _lib.check("zp_basis_plan", lib.zp_basis_plan(  # noqa: E731
+        pld.handle, rd.data_ptr(), td.data_ptr(), rd.numel(), 0, od.data_ptr(), None, sp))
+    dup()
+    t_dup = _events_ms(stream, dup, 5)
+    wbytes = od.numel() * 8
+    res["duplicated_modes_n24_x16"] = {"distinct_modes": len(n24), "columns": len(nd), "points": rd.numel(),
+                                       "ms": t_dup, "values_per_s": od.numel() / (t_dup * 1e-3),
+                                       "write_gbs": wbytes / (t_dup * 1e-3) / 1e9}
+    del od
     return res
 
 
