@@ -66,8 +66,13 @@ typedef enum {
                          cores; outputs float32 (batched forward only) */
   ZP_PREC_FP64_EMULATED = 4 /* float64-accurate contraction on the tensor cores: rows of Z and
                          columns of C scaled by powers of two and cut into small-integer bf16
-                         slices (error-free), exact float32 sums per slice diagonal, float64
-                         recombination; outputs float64 (zp_series_eval only, <= 16320 modes) */
+                         slices (54 bits, error-free), exact sums per slice diagonal, exact
+                         integer recombination rounded once to float64; outputs float64
+                         (zp_series_eval only, <= 16320 modes).  The error is bounded by the
+                         scales, about n_modes * 2^-54 * max_j |Z[j][p]| * max_j |C[j][s]| for
+                         F[p][s], rather than by sum_j |Z C| as for float64 arithmetic: a
+                         coefficient set whose entries span many orders of magnitude keeps
+                         fewer bits on its small entries than the FP64 path */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */

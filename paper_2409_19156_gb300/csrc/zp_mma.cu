@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kCoeffThreads) split_coeff_kernel(CoeffArgs a)
 struct GemmArgs {
   const uint8_t* A;  // slab: [tiles][KC][A_CHUNK] (slice 0 for KIND_SLICE)
   const uint8_t* B;  // [NT][KC][B_CHUNK] (slice 0 for KIND_SLICE)
-  float* F;          // [P][S]
+  float* F;          // [P][S] (KIND_SLICE: int32 values)
   int64_t P, S;
   int64_t mt_base;
   int64_t m_tiles;  // tiles in this slab
@@ -495,6 +495,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         uint32_t v[32];
         ptx::tmem_ld_32x32b_x32(tmem_base + ((q * 32u) << 16) + acc * BN + (uint32_t)c0, v);
         ptx::tmem_ld_wait();
+        if constexpr (KIND == KIND_SLICE) {
+          // Slice products sum to integers below 2^24 (exact in float32): store them as int32.
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
+        }
         if (valid_tile && p < a.P) {
           const int64_t cbase = col0 + c0;
           if (vec && cbase + 32 <= a.S) {
@@ -678,8 +683,10 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 // and cut into s slices of beta bits, x = sum_t a_t 2^(-beta t) with every a_t an integer of
 // at most beta bits (exact in bfloat16).  For each slice diagonal d = t + u the GEMM sums all
 // pairs (t, u) along a concatenated K into float32; every partial sum is an integer below
-// 2^24, so it is exact.  A float64 pass forms F = sigma_p sigma_s sum_d 2^(-beta d) T_d.
-// Pairs with t + u > s + 1 are dropped (their total is below 2^(-beta s) of the scale).
+// 2^24, so it is exact.  F = sigma_p sigma_s sum_d 2^(-beta d) T_d is then formed exactly in
+// integers and rounded once to float64.  Pairs with t + u > s + 1 are dropped (their total is
+// below 2^(-beta s) of the scale).  Slicing and recombination run on the integer pipe: GB300's
+// float64 pipe issues at 1/64 of its float32 rate.
 
 struct SliceParams {
   int beta = 6, s = 9;
@@ -705,43 +712,87 @@ bool choose_slices(int64_t k_pad, SliceParams* sp) {
   return false;
 }
 
-// Power-of-two scale per point: exponent e with 2^e >= max_j |Z[j][p]| (0 for a zero row).
+// Exponent e with 2^e > |x| for the largest |x| given as its float64 bits with the sign
+// cleared (positive doubles order like their bit patterns); 0 for zero.  Subnormals get -1022.
+__device__ __forceinline__ int scale_exponent(unsigned long long max_abs_bits) {
+  if (max_abs_bits == 0) return 0;
+  const int ef = (int)(max_abs_bits >> 52);
+  return ef ? ef - 1022 : -1022;
+}
+
+// Power-of-two scale per point: exponent e with 2^e > max_j |Z[j][p]| (0 for a zero row).
 __global__ void row_scale_kernel(const double* __restrict__ Z, int64_t J, int64_t P, int* __restrict__ expo) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  double mx = 0.0;
-  for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(Z[j * P + p]));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  expo[p] = e;
+  unsigned long long mx = 0;
+  for (int64_t j = 0; j < J; ++j) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(Z[j * P + p]) & 0x7fffffffffffffffull;
+    mx = b > mx ? b : mx;
+  }
+  expo[p] = scale_exponent(mx);
 }
 
-// Power-of-two scale per coefficient set: exponent e with 2^e >= max_j |C[j][s]|.
+// Power-of-two scale per coefficient set: exponent e with 2^e > max_j |C[j][s]|.
 __global__ void col_scale_kernel(const double* __restrict__ C, int64_t J, int64_t S, int* __restrict__ expo) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
-  double mx = 0.0;
-  for (int64_t j = 0; j < J; ++j) mx = fmax(mx, fabs(C[j * S + s]));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  expo[s] = e;
+  unsigned long long mx = 0;
+  for (int64_t j = 0; j < J; ++j) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(C[j * S + s]) & 0x7fffffffffffffffull;
+    mx = b > mx ? b : mx;
+  }
+  expo[s] = scale_exponent(mx);
 }
 
-// Cuts 8 consecutive K values x[0..7] (already scaled into [-1, 1]) into `s` slices and writes
-// each slice's 16-byte unit at `dst + t * slice_stride` (bf16 integers of at most beta bits).
-__device__ __forceinline__ void cut_slices(double (&x)[8], int beta, int s, uint8_t* dst, int64_t slice_stride) {
-  const double up = ldexp(1.0, beta);
-  for (int t = 0; t < s; ++t) {
+// X = round-half-even(z * 2^shift) for shift = beta * s - e, i.e. x = z 2^(-e) in [-1, 1] as a
+// fixed-point integer with beta * s fraction bits (|X| <= 2^(beta s) <= 2^56), from z's bits.
+__device__ __forceinline__ long long to_fixed(double z, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(z);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  const unsigned long long frac = b & 0xfffffffffffffull;
+  const unsigned long long m = ef ? (frac | (1ull << 52)) : frac;  // |z| = m 2^(max(ef,1) - 1075)
+  const int sh = (ef ? ef : 1) - 1075 + shift;
+  unsigned long long mag;
+  if (sh >= 0) {
+    mag = m << sh;  // |z| < 2^e keeps this below 2^(beta s)
+  } else if (sh <= -64) {
+    mag = 0;  // m 2^sh < 2^-11
+  } else {
+    const int r = -sh;
+    mag = m >> r;
+    const unsigned long long rem = m & ((1ull << r) - 1);
+    const unsigned long long half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (mag & 1))) ++mag;
+  }
+  return (b >> 63) ? -(long long)mag : (long long)mag;
+}
+
+// Cuts 8 fixed-point values X[0..7] (beta * s fraction bits) into s balanced base-2^beta digits
+// and writes slice t's 16-byte unit of bf16 integers at `dst + t * slice_stride`.  Digits are
+// taken from the least significant end: a = X mod 2^beta moved into [-2^(beta-1), 2^(beta-1)),
+// X = (X - a) / 2^beta (exact); the most significant digit is what remains (|a_1| <= 2^beta).
+__device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, uint8_t* dst, int64_t slice_stride) {
+  const long long mask = (1ll << beta) - 1, half = 1ll << (beta - 1), full = 1ll << beta;
+  for (int t = s - 1; t >= 0; --t) {
     uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double y0 = x[2 * i] * up, y1 = x[2 * i + 1] * up;
-      const double a0 = rint(y0), a1 = rint(y1);
-      x[2 * i] = y0 - a0;  // exact: y has at most 53 significant bits and a is its nearest integer
-      x[2 * i + 1] = y1 - a1;
-      const uint32_t h0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)a0));
-      const uint32_t h1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)a1));
-      w[i] = h0 | (h1 << 16);
+      uint32_t h[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        long long& x = X[2 * i + k];
+        int a;
+        if (t > 0) {
+          const long long low = x & mask;
+          const long long d = low >= half ? low - full : low;
+          x = (x - d) >> beta;
+          a = (int)d;
+        } else {
+          a = (int)x;
+        }
+        h[k] = __float_as_uint(__int2float_rn(a)) >> 16;  // |a| <= 128: exact in bf16
+      }
+      w[i] = h[0] | (h[1] << 16);
     }
     *reinterpret_cast<uint4*>(dst + (size_t)t * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
   }
@@ -756,10 +807,10 @@ __global__ void slice_a_kernel(const double* __restrict__ Z, const int* __restri
     const int64_t p = i % (tiles * BM);  // point fastest: coalesced reads of Z[j][p]
     const int64_t g = i / (tiles * BM);
     const int64_t j0 = g * 8;
-    const double inv = p < Ps ? ldexp(1.0, -expo[p]) : 0.0;  // a power of two: exact
-    double x[8];
+    const int shift = p < Ps ? sp.beta * sp.s - expo[p] : 0;
+    long long x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (p < Ps && j0 + q < J) ? Z[(j0 + q) * Ps + p] * inv : 0.0;
+    for (int q = 0; q < 8; ++q) x[q] = (p < Ps && j0 + q < J) ? to_fixed(Z[(j0 + q) * Ps + p], shift) : 0;
     const int64_t tile = p / BM;
     const uint32_t row = (uint32_t)(p % BM);
     const int kc = (int)(j0 / 64);
@@ -776,10 +827,10 @@ __global__ void slice_b_kernel(const double* __restrict__ C, const int* __restri
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sidx = i % rows;
     const int64_t j0 = (i / rows) * 8;
-    const double inv = sidx < S ? ldexp(1.0, -expo[sidx]) : 0.0;
-    double x[8];
+    const int shift = sidx < S ? sp.beta * sp.s - expo[sidx] : 0;
+    long long x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (sidx < S && j0 + q < J) ? C[(j0 + q) * S + sidx] * inv : 0.0;
+    for (int q = 0; q < 8; ++q) x[q] = (sidx < S && j0 + q < J) ? to_fixed(C[(j0 + q) * S + sidx], shift) : 0;
     const int64_t nt = sidx / BN;
     const uint32_t row = (uint32_t)(sidx % BN);
     const int kc = (int)(j0 / 64);
@@ -788,39 +839,99 @@ __global__ void slice_b_kernel(const double* __restrict__ C, const int* __restri
   }
 }
 
-// Exact float32 -> float64 of an integer-valued float by bit assembly (integer pipe; the
-// float64 pipe is the scarce one on GB300).  |v| < 2^24, so the value is normal or zero.
-__device__ __forceinline__ double int_float_to_double(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t e8 = (b >> 23) & 0xffu;
-  const uint32_t hi = (b & 0x80000000u) | ((e8 + 896u) << 20) | ((b >> 3) & 0x000fffffu);
-  const uint32_t lo = b << 29;
-  return e8 ? __hiloint2double((int)hi, (int)lo) : 0.0;
+// Correctly rounded float64 of N * 2^e2 (round half to even), N a signed 128-bit integer.
+// The mantissa and exponent are assembled on the integer pipe; results outside the normal
+// range (never reached by scaled series values) go through ldexp.
+__device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
+  if (N == 0) return 0.0;
+  const bool neg = N < 0;
+  const unsigned __int128 M = neg ? (unsigned __int128)0 - (unsigned __int128)N : (unsigned __int128)N;
+  const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;
+  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  unsigned long long mant;
+  if (nbits <= 53) {
+    mant = lo << (53 - nbits);
+  } else {
+    const int r = nbits - 53;
+    const unsigned __int128 q = M >> r;
+    mant = (unsigned long long)q;
+    const unsigned __int128 rem = M - (q << r);
+    const unsigned __int128 half = (unsigned __int128)1 << (r - 1);
+    if (rem > half || (rem == half && (mant & 1))) ++mant;
+  }
+  int ex = nbits - 1 + e2;  // N 2^e2 = (mant / 2^52) 2^ex
+  if (mant == (1ull << 53)) {
+    mant >>= 1;
+    ++ex;
+  }
+  if (ex < -1022 || ex > 1023) {
+    const double v = ldexp((double)mant, ex - 52);
+    return neg ? -v : v;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                  (mant & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
 }
 
-// Multiplies a float64 by 2^e by adding e to its exponent field (integer pipe); x == 0 stays 0.
-// The scales keep |F| far inside the normal range, so no over- or underflow handling is needed.
-__device__ __forceinline__ double times_pow2(double x, int e) {
-  if (x == 0.0) return 0.0;
-  const int hi = __double2hiint(x) + (e << 20);
-  return __hiloint2double(hi, __double2loint(x));
+// Horner step acc * 2^beta + t in two's-complement int64 (the true value fits; see `split`).
+__device__ __forceinline__ long long horner(long long acc, int beta, int t) {
+  return (long long)(((unsigned long long)acc << beta) + (unsigned long long)(long long)t);
 }
 
-// F[p][s] = sigma_p sigma_s sum_{d=2}^{s+1} 2^(-beta d) T_d[p][s], smallest terms first: one
-// float64 FMA per diagonal; conversions and the power-of-two scales on the integer pipe.
-__global__ void recombine_kernel(const float* __restrict__ T, int64_t diag_stride, int ndiag, int beta,
+// F[p][s] = sigma_p sigma_s 2^(-beta (ndiag+1)) N with N = sum_d T_d 2^(beta (ndiag+1-d)),
+// d = 2..ndiag+1, formed exactly: the first `split` diagonals in one int64 Horner chain, the
+// rest in another, joined into 128 bits and rounded once.  Row of threads = row p of F.
+__global__ void recombine_kernel(const int* __restrict__ T, int64_t diag_stride, int ndiag, int split, int beta,
                                  const int* __restrict__ rexp, const int* __restrict__ cexp, int64_t Ps, int64_t S,
                                  double* __restrict__ F) {
-  double c[16];
+  const int lo_shift = beta * (ndiag - split);
+  const int e_base = -beta * (ndiag + 1);
+  const bool vec = (S % 4) == 0;
+  for (int64_t p = blockIdx.x; p < Ps; p += gridDim.x) {
+    const int ep = rexp[p] + e_base;
+    const int* trow = T + p * S;
+    double* frow = F + p * S;
+    if (vec) {
+      for (int64_t s4 = (int64_t)threadIdx.x * 4; s4 < S; s4 += (int64_t)blockDim.x * 4) {
+        long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int q = 0; q < 16; ++q) c[q] = q < ndiag ? ldexp(1.0, -beta * (q + 2)) : 0.0;
-  const int64_t n = Ps * S;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+        for (int q = 0; q < 16; ++q) {
+          if (q < ndiag) {
+            const int4 t = __ldcs(reinterpret_cast<const int4*>(trow + (size_t)q * diag_stride + s4));
+            if (q < split) {
+              hi[0] = horner(hi[0], beta, t.x), hi[1] = horner(hi[1], beta, t.y);
+              hi[2] = horner(hi[2], beta, t.z), hi[3] = horner(hi[3], beta, t.w);
+            } else {
+              lo[0] = horner(lo[0], beta, t.x), lo[1] = horner(lo[1], beta, t.y);
+              lo[2] = horner(lo[2], beta, t.z), lo[3] = horner(lo[3], beta, t.w);
+            }
+          }
+        }
+        const int4 ce = *reinterpret_cast<const int4*>(cexp + s4);
+        const int e[4] = {ce.x, ce.y, ce.z, ce.w};
+        double v[4];
 #pragma unroll
-    for (int q = 15; q >= 0; --q)
-      if (q < ndiag) acc = fma(c[q], int_float_to_double(T[(size_t)q * diag_stride + i]), acc);
-    F[i] = times_pow2(acc, rexp[i / S] + cexp[i % S]);
+        for (int k = 0; k < 4; ++k)
+          v[k] = int128_to_double(
+              (__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k], ep + e[k]);
+        __stcs(reinterpret_cast<double2*>(frow + s4), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2*>(frow + s4 + 2), make_double2(v[2], v[3]));
+      }
+    } else {
+      for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+        long long hi = 0, lo = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q < ndiag) {
+            const int t = trow[(size_t)q * diag_stride + s];
+            if (q < split) hi = horner(hi, beta, t);
+            else lo = horner(lo, beta, t);
+          }
+        }
+        frow[s] = int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
+                                   ep + cexp[s]);
+      }
+    }
   }
 }
 
@@ -895,8 +1006,12 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int pairs = gemm_pairs<KIND_SLICE>(sms);
   if (pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
-  // Slab of point tiles: float32 diagonal sums (s x rows x S x 4 B) within about 4 GB.
-  const size_t tdiag_tile = (size_t)BM * S * sizeof(float);
+  // Recombination chains: the first `split` diagonals in one int64 Horner chain need
+  // 24 + beta (split - 1) + 1 <= 63 bits; the rest (at most 4 diagonals for every choice of
+  // choose_slices) need far fewer.
+  const int split = std::min(sp.s, 38 / sp.beta + 1);
+  // Slab of point tiles: int32 diagonal sums (s x rows x S x 4 B) within about 4 GB.
+  const size_t tdiag_tile = (size_t)BM * S * sizeof(int);
   const int64_t slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / (sp.s * tdiag_tile))));
   const int64_t rows = slab * BM;
   const int64_t a_stride = slab * KC * (int64_t)C::A_CHUNK;
@@ -931,9 +1046,9 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
       ga.b_slice_stride = b_stride;
       ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, NT, sms, pairs, stream));
     }
-    recombine_kernel<<<2048, 256, 0, stream>>>((const float*)tbuf.ptr, rows * S, sp.s, sp.beta,
-                                               (const int*)rsc.ptr, (const int*)csc.ptr, Ps, S,
-                                               out + (size_t)p0 * S);
+    recombine_kernel<<<(unsigned)std::min<int64_t>(Ps, 8 * sms), 256, 0, stream>>>(
+        (const int*)tbuf.ptr, rows * S, sp.s, split, sp.beta, (const int*)rsc.ptr, (const int*)csc.ptr, Ps, S,
+        out + (size_t)p0 * S);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "recombine_kernel launch");
   }
   return ZP_OK;

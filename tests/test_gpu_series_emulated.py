@@ -68,3 +68,27 @@ def test_emulated_fp64_series_n24_full_size():
     want = np.array(oseries.series_eval(ns, ms, r[rows], th[rows], C.tolist()))
     tol = 1e-13 * (1.0 + abs_bound(ns, ms, r[rows], th[rows], C))
     assert (np.abs(F[torch.as_tensor(rows, device=DEV)].cpu().numpy() - want) <= tol).all()
+
+
+def test_emulated_fp64_extreme_column_scales():
+    """Coefficient sets scaled by 2^300, 2^-300 and 2^-1000, an all-zero set and one dominant
+    coefficient: the power-of-two scales and the final rounding keep float64 accuracy.  Set 4
+    (one coefficient 1e10 beside entries of order 1) is held to the scheme's scale-relative
+    bound: every operand is cut to 54 bits of its row / column scale, so F[p][s] is exact to
+    about J 2^-54 max_j |Z[j][p]| max_j |C[j][s]| (2^-48 leaves a factor 64 of slack)."""
+    ns, ms = inputs.full_zernike_modes(10)
+    r, th = inputs.uniform_points(150, 71)
+    C = inputs.scaled_normal_coeffs(ns, 6, 71)
+    C[:, 0] *= 2.0 ** 300
+    C[:, 1] *= 2.0 ** -300
+    C[:, 2] = 0.0
+    C[:, 3] *= 2.0 ** -1000
+    C[5, 4] = 1e10
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), "fp64emu").cpu().numpy()
+    want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
+    Z = np.abs(np.array(obasis.basis_table(ns, ms, r, th, 0)[0][0]))
+    scale_bound = len(ns) * 2.0 ** -48 * np.outer(Z.max(axis=0), np.abs(C).max(axis=0))
+    tol = 1e-13 * abs_bound(ns, ms, r, th, C) + 1e-320
+    tol[:, 4] += scale_bound[:, 4]
+    assert (F[:, 2] == 0.0).all()
+    assert (np.abs(F - want) <= tol).all(), float(np.max(np.abs(F - want) / tol))
