@@ -83,6 +83,28 @@ __device__ __forceinline__ void put_elem(uint8_t* chunk, uint32_t row, uint32_t 
   }
 }
 
+// float of a float64 by truncating its significand (integer pipe: the float64 pipe is the
+// scarce one).  Relative error below 2^-23; magnitudes under the float normal range give a
+// signed zero, finite ones above it infinity; infinities and NaNs are kept.  The split
+// operands carry 16 (BF16x3) or 11 (TF32) significant bits, so truncation is harmless.
+__device__ __forceinline__ float float_of_double(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  uint32_t bits;
+  if (e == 0x7ffu) {
+    bits = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  } else if (e <= 896u) {
+    bits = sign;
+  } else if (e >= 896u + 255u) {
+    bits = sign | 0x7f800000u;
+  } else {
+    bits = sign | ((e - 896u) << 23) | mant;
+  }
+  return __uint_as_float(bits);
+}
+
 __device__ __forceinline__ double pow_uint_m(double x, int e) {
   double result = 1.0, base = x;
   while (e) {
@@ -226,41 +248,57 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
         sincos((double)m * th, &sm[i], &cm[i]);
         pm[i] = pow_uint_m(rho[i], m);
       }
-      cf[i] = (float)cm[i];
-      sf[i] = (float)sm[i];
+      cf[i] = float_of_double(cm[i]);
+      sf[i] = float_of_double(sm[i]);
       T[i] = pm[i];
       S[i] = fma(h[4], pm[i] * u[i], -(h[8] * pm[i]));
     }
     m_prev = m;
     const int32_t* sp = a.slot_ptr + col.slot_base;
-    for (int N = 0; N < col.n_steps; ++N) {
-      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
-      const double A = row[0], B = row[1], W = row[3], zero = row[7];
+    // Step N's recursion value is formed before step N - 1's outputs are emitted, so the
+    // float64 latency of the recursion overlaps the conversions, products and packing.  Per
+    // value the float64 pipe sees only the two recursion FMAs: the weight W = k! w_N and the
+    // angular factor are applied in float32 (converted on the integer pipe).
+    double q_prev[Q];
+    float W_prev = 0.0f;
+    int sb_prev = 0, se_prev = 0;
+    auto emit = [&]() {
       float Rf[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        double q;
-        if (N == 0) {
-          q = T[i];
-        } else if (N == 1) {
-          q = S[i];
-        } else {
-          const double g = fma(A, u[i], -B);
-          q = fma(g, S[i], -T[i]);
-          T[i] = S[i];
-          S[i] = q;
-        }
-        Rf[i] = (float)fma(W, q, zero);  // zero = row[7] = 0: a DFMA issues faster than a DMUL
-      }
-      const int sb = sp[N], se = sp[N + 1];
-      for (int s = sb; s < se; ++s) {
+      for (int i = 0; i < Q; ++i) Rf[i] = float_of_double(q_prev[i]) * W_prev;
+      for (int s = sb_prev; s < se_prev; ++s) {
         const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
         float z[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) z[i] = Rf[i] * ((code >> 31) ? sf[i] : cf[i]);
         push(z);
       }
+    };
+    for (int N = 0; N < col.n_steps; ++N) {
+      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
+      const double A = row[0], B = row[1], W = row[3];
+      double q[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (N == 0) {
+          q[i] = T[i];
+        } else if (N == 1) {
+          q[i] = S[i];
+        } else {
+          const double g = fma(A, u[i], -B);
+          q[i] = fma(g, S[i], -T[i]);
+          T[i] = S[i];
+          S[i] = q[i];
+        }
+      }
+      if (N > 0) emit();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) q_prev[i] = q[i];
+      W_prev = float_of_double(W);
+      sb_prev = sp[N];
+      se_prev = sp[N + 1];
     }
+    if (col.n_steps > 0) emit();
   }
   const float zeros[Q] = {};
   while (k % C::BK != 0) push(zeros);
@@ -477,7 +515,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     for (int64_t t = cid; t < total; t += nclusters, ++local) {
       const uint32_t acc = (uint32_t)(local & 1);
       const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
-      if (!ptx::mbar_wait(&tmem_full[acc], acc_phase, abort_flag)) {
+      // One lane per warp polls the barrier; the shuffle hands its answer to the warp.
+      bool ok = true;
+      if (lane == 0) ok = ptx::mbar_wait(&tmem_full[acc], acc_phase, abort_flag);
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
         fail();
         break;
       }

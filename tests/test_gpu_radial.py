@@ -146,3 +146,18 @@ def test_high_order_modes_n300():
     want = np.array(oradial.radial_table(ns, ms, r, 3))
     assert_radial_close(got, want, ns, "n<=300")
     assert np.max(np.abs(got[0][:, 1] - 1.0)) < 1e-11
+
+
+def test_maximum_order_modes_n1000():
+    """The largest accepted order (ZP_MAX_N = 1000; 500 recursion steps for m = 0, a
+    32-kilobyte table in shared memory): all derivatives against the oracle, R_n^m(1) = 1, and
+    n = 1001 rejected."""
+    ns = [1000, 1000, 999, 1000, 998, 1000]
+    ms = [0, 1000, 1, 500, 996, 2]
+    r = np.concatenate([[0.0, 1.0, 0.5, 0.999], inputs.uniform_points(12, 78)[0]])
+    got = run_radial(ns, ms, r, 3)
+    want = np.array(oradial.radial_table(ns, ms, r, 3))
+    assert_radial_close(got, want, ns, "n=1000")
+    assert np.max(np.abs(got[0][:, 1] - 1.0)) < 1e-11
+    with pytest.raises(zp.ZernikeError):
+        zp.radial([1001], [1], torch.as_tensor(r, device=DEV), 0)

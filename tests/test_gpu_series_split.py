@@ -102,3 +102,44 @@ def test_mixed_n32_full_size_sampled():
     rel = float((F[sl].double() - F64).norm() / F64.norm())
     assert rel < 2e-5, rel
     assert bool(torch.isfinite(F).all())
+
+
+@pytest.mark.parametrize("prec,code", [("bf16x3", 1), ("tf32", 2)])
+@pytest.mark.parametrize("nmax,P,S", [(20, 20_000, 300), (32, 3_001, 256), (5, 129, 7)])
+def test_slab_size_does_not_change_the_result(prec, code, nmax, P, S):
+    """zp_series_eval (slabs of up to 512 MB of split basis) and zp_series_eval_static (its
+    64 MB array: many smaller slabs, other CTA-pair boundaries) compute the same basis values
+    and the same MMA sequence per tile, so their outputs are identical, for an odd number of
+    point tiles too (a pair's missing second tile)."""
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.sqrt_uniform_points(P, 90 + nmax)
+    C = inputs.scaled_normal_coeffs(ns, S, 90 + nmax)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    regular = zp.series_eval(ns, ms, rt, tt, Ct, prec)
+    lib = _lib.load()
+    n, m = _lib.modes_i32(ns), _lib.modes_i32(ms)
+    static = torch.full((P, S), float("nan"), dtype=torch.float32, device=DEV)
+    _lib.check("zp_series_eval_static", lib.zp_series_eval_static(
+        _lib.i32_ptr(n), _lib.i32_ptr(m), len(n), rt.data_ptr(), tt.data_ptr(), P, Ct.data_ptr(), S, code,
+        static.data_ptr(), torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    wait_ok()
+    assert torch.equal(regular, static)
+
+
+def test_split_long_column_plan():
+    """Modes of order 900 and 899 (451-step columns) beside a small full set, against the
+    float64 path."""
+    ns, ms = inputs.full_zernike_modes(6)
+    ns = list(ns) + [900, 899]
+    ms = list(ms) + [0, -1]
+    r, th = inputs.sqrt_uniform_points(700, 95)
+    C = inputs.scaled_normal_coeffs(np.asarray(ns), 40, 95)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    for prec in ("bf16x3", "tf32"):
+        F = zp.series_eval(ns, ms, rt, tt, Ct, prec).double()
+        F64 = zp.series_eval(ns, ms, rt, tt, Ct, "fp64")
+        z = zp.basis(ns, ms, rt, tt, 0)[0][0].abs()
+        bound = REL[prec] * (z.T @ Ct.abs()) + 1e-6
+        wait_ok()
+        assert bool(((F - F64).abs() <= bound).all())
