@@ -38,10 +38,11 @@ DP_OPS_PEAK = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
 # float64 operations per (point, mode) of the k <= 3 walk: 1 (g) + 1 (g') + 1 + 2 + 3 + 3
 # (Taylor lanes 0..3) + 4 (stores scaled by k! w_N).
 DP_OPS_PER_VALUE_TUPLE = 15
-# DRAM bytes (read + write) of one walk_kernel<3,false,true> launch, from the ncu capture in
-# profiles/walk_kernel_radial_n100.md (20000 points: 1.603771 GB written + 0.415 MB read),
-# scaled to 100000 points (the traffic is the output, proportional to the point count).
-WALK_TRAFFIC_20000 = 1.603771e9 + 0.414976e6
+# DRAM bytes (read + write) of one walk_kernel<3,false,true> launch at 20000 points, from the
+# ncu capture in profiles/walk_kernel_radial_n100.md (1.604159 GB written + 17.184 MB read:
+# the output and one read of the power table), scaled to 100000 points (both proportional to
+# the point count).
+WALK_TRAFFIC_20000 = 1.604159e9 + 17.184256e6
 
 
 def parse_args():
@@ -323,9 +324,21 @@ def run_ours(args) -> None:
     values_per_step = P * J * K
     value = aggregate_value(values_per_step, world, ms_per_step)
 
-    # Roofline: the walk kernel is the only launch of a step (float64-issue bound).
+    # Roofline of the walk kernel (float64-issue bound), the dominant of the step's two
+    # launches (point preparation, walk): its own device time from the timed entry point,
+    # which records CUDA events around each launch on this stream.
+    import ctypes
+
+    phase = (ctypes.c_float * 2)()
+    prep_ms, walk_ms = [], []
+    for i in range(10):
+        flush.fill_(i & 0xFF)
+        _lib.check("zp_radial_plan_timed", lib.zp_radial_plan_timed(plan.handle, rt.data_ptr(), P, 3, out.data_ptr(),
+                                                                     sp, phase))
+        prep_ms.append(phase[0])
+        walk_ms.append(phase[1])
     dp_ops = DP_OPS_PER_VALUE_TUPLE * P * J
-    kernel_ms = statistics.mean(ms_steps)
+    kernel_ms = statistics.mean(walk_ms)
     achieved = dp_ops / (kernel_ms * 1e-3)
     out_bytes = values_per_step * 8
     peaks = {}
@@ -429,9 +442,10 @@ def run_ours(args) -> None:
                        "l2": "256 MB write between steps, outside the per-step CUDA events; each step writes 8.3 GB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": DP_OPS_PEAK / 1e9,
                          "unit": "G float64 ops/s", "frac": achieved / DP_OPS_PEAK,
-                         "traffic": WALK_TRAFFIC_20000 * P / 20000,
+                         "traffic": WALK_TRAFFIC_20000 * P / 20000 if WALK_TRAFFIC_20000 else None,
                          "traffic_note": "ncu dram__bytes_read+write of a 20000-point launch scaled by points",
                          "kernel": "walk_kernel<3,false,true>", "ops_per_launch": dp_ops,
+                         "kernel_ms": kernel_ms, "point_prep_kernel_ms": statistics.mean(prep_ms),
                          "peak_source": "2 float64 lanes/SM/clk x 152 SMs x 2070 MHz (probe measured 1.91)",
                          "hbm_write_gbs": out_bytes / (kernel_ms * 1e-3) / 1e9,
                          "hbm_frac_of_measured_copy": out_bytes / (kernel_ms * 1e-3) / 1e9 / hbm_peak},
@@ -439,7 +453,7 @@ def run_ours(args) -> None:
             "cpu_baseline": cpu,
             "cpu_alg1_numpy": cpu_alg1,
             "clocks": clk,
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # point_prep_kernel + walk_kernel per step
             "wall_s_timed": wall,
             "extras": extras,
         }

@@ -116,6 +116,15 @@ ZP_API zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes,
                     double* out, void* stream);
 ZP_API zp_status zp_radial_plan(const zp_plan* plan, const double* r, int64_t n_points,
                          int32_t max_deriv, double* out, void* stream);
+/*
+ * zp_radial_plan with per-kernel timing: CUDA events are recorded on `stream` around each
+ * launch and phase_ms[0] receives the device time of the point-preparation kernel (powers of
+ * rho; 0 when the launch is too small to use it), phase_ms[1] that of the recursion walk.
+ * Same outputs as zp_radial_plan.  The call synchronises `stream` before returning
+ * (instrumentation; not for graph capture).
+ */
+ZP_API zp_status zp_radial_plan_timed(const zp_plan* plan, const double* r, int64_t n_points,
+                                      int32_t max_deriv, double* out, void* stream, float* phase_ms);
 
 /*
  * Zernike functions (Sec. 2 definition of Z) and their derivatives.

@@ -28,6 +28,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int32)]),
     "zp_radial": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, ctypes.c_int64, ctypes.c_int32, c_dp, c_dp]),
     "zp_radial_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, ctypes.c_int64, ctypes.c_int32, c_dp, c_dp]),
+    "zp_radial_plan_timed": (ctypes.c_int, [ctypes.c_void_p, c_dp, ctypes.c_int64, ctypes.c_int32, c_dp, c_dp,
+                                            ctypes.POINTER(ctypes.c_float)]),
     "zp_basis": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, ctypes.c_int32, c_dp, c_dp,
                                 c_dp]),
     "zp_basis_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, ctypes.c_int32, c_dp, c_dp, c_dp]),

@@ -35,7 +35,8 @@ zp_status check_device_array(const void* ptr, const char* name, size_t align) {
 using namespace zp;
 
 static zp_status radial_common(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
-                               int32_t max_deriv, double* out, double* out_dtheta, void* stream, bool angular) {
+                               int32_t max_deriv, double* out, double* out_dtheta, void* stream, bool angular,
+                               float* phase_ms = nullptr) {
   ZP_TRY(check_plan_device(plan));
   if (n_points < 0) return set_error(ZP_ERR_INVALID_ARG, "n_points < 0");
   if (max_deriv < 0 || max_deriv > 3) return set_error(ZP_ERR_DERIV_ORDER, "max_deriv must be 0..3");
@@ -45,7 +46,7 @@ static zp_status radial_common(const zp_plan* plan, const double* r, const doubl
   ZP_TRY(check_device_array(out, "out", 8));
   if (out_dtheta) ZP_TRY(check_device_array(out_dtheta, "out_dtheta", 8));
   return launch_walk(plan, r, angular ? theta : nullptr, n_points, max_deriv, out, angular ? out_dtheta : nullptr,
-                     (cudaStream_t)stream);
+                     (cudaStream_t)stream, phase_ms);
 }
 
 extern "C" {
@@ -54,6 +55,13 @@ zp_status zp_radial_plan(const zp_plan* plan, const double* r, int64_t n_points,
                          void* stream) {
   clear_error();
   return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false);
+}
+
+zp_status zp_radial_plan_timed(const zp_plan* plan, const double* r, int64_t n_points, int32_t max_deriv, double* out,
+                               void* stream, float* phase_ms) {
+  clear_error();
+  if (!phase_ms) return set_error(ZP_ERR_INVALID_ARG, "phase_ms is NULL");
+  return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false, phase_ms);
 }
 
 zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, int64_t n_points,

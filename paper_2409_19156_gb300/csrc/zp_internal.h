@@ -78,8 +78,11 @@ zp_status cached_plan(const int32_t* n, const int32_t* m, int64_t n_modes, std::
 zp_status check_plan_device(const zp_plan* plan);
 
 // Kernel launchers (zp_walk.cu).
+// phase_ms: NULL, or [2] receiving the device time of the point preparation and of the walk
+// (events around each launch; the stream is synchronised).
 zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
-                      int max_deriv, double* out, double* out_dtheta, cudaStream_t stream);
+                      int max_deriv, double* out, double* out_dtheta, cudaStream_t stream,
+                      float* phase_ms = nullptr);
 zp_status launch_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out,
                           cudaStream_t stream);
 

@@ -16,11 +16,17 @@
 //
 // Seeds (Sec. 2 explicit Jacobi sum for P_0, P_1 through the Jacobi relation):
 //   R_{m}^{m} = rho^m,   R_{m+2}^{m} = (m+2) rho^(m+2) - (m+1) rho^m.
+// For large launches a point-preparation kernel first tabulates rho^j and cos / sin(j theta)
+// per point (j up to the largest |m| + 2), so each (point, column) seed costs a few loads
+// instead of a power by squaring and a sincos.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
+#include "zp_api_common.h"
 #include "zp_internal.h"
+#include "zp_series_internal.h"
 
 namespace zp {
 namespace {
@@ -40,7 +46,21 @@ struct WalkArgs {
   int64_t J;
   double* out;
   double* out_dtheta;
+  // Optional point tables [j][P] (NULL: computed per thread): pw = rho^j (j <= pw_max),
+  // cs / sn = cos / sin(j theta) (j <= the largest |m|).
+  const double* pw = nullptr;
+  const double* cs = nullptr;
+  const double* sn = nullptr;
+  int pw_max = 0;
 };
+
+// Point preparation: rho^j for j = 0..pw_max and (theta given) cos / sin(j theta) for
+// j = 0..trig_max, point-fastest rows.  Every 16th entry is computed directly (a power by
+// squaring, a sincos of j theta) and the entries between by one multiplication (rho^(j+1) =
+// rho^j rho) or one angle addition, so rounding errors grow over at most 15 steps.
+__global__ void __launch_bounds__(128) point_prep_kernel(const double* __restrict__ r, const double* __restrict__ theta,
+                                                         int64_t P, int pw_max, int trig_max, double* __restrict__ pw,
+                                                         double* __restrict__ cs, double* __restrict__ sn);
 
 __device__ __forceinline__ double pow_uint(double x, int e) {
   double result = 1.0;
@@ -51,6 +71,35 @@ __device__ __forceinline__ double pow_uint(double x, int e) {
     e >>= 1;
   }
   return result;
+}
+
+__global__ void __launch_bounds__(128) point_prep_kernel(const double* __restrict__ r, const double* __restrict__ theta,
+                                                         int64_t P, int pw_max, int trig_max, double* __restrict__ pw,
+                                                         double* __restrict__ cs, double* __restrict__ sn) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double rho = r[p];
+  double v = 1.0;
+  for (int j = 0; j <= pw_max; ++j) {
+    v = (j % 16 == 0) ? pow_uint(rho, j) : v * rho;
+    __stcg(pw + (int64_t)j * P + p, v);
+  }
+  if (theta == nullptr) return;
+  const double th = theta[p];
+  double s1, c1;
+  sincos(th, &s1, &c1);
+  double c = 1.0, s = 0.0;
+  for (int j = 0; j <= trig_max; ++j) {
+    if (j % 16 == 0) {
+      sincos((double)j * th, &s, &c);
+    } else {
+      const double cn = fma(c, c1, -s * s1);
+      s = fma(s, c1, c * s1);
+      c = cn;
+    }
+    __stcg(cs + (int64_t)j * P + p, c);
+    __stcg(sn + (int64_t)j * P + p, s);
+  }
 }
 
 __device__ __forceinline__ void store_pair(double* dst, int64_t p, double v0, double v1, bool two, bool vec) {
@@ -97,7 +146,14 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
       cs[i] = 1.0;
       sn[i] = 0.0;
     }
-    if (m != 0) {
+    if (a.cs != nullptr) {
+      cs[0] = a.cs[(int64_t)m * a.P + p0];
+      sn[0] = a.sn[(int64_t)m * a.P + p0];
+      if (two) {
+        cs[1] = a.cs[(int64_t)m * a.P + p0 + 1];
+        sn[1] = a.sn[(int64_t)m * a.P + p0 + 1];
+      }
+    } else if (m != 0) {
       const double th0 = a.theta[p0];
       const double th1 = two ? a.theta[p0 + 1] : 0.0;
       sincos((double)m * th0, &sn[0], &cs[0]);
@@ -114,11 +170,17 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
       double pw[KMAX + 3];
-      double cur = e0 >= 0 ? pow_uint(rho[i], e0) : 0.0;
+      if (a.pw != nullptr) {
+        const int64_t pi = (i == 0 || two) ? p0 + i : p0;
 #pragma unroll
-      for (int t = 0; t < KMAX + 3; ++t) {
-        if (t > 0) cur = (e0 + t == 0) ? 1.0 : cur * rho[i];
-        pw[t] = cur;
+        for (int t = 0; t < KMAX + 3; ++t) pw[t] = e0 + t >= 0 ? a.pw[(int64_t)(e0 + t) * a.P + pi] : 0.0;
+      } else {
+        double cur = e0 >= 0 ? pow_uint(rho[i], e0) : 0.0;
+#pragma unroll
+        for (int t = 0; t < KMAX + 3; ++t) {
+          if (t > 0) cur = (e0 + t == 0) ? 1.0 : cur * rho[i];
+          pw[t] = cur;
+        }
       }
 #pragma unroll
       for (int k = 0; k <= KMAX; ++k) {
@@ -233,9 +295,43 @@ cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, size_t smem, bool vec, c
 
 }  // namespace
 
+namespace {
+// Events around the launches of one call, for zp_radial_plan_timed.
+struct WalkTimer {
+  float* ms;
+  cudaStream_t stream;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool prep = false;
+  WalkTimer(float* m, cudaStream_t s) : ms(m), stream(s) {
+    if (!ms) return;
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], stream);
+  }
+  void mark(int i) {
+    if (ms) cudaEventRecord(ev[i], stream);
+  }
+  zp_status finish() {
+    if (!ms) return ZP_OK;
+    cudaError_t e = cudaEventSynchronize(ev[2]);
+    float t0 = 0.0f, t1 = 0.0f;
+    if (e == cudaSuccess && prep) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, prep ? ev[1] : ev[0], ev[2]);
+    ms[0] = t0;
+    ms[1] = t1;
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "walk timing");
+  }
+  ~WalkTimer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
 zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points, int max_deriv,
-                      double* out, double* out_dtheta, cudaStream_t stream) {
+                      double* out, double* out_dtheta, cudaStream_t stream, float* phase_ms) {
+  if (phase_ms) phase_ms[0] = phase_ms[1] = 0.0f;
   if (n_points == 0 || plan->n_modes == 0) return ZP_OK;
+  WalkTimer timer(phase_ms, stream);
   WalkArgs a;
   a.cols = plan->dev.cols;
   a.table = plan->dev.table;
@@ -256,6 +352,28 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
                    (out_dtheta == nullptr || (uintptr_t)out_dtheta % 16 == 0);
   const bool ang = theta != nullptr;
   cudaError_t e;
+  // Point tables when they pay: enough points and columns to amortise one more launch, and
+  // orders low enough that the tables stay small (at most 2 + 2 x 131 rows of P doubles).
+  int m_max = 0;
+  for (const Column& c : plan->cols) m_max = std::max(m_max, (int)c.m);
+  ScratchBuffer tables;
+  if (n_points >= 8192 && plan->cols.size() >= 4 && m_max <= 128) {
+    const int pw_max = m_max + 2;
+    const size_t rows = (size_t)(pw_max + 1) + (ang ? 2 * (size_t)(m_max + 1) : 0);
+    ZP_TRY(tables.alloc(rows * (size_t)n_points * sizeof(double), stream));
+    double* pw = (double*)tables.ptr;
+    double* cs = ang ? pw + (size_t)(pw_max + 1) * n_points : nullptr;
+    double* sn = ang ? cs + (size_t)(m_max + 1) * n_points : nullptr;
+    point_prep_kernel<<<(unsigned)((n_points + 127) / 128), 128, 0, stream>>>(r, theta, n_points, pw_max, m_max, pw,
+                                                                             cs, sn);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "point_prep_kernel launch");
+    timer.prep = true;
+    timer.mark(1);
+    a.pw = pw;
+    a.pw_max = pw_max;
+    a.cs = cs;
+    a.sn = sn;
+  }
   switch (max_deriv) {
     case 0: e = ang ? launch_walk_t<0, true>(a, grid, smem, vec, stream) : launch_walk_t<0, false>(a, grid, smem, vec, stream); break;
     case 1: e = ang ? launch_walk_t<1, true>(a, grid, smem, vec, stream) : launch_walk_t<1, false>(a, grid, smem, vec, stream); break;
@@ -264,7 +382,8 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
     default: return set_error(ZP_ERR_DERIV_ORDER, "max_deriv outside 0..3");
   }
   if (e != cudaSuccess) return cuda_error(e, "walk_kernel launch");
-  return ZP_OK;
+  timer.mark(2);
+  return timer.finish();
 }
 
 zp_status launch_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out, cudaStream_t stream) {
