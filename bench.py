@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--series-points", type=int, default=1_000_000)
     ap.add_argument("--series-emulated", action="store_true",
                     help="with --series-only: also time the emulated float64 contraction")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the series_n24 forward / adjoint / fit measurement (profiling captures)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
@@ -590,6 +592,9 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan)
     fwd_emu = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan), steps)
     adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan), steps)
+    zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu")
+    adj_emu = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu"),
+                         steps)
     # Least-squares fit of the same coefficients back from the series values, with the
     # grid's exact quadrature weights (Gauss-Legendre in r^2 x uniform theta).
     import numpy as np
@@ -602,10 +607,16 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     for _ in range(steps):
         zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
     fit_ms = (time.perf_counter() - t0) * 1e3 / steps  # the fit synchronises its stream
+    Cfit_emu = zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64emu")
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64emu")
+    fit_emu_ms = (time.perf_counter() - t0) * 1e3 / steps
     return {"workload": "series_n24", "modes": len(ns), "points": len(r), "sets": C.shape[1],
             "fp64_forward_ms": fwd, "fp64_emulated_forward_ms": fwd_emu, "fp64_adjoint_ms": adj,
-            "fp64_fit_ms": fit_ms,
-            "fit_roundtrip_max_abs_err": float((Cfit - Ct).abs().max())}
+            "fp64_emulated_adjoint_ms": adj_emu, "fp64_fit_ms": fit_ms, "fp64_emulated_fit_ms": fit_emu_ms,
+            "fit_roundtrip_max_abs_err": float((Cfit - Ct).abs().max()),
+            "fit_emulated_roundtrip_max_abs_err": float((Cfit_emu - Ct).abs().max())}
 
 
 def measure_paper_shapes(dev, steps: int = 50) -> dict:
@@ -805,6 +816,12 @@ def main():
         res = measure_batched(torch.device("cuda", 0), steps=args.steps, n_instances=args.batched_instances,
                               point_scale=args.batched_point_scale, tune=False)
         print(json.dumps({"batched_only": res}), flush=True)
+        return
+    if args.adjoint_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"adjoint_only": measure_adjoint(torch.device("cuda", 0), steps=args.steps)}), flush=True)
         return
     if args.series_only:
         import torch

@@ -194,6 +194,18 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  int64_t n_points, const double* coeffs, int64_t n_sets,
                                  const double* grad_out, double* grad_coeffs, double* grad_r,
                                  double* grad_theta, void* stream);
+/*
+ * zp_series_adjoint_plan with a choice of contraction arithmetic: ZP_PREC_FP64 (cuBLAS
+ * DGEMM, as above) or ZP_PREC_FP64_EMULATED (grad_coeffs = Z G and H = C G^T by the
+ * float64-accurate tensor-core GEMM of ZP_PREC_FP64_EMULATED, with the scale-relative error
+ * bound stated there: about K 2^-54 times the largest operand magnitudes of the row and
+ * column, K = n_points for grad_coeffs and n_sets for H).  grad_r and grad_theta are then
+ * reduced in float64 as for ZP_PREC_FP64.  Other precisions: ZP_ERR_INVALID_ARG.
+ */
+ZP_API zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta,
+                                             int64_t n_points, const double* coeffs, int64_t n_sets,
+                                             const double* grad_out, double* grad_coeffs, double* grad_r,
+                                             double* grad_theta, zp_precision prec, void* stream);
 
 /*
  * Second derivatives for Jacobian/Hessian work (Sec. 3 mentions Jacobian and Hessian
@@ -221,7 +233,7 @@ ZP_API zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double*
  * Least-squares fit of series coefficients (the "fit" counterpart of zp_series_eval):
  *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
  * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 throughout (basis by
- * the recursion walk, Gram matrix by DSYRK, right-hand side by DGEMM, Cholesky by cuSOLVER).
+ * the recursion walk, Gram matrix and right-hand side by DGEMM, Cholesky by cuSOLVER).
  *   weights: DEVICE float64 [n_points] (w_p >= 0) or NULL (all 1).
  *   samples: DEVICE float64 [n_points][n_sets] (Y, row-major).
  *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
@@ -238,6 +250,17 @@ ZP_API zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_mod
 ZP_API zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta,
                                     const double* weights, int64_t n_points, const double* samples,
                                     int64_t n_sets, double ridge, double* coeffs, void* stream);
+/*
+ * zp_series_fit_plan with a choice of arithmetic for the Gram matrix Z W Z^T and the
+ * right-hand side Z W Y: ZP_PREC_FP64 (cuBLAS DGEMM) or ZP_PREC_FP64_EMULATED (the
+ * float64-accurate tensor-core GEMM, error about n_points 2^-54 times the largest magnitudes
+ * of the rows involved).  The Cholesky factorisation and solve are float64 (cuSOLVER) either
+ * way.  Other precisions: ZP_ERR_INVALID_ARG.
+ */
+ZP_API zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta,
+                                         const double* weights, int64_t n_points, const double* samples,
+                                         int64_t n_sets, double ridge, double* coeffs, zp_precision prec,
+                                         void* stream);
 
 /*
  * Batched series over many instances of uneven size (different mode lists, point counts)

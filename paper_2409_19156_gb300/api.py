@@ -135,7 +135,12 @@ def series_eval(n, m, r, theta, coeffs, prec: str = "fp64", plan: Plan | None = 
     return out
 
 
-def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), plan: Plan | None = None):
+def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), plan: Plan | None = None,
+                   prec: str = "fp64"):
+    """(grad_coeffs [J][S], grad_r [P], grad_theta [P]) for upstream grad_out [P][S]; prec
+    "fp64" (DGEMM contractions) or "fp64emu" (float64-accurate tensor-core contractions)."""
+    if prec not in ("fp64", "fp64emu"):
+        raise ValueError("series_adjoint takes prec 'fp64' or 'fp64emu'")
     r = _dev_f64(r, "r")
     theta = _dev_f64(theta, "theta")
     coeffs = _dev_f64(coeffs, "coeffs")
@@ -151,12 +156,13 @@ def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), pl
     gt = torch.empty(P, dtype=torch.float64, device=dev) if need[2] else None
     st = _stream(dev)
     with torch.cuda.device(dev):
-        if plan is not None:
-            _lib.call("zp_series_adjoint_plan", plan.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(), S,
-                      grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), st)
-        else:
+        if plan is None and prec == "fp64":
             _lib.call("zp_series_adjoint", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(), P,
                       coeffs.data_ptr(), S, grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), st)
+        else:
+            pl = plan if plan is not None else Plan(nn, mm, device=dev)
+            _lib.call("zp_series_adjoint_plan_prec", pl.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(),
+                      S, grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), PREC[prec], st)
     return gC, gr, gt
 
 
@@ -191,9 +197,13 @@ def point_hvp(hess, v_r, v_theta):
     return hrr * v_r + hrt * v_theta, hrt * v_r + htt * v_theta
 
 
-def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: Plan | None = None):
+def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: Plan | None = None,
+               prec: str = "fp64"):
     """Least-squares coefficients C [J][S] with sum_j Z_j(p) C[j, s] ~ samples[p, s] (weighted,
-    optional ridge); float64 throughout."""
+    optional ridge); float64 throughout, the Gram matrix and right-hand side by DGEMM ("fp64")
+    or by the float64-accurate tensor-core GEMM ("fp64emu")."""
+    if prec not in ("fp64", "fp64emu"):
+        raise ValueError("series_fit takes prec 'fp64' or 'fp64emu'")
     r = _dev_f64(r, "r")
     theta = _dev_f64(theta, "theta")
     Y = _dev_f64(samples, "samples")
@@ -206,38 +216,45 @@ def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: 
     out = torch.empty((J, S), dtype=torch.float64, device=r.device)
     st = _stream(r.device)
     with torch.cuda.device(r.device):
-        if plan is not None:
-            _lib.call("zp_series_fit_plan", plan.handle, r.data_ptr(), theta.data_ptr(), _lib.ptr(w), P, Y.data_ptr(),
-                      S, float(ridge), out.data_ptr(), st)
-        else:
+        if plan is None and prec == "fp64":
             _lib.call("zp_series_fit", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(),
                       _lib.ptr(w), P, Y.data_ptr(), S, float(ridge), out.data_ptr(), st)
+        else:
+            pl = plan if plan is not None else Plan(nn, mm, device=r.device)
+            _lib.call("zp_series_fit_plan_prec", pl.handle, r.data_ptr(), theta.data_ptr(), _lib.ptr(w), P,
+                      Y.data_ptr(), S, float(ridge), out.data_ptr(), PREC[prec], st)
     return out
 
 
 class ZernikeSeries(torch.autograd.Function):
     """F = Z(r, theta) C with gradients for C, r and theta from the library's adjoint
-    (basis recomputed in the backward pass, never stored).  float64 throughout."""
+    (basis recomputed in the backward pass, never stored).  float64 throughout; prec "fp64"
+    (DGEMM contractions) or "fp64emu" (float64-accurate tensor-core contractions) for both
+    passes."""
 
     @staticmethod
-    def forward(ctx, r, theta, coeffs, plan: Plan):
+    def forward(ctx, r, theta, coeffs, plan: Plan, prec: str = "fp64"):
+        if prec not in ("fp64", "fp64emu"):
+            raise ValueError("zernike_series takes prec 'fp64' or 'fp64emu'")
         ctx.plan = plan
+        ctx.prec = prec
         ctx.save_for_backward(r, theta, coeffs)
-        return series_eval(None, None, r, theta, coeffs, "fp64", plan=plan)
+        return series_eval(None, None, r, theta, coeffs, prec, plan=plan)
 
     @staticmethod
     def backward(ctx, grad_out):
         r, theta, coeffs = ctx.saved_tensors
         need = (ctx.needs_input_grad[2], ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         if not any(need):
-            return None, None, None, None
-        gC, gr, gt = series_adjoint(None, None, r, theta, coeffs, grad_out.contiguous(), need=need, plan=ctx.plan)
-        return gr, gt, gC, None
+            return None, None, None, None, None
+        gC, gr, gt = series_adjoint(None, None, r, theta, coeffs, grad_out.contiguous(), need=need, plan=ctx.plan,
+                                    prec=ctx.prec)
+        return gr, gt, gC, None, None
 
 
-def zernike_series(r, theta, coeffs, plan: Plan) -> torch.Tensor:
+def zernike_series(r, theta, coeffs, plan: Plan, prec: str = "fp64") -> torch.Tensor:
     """Differentiable float64 series F[p, s] = sum_j Z_j(r_p, theta_p) coeffs[j, s]."""
-    return ZernikeSeries.apply(r, theta, coeffs, plan)
+    return ZernikeSeries.apply(r, theta, coeffs, plan, prec)
 
 
 class Batch:

@@ -4,7 +4,8 @@
 //   =>  (Z W Z^T + ridge I) C = Z W Y          (normal equations, Z = basis [J][P])
 //
 // Steps: the basis by the walk kernel (float64, into scratch), the rows scaled by sqrt(w) when
-// weights are given, the Gram matrix by cuBLAS DSYRK, the right-hand side by DGEMM, the
+// weights are given, the Gram matrix and the right-hand side by cuBLAS DGEMM (or by the
+// float64-accurate tensor-core GEMM of zp_mma.cu for ZP_PREC_FP64_EMULATED), the
 // ridge added on the diagonal, a Cholesky factorisation and solve by cuSOLVER, and a DGEAM
 // transpose into the caller's row-major [J][S] output.  The call synchronises its stream at
 // the end to read the factorisation status.
@@ -79,7 +80,8 @@ SolverHandles& solver_handles() {
 }  // namespace
 
 zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* theta, const double* w, int64_t P,
-                          const double* Y, int64_t S, double ridge, double* coeffs, cudaStream_t stream) {
+                          const double* Y, int64_t S, double ridge, double* coeffs, cudaStream_t stream,
+                          bool emulated) {
   const int64_t J = plan->n_modes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -115,14 +117,22 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
     Yuse = (const double*)ybuf.ptr;
   }
   const double one = 1.0, zero = 0.0;
-  // Z row-major [J][P] is column-major P x J (Zc).  Gram = Zc^T Zc (lower triangle).
-  if (cublasDsyrk_64(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, J, P, &one, Z, P, &zero, (double*)gram.ptr, J) !=
-      CUBLAS_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cublasDsyrk failed");
-  // RHS (column-major J x S) = Zc^T (J x P) * Yc^T (P x S), Y row-major [P][S] = column-major S x P.
-  if (cublasDgemm_64(blas, CUBLAS_OP_T, CUBLAS_OP_T, J, S, P, &one, Z, P, Yuse, S, &zero, (double*)rhs.ptr, J) !=
-      CUBLAS_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cublasDgemm failed");
+  if (emulated) {
+    // Gram[i][j] = sum_p Z[i][p] Z[j][p] (exactly symmetric: both operands carry the same
+    // scales and slices); RHS column-major J x S = row-major [S][J]: rhs[s][j] = sum_p Y[p][s] Z[j][p].
+    ZP_TRY(emulated_gemm_fp64(J, J, P, Z, P, 1, Z, P, 1, (double*)gram.ptr, J, stream));
+    ZP_TRY(emulated_gemm_fp64(S, J, P, Yuse, 1, S, Z, P, 1, (double*)rhs.ptr, J, stream));
+  } else {
+    // Z row-major [J][P] is column-major P x J (Zc).  Gram = Zc^T Zc: a full DGEMM (cuBLAS's
+    // DSYRK measured three times slower for these shapes), of which potrf reads the lower half.
+    if (cublasDgemm_64(blas, CUBLAS_OP_T, CUBLAS_OP_N, J, J, P, &one, Z, P, Z, P, &zero, (double*)gram.ptr, J) !=
+        CUBLAS_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cublasDgemm (Gram) failed");
+    // RHS (column-major J x S) = Zc^T (J x P) * Yc^T (P x S), Y row-major [P][S] = column-major S x P.
+    if (cublasDgemm_64(blas, CUBLAS_OP_T, CUBLAS_OP_T, J, S, P, &one, Z, P, Yuse, S, &zero, (double*)rhs.ptr, J) !=
+        CUBLAS_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cublasDgemm failed");
+  }
   if (ridge > 0.0) {
     add_ridge_kernel<<<(unsigned)((J + 255) / 256), 256, 0, stream>>>((double*)gram.ptr, J, ridge);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "add_ridge_kernel launch");
@@ -170,7 +180,16 @@ extern "C" {
 zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta, const double* weights,
                              int64_t n_points, const double* samples, int64_t n_sets, double ridge, double* coeffs,
                              void* stream) {
+  return zp_series_fit_plan_prec(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, ZP_PREC_FP64,
+                                 stream);
+}
+
+zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta, const double* weights,
+                                  int64_t n_points, const double* samples, int64_t n_sets, double ridge,
+                                  double* coeffs, zp_precision prec, void* stream) {
   clear_error();
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP64_EMULATED)
+    return set_error(ZP_ERR_INVALID_ARG, "the fit takes ZP_PREC_FP64 or ZP_PREC_FP64_EMULATED");
   ZP_TRY(check_plan_device(plan));
   if (n_points < 0 || n_sets < 0) return set_error(ZP_ERR_INVALID_ARG, "negative size");
   if (!(ridge >= 0.0)) return set_error(ZP_ERR_INVALID_ARG, "ridge must be >= 0");
@@ -184,7 +203,8 @@ zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double*
   if (weights) ZP_TRY(check_device_array(weights, "weights", 8));
   if (n_sets > 0x7fffffff || plan->n_modes * n_sets > 0x7fffffffLL)
     return set_error(ZP_ERR_UNSUPPORTED, "fit output too large");
-  return series_fit_fp64(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, (cudaStream_t)stream);
+  return series_fit_fp64(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, (cudaStream_t)stream,
+                         prec == ZP_PREC_FP64_EMULATED);
 }
 
 zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,

@@ -358,6 +358,11 @@ struct GemmArgs {
   int npairs = 1;
   int64_t a_slice_stride = 0;
   int64_t b_slice_stride = 0;
+  // KIND_SLICE split over K: k batch kb covers K chunks [kb * kc_per_batch, min(KC, ...)) and
+  // writes its sums t_batch_stride elements after batch kb - 1 (kc_per_batch 0: one batch).
+  int k_batches = 1;
+  int kc_per_batch = 0;
+  int64_t t_batch_stride = 0;
 };
 
 // CL = 1: one CTA per tile.  CL = 2: CTA pairs (a cluster of two) work on two point tiles of
@@ -403,9 +408,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
 
-  // Tile t of this cluster: point-tile group t / n_tiles (CL point tiles), set tile t % n_tiles.
+  // Tile t of this cluster: k batch t / (groups * n_tiles), then point-tile group (CL point
+  // tiles) and set tile, set tile fastest.
   const int64_t groups = (a.m_tiles + CL - 1) / CL;
-  const int64_t total = groups * a.n_tiles;
+  const int64_t per_batch = groups * a.n_tiles;
+  const int64_t total = per_batch * a.k_batches;
+  const int kcb = a.kc_per_batch > 0 ? a.kc_per_batch : a.KC;
+  // K chunks [kc0, kc0 + nkc) of tile t.
+  auto k_range = [&](int64_t t, int& kc0, int& nkc) {
+    const int kb = (int)(t / per_batch);
+    kc0 = kb * kcb;
+    nkc = (kc0 + kcb < a.KC ? kc0 + kcb : a.KC) - kc0;
+  };
   auto fail = [&]() {
     *abort_flag = 1;
     atomicOr(&g_split_error, 1u);
@@ -416,21 +430,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       int stage = 0;
       uint32_t phase = 0;
       for (int64_t t = cid; t < total && !*abort_flag; t += nclusters) {
-        const int64_t mt = (t / a.n_tiles) * CL + rank;
-        const int nt = (int)(t % a.n_tiles);
+        const int64_t tm = t % per_batch;
+        const int64_t mt = (tm / a.n_tiles) * CL + rank;
+        const int nt = (int)(tm % a.n_tiles);
+        int kc0, nkc;
+        k_range(t, kc0, nkc);
         // A pair's second tile past the slab end reuses the last valid tile's data (its rows
         // are never stored); it still takes part in the shared B loads.
         const int64_t mt_src = mt < a.m_tiles ? mt : a.m_tiles - 1;
         const uint8_t* gA0 = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
         const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
-        for (int kk = 0; kk < a.npairs * a.KC; ++kk) {
+        for (int kk = 0; kk < a.npairs * nkc; ++kk) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
             break;
           }
-          const int t = kk / a.KC, kc = kk % a.KC;
-          const uint8_t* gA = gA0 + (size_t)t * a.a_slice_stride;
-          const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - t) * a.b_slice_stride;
+          const int ts = kk / nkc, kc = kc0 + kk % nkc;  // slice pair (ts, npairs - 1 - ts)
+          const uint8_t* gA = gA0 + (size_t)ts * a.a_slice_stride;
+          const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride;
           uint8_t* sA = smem + stage * C::STAGE;
           ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
           ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
@@ -463,8 +480,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * BN;
+        int kc0, nkc;
+        k_range(t, kc0, nkc);
         bool ok = true;
-        for (int kk = 0; kk < a.npairs * a.KC; ++kk) {
+        for (int kk = 0; kk < a.npairs * nkc; ++kk) {
           if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
             fail();
             ok = false;
@@ -523,13 +542,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         break;
       }
       ptx::tc_fence_after();
-      const int64_t mt_local = (t / a.n_tiles) * CL + rank;
+      const int64_t tm = t % per_batch;
+      const int64_t mt_local = (tm / a.n_tiles) * CL + rank;
       const bool valid_tile = mt_local < a.m_tiles;
       const int64_t mt = a.mt_base + mt_local;
-      const int nt = (int)(t % a.n_tiles);
+      const int nt = (int)(tm % a.n_tiles);
       const int64_t p = mt * BM + row;
       const int64_t col0 = (int64_t)nt * BN;
-      float* frow = a.F + p * a.S;
+      float* frow = a.F + (t / per_batch) * a.t_batch_stride + p * a.S;
       const bool vec = (a.S % 4) == 0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -719,38 +739,93 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 }
 
 // ---------------------------------------------------------------------------------------
-// Float64-accurate contraction emulated on the tensor cores (Ozaki-style error-free slicing,
-// a published scheme): rows of Z and columns of C are scaled by powers of two into [-1, 1]
-// and cut into s slices of beta bits, x = sum_t a_t 2^(-beta t) with every a_t an integer of
-// at most beta bits (exact in bfloat16).  For each slice diagonal d = t + u the GEMM sums all
-// pairs (t, u) along a concatenated K into float32; every partial sum is an integer below
-// 2^24, so it is exact.  F = sigma_p sigma_s sum_d 2^(-beta d) T_d is then formed exactly in
-// integers and rounded once to float64.  Pairs with t + u > s + 1 are dropped (their total is
-// below 2^(-beta s) of the scale).  Slicing and recombination run on the integer pipe: GB300's
+// Float64-accurate GEMM emulated on the tensor cores (Ozaki-style error-free slicing, a
+// published scheme):  C[m][n] = sum_k A(m, k) B(n, k)  for float64 A, B.  Rows of A and of B
+// are scaled by powers of two into [-1, 1], rounded to fixed point with beta * s >= 54
+// fraction bits and cut into s balanced digits of beta bits, x = sum_t a_t 2^(-beta t) (small
+// integers, exact in bfloat16).  For each slice diagonal d = t + u the GEMM sums all pairs
+// (t, u) along a concatenated K into float32; with K cut into batches short enough, every
+// partial sum is an integer below 2^24, hence exact, and is stored as int32.  The batches'
+// sums are added and C = sigma_m sigma_n sum_d 2^(-beta d) T_d is formed exactly in integers
+// and rounded once to float64.  Pairs with t + u > s + 1 are dropped (their total is below
+// 2^(-beta s) of the scales).  Slicing and recombination run on the integer pipe: GB300's
 // float64 pipe issues at 1/64 of its float32 rate.
 
 struct SliceParams {
   int beta = 6, s = 9;
 };
 
-// beta and the slice count for a padded K such that every float32 partial sum stays an
-// integer below 2^24 (exact).  With |a_1| <= 2^beta and |a_t| <= 2^(beta-1) for t >= 2 (each
-// later slice cuts a remainder of at most 1/2), diagonal d sums K * (2 * 2^beta * 2^(beta-1) +
-// (d-3) * 2^(2 beta - 2)) at most, largest at d = s + 1: K * 2^(2 beta) * (1 + (s-2)/4).
-// Candidates in order of fewest slice pairs (s (s+1) / 2), all with beta * s >= 54 bits.
-bool choose_slices(int64_t k_pad, SliceParams* sp) {
-  const struct {
-    int beta, s;
-  } opts[] = {{7, 8}, {6, 9}, {5, 11}, {4, 14}};
-  for (auto o : opts) {
-    const double worst = (double)k_pad * std::ldexp(1.0, 2 * o.beta) * (1.0 + (o.s - 2) / 4.0);
-    if (worst < 16777216.0) {
-      sp->beta = o.beta;
-      sp->s = o.s;
-      return true;
+// Slice widths, fewest slice pairs (s (s+1) / 2) first, all with beta * s >= 54 bits.
+constexpr int kSliceOpts = 4;
+constexpr int kSliceBeta[kSliceOpts] = {7, 6, 5, 4};
+constexpr int kSliceS[kSliceOpts] = {8, 9, 11, 14};
+
+// Largest number of 64-element K chunks one batch may hold with slice option o: with
+// |a_1| <= 2^beta and |a_t| <= 2^(beta-1) for t >= 2 (each later digit cuts a remainder of at
+// most 1/2), diagonal d sums K * (2 * 2^beta * 2^(beta-1) + (d-3) * 2^(2 beta - 2)) at most,
+// largest at d = s + 1: K * 2^(2 beta) * (1 + (s-2)/4), which must stay below 2^24.
+int max_batch_chunks(int o) {
+  const double per_k = std::ldexp(1.0, 2 * kSliceBeta[o]) * (1.0 + (kSliceS[o] - 2) / 4.0);
+  return (int)std::floor((16777216.0 - 1.0) / (per_k * Cfg<KIND_SLICE>::BK));
+}
+
+// How K is cut: slice option, chunks per batch, batches, and the recombination's Horner split.
+struct EmuShape {
+  SliceParams sp;
+  int KC = 0;            // 64-element K chunks
+  int kc_per_batch = 0;  // chunks per K batch
+  int k_batches = 1;
+  int split = 0;         // diagonals in the first Horner chain
+};
+
+// A large output (M x N tiles filling the GPU twice) takes one K batch with the fewest slice
+// pairs that K allows, since every batch adds a full set of int32 sums to write and read.  A
+// small output is cut along K into about enough batches to fill two tiles per SM, with the
+// fewest-pair width whose batch length allows it.  Beyond one batch, or when no width allows
+// one, the batch count is kept within 1024.  The recombination adds the batches' sums (below
+// k_batches * 2^24) and runs two int64 Horner chains; the split keeps both within 63 bits.
+bool choose_emu_shape(int64_t K, int64_t mn_tiles, int sms, EmuShape* e) {
+  constexpr int BK = Cfg<KIND_SLICE>::BK;
+  const int KC = (int)((K + BK - 1) / BK);
+  e->KC = KC;
+  const int64_t target = 2 * (int64_t)sms;
+  int o = -1, cpb = 0;
+  if (mn_tiles >= target) {
+    for (int i = 0; i < kSliceOpts && o < 0; ++i)
+      if (KC <= max_batch_chunks(i)) {
+        o = i;
+        cpb = KC;
+      }
+  } else {
+    const int want = (int)std::min<int64_t>(KC, (target + mn_tiles - 1) / mn_tiles);
+    const int need = (KC + want - 1) / want;
+    for (int i = 0; i < kSliceOpts && o < 0; ++i) {
+      const int c = std::min(max_batch_chunks(i), need);
+      if ((KC + c - 1) / c <= 1024) {
+        o = i;
+        cpb = c;
+      }
     }
   }
-  return false;
+  for (int i = 0; i < kSliceOpts && o < 0; ++i) {
+    const int mx = max_batch_chunks(i);
+    if ((KC + mx - 1) / mx <= 1024) {
+      o = i;
+      cpb = mx;
+    }
+  }
+  if (o < 0) return false;
+  e->sp.beta = kSliceBeta[o];
+  e->sp.s = kSliceS[o];
+  e->kc_per_batch = cpb;
+  e->k_batches = (KC + cpb - 1) / cpb;
+  int tb = 24;  // bits of |sum over batches of T_d|
+  while ((1ll << (tb - 24)) < e->k_batches) ++tb;
+  const int beta = e->sp.beta, s = e->sp.s;
+  e->split = std::min(s, (62 - tb) / beta + 1);
+  // The second chain holds s - split diagonals: tb + beta (s - split - 1) + 1 bits.
+  if (s > e->split && tb + beta * (s - e->split - 1) + 1 > 63) return false;
+  return true;
 }
 
 // Exponent e with 2^e > |x| for the largest |x| given as its float64 bits with the sign
@@ -761,28 +836,74 @@ __device__ __forceinline__ int scale_exponent(unsigned long long max_abs_bits) {
   return ef ? ef - 1022 : -1022;
 }
 
-// Power-of-two scale per point: exponent e with 2^e > max_j |Z[j][p]| (0 for a zero row).
-__global__ void row_scale_kernel(const double* __restrict__ Z, int64_t J, int64_t P, int* __restrict__ expo) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+// A float64 operand read with strides: X(row, k) = x[row * sr + k * sk].
+struct Operand {
+  const double* x;
+  int64_t sr, sk;
+};
+
+// Largest |X(row, k)| of every row as float64 bits with the sign cleared (positive doubles
+// order like their bit patterns), combined over K ranges by atomicMax into bits[row] (zeroed
+// first).  Grid y = K range of k_per_block.  ROWS_FAST: thread = row (coalesced when
+// sr == 1); otherwise warp = row, lanes across K (coalesced when sk == 1).
+template <bool ROWS_FAST>
+__global__ void row_absmax_kernel(Operand X, int64_t rows, int64_t K, int64_t k_per_block,
+                                  unsigned long long* __restrict__ bits) {
+  const int64_t k0 = (int64_t)blockIdx.y * k_per_block;
+  const int64_t k1 = k0 + k_per_block < K ? k0 + k_per_block : K;
   unsigned long long mx = 0;
-  for (int64_t j = 0; j < J; ++j) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(Z[j * P + p]) & 0x7fffffffffffffffull;
-    mx = b > mx ? b : mx;
+  if constexpr (ROWS_FAST) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    for (int64_t k = k0; k < k1; ++k) {
+      const unsigned long long v =
+          (unsigned long long)__double_as_longlong(X.x[row * X.sr + k * X.sk]) & 0x7fffffffffffffffull;
+      mx = v > mx ? v : mx;
+    }
+    if (mx) atomicMax(bits + row, mx);
+  } else {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= rows) return;
+    for (int64_t k = k0 + lane; k < k1; k += 32) {
+      const unsigned long long v =
+          (unsigned long long)__double_as_longlong(X.x[row * X.sr + k * X.sk]) & 0x7fffffffffffffffull;
+      mx = v > mx ? v : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_down_sync(0xffffffffu, mx, off);
+      mx = o > mx ? o : mx;
+    }
+    if (lane == 0 && mx) atomicMax(bits + row, mx);
   }
-  expo[p] = scale_exponent(mx);
 }
 
-// Power-of-two scale per coefficient set: exponent e with 2^e > max_j |C[j][s]|.
-__global__ void col_scale_kernel(const double* __restrict__ C, int64_t J, int64_t S, int* __restrict__ expo) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  unsigned long long mx = 0;
-  for (int64_t j = 0; j < J; ++j) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(C[j * S + s]) & 0x7fffffffffffffffull;
-    mx = b > mx ? b : mx;
-  }
-  expo[s] = scale_exponent(mx);
+__global__ void row_exponent_kernel(const unsigned long long* __restrict__ bits, int64_t rows, int* __restrict__ expo) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < rows) expo[row] = scale_exponent(bits[row]);
+}
+
+// Power-of-two scale exponent of every row (2^e > max_k |X(row, k)|), with enough K ranges
+// in flight to fill the GPU.  `bits` is scratch of `rows` words.
+zp_status scale_rows(Operand X, int64_t rows, int64_t K, unsigned long long* bits, int* expo, cudaStream_t stream) {
+  if (rows <= 0) return ZP_OK;
+  cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)rows * sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+  const bool rows_fast = X.sr == 1 || K < 32;
+  const int64_t row_threads = rows_fast ? rows : rows * 32;
+  const int64_t want = 152 * 1024;  // about the threads that fill the GPU (152 SMs x 1024)
+  int64_t k_blocks = std::max<int64_t>(1, std::min<int64_t>((want + row_threads - 1) / row_threads, (K + 63) / 64));
+  k_blocks = std::min<int64_t>(k_blocks, 65535);
+  const int64_t kpb = (K + k_blocks - 1) / k_blocks;
+  k_blocks = (K + kpb - 1) / kpb;
+  const dim3 grid((unsigned)((row_threads + 255) / 256), (unsigned)k_blocks);
+  if (rows_fast)
+    row_absmax_kernel<true><<<grid, 256, 0, stream>>>(X, rows, K, kpb, bits);
+  else
+    row_absmax_kernel<false><<<grid, 256, 0, stream>>>(X, rows, K, kpb, bits);
+  row_exponent_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, stream>>>(bits, rows, expo);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "row scale launch");
 }
 
 // X = round-half-even(z * 2^shift) for shift = beta * s - e, i.e. x = z 2^(-e) in [-1, 1] as a
@@ -839,50 +960,34 @@ __device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, u
   }
 }
 
-// A slices of one slab: thread = (point row of the slab, group of 8 consecutive modes).
-__global__ void slice_a_kernel(const double* __restrict__ Z, const int* __restrict__ expo, int64_t J,
-                               int64_t Ps, int64_t tiles, int KC, SliceParams sp, uint8_t* A, int64_t slice_stride) {
-  const int64_t groups = (int64_t)KC * 8;  // 8-mode groups per row
-  const int64_t total = tiles * BM * groups;
+// Slices of an operand's rows in the tensor core's K-major 128-byte-swizzled chunks: tile
+// (row / ROWS) x K chunk kc at ((tile * KC + kc) * ROWS * 128) bytes, slice t a further
+// t * slice_stride.  Thread = (row, group of 8 consecutive K), rows fastest.  Rows past `rows`
+// and K past `K` are zero.
+template <int ROWS>
+__global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
+                                  const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride) {
+  const int64_t rows_pad = tiles * ROWS;
+  const int64_t total = rows_pad * KC * 8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i % (tiles * BM);  // point fastest: coalesced reads of Z[j][p]
-    const int64_t g = i / (tiles * BM);
-    const int64_t j0 = g * 8;
-    const int shift = p < Ps ? sp.beta * sp.s - expo[p] : 0;
+    const int64_t row = i % rows_pad;
+    const int64_t k0 = (i / rows_pad) * 8;
+    const bool valid = row < rows;
+    const int shift = valid ? sp.beta * sp.s - expo[row] : 0;
     long long x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (p < Ps && j0 + q < J) ? to_fixed(Z[(j0 + q) * Ps + p], shift) : 0;
-    const int64_t tile = p / BM;
-    const uint32_t row = (uint32_t)(p % BM);
-    const int kc = (int)(j0 / 64);
-    uint8_t* dst = A + ((size_t)tile * KC + kc) * kAPart + ptx::sw128_offset_b16(row, (uint32_t)(j0 % 64));
-    cut_slices(x, sp.beta, sp.s, dst, slice_stride);
-  }
-}
-
-// B slices: thread = (set, group of 8 consecutive modes).
-__global__ void slice_b_kernel(const double* __restrict__ C, const int* __restrict__ expo, int64_t J, int64_t S,
-                               int NT, int KC, SliceParams sp, uint8_t* B, int64_t slice_stride) {
-  const int64_t rows = (int64_t)NT * BN;
-  const int64_t total = rows * KC * 8;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sidx = i % rows;
-    const int64_t j0 = (i / rows) * 8;
-    const int shift = sidx < S ? sp.beta * sp.s - expo[sidx] : 0;
-    long long x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (sidx < S && j0 + q < J) ? to_fixed(C[(j0 + q) * S + sidx], shift) : 0;
-    const int64_t nt = sidx / BN;
-    const uint32_t row = (uint32_t)(sidx % BN);
-    const int kc = (int)(j0 / 64);
-    uint8_t* dst = B + ((size_t)nt * KC + kc) * kBPart + ptx::sw128_offset_b16(row, (uint32_t)(j0 % 64));
-    cut_slices(x, sp.beta, sp.s, dst, slice_stride);
+    for (int q = 0; q < 8; ++q) x[q] = (valid && k0 + q < K) ? to_fixed(X.x[row * X.sr + (k0 + q) * X.sk], shift) : 0;
+    const int64_t tile = row / ROWS;
+    const uint32_t r = (uint32_t)(row % ROWS);
+    const int kc = (int)(k0 / 64);
+    uint8_t* d = dst + ((size_t)tile * KC + kc) * (ROWS * kRowBytes) + ptx::sw128_offset_b16(r, (uint32_t)(k0 % 64));
+    cut_slices(x, sp.beta, sp.s, d, slice_stride);
   }
 }
 
 // Correctly rounded float64 of N * 2^e2 (round half to even), N a signed 128-bit integer.
 // The mantissa and exponent are assembled on the integer pipe; results outside the normal
-// range (never reached by scaled series values) go through ldexp.
+// range go through ldexp.
 __device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
   if (N == 0) return 0.0;
   const bool neg = N < 0;
@@ -915,62 +1020,71 @@ __device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
 }
 
 // Horner step acc * 2^beta + t in two's-complement int64 (the true value fits; see `split`).
-__device__ __forceinline__ long long horner(long long acc, int beta, int t) {
-  return (long long)(((unsigned long long)acc << beta) + (unsigned long long)(long long)t);
+__device__ __forceinline__ long long horner(long long acc, int beta, long long t) {
+  return (long long)(((unsigned long long)acc << beta) + (unsigned long long)t);
 }
 
-// F[p][s] = sigma_p sigma_s 2^(-beta (ndiag+1)) N with N = sum_d T_d 2^(beta (ndiag+1-d)),
-// d = 2..ndiag+1, formed exactly: the first `split` diagonals in one int64 Horner chain, the
-// rest in another, joined into 128 bits and rounded once.  Row of threads = row p of F.
-__global__ void recombine_kernel(const int* __restrict__ T, int64_t diag_stride, int ndiag, int split, int beta,
-                                 const int* __restrict__ rexp, const int* __restrict__ cexp, int64_t Ps, int64_t S,
-                                 double* __restrict__ F) {
-  const int lo_shift = beta * (ndiag - split);
-  const int e_base = -beta * (ndiag + 1);
-  const bool vec = (S % 4) == 0;
-  for (int64_t p = blockIdx.x; p < Ps; p += gridDim.x) {
-    const int ep = rexp[p] + e_base;
-    const int* trow = T + p * S;
-    double* frow = F + p * S;
+struct RecombineArgs {
+  const int* T;            // [k_batches][ndiag][rows][N] int32 diagonal sums
+  int64_t diag_stride;     // rows * N
+  int64_t batch_stride;    // ndiag * rows * N
+  int k_batches, ndiag, split, beta;
+  const int* rexp;         // [rows]
+  const int* cexp;         // [N]
+  int64_t rows, N;
+  double* C;               // row m at C + m * ldc
+  int64_t ldc;
+};
+
+// C[m][n] = sigma_m sigma_n 2^(-beta (ndiag+1)) Nmn with Nmn = sum_d (sum_batches T_d)
+// 2^(beta (ndiag+1-d)), d = 2..ndiag+1, formed exactly: the first `split` diagonals in one
+// int64 Horner chain, the rest in another, joined into 128 bits and rounded once.
+// Block = row m of C (grid-stride), threads across n.
+__global__ void recombine_kernel(RecombineArgs a) {
+  const int lo_shift = a.beta * (a.ndiag - a.split);
+  const int e_base = -a.beta * (a.ndiag + 1);
+  // Vector path: int4 loads of T (its rows are 4-aligned when N is) and 16-byte stores of C.
+  const bool vec = (a.N % 4) == 0 && (a.ldc % 2) == 0 && ((uintptr_t)a.C % 16) == 0;
+  for (int64_t m = blockIdx.x; m < a.rows; m += gridDim.x) {
+    const int em = a.rexp[m] + e_base;
+    const int* trow = a.T + m * a.N;
+    double* crow = a.C + m * a.ldc;
     if (vec) {
-      for (int64_t s4 = (int64_t)threadIdx.x * 4; s4 < S; s4 += (int64_t)blockDim.x * 4) {
+      for (int64_t n4 = (int64_t)threadIdx.x * 4; n4 < a.N; n4 += (int64_t)blockDim.x * 4) {
         long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+        for (int q = 0; q < a.ndiag; ++q) {
+          long long t[4] = {0, 0, 0, 0};
+          for (int kb = 0; kb < a.k_batches; ++kb) {
+            const int4 v = __ldcs(reinterpret_cast<const int4*>(trow + kb * a.batch_stride + q * a.diag_stride + n4));
+            t[0] += v.x, t[1] += v.y, t[2] += v.z, t[3] += v.w;
+          }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          if (q < ndiag) {
-            const int4 t = __ldcs(reinterpret_cast<const int4*>(trow + (size_t)q * diag_stride + s4));
-            if (q < split) {
-              hi[0] = horner(hi[0], beta, t.x), hi[1] = horner(hi[1], beta, t.y);
-              hi[2] = horner(hi[2], beta, t.z), hi[3] = horner(hi[3], beta, t.w);
-            } else {
-              lo[0] = horner(lo[0], beta, t.x), lo[1] = horner(lo[1], beta, t.y);
-              lo[2] = horner(lo[2], beta, t.z), lo[3] = horner(lo[3], beta, t.w);
-            }
+          for (int k = 0; k < 4; ++k) {
+            if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
+            else lo[k] = horner(lo[k], a.beta, t[k]);
           }
         }
-        const int4 ce = *reinterpret_cast<const int4*>(cexp + s4);
+        const int4 ce = *reinterpret_cast<const int4*>(a.cexp + n4);
         const int e[4] = {ce.x, ce.y, ce.z, ce.w};
         double v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          v[k] = int128_to_double(
-              (__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k], ep + e[k]);
-        __stcs(reinterpret_cast<double2*>(frow + s4), make_double2(v[0], v[1]));
-        __stcs(reinterpret_cast<double2*>(frow + s4 + 2), make_double2(v[2], v[3]));
+          v[k] = int128_to_double((__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k],
+                                  em + e[k]);
+        __stcs(reinterpret_cast<double2*>(crow + n4), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2*>(crow + n4 + 2), make_double2(v[2], v[3]));
       }
     } else {
-      for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+      for (int64_t n = threadIdx.x; n < a.N; n += blockDim.x) {
         long long hi = 0, lo = 0;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          if (q < ndiag) {
-            const int t = trow[(size_t)q * diag_stride + s];
-            if (q < split) hi = horner(hi, beta, t);
-            else lo = horner(lo, beta, t);
-          }
+        for (int q = 0; q < a.ndiag; ++q) {
+          long long t = 0;
+          for (int kb = 0; kb < a.k_batches; ++kb) t += trow[kb * a.batch_stride + q * a.diag_stride + n];
+          if (q < a.split) hi = horner(hi, a.beta, t);
+          else lo = horner(lo, a.beta, t);
         }
-        frow[s] = int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
-                                   ep + cexp[s]);
+        crow[n] = int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
+                                   em + a.cexp[n]);
       }
     }
   }
@@ -980,8 +1094,9 @@ template <int KIND>
 zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, int sms, int pairs, cudaStream_t stream) {
   using C = Cfg<KIND>;
   cudaError_t e;
+  const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
   if (pairs > 0 && tiles >= 2) {
-    const int64_t groups = ((tiles + 1) / 2) * NT;
+    const int64_t groups = ((tiles + 1) / 2) * NT * kb;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(2 * (unsigned)std::min<int64_t>(groups, pairs));
     lc.blockDim = dim3(kGemmThreads);
@@ -996,7 +1111,7 @@ zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, int sms, int pa
     lc.numAttrs = 1;
     e = cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, 2>, ga);
   } else {
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT, sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, sms);
     split_gemm_kernel<KIND, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
     e = cudaGetLastError();
   }
@@ -1032,65 +1147,93 @@ int gemm_pairs(int sms) {
   return pairs;
 }
 
-zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
-                            const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
-  using C = Cfg<KIND_SLICE>;
-  const int64_t J = plan->n_modes;
-  const int KC = (int)((J + C::BK - 1) / C::BK);
-  const int64_t MT = (P + BM - 1) / BM;
-  const int NT = (int)((S + BN - 1) / BN);
-  SliceParams sp;
-  if (!choose_slices((int64_t)KC * C::BK, &sp))
-    return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 contraction supports at most 16320 modes");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int pairs = gemm_pairs<KIND_SLICE>(sms);
-  if (pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
-  // Recombination chains: the first `split` diagonals in one int64 Horner chain need
-  // 24 + beta (split - 1) + 1 <= 63 bits; the rest (at most 4 diagonals for every choice of
-  // choose_slices) need far fewer.
-  const int split = std::min(sp.s, 38 / sp.beta + 1);
-  // Slab of point tiles: int32 diagonal sums (s x rows x S x 4 B) within about 4 GB.
-  const size_t tdiag_tile = (size_t)BM * S * sizeof(int);
-  const int64_t slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / (sp.s * tdiag_tile))));
-  const int64_t rows = slab * BM;
-  const int64_t a_stride = slab * KC * (int64_t)C::A_CHUNK;
-  const int64_t b_stride = (int64_t)NT * KC * C::B_CHUNK;
-  ScratchBuffer zbuf, rsc, csc, abuf, bbuf, tbuf;
-  ZP_TRY(zbuf.alloc((size_t)J * rows * sizeof(double), stream));
-  ZP_TRY(rsc.alloc((size_t)rows * sizeof(int), stream));
-  ZP_TRY(csc.alloc((size_t)S * sizeof(int), stream));
-  ZP_TRY(abuf.alloc((size_t)sp.s * a_stride, stream));
-  ZP_TRY(bbuf.alloc((size_t)sp.s * b_stride, stream));
-  ZP_TRY(tbuf.alloc((size_t)sp.s * rows * S * sizeof(float), stream));
-  cudaError_t e;
-  col_scale_kernel<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(coeffs, J, S, (int*)csc.ptr);
-  slice_b_kernel<<<1024, 256, 0, stream>>>(coeffs, (const int*)csc.ptr, J, S, NT, KC, sp, (uint8_t*)bbuf.ptr,
-                                           b_stride);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "coefficient slicing launch");
-  for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
-    const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
-    const int64_t p0 = mt0 * BM;
-    const int64_t Ps = std::min<int64_t>(tiles * BM, P - p0);
-    ZP_TRY(launch_walk(plan, r + p0, theta + p0, Ps, 0, (double*)zbuf.ptr, nullptr, stream));
-    row_scale_kernel<<<(unsigned)((Ps + 127) / 128), 128, 0, stream>>>((const double*)zbuf.ptr, J, Ps,
-                                                                      (int*)rsc.ptr);
-    slice_a_kernel<<<2048, 256, 0, stream>>>((const double*)zbuf.ptr, (const int*)rsc.ptr, J, Ps, tiles, KC, sp,
-                                             (uint8_t*)abuf.ptr, slab * KC * (int64_t)C::A_CHUNK);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "basis slicing launch");
-    for (int d = 2; d <= sp.s + 1; ++d) {
-      GemmArgs ga{(const uint8_t*)abuf.ptr, (const uint8_t*)bbuf.ptr,
-                  (float*)tbuf.ptr + (size_t)(d - 2) * rows * S, Ps, S, 0, tiles, NT, KC};
+// An emulated GEMM in progress: the B operand sliced once (all N rows), then A in slabs of
+// row tiles, each slab: row scales, slices, one GEMM launch per slice diagonal (all pairs of
+// the diagonal and all K batches), recombination into C.
+struct EmuGemm {
+  EmuShape sh;
+  int64_t N = 0, K = 0, NT = 0;
+  int sms = 0, pairs = 0;
+  int64_t slab_tiles = 0;  // row tiles per slab
+  ScratchBuffer bsl, cexp, asl, rexp, tbuf, maxbits;
+  int64_t a_stride = 0, b_stride = 0;
+
+  // Chooses the shape for M rows, slices B (B(n, k), n < N) and sizes the slab scratch.
+  zp_status prepare(int64_t M, int64_t N_, int64_t K_, Operand B, cudaStream_t stream) {
+    using C = Cfg<KIND_SLICE>;
+    N = N_;
+    K = K_;
+    NT = (N + BN - 1) / BN;
+    const int64_t MT = (M + BM - 1) / BM;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!choose_emu_shape(K, MT * NT, sms, &sh))
+      return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");
+    pairs = gemm_pairs<KIND_SLICE>(sms);
+    if (pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+    // Slab: int32 sums (k_batches x s x rows x N x 4 B) within about 4 GB.
+    const size_t t_tile = (size_t)sh.k_batches * sh.sp.s * BM * N * sizeof(int);
+    slab_tiles = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / t_tile)));
+    a_stride = slab_tiles * sh.KC * (int64_t)C::A_CHUNK;
+    b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;
+    ZP_TRY(bsl.alloc((size_t)sh.sp.s * b_stride, stream));
+    ZP_TRY(cexp.alloc((size_t)N * sizeof(int), stream));
+    ZP_TRY(asl.alloc((size_t)sh.sp.s * a_stride, stream));
+    ZP_TRY(rexp.alloc((size_t)slab_tiles * BM * sizeof(int), stream));
+    ZP_TRY(tbuf.alloc((size_t)slab_tiles * t_tile, stream));
+    ZP_TRY(maxbits.alloc((size_t)std::max<int64_t>(N, slab_tiles * BM) * sizeof(unsigned long long), stream));
+    ZP_TRY(scale_rows(B, N, K, (unsigned long long*)maxbits.ptr, (int*)cexp.ptr, stream));
+    slice_rows_kernel<BN><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                    (uint8_t*)bsl.ptr, b_stride);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "B slicing launch");
+  }
+
+  // C rows [0, rows) (rows <= slab_tiles * BM) = A rows [0, rows) times B^T.
+  zp_status run_slab(int64_t rows, Operand A, double* Cout, int64_t ldc, cudaStream_t stream) {
+    using C = Cfg<KIND_SLICE>;
+    const int64_t tiles = (rows + BM - 1) / BM;
+    ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
+    slice_rows_kernel<BM><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
+                                                    (uint8_t*)asl.ptr, a_stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "A slicing launch");
+    const int64_t trows = slab_tiles * BM;
+    const int64_t diag_stride = trows * N, batch_stride = (int64_t)sh.sp.s * diag_stride;
+    for (int d = 2; d <= sh.sp.s + 1; ++d) {
+      GemmArgs ga{(const uint8_t*)asl.ptr, (const uint8_t*)bsl.ptr,
+                  (float*)tbuf.ptr + (size_t)(d - 2) * diag_stride, rows, N, 0, tiles, (int)NT, sh.KC};
       ga.npairs = d - 1;
       ga.a_slice_stride = a_stride;
       ga.b_slice_stride = b_stride;
-      ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, NT, sms, pairs, stream));
+      ga.k_batches = sh.k_batches;
+      ga.kc_per_batch = sh.kc_per_batch;
+      ga.t_batch_stride = batch_stride;
+      ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, sms, pairs, stream));
     }
-    recombine_kernel<<<(unsigned)std::min<int64_t>(Ps, 8 * sms), 256, 0, stream>>>(
-        (const int*)tbuf.ptr, rows * S, sp.s, split, sp.beta, (const int*)rsc.ptr, (const int*)csc.ptr, Ps, S,
-        out + (size_t)p0 * S);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "recombine_kernel launch");
+    RecombineArgs ra{(const int*)tbuf.ptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
+                     sh.sp.beta, (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
+    recombine_kernel<<<(unsigned)std::min<int64_t>(rows, 8 * (int64_t)sms), 256, 0, stream>>>(ra);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "recombine_kernel launch");
+  }
+};
+
+zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
+                            const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
+  const int64_t J = plan->n_modes;
+  EmuGemm g;
+  // B(n = set s, k = mode j) = C[j][s].
+  ZP_TRY(g.prepare(P, S, J, Operand{coeffs, 1, S}, stream));
+  const int64_t slab_rows = g.slab_tiles * BM;
+  ScratchBuffer zbuf;
+  ZP_TRY(zbuf.alloc((size_t)J * slab_rows * sizeof(double), stream));
+  for (int64_t p0 = 0; p0 < P; p0 += slab_rows) {
+    const int64_t Ps = std::min<int64_t>(slab_rows, P - p0);
+    ZP_TRY(launch_walk(plan, r + p0, theta + p0, Ps, 0, (double*)zbuf.ptr, nullptr, stream));
+    // A(m = point p, k = mode j) = Z[j][p] of this slab.
+    ZP_TRY(g.run_slab(Ps, Operand{(const double*)zbuf.ptr, 1, Ps}, out + (size_t)p0 * S, S, stream));
   }
   return ZP_OK;
 }
@@ -1100,6 +1243,27 @@ zp_status run_emulated_fp64(const zp_plan* plan, const double* r, const double* 
 zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                                     const double* coeffs, int64_t S, double* out, cudaStream_t stream) {
   return run_emulated_fp64(plan, r, theta, P, coeffs, S, out, stream);
+}
+
+zp_status emulated_gemm_fp64(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_sm, int64_t a_sk,
+                             const double* B, int64_t b_sn, int64_t b_sk, double* C, int64_t ldc,
+                             cudaStream_t stream) {
+  if (M <= 0 || N <= 0) return ZP_OK;
+  if (K <= 0) {
+    for (int64_t m = 0; m < M; ++m) {
+      const cudaError_t e = cudaMemsetAsync(C + m * ldc, 0, (size_t)N * sizeof(double), stream);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    }
+    return ZP_OK;
+  }
+  EmuGemm g;
+  ZP_TRY(g.prepare(M, N, K, Operand{B, b_sn, b_sk}, stream));
+  const int64_t slab_rows = g.slab_tiles * BM;
+  for (int64_t m0 = 0; m0 < M; m0 += slab_rows) {
+    const int64_t rows = std::min<int64_t>(slab_rows, M - m0);
+    ZP_TRY(g.run_slab(rows, Operand{A + m0 * a_sm, a_sm, a_sk}, C + m0 * ldc, ldc, stream));
+  }
+  return ZP_OK;
 }
 
 zp_status series_eval_split(const zp_plan* plan, const double* r, const double* theta, int64_t P,

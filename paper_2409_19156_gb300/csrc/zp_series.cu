@@ -211,7 +211,7 @@ zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* t
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs, double* grad_r,
                               double* grad_theta, cudaStream_t stream, double* hess_rr, double* hess_rt,
-                              double* hess_tt) {
+                              double* hess_tt, bool emulated) {
   const int64_t J = plan->n_modes;
   const bool need_h = grad_r || grad_theta || hess_rr || hess_rt || hess_tt;
   ScratchBuffer z, hbuf;
@@ -219,17 +219,27 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
   if (grad_coeffs) {
     ZP_TRY(z.alloc((size_t)J * P * sizeof(double), stream));
     ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream));
-    ZP_TRY(get_cublas(cl, stream));
-    // grad_C row-major [J][S] = column-major S x J = G^T (S x P) * Z^T (P x J):
-    //   G row-major [P][S] is column-major S x P; Z row-major [J][P] is column-major P x J.
-    ZP_TRY(dgemm(cl.h, false, false, S, J, P, G, S, (const double*)z.ptr, P, grad_coeffs, S));
+    if (emulated) {
+      // grad_C[j][s] = sum_p Z[j][p] G[p][s]: A(j, p) = Z[j * P + p], B(s, p) = G[p * S + s].
+      ZP_TRY(emulated_gemm_fp64(J, S, P, (const double*)z.ptr, P, 1, G, 1, S, grad_coeffs, S, stream));
+    } else {
+      ZP_TRY(get_cublas(cl, stream));
+      // grad_C row-major [J][S] = column-major S x J = G^T (S x P) * Z^T (P x J):
+      //   G row-major [P][S] is column-major S x P; Z row-major [J][P] is column-major P x J.
+      ZP_TRY(dgemm(cl.h, false, false, S, J, P, G, S, (const double*)z.ptr, P, grad_coeffs, S));
+    }
   }
   if (need_h) {
     ZP_TRY(hbuf.alloc((size_t)J * P * sizeof(double), stream));
-    if (!cl.h) ZP_TRY(get_cublas(cl, stream));
-    // H row-major [J][P] = column-major P x J = G (P x S) * C^T (S x J):
-    //   G column-major S x P -> op T; C column-major S x J -> op N.
-    ZP_TRY(dgemm(cl.h, true, false, P, J, S, G, S, coeffs, S, (double*)hbuf.ptr, P));
+    if (emulated) {
+      // H[j][p] = sum_s C[j][s] G[p][s]: A(j, s) = C[j * S + s], B(p, s) = G[p * S + s].
+      ZP_TRY(emulated_gemm_fp64(J, P, S, coeffs, S, 1, G, S, 1, (double*)hbuf.ptr, P, stream));
+    } else {
+      if (!cl.h) ZP_TRY(get_cublas(cl, stream));
+      // H row-major [J][P] = column-major P x J = G (P x S) * C^T (S x J):
+      //   G column-major S x P -> op T; C column-major S x J -> op N.
+      ZP_TRY(dgemm(cl.h, true, false, P, J, S, G, S, coeffs, S, (double*)hbuf.ptr, P));
+    }
     const int64_t blocks = (P + kRedThreads - 1) / kRedThreads;
     if (hess_rr || hess_rt || hess_tt)
       adjoint_point_kernel<true><<<(unsigned)blocks, kRedThreads, 0, stream>>>(
@@ -312,7 +322,17 @@ zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, co
 zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                  const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_coeffs,
                                  double* grad_r, double* grad_theta, void* stream) {
+  return zp_series_adjoint_plan_prec(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r,
+                                     grad_theta, ZP_PREC_FP64, stream);
+}
+
+zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                      const double* coeffs, int64_t n_sets, const double* grad_out,
+                                      double* grad_coeffs, double* grad_r, double* grad_theta, zp_precision prec,
+                                      void* stream) {
   clear_error();
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP64_EMULATED)
+    return set_error(ZP_ERR_INVALID_ARG, "the adjoint takes ZP_PREC_FP64 or ZP_PREC_FP64_EMULATED");
   ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
   if (grad_coeffs) ZP_TRY(check_device_array(grad_coeffs, "grad_coeffs", 8));
   if (grad_r) ZP_TRY(check_device_array(grad_r, "grad_r", 8));
@@ -328,7 +348,8 @@ zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const dou
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
   }
   ZP_TRY(check_device_array(grad_out, "grad_out", 8));
-  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st);
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st, nullptr,
+                             nullptr, nullptr, prec == ZP_PREC_FP64_EMULATED);
 }
 
 zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,

@@ -23,11 +23,19 @@ zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* t
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
                               double* grad_r, double* grad_theta, cudaStream_t stream,
-                              double* hess_rr = nullptr, double* hess_rt = nullptr, double* hess_tt = nullptr);
+                              double* hess_rr = nullptr, double* hess_rt = nullptr, double* hess_tt = nullptr,
+                              bool emulated = false);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
 // Float64-accurate series by error-free slicing on the tensor cores (float64 output).
 zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                                     const double* coeffs, int64_t S, double* out, cudaStream_t stream);
+// Float64-accurate GEMM on the tensor cores by the same slicing:
+//   C[m * ldc + n] = sum_k A[m * a_sm + k * a_sk] * B[n * b_sn + k * b_sk],  m < M, n < N.
+// Error bound: about K 2^-54 max_k |A(m, k)| max_k |B(n, k)| per element.  Scratch is
+// allocated stream-ordered on `stream`.
+zp_status emulated_gemm_fp64(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_sm, int64_t a_sk,
+                             const double* B, int64_t b_sn, int64_t b_sk, double* C, int64_t ldc,
+                             cudaStream_t stream);
 
 // Caller-provided scratch for the split path: `b` holds the split coefficient tiles,
 // `a` the split basis of as many point tiles as fit (at least one).

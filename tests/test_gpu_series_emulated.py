@@ -92,3 +92,74 @@ def test_emulated_fp64_extreme_column_scales():
     tol[:, 4] += scale_bound[:, 4]
     assert (F[:, 2] == 0.0).all()
     assert (np.abs(F - want) <= tol).all(), float(np.max(np.abs(F - want) / tol))
+
+
+def scale_bound(K, A_rows, B_rows):
+    """The slicing scheme's bound for C[m][n] = sum_k A[m][k] B[n][k]: every operand is cut to
+    54 bits of its row's power-of-two scale, so the error is about K 2^-54 max_k |A[m]|
+    max_k |B[n]|; 2^-48 leaves a factor 64 of slack."""
+    return K * 2.0 ** -48 * np.outer(np.abs(A_rows).max(axis=1), np.abs(B_rows).max(axis=1))
+
+
+@pytest.mark.parametrize("nmax,P,S", [(7, 90, 4), (3, 1500, 3)])
+def test_emulated_adjoint_against_oracle(nmax, P, S):
+    """grad_C = Z G (contraction over the points; 1500 points with 10 modes cut K into many
+    batches) and grad_r, grad_theta through H = C G^T, all by the emulated contraction."""
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.uniform_points(P, 22 + nmax)
+    C = inputs.scaled_normal_coeffs(ns, S, 22)
+    G = np.random.default_rng(5).standard_normal((P, S))
+    gC, gr, gt = zp.series_adjoint(ns, ms, dev(r), dev(th), dev(C), dev(G), prec="fp64emu")
+    wC, wr, wt = oseries.series_adjoint(ns, ms, r, th, C.tolist(), G.tolist())
+    Z = np.array(obasis.basis_table(ns, ms, r, th, 0)[0][0])  # [J][P]
+    tolC = 1e-13 * (1.0 + np.abs(Z) @ np.abs(G)) + scale_bound(P, Z, G.T)
+    assert (np.abs(gC.cpu().numpy() - np.array(wC)) <= tolC).all()
+    scale = 1.0 + np.abs(G).sum(1) * np.abs(C).sum() * max(nmax, 1) ** 2
+    assert (np.abs(gr.cpu().numpy() - np.array(wr)) <= 1e-12 * scale).all()
+    assert (np.abs(gt.cpu().numpy() - np.array(wt)) <= 1e-12 * scale).all()
+
+
+def test_emulated_adjoint_series_n24_full_size_against_fp64():
+    """The 325-mode, 50000-point, 256-set adjoint: the emulated contractions (grad_C over 50000
+    points in K batches, H over 256 sets) against the DGEMM path."""
+    cfg = inputs.WORKLOADS["series_n24"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.polar_grid(cfg["n_r"], cfg["n_theta"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    plan = zp.Plan(ns, ms)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    G = torch.randn((len(r), C.shape[1]), dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(DEV).manual_seed(3))
+    e = zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu")
+    f = zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
+    Z = zp.basis(None, None, rt, tt, 0, plan=plan)[0][0]
+    bC = 1e-12 * (1.0 + Z.abs() @ G.abs()) + len(r) * 2.0 ** -48 * torch.outer(Z.abs().amax(1), G.abs().amax(0))
+    assert bool(((e[0] - f[0]).abs() <= bC).all())
+    for a, b in zip(e[1:], f[1:]):
+        assert bool(((a - b).abs() <= 1e-10 * (1.0 + b.abs().max())).all())
+
+
+def test_emulated_fit_against_oracle_and_fp64():
+    """Weighted least squares with the Gram matrix and right-hand side by the emulated
+    contraction: against the oracle fit, and the full-size series_n24 round trip."""
+    from oracle import fit as ofit
+
+    ns, ms = inputs.full_zernike_modes(10)
+    r, th = inputs.polar_grid(12, 24)
+    _, wgl = np.polynomial.legendre.leggauss(12)
+    w = np.repeat(0.25 * wgl, 24) * (2.0 * np.pi / 24)
+    Y = np.random.default_rng(1).standard_normal((len(r), 5))
+    got = zp.series_fit(ns, ms, dev(r), dev(th), dev(Y), weights=dev(w), prec="fp64emu").cpu().numpy()
+    want = ofit.series_fit(ns, ms, r, th, Y, w)
+    assert np.max(np.abs(got - want)) < 1e-10 * (1 + np.max(np.abs(want)))
+    cfg = inputs.WORKLOADS["series_n24"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.polar_grid(cfg["n_r"], cfg["n_theta"])
+    _, wgl = np.polynomial.legendre.leggauss(cfg["n_r"])
+    w = np.repeat(0.25 * wgl, cfg["n_theta"]) * (2.0 * np.pi / cfg["n_theta"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    plan = zp.Plan(ns, ms)
+    rt, tt = dev(r), dev(th)
+    Yf = zp.series_eval(None, None, rt, tt, dev(C), plan=plan)
+    got = zp.series_fit(None, None, rt, tt, Yf, weights=dev(w), plan=plan, prec="fp64emu").cpu().numpy()
+    assert np.max(np.abs(got - C)) < 1e-10
