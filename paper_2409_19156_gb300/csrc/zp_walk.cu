@@ -112,8 +112,9 @@ __device__ __forceinline__ void store_pair(double* dst, int64_t p, double v0, do
 }
 
 // KMAX: highest rho-derivative; ANG: multiply by cos/sin(|m| theta) (Z instead of R);
-// VEC: 16-byte stores (P even and outputs 16-byte aligned).
-template <int KMAX, bool ANG, bool VEC>
+// VEC: 16-byte stores (P even and outputs 16-byte aligned); DUP (with ANG): the plan has steps
+// with more than two outputs (duplicated modes), whose angular products are formed once.
+template <int KMAX, bool ANG, bool VEC, bool DUP = false>
 __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
   extern __shared__ double smem[];
   const Column col = a.cols[blockIdx.y];
@@ -204,6 +205,45 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
 #pragma unroll
       for (int i = 0; i < kPPT; ++i) R[i][k] = fma(W, V[i][k], zero);
     }
+    if constexpr (ANG && DUP) {
+      if (s_end - s_begin > 2) {
+        // Duplicated modes (several outputs per (column, N)): each angular product once per
+        // (step, k), stored to every output of the step.
+#pragma unroll
+        for (int k = 0; k <= KMAX; ++k) {
+          double rc[kPPT], rs[kPPT];
+#pragma unroll
+          for (int i = 0; i < kPPT; ++i) {
+            rc[i] = fma(R[i][k], cs[i], zero);
+            rs[i] = fma(R[i][k], sn[i], zero);
+          }
+          for (int s = s_begin; s < s_end; ++s) {
+            const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+            const int64_t j = (int64_t)(code & 0x7fffffffu);
+            const bool is_sin = (code >> 31) != 0;
+            store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, is_sin ? rs[0] : rc[0], is_sin ? rs[1] : rc[1], two,
+                       VEC);
+          }
+        }
+        if (a.out_dtheta) {
+          // d/dtheta: m R cos(m theta) for a sin output, -m R sin(m theta) for a cos output.
+          const double md = (double)m;
+          double dsn[kPPT], dcs[kPPT];
+#pragma unroll
+          for (int i = 0; i < kPPT; ++i) {
+            dsn[i] = fma(R[i][0], md * cs[i], zero);
+            dcs[i] = fma(R[i][0], -md * sn[i], zero);
+          }
+          for (int s = s_begin; s < s_end; ++s) {
+            const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+            const int64_t j = (int64_t)(code & 0x7fffffffu);
+            const bool is_sin = (code >> 31) != 0;
+            store_pair(a.out_dtheta + j * a.P, p0, is_sin ? dsn[0] : dcs[0], is_sin ? dsn[1] : dcs[1], two, VEC);
+          }
+        }
+        return;
+      }
+    }
     for (int s = s_begin; s < s_end; ++s) {
       const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
       const int64_t j = (int64_t)(code & 0x7fffffffu);
@@ -285,11 +325,17 @@ __global__ void __launch_bounds__(kThreads) per_mode_kernel(const Column* cols, 
 }
 
 template <int KMAX, bool ANG>
-cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, size_t smem, bool vec, cudaStream_t st) {
-  if (vec)
+cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, size_t smem, bool vec, bool dup, cudaStream_t st) {
+  if (ANG && dup) {
+    if (vec)
+      walk_kernel<KMAX, ANG, true, true><<<grid, kThreads, smem, st>>>(a);
+    else
+      walk_kernel<KMAX, ANG, false, true><<<grid, kThreads, smem, st>>>(a);
+  } else if (vec) {
     walk_kernel<KMAX, ANG, true><<<grid, kThreads, smem, st>>>(a);
-  else
+  } else {
     walk_kernel<KMAX, ANG, false><<<grid, kThreads, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -374,11 +420,14 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
     a.cs = cs;
     a.sn = sn;
   }
+  // Duplicated modes: some (column, N) step stores to more than two outputs.
+  bool dup = false;
+  for (size_t i = 0; i + 1 < plan->slot_ptr.size() && !dup; ++i) dup = plan->slot_ptr[i + 1] - plan->slot_ptr[i] > 2;
   switch (max_deriv) {
-    case 0: e = ang ? launch_walk_t<0, true>(a, grid, smem, vec, stream) : launch_walk_t<0, false>(a, grid, smem, vec, stream); break;
-    case 1: e = ang ? launch_walk_t<1, true>(a, grid, smem, vec, stream) : launch_walk_t<1, false>(a, grid, smem, vec, stream); break;
-    case 2: e = ang ? launch_walk_t<2, true>(a, grid, smem, vec, stream) : launch_walk_t<2, false>(a, grid, smem, vec, stream); break;
-    case 3: e = ang ? launch_walk_t<3, true>(a, grid, smem, vec, stream) : launch_walk_t<3, false>(a, grid, smem, vec, stream); break;
+    case 0: e = ang ? launch_walk_t<0, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<0, false>(a, grid, smem, vec, dup, stream); break;
+    case 1: e = ang ? launch_walk_t<1, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<1, false>(a, grid, smem, vec, dup, stream); break;
+    case 2: e = ang ? launch_walk_t<2, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<2, false>(a, grid, smem, vec, dup, stream); break;
+    case 3: e = ang ? launch_walk_t<3, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<3, false>(a, grid, smem, vec, dup, stream); break;
     default: return set_error(ZP_ERR_DERIV_ORDER, "max_deriv outside 0..3");
   }
   if (e != cudaSuccess) return cuda_error(e, "walk_kernel launch");

@@ -8,7 +8,7 @@ import paper_2409_19156_gb300 as zp  # noqa: E402
 from paper_2409_19156_gb300 import inputs  # noqa: E402
 from oracle import basis as obasis  # noqa: E402
 
-from helpers import radial_tolerance  # noqa: E402
+from helpers import assert_radial_close, radial_tolerance  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -61,3 +61,26 @@ def test_basis_duplicates_and_large_theta():
     th = th * 7.0  # angles beyond 2 pi
     got = check(ns, ms, r, th, 1, what="dups")
     assert np.array_equal(got[:, 0], got[:, 3])
+
+
+def test_basis_many_duplicates_per_step():
+    """A mode list repeated 16 times (the Zernike x Fourier expansion of the Sec. 3 footnote):
+    every step stores its value to many outputs (the angular products are formed once per
+    step); each copy equals the unduplicated evaluation bit for bit, all derivatives and
+    d/dtheta included, with the point tables in use (> 8192 points)."""
+    ns, ms = inputs.full_zernike_modes(6)
+    L = 16
+    nd, md = np.repeat(ns, L), np.repeat(ms, L)
+    r, th = inputs.uniform_points(9000, 44)
+    rt, tt = dev(r), dev(th)
+    Z1, T1 = zp.basis(ns, ms, rt, tt, 3, dtheta=True)
+    Zd, Td = zp.basis(nd, md, rt, tt, 3, dtheta=True)
+    torch.cuda.synchronize()
+    for c in range(L):
+        assert torch.equal(Zd[:, c::L, :], Z1)
+        assert torch.equal(Td[c::L, :], T1)
+    sub = np.array([0, 17, 4500, 8999])
+    want_z, want_t = obasis.basis_table(ns, ms, r[sub], th[sub], 3, with_dtheta=True)
+    got = Z1[:, :, torch.as_tensor(sub, device=DEV)].cpu().numpy()
+    assert_radial_close(got, np.array(want_z), ns, "dup basis")
+    assert np.max(np.abs(T1[:, torch.as_tensor(sub, device=DEV)].cpu().numpy() - np.array(want_t))) < 1e-11 * 36
