@@ -63,6 +63,8 @@ def parse_args():
                     help="with --series-only: also time the emulated float64 contraction")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the series_n24 forward / adjoint / fit measurement (profiling captures)")
+    ap.add_argument("--adjoint-emulated-only", action="store_true",
+                    help="run only the series_n24 emulated-float64 adjoint (profiling captures)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
@@ -619,6 +621,26 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
             "fit_emulated_roundtrip_max_abs_err": float((Cfit_emu - Ct).abs().max())}
 
 
+def measure_adjoint_emulated(dev, steps: int = 2) -> dict:
+    """series_n24 emulated-float64 adjoint alone (one warm-up call, then `steps` timed calls)."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import inputs
+
+    cfg = inputs.WORKLOADS["series_n24"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.polar_grid(cfg["n_r"], cfg["n_theta"])
+    C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    G = torch.randn((len(r), C.shape[1]), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(2))
+    plan = zp.Plan(ns, ms, device=dev)
+    rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
+    stream = torch.cuda.current_stream(dev)
+    zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu")
+    ms_ = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu"), steps)
+    return {"workload": "series_n24", "fp64_emulated_adjoint_ms": ms_}
+
+
 def measure_paper_shapes(dev, steps: int = 50) -> dict:
     """The paper's own timing shapes.  (1) Algorithm 2 (one recursion per mode) against the
     per-column walk (Algorithm 1's decomposition) on the 2601-mode radial set, k = 0, 100000
@@ -816,6 +838,13 @@ def main():
         res = measure_batched(torch.device("cuda", 0), steps=args.steps, n_instances=args.batched_instances,
                               point_scale=args.batched_point_scale, tune=False)
         print(json.dumps({"batched_only": res}), flush=True)
+        return
+    if args.adjoint_emulated_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"adjoint_emulated_only": measure_adjoint_emulated(torch.device("cuda", 0),
+                                                                            steps=args.steps)}), flush=True)
         return
     if args.adjoint_only:
         import torch
