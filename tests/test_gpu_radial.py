@@ -161,3 +161,17 @@ def test_maximum_order_modes_n1000():
     assert np.max(np.abs(got[0][:, 1] - 1.0)) < 1e-11
     with pytest.raises(zp.ZernikeError):
         zp.radial([1001], [1], torch.as_tensor(r, device=DEV), 0)
+
+
+def test_point_tables_match_direct_seeds():
+    """Launches of >= 8192 points take their seeds from the per-point tables of rho^j; the
+    same points in a short launch compute them directly.  Both agree with the oracle,
+    including points outside [0, 1] (evaluated as polynomials) and the exact endpoints."""
+    ns, ms = inputs.radial_modes(40)
+    r = np.concatenate([[0.0, 1.0, 1.0 + 1e-6, 1.3, -0.2, -1.0], inputs.uniform_points(9000, 81)[0]])
+    big = run_radial(ns, ms, r, 3)
+    sub = np.arange(12)
+    small = run_radial(ns, ms, r[sub], 3)
+    want = np.array(oradial.radial_table(ns, ms, r[sub], 3))
+    assert_radial_close(big[:, :, sub], want, ns, "tables")
+    assert_radial_close(small, want, ns, "direct")
