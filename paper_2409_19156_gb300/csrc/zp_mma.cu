@@ -1052,16 +1052,33 @@ __global__ void recombine_kernel(RecombineArgs a) {
     if (vec) {
       for (int64_t n4 = (int64_t)threadIdx.x * 4; n4 < a.N; n4 += (int64_t)blockDim.x * 4) {
         long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
-        for (int q = 0; q < a.ndiag; ++q) {
-          long long t[4] = {0, 0, 0, 0};
-          for (int kb = 0; kb < a.k_batches; ++kb) {
-            const int4 v = __ldcs(reinterpret_cast<const int4*>(trow + kb * a.batch_stride + q * a.diag_stride + n4));
-            t[0] += v.x, t[1] += v.y, t[2] += v.z, t[3] += v.w;
-          }
+        if (a.k_batches == 1) {
+          // One batch: the diagonal loads are independent, unrolled so they are all in flight.
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
-            else lo[k] = horner(lo[k], a.beta, t[k]);
+          for (int q = 0; q < 16; ++q) {
+            if (q < a.ndiag) {
+              const int4 v = __ldcs(reinterpret_cast<const int4*>(trow + q * a.diag_stride + n4));
+              const long long t[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
+                else lo[k] = horner(lo[k], a.beta, t[k]);
+              }
+            }
+          }
+        } else {
+          for (int q = 0; q < a.ndiag; ++q) {
+            long long t[4] = {0, 0, 0, 0};
+            for (int kb = 0; kb < a.k_batches; ++kb) {
+              const int4 v =
+                  __ldcs(reinterpret_cast<const int4*>(trow + kb * a.batch_stride + q * a.diag_stride + n4));
+              t[0] += v.x, t[1] += v.y, t[2] += v.z, t[3] += v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
+              else lo[k] = horner(lo[k], a.beta, t[k]);
+            }
           }
         }
         const int4 ce = *reinterpret_cast<const int4*>(a.cexp + n4);
