@@ -51,17 +51,34 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
   if (p >= P) return;
   const double rho = r[p], u = rho * rho, th = theta[p];
   double acc_r = 0.0, acc_t = 0.0, acc_rr = 0.0, acc_rt = 0.0, acc_tt = 0.0;
+  // cos / sin(m theta) and rho^(m-2), rho^(m-1), rho^m: advanced by one angle addition and one
+  // product when the next column has m + 1 (the usual column order), else computed directly.
+  double s1, c1;
+  sincos(th, &s1, &c1);
+  double cs = 1.0, sn = 0.0, pm2 = 0.0, pm1 = 0.0, pm = 1.0;
+  int m_prev = 0;
   for (int c = 0; c < n_cols; ++c) {
     const Column col = cols[c];
     const int m = col.m;
     const double* h = table + (size_t)col.table_row * kRow;
     const int32_t* sp = slot_ptr + col.slot_base;
-    double cs = 1.0, sn = 0.0;
-    if (m != 0) sincos((double)m * th, &sn, &cs);
-    // Seeds of the Taylor lanes: N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
-    const double pm2 = m >= 2 ? pow_uint_r(rho, m - 2) : 0.0;
-    const double pm1 = m >= 2 ? pm2 * rho : (m == 1 ? 1.0 : 0.0);
-    const double pm = m >= 1 ? pm1 * rho : 1.0;
+    if (c > 0 && m == m_prev + 1) {
+      const double cn = fma(cs, c1, -sn * s1);
+      sn = fma(sn, c1, cs * s1);
+      cs = cn;
+      pm2 = pm1;
+      pm1 = pm;
+      pm *= rho;
+    } else if (c == 0 || m != m_prev) {
+      cs = 1.0;
+      sn = 0.0;
+      if (m != 0) sincos((double)m * th, &sn, &cs);
+      // Seeds of the Taylor lanes: N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
+      pm2 = m >= 2 ? pow_uint_r(rho, m - 2) : 0.0;
+      pm1 = m >= 2 ? pm2 * rho : (m == 1 ? 1.0 : 0.0);
+      pm = m >= 1 ? pm1 * rho : 1.0;
+    }
+    m_prev = m;
     double T0 = pm, T1 = h[1] * pm1, T2 = HESS ? h[2] * pm2 : 0.0;
     double S0 = fma(h[4], pm * u, -(h[8] * pm));
     double S1 = fma(h[5], pm * rho, -(h[9] * pm1));
