@@ -57,9 +57,12 @@ def test_plan_cache_eviction_keeps_results_correct():
             assert np.max(np.abs(out - want)) < 1e-12
 
 
-def test_plan_entry_points_capture_in_a_cuda_graph():
+@pytest.mark.parametrize("P", [1000, 10000])
+def test_plan_entry_points_capture_in_a_cuda_graph(P):
+    """1000 points: the walk alone; 10000 points: the point-table kernel and its stream-ordered
+    scratch allocation are captured too."""
     ns, ms = inputs.full_zernike_modes(12)
-    r, th = inputs.uniform_points(1000, 7)
+    r, th = inputs.uniform_points(P, 7)
     rt, tt = torch.as_tensor(r, device=DEV), torch.as_tensor(th, device=DEV)
     plan = zp.Plan(ns, ms)
     ref, _ = zp.basis(None, None, rt, tt, 2, plan=plan)
@@ -76,7 +79,7 @@ def test_plan_entry_points_capture_in_a_cuda_graph():
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     # new inputs in the same buffers, replay again
-    r2 = inputs.uniform_points(1000, 8)[0]
+    r2 = inputs.uniform_points(P, 8)[0]
     rt.copy_(torch.as_tensor(r2, device=DEV))
     g.replay()
     torch.cuda.synchronize()
