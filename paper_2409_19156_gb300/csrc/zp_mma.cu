@@ -384,12 +384,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t rank = CL == 2 ? ptx::cluster_ctarank() : 0u;
+  const uint32_t rank = CL > 1 ? ptx::cluster_ctarank() : 0u;
   const int64_t cid = blockIdx.x / CL, nclusters = gridDim.x / CL;
+  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
+  // Cluster geometry: CL point tiles x one set tile; this CTA holds point tile mi of the group.
+  constexpr int CM = CL, CN = 1;
+  const uint32_t mi = rank, ni = 0u;
+  // CTAs whose bulk copies write into this CTA's stages: each of their MMA commits frees a stage.
+  constexpr uint32_t kWriters = (uint32_t)CL;
+  const uint16_t commit_mask = (uint16_t)0x3;
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::STAGES; ++i) {
       ptx::mbar_init(&full[i], 1);
-      ptx::mbar_init(&empty[i], CL);
+      ptx::mbar_init(&empty[i], kWriters);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tmem_full[i], 1);
@@ -404,14 +411,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) ptx::cluster_sync();  // peers' barriers exist before any multicast
+  if constexpr (CL > 1) ptx::cluster_sync();  // peers' barriers exist before any multicast
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
 
-  // Tile t of this cluster: k batch t / (groups * n_tiles), then point-tile group (CL point
-  // tiles) and set tile, set tile fastest.
-  const int64_t groups = (a.m_tiles + CL - 1) / CL;
-  const int64_t per_batch = groups * a.n_tiles;
+  // Tile t of this cluster: k batch t / per_batch, then point-tile group (CM point tiles) and
+  // set-tile group (CN set tiles), set-tile group fastest.
+  const int64_t groups = (a.m_tiles + CM - 1) / CM;
+  const int64_t groups_n = (a.n_tiles + CN - 1) / CN;
+  const int64_t per_batch = groups * groups_n;
   const int64_t total = per_batch * a.k_batches;
   const int kcb = a.kc_per_batch > 0 ? a.kc_per_batch : a.KC;
   // K chunks [kc0, kc0 + nkc) of tile t.
@@ -431,15 +439,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       uint32_t phase = 0;
       for (int64_t t = cid; t < total && !*abort_flag; t += nclusters) {
         const int64_t tm = t % per_batch;
-        const int64_t mt = (tm / a.n_tiles) * CL + rank;
-        const int nt = (int)(tm % a.n_tiles);
+        const int64_t mt = (tm / groups_n) * CM + mi;
+        const int nt = (int)((tm % groups_n) * CN + ni);
         int kc0, nkc;
         k_range(t, kc0, nkc);
-        // A pair's second tile past the slab end reuses the last valid tile's data (its rows
-        // are never stored); it still takes part in the shared B loads.
+        // A group's tiles past the slab end (or the last set tile) reuse the last valid tile's
+        // data (their outputs are never stored); they still take part in the shared loads.
         const int64_t mt_src = mt < a.m_tiles ? mt : a.m_tiles - 1;
+        const int nt_src = nt < a.n_tiles ? nt : a.n_tiles - 1;
         const uint8_t* gA0 = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
-        const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
+        const uint8_t* gB0 = a.B + (size_t)nt_src * a.KC * C::B_CHUNK;
         for (int kk = 0; kk < a.npairs * nkc; ++kk) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
@@ -450,11 +459,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride;
           uint8_t* sA = smem + stage * C::STAGE;
           ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
-          ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
           if constexpr (CL == 1) {
+            ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
             ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
           } else {
             constexpr uint32_t HALF = C::B_CHUNK / 2;
+            ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
             ptx::bulk_g2s_multicast(sA + C::A_CHUNK + rank * HALF, gB + (size_t)kc * C::B_CHUNK + rank * HALF, HALF,
                                     &full[stage], (uint16_t)0x3);
           }
@@ -515,7 +525,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           if constexpr (CL == 1) {
             ptx::mma_commit(&empty[stage]);
           } else {
-            ptx::mma_commit_multicast(&empty[stage], (uint16_t)0x3);
+            ptx::mma_commit_multicast(&empty[stage], commit_mask);
           }
           if (++stage == C::STAGES) {
             stage = 0;
@@ -543,10 +553,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       }
       ptx::tc_fence_after();
       const int64_t tm = t % per_batch;
-      const int64_t mt_local = (tm / a.n_tiles) * CL + rank;
-      const bool valid_tile = mt_local < a.m_tiles;
+      const int64_t mt_local = (tm / groups_n) * CM + mi;
+      const int nt = (int)((tm % groups_n) * CN + ni);
+      const bool valid_tile = mt_local < a.m_tiles && nt < a.n_tiles;
       const int64_t mt = a.mt_base + mt_local;
-      const int nt = (int)(tm % a.n_tiles);
       const int64_t p = mt * BM + row;
       const int64_t col0 = (int64_t)nt * BN;
       float* frow = a.F + (t / per_batch) * a.t_batch_stride + p * a.S;
@@ -582,8 +592,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
-  // No CTA of a pair leaves while its peer may still multicast into it or arrive on its barriers.
-  if constexpr (CL == 2) ptx::cluster_sync();
+  // No CTA of a cluster leaves while a peer may still multicast into it or arrive on its barriers.
+  if constexpr (CL > 1) ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, 512);
@@ -628,6 +638,92 @@ struct PhaseTimer {
   }
 };
 
+// Co-scheduling of the GEMM's CTA pairs (point-tile pairs sharing B): how many fit on the GPU
+// at once (0: pairs cannot run).  (2 x 2 clusters sharing A as well were built and measured
+// 2-3 % slower on GB300, so the kernel keeps pairs.)
+struct GemmShape {
+  int sms = 0, pairs = 0;
+};
+
+template <int KIND, int CL>
+int max_active_clusters(int sms) {
+  using C = Cfg<KIND>;
+  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int n = 0;
+  cudaLaunchConfig_t q = {};
+  q.gridDim = dim3(CL * (unsigned)sms);
+  q.blockDim = dim3(kGemmThreads);
+  q.dynamicSmemBytes = C::SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  q.attrs = at;
+  q.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<KIND, CL>, &q) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  return n;
+}
+
+template <int KIND>
+zp_status gemm_shape(GemmShape* g) {
+  using C = Cfg<KIND>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+  }
+  g->pairs = max_active_clusters<KIND, 2>(g->sms);
+  if (g->pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+  return ZP_OK;
+}
+
+template <int KIND, int CL>
+cudaError_t launch_clustered(const GemmArgs& ga, unsigned clusters, cudaStream_t stream) {
+  using C = Cfg<KIND>;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(CL * clusters);
+  lc.blockDim = dim3(kGemmThreads);
+  lc.dynamicSmemBytes = C::SMEM;
+  lc.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, CL>, ga);
+}
+
+// Persistent launch over `tiles` point tiles x NT set tiles (x K batches): CTA pairs when they
+// can run and there are two point tiles, else single CTAs; at most as many as are co-resident.
+template <int KIND>
+zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, const GemmShape& g, cudaStream_t stream) {
+  using C = Cfg<KIND>;
+  const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
+  cudaError_t e;
+  if (g.pairs > 0 && tiles >= 2) {
+    const int64_t groups = ((tiles + 1) / 2) * NT * kb;
+    e = launch_clustered<KIND, 2>(ga, (unsigned)std::min<int64_t>(groups, g.pairs), stream);
+  } else {
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, g.sms);
+    split_gemm_kernel<KIND, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "split_gemm_kernel launch");
+}
+
 template <bool TF32>
 zp_status run_split(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
                     int64_t S, float* out, cudaStream_t stream, float* phase_ms, const SplitScratch* preset) {
@@ -640,9 +736,6 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   const int KC = (int)((J + C::BK - 1) / C::BK);
   const int64_t MT = (P + BM - 1) / BM;
   const int NT = (int)((S + BN - 1) / BN);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t tile_bytes = (size_t)KC * C::A_CHUNK;
   const size_t b_bytes = (size_t)NT * KC * C::B_CHUNK;
   ScratchBuffer bbuf, abuf;
@@ -667,34 +760,14 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     B = (uint8_t*)bbuf.ptr;
   }
 
+  constexpr int KIND = TF32 ? KIND_TF32 : KIND_BF16X3;
   const uint32_t coeff_smem = C::B_CHUNK + 1024;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
-          cudaSuccess)
-    return cuda_error(e, "cudaFuncSetAttribute(split kernels)");
-  // CTA pairs when the GPU can co-schedule them (the occupancy query says how many pairs fit).
-  int pairs = 0;
-  {
-    cudaLaunchConfig_t q = {};
-    q.gridDim = dim3(2 * (unsigned)sms);
-    q.blockDim = dim3(kGemmThreads);
-    q.dynamicSmemBytes = C::SMEM;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    q.attrs = at;
-    q.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, &q) != cudaSuccess) {
-      cudaGetLastError();
-      pairs = 0;
-    }
-  }
+      cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute(split_coeff_kernel)");
+  GemmShape gs;
+  ZP_TRY(gemm_shape<KIND>(&gs));
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
   timer.begin(0, &ev0, stream);
@@ -712,27 +785,7 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
     timer.end(1, ev0, stream);
     GemmArgs ga{A, B, out, P, S, mt0, tiles, NT, KC};
     timer.begin(2, &ev0, stream);
-    if (pairs > 0 && tiles >= 2) {
-      const int64_t groups = ((tiles + 1) / 2) * NT;
-      cudaLaunchConfig_t lc = {};
-      lc.gridDim = dim3(2 * (unsigned)std::min<int64_t>(groups, pairs));
-      lc.blockDim = dim3(kGemmThreads);
-      lc.dynamicSmemBytes = C::SMEM;
-      lc.stream = stream;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 2;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      lc.attrs = at;
-      lc.numAttrs = 1;
-      e = cudaLaunchKernelEx(&lc, split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 2>, ga);
-    } else {
-      const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT, sms);
-      split_gemm_kernel<TF32 ? KIND_TF32 : KIND_BF16X3, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
-      e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return cuda_error(e, "split_gemm_kernel launch");
+    ZP_TRY(launch_gemm<KIND>(ga, tiles, NT, gs, stream));
     timer.end(2, ev0, stream);
   }
   return timer.finish();
@@ -1107,70 +1160,14 @@ __global__ void recombine_kernel(RecombineArgs a) {
   }
 }
 
-template <int KIND>
-zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, int sms, int pairs, cudaStream_t stream) {
-  using C = Cfg<KIND>;
-  cudaError_t e;
-  const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
-  if (pairs > 0 && tiles >= 2) {
-    const int64_t groups = ((tiles + 1) / 2) * NT * kb;
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(2 * (unsigned)std::min<int64_t>(groups, pairs));
-    lc.blockDim = dim3(kGemmThreads);
-    lc.dynamicSmemBytes = C::SMEM;
-    lc.stream = stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    e = cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, 2>, ga);
-  } else {
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, sms);
-    split_gemm_kernel<KIND, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
-    e = cudaGetLastError();
-  }
-  return e == cudaSuccess ? ZP_OK : cuda_error(e, "split_gemm_kernel launch");
-}
-
-template <int KIND>
-int gemm_pairs(int sms) {
-  using C = Cfg<KIND>;
-  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(split_gemm_kernel<KIND, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  int pairs = 0;
-  cudaLaunchConfig_t q = {};
-  q.gridDim = dim3(2 * (unsigned)sms);
-  q.blockDim = dim3(kGemmThreads);
-  q.dynamicSmemBytes = C::SMEM;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  q.attrs = at;
-  q.numAttrs = 1;
-  if (cudaOccupancyMaxActiveClusters(&pairs, split_gemm_kernel<KIND, 2>, &q) != cudaSuccess) {
-    cudaGetLastError();
-    pairs = 0;
-  }
-  return pairs;
-}
-
 // An emulated GEMM in progress: the B operand sliced once (all N rows), then A in slabs of
 // row tiles, each slab: row scales, slices, one GEMM launch per slice diagonal (all pairs of
 // the diagonal and all K batches), recombination into C.
 struct EmuGemm {
   EmuShape sh;
   int64_t N = 0, K = 0, NT = 0;
-  int sms = 0, pairs = 0;
+  int sms = 0;
+  GemmShape gs;
   int64_t slab_tiles = 0;  // row tiles per slab
   ScratchBuffer bsl, cexp, asl, rexp, tbuf, maxbits;
   int64_t a_stride = 0, b_stride = 0;
@@ -1182,13 +1179,10 @@ struct EmuGemm {
     K = K_;
     NT = (N + BN - 1) / BN;
     const int64_t MT = (M + BM - 1) / BM;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ZP_TRY(gemm_shape<KIND_SLICE>(&gs));
+    sms = gs.sms;
     if (!choose_emu_shape(K, MT * NT, sms, &sh))
       return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");
-    pairs = gemm_pairs<KIND_SLICE>(sms);
-    if (pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
     // Slab: int32 sums (k_batches x s x rows x N x 4 B) within about 4 GB.
     const size_t t_tile = (size_t)sh.k_batches * sh.sp.s * BM * N * sizeof(int);
     slab_tiles = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / t_tile)));
@@ -1227,7 +1221,7 @@ struct EmuGemm {
       ga.k_batches = sh.k_batches;
       ga.kc_per_batch = sh.kc_per_batch;
       ga.t_batch_stride = batch_stride;
-      ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, sms, pairs, stream));
+      ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, gs, stream));
     }
     RecombineArgs ra{(const int*)tbuf.ptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
                      sh.sp.beta, (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
