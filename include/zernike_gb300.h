@@ -72,7 +72,9 @@ typedef enum {
                          scales, about n_modes * 2^-54 * max_j |Z[j][p]| * max_j |C[j][s]| for
                          F[p][s], rather than by sum_j |Z C| as for float64 arithmetic: a
                          coefficient set whose entries span many orders of magnitude keeps
-                         fewer bits on its small entries than the FP64 path */
+                         fewer bits on its small entries than the FP64 path.  An infinity or
+                         NaN in a coefficient set (or in a point's basis row) makes that set's
+                         (point's) outputs NaN */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */

@@ -881,11 +881,17 @@ bool choose_emu_shape(int64_t K, int64_t mn_tiles, int sms, EmuShape* e) {
   return true;
 }
 
+// Row exponent marking a row that holds an infinity or a NaN: its slices are zero and every
+// output that involves it is NaN.
+constexpr int kNonFiniteRow = 1 << 20;
+
 // Exponent e with 2^e > |x| for the largest |x| given as its float64 bits with the sign
-// cleared (positive doubles order like their bit patterns); 0 for zero.  Subnormals get -1022.
+// cleared (positive doubles order like their bit patterns, infinities and NaNs above all
+// finite values); 0 for zero, -1022 for subnormals, kNonFiniteRow for a non-finite row.
 __device__ __forceinline__ int scale_exponent(unsigned long long max_abs_bits) {
   if (max_abs_bits == 0) return 0;
   const int ef = (int)(max_abs_bits >> 52);
+  if (ef == 0x7ff) return kNonFiniteRow;
   return ef ? ef - 1022 : -1022;
 }
 
@@ -1026,10 +1032,12 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     const int64_t row = i % rows_pad;
     const int64_t k0 = (i / rows_pad) * 8;
     const bool valid = row < rows;
-    const int shift = valid ? sp.beta * sp.s - expo[row] : 0;
+    const int ex = valid ? expo[row] : 0;
+    const bool use = valid && ex != kNonFiniteRow;
+    const int shift = sp.beta * sp.s - ex;
     long long x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (valid && k0 + q < K) ? to_fixed(X.x[row * X.sr + (k0 + q) * X.sk], shift) : 0;
+    for (int q = 0; q < 8; ++q) x[q] = (use && k0 + q < K) ? to_fixed(X.x[row * X.sr + (k0 + q) * X.sk], shift) : 0;
     const int64_t tile = row / ROWS;
     const uint32_t r = (uint32_t)(row % ROWS);
     const int kc = (int)(k0 / 64);
@@ -1099,6 +1107,7 @@ __global__ void recombine_kernel(RecombineArgs a) {
   // Vector path: int4 loads of T (its rows are 4-aligned when N is) and 16-byte stores of C.
   const bool vec = (a.N % 4) == 0 && (a.ldc % 2) == 0 && ((uintptr_t)a.C % 16) == 0;
   for (int64_t m = blockIdx.x; m < a.rows; m += gridDim.x) {
+    const bool row_bad = a.rexp[m] == kNonFiniteRow;
     const int em = a.rexp[m] + e_base;
     const int* trow = a.T + m * a.N;
     double* crow = a.C + m * a.ldc;
@@ -1139,8 +1148,10 @@ __global__ void recombine_kernel(RecombineArgs a) {
         double v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          v[k] = int128_to_double((__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k],
-                                  em + e[k]);
+          v[k] = (row_bad || e[k] == kNonFiniteRow)
+                     ? __longlong_as_double(0x7ff8000000000000ll)
+                     : int128_to_double((__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k],
+                                        em + e[k]);
         __stcs(reinterpret_cast<double2*>(crow + n4), make_double2(v[0], v[1]));
         __stcs(reinterpret_cast<double2*>(crow + n4 + 2), make_double2(v[2], v[3]));
       }
@@ -1153,8 +1164,10 @@ __global__ void recombine_kernel(RecombineArgs a) {
           if (q < a.split) hi = horner(hi, a.beta, t);
           else lo = horner(lo, a.beta, t);
         }
-        crow[n] = int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
-                                   em + a.cexp[n]);
+        crow[n] = (row_bad || a.cexp[n] == kNonFiniteRow)
+                      ? __longlong_as_double(0x7ff8000000000000ll)
+                      : int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
+                                         em + a.cexp[n]);
       }
     }
   }

@@ -181,3 +181,22 @@ def test_emulated_autograd_matches_fp64_autograd():
         grads.append((F.detach(), rt.grad, tt.grad, Ct.grad))
     for a, b in zip(grads[0], grads[1]):
         assert bool(((a - b).abs() <= 1e-11 * (1.0 + b.abs().max())).all())
+
+
+def test_emulated_non_finite_inputs_give_nan_rows_and_sets():
+    """An infinity or NaN in a coefficient set makes that set's outputs NaN, a NaN point makes
+    that point's outputs NaN; every other output keeps float64 accuracy."""
+    ns, ms = inputs.full_zernike_modes(6)
+    r, th = inputs.uniform_points(300, 12)
+    r[7] = np.nan
+    C = inputs.scaled_normal_coeffs(ns, 5, 12)
+    C[3, 1] = np.nan
+    C[0, 2] = np.inf
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), "fp64emu").cpu().numpy()
+    assert np.isnan(F[:, 1]).all() and np.isnan(F[:, 2]).all() and np.isnan(F[7]).all()
+    ok_rows = np.array([p for p in range(300) if p != 7])
+    good = np.ix_(ok_rows, [0, 3, 4])
+    Cg = C[:, [0, 3, 4]]
+    want = np.array(oseries.series_eval(ns, ms, r[ok_rows], th[ok_rows], Cg.tolist()))
+    tol = 1e-13 * (1.0 + abs_bound(ns, ms, r[ok_rows], th[ok_rows], Cg))
+    assert (np.abs(F[good] - want) <= tol).all()
