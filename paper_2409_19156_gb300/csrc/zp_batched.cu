@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "zp_device.cuh"
 #include "zp_api_common.h"
 #include "zp_series_internal.h"
 
@@ -75,16 +76,6 @@ struct BatchArgs {
   int persistent;
 };
 
-__device__ __forceinline__ double pow_uint_b(double x, int e) {
-  double result = 1.0, base = x;
-  while (e) {
-    if (e & 1) result *= base;
-    base *= base;
-    e >>= 1;
-  }
-  return result;
-}
-
 // One point of one instance: forward (F row) or the point part of the adjoint.
 template <int MODE>
 __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
@@ -127,7 +118,7 @@ __device__ void point_work(const InstanceDesc& d, int64_t p, int64_t S) {
           cm = 1.0;
           sm = 0.0;
         }
-        pm1 = m >= 1 ? pow_uint_b(rho, m - 1) : 0.0;
+        pm1 = m >= 1 ? pow_uint(rho, m - 1) : 0.0;
         pm = m >= 1 ? pm1 * rho : 1.0;
       }
       m_prev = m;
@@ -323,7 +314,7 @@ __global__ void batched_column_kernel(BatchArgs a, int max_slots) {
             cm[k] = 0.0;  // invalid points contribute nothing
             sm[k] = 0.0;
           }
-          const double pm = pow_uint_b(rho[k], m);
+          const double pm = pow_uint(rho[k], m);
           T[k] = pm;
           Sx[k] = fma(h[4], pm * u[k], -(h[8] * pm));
 #pragma unroll

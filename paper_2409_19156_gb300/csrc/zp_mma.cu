@@ -27,6 +27,7 @@
 #include <utility>
 #include <vector>
 
+#include "zp_device.cuh"
 #include "zp_api_common.h"
 #include "zp_ptx.cuh"
 #include "zp_series_internal.h"
@@ -103,16 +104,6 @@ __device__ __forceinline__ float float_of_double(double x) {
     bits = sign | ((e - 896u) << 23) | mant;
   }
   return __uint_as_float(bits);
-}
-
-__device__ __forceinline__ double pow_uint_m(double x, int e) {
-  double result = 1.0, base = x;
-  while (e) {
-    if (e & 1) result *= base;
-    base *= base;
-    e >>= 1;
-  }
-  return result;
 }
 
 struct BasisArgs {
@@ -246,7 +237,7 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
         const int64_t p = (a.mt_base + tile) * BM + rowi[i];
         const double th = p < a.P ? a.theta[p] : 0.0;
         sincos((double)m * th, &sm[i], &cm[i]);
-        pm[i] = pow_uint_m(rho[i], m);
+        pm[i] = pow_uint(rho[i], m);
       }
       cf[i] = float_of_double(cm[i]);
       sf[i] = float_of_double(sm[i]);

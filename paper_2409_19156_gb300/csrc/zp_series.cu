@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "zp_device.cuh"
 #include "zp_api_common.h"
 #include "zp_series_internal.h"
 
@@ -23,16 +24,6 @@ namespace zp {
 namespace {
 
 constexpr int kRedThreads = 128;
-
-__device__ __forceinline__ double pow_uint_r(double x, int e) {
-  double result = 1.0, base = x;
-  while (e) {
-    if (e & 1) result *= base;
-    base *= base;
-    e >>= 1;
-  }
-  return result;
-}
 
 // One thread per point: walks every |m| column (Taylor lanes k <= 1, or k <= 2 with HESS) and
 // accumulates, with H[j][p] = sum_s C[j, s] G[p, s],
@@ -74,7 +65,7 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
       sn = 0.0;
       if (m != 0) sincos((double)m * th, &sn, &cs);
       // Seeds of the Taylor lanes: N = 0 -> rho^m, N = 1 -> (m+2) rho^(m+2) - (m+1) rho^m.
-      pm2 = m >= 2 ? pow_uint_r(rho, m - 2) : 0.0;
+      pm2 = m >= 2 ? pow_uint(rho, m - 2) : 0.0;
       pm1 = m >= 2 ? pm2 * rho : (m == 1 ? 1.0 : 0.0);
       pm = m >= 1 ? pm1 * rho : 1.0;
     }

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "zp_device.cuh"
 #include "zp_api_common.h"
 #include "zp_internal.h"
 #include "zp_series_internal.h"
@@ -61,17 +62,6 @@ struct WalkArgs {
 __global__ void __launch_bounds__(128) point_prep_kernel(const double* __restrict__ r, const double* __restrict__ theta,
                                                          int64_t P, int pw_max, int trig_max, double* __restrict__ pw,
                                                          double* __restrict__ cs, double* __restrict__ sn);
-
-__device__ __forceinline__ double pow_uint(double x, int e) {
-  double result = 1.0;
-  double base = x;
-  while (e) {
-    if (e & 1) result *= base;
-    base *= base;
-    e >>= 1;
-  }
-  return result;
-}
 
 __global__ void __launch_bounds__(128) point_prep_kernel(const double* __restrict__ r, const double* __restrict__ theta,
                                                          int64_t P, int pw_max, int trig_max, double* __restrict__ pw,
