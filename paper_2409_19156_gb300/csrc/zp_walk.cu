@@ -1,7 +1,7 @@
 // The per-(point, |m|-column) recursion walk: radial polynomials, rho-derivatives, Z.
 //
 // Work decomposition (Algorithm 1 of Sec. 3, mapped to the GPU): one thread owns
-// kPPT consecutive points of one |m| column and walks the Jacobi degree N = 0 .. N_max in
+// one or two consecutive points of one |m| column and walks the Jacobi degree N = 0 .. N_max in
 // registers, storing every requested (n, m) of that column as it passes (the store list
 // comes from the plan; the duplicated-modes variant of Sec. 3 is several entries per N).
 // The recursion is the beta = 0 Jacobi recursion of Sec. 2 in the rescaled form built by
@@ -32,9 +32,9 @@
 namespace zp {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;      // threads per block of a full-size launch, 2 points each
+constexpr int kThreadsSmall = 32;  // short launches: 1 point per thread, more and shorter warps
 constexpr int kPPT = 2;
-constexpr int kPointsPerBlock = kThreads * kPPT;
 
 struct WalkArgs {
   const Column* cols;
@@ -92,7 +92,12 @@ __global__ void __launch_bounds__(128) point_prep_kernel(const double* __restric
   }
 }
 
-__device__ __forceinline__ void store_pair(double* dst, int64_t p, double v0, double v1, bool two, bool vec) {
+template <int PPT>
+__device__ __forceinline__ void store_pts(double* dst, int64_t p, double v0, double v1, bool two, bool vec) {
+  if constexpr (PPT == 1) {
+    __stcs(dst + p, v0);
+    return;
+  }
   if (vec) {
     __stcs(reinterpret_cast<double2*>(dst + p), make_double2(v0, v1));
   } else {
@@ -104,8 +109,12 @@ __device__ __forceinline__ void store_pair(double* dst, int64_t p, double v0, do
 // KMAX: highest rho-derivative; ANG: multiply by cos/sin(|m| theta) (Z instead of R);
 // VEC: 16-byte stores (P even and outputs 16-byte aligned); DUP (with ANG): the plan has steps
 // with more than two outputs (duplicated modes), whose angular products are formed once.
-template <int KMAX, bool ANG, bool VEC, bool DUP = false>
-__global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
+// TPB: threads per block: 128 with two points per thread, or 32 with one point per thread for
+// short launches (a short launch is bound by its longest warp's dependent float64 chain, so
+// more, shorter warps spread over more SMs finish sooner).
+template <int KMAX, bool ANG, bool VEC, bool DUP = false, int TPB = kThreads>
+__global__ void __launch_bounds__(TPB) walk_kernel(WalkArgs a) {
+  constexpr int PPT = TPB == kThreads ? kPPT : 1;
   extern __shared__ double smem[];
   const Column col = a.cols[blockIdx.y];
   const int n_rows = kHeaderRows + col.n_steps;
@@ -113,53 +122,56 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
   int32_t* sptr = reinterpret_cast<int32_t*>(smem + (size_t)n_rows * kRow);
   {
     const double* src = a.table + (size_t)col.table_row * kRow;
-    for (int i = threadIdx.x; i < n_rows * kRow; i += kThreads) tab[i] = src[i];
+    for (int i = threadIdx.x; i < n_rows * kRow; i += TPB) tab[i] = src[i];
     const int32_t* s2 = a.slot_ptr + col.slot_base;
-    for (int i = threadIdx.x; i <= col.n_steps; i += kThreads) sptr[i] = s2[i];
+    for (int i = threadIdx.x; i <= col.n_steps; i += TPB) sptr[i] = s2[i];
   }
   __syncthreads();
 
-  const int64_t p0 = (int64_t)blockIdx.x * kPointsPerBlock + (int64_t)threadIdx.x * kPPT;
+  const int64_t p0 = ((int64_t)blockIdx.x * TPB + (int64_t)threadIdx.x) * PPT;
   if (p0 >= a.P) return;
-  const bool two = p0 + 1 < a.P;
+  const bool two = PPT == 2 && p0 + 1 < a.P;
   const int m = col.m;
 
-  double rho[kPPT], u[kPPT];
+  double rho[PPT], u[PPT];
   rho[0] = a.r[p0];
-  rho[1] = two ? a.r[p0 + 1] : 0.0;
+  if constexpr (PPT == 2) rho[PPT - 1] = two ? a.r[p0 + 1] : 0.0;
 #pragma unroll
-  for (int i = 0; i < kPPT; ++i) u[i] = rho[i] * rho[i];
+  for (int i = 0; i < PPT; ++i) u[i] = rho[i] * rho[i];
 
-  double cs[kPPT], sn[kPPT];
+  double cs[PPT], sn[PPT];
   if constexpr (ANG) {
 #pragma unroll
-    for (int i = 0; i < kPPT; ++i) {
+    for (int i = 0; i < PPT; ++i) {
       cs[i] = 1.0;
       sn[i] = 0.0;
     }
     if (a.cs != nullptr) {
       cs[0] = a.cs[(int64_t)m * a.P + p0];
       sn[0] = a.sn[(int64_t)m * a.P + p0];
-      if (two) {
-        cs[1] = a.cs[(int64_t)m * a.P + p0 + 1];
-        sn[1] = a.sn[(int64_t)m * a.P + p0 + 1];
+      if constexpr (PPT == 2) {
+        if (two) {
+          cs[PPT - 1] = a.cs[(int64_t)m * a.P + p0 + 1];
+          sn[PPT - 1] = a.sn[(int64_t)m * a.P + p0 + 1];
+        }
       }
     } else if (m != 0) {
-      const double th0 = a.theta[p0];
-      const double th1 = two ? a.theta[p0 + 1] : 0.0;
-      sincos((double)m * th0, &sn[0], &cs[0]);
-      sincos((double)m * th1, &sn[1], &cs[1]);
+      sincos((double)m * a.theta[p0], &sn[0], &cs[0]);
+      if constexpr (PPT == 2) {
+        const double th1 = two ? a.theta[p0 + 1] : 0.0;
+        sincos((double)m * th1, &sn[PPT - 1], &cs[PPT - 1]);
+      }
     }
   }
 
   // Seeds.  pw[i] = rho^(m - KMAX + i) for i = 0 .. KMAX+2 (0 for negative exponents, whose
   // coefficients vanish).
-  double S[kPPT][KMAX + 1], T[kPPT][KMAX + 1];
+  double S[PPT][KMAX + 1], T[PPT][KMAX + 1];
   {
     const double* h = tab;
     const int e0 = m - KMAX;
 #pragma unroll
-    for (int i = 0; i < kPPT; ++i) {
+    for (int i = 0; i < PPT; ++i) {
       double pw[KMAX + 3];
       if (a.pw != nullptr) {
         const int64_t pi = (i == 0 || two) ? p0 + i : p0;
@@ -181,19 +193,19 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
     }
   }
 
-  auto store_step = [&](int N, const double (&V)[kPPT][KMAX + 1]) {
+  auto store_step = [&](int N, const double (&V)[PPT][KMAX + 1]) {
     const int s_begin = sptr[N], s_end = sptr[N + 1];
     if (s_begin == s_end) return;
     const double* row = tab + (size_t)(kHeaderRows + N) * kRow;
     // row[7] holds 0.0: multiplies are issued as FMAs with a zero addend the compiler cannot
     // fold away, because GB300 issues DFMA faster than DMUL (1.88 vs 1.59 lanes/SM/clk).
     const double zero = row[7];
-    double R[kPPT][KMAX + 1];
+    double R[PPT][KMAX + 1];
 #pragma unroll
     for (int k = 0; k <= KMAX; ++k) {
       const double W = row[3 + k];
 #pragma unroll
-      for (int i = 0; i < kPPT; ++i) R[i][k] = fma(W, V[i][k], zero);
+      for (int i = 0; i < PPT; ++i) R[i][k] = fma(W, V[i][k], zero);
     }
     if constexpr (ANG && DUP) {
       if (s_end - s_begin > 2) {
@@ -201,9 +213,9 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
         // (step, k), stored to every output of the step.
 #pragma unroll
         for (int k = 0; k <= KMAX; ++k) {
-          double rc[kPPT], rs[kPPT];
+          double rc[PPT], rs[PPT];
 #pragma unroll
-          for (int i = 0; i < kPPT; ++i) {
+          for (int i = 0; i < PPT; ++i) {
             rc[i] = fma(R[i][k], cs[i], zero);
             rs[i] = fma(R[i][k], sn[i], zero);
           }
@@ -211,16 +223,16 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
             const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
             const int64_t j = (int64_t)(code & 0x7fffffffu);
             const bool is_sin = (code >> 31) != 0;
-            store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, is_sin ? rs[0] : rc[0], is_sin ? rs[1] : rc[1], two,
+            store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, is_sin ? rs[0] : rc[0], is_sin ? rs[PPT - 1] : rc[PPT - 1], two,
                        VEC);
           }
         }
         if (a.out_dtheta) {
           // d/dtheta: m R cos(m theta) for a sin output, -m R sin(m theta) for a cos output.
           const double md = (double)m;
-          double dsn[kPPT], dcs[kPPT];
+          double dsn[PPT], dcs[PPT];
 #pragma unroll
-          for (int i = 0; i < kPPT; ++i) {
+          for (int i = 0; i < PPT; ++i) {
             dsn[i] = fma(R[i][0], md * cs[i], zero);
             dcs[i] = fma(R[i][0], -md * sn[i], zero);
           }
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
             const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
             const int64_t j = (int64_t)(code & 0x7fffffffu);
             const bool is_sin = (code >> 31) != 0;
-            store_pair(a.out_dtheta + j * a.P, p0, is_sin ? dsn[0] : dcs[0], is_sin ? dsn[1] : dcs[1], two, VEC);
+            store_pts<PPT>(a.out_dtheta + j * a.P, p0, is_sin ? dsn[0] : dcs[0], is_sin ? dsn[PPT - 1] : dcs[PPT - 1], two, VEC);
           }
         }
         return;
@@ -239,24 +251,24 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
       const int64_t j = (int64_t)(code & 0x7fffffffu);
       if constexpr (ANG) {
         const bool is_sin = (code >> 31) != 0;
-        double f[kPPT];
+        double f[PPT];
 #pragma unroll
-        for (int i = 0; i < kPPT; ++i) f[i] = is_sin ? sn[i] : cs[i];
+        for (int i = 0; i < PPT; ++i) f[i] = is_sin ? sn[i] : cs[i];
 #pragma unroll
         for (int k = 0; k <= KMAX; ++k)
-          store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, fma(R[0][k], f[0], zero), fma(R[1][k], f[1], zero),
+          store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, fma(R[0][k], f[0], zero), fma(R[PPT - 1][k], f[PPT - 1], zero),
                      two, VEC);
         if (a.out_dtheta) {
           const double md = (double)m;
-          double dt[kPPT];
+          double dt[PPT];
 #pragma unroll
-          for (int i = 0; i < kPPT; ++i) dt[i] = is_sin ? md * cs[i] : -md * sn[i];
-          store_pair(a.out_dtheta + j * a.P, p0, fma(R[0][0], dt[0], zero), fma(R[1][0], dt[1], zero), two, VEC);
+          for (int i = 0; i < PPT; ++i) dt[i] = is_sin ? md * cs[i] : -md * sn[i];
+          store_pts<PPT>(a.out_dtheta + j * a.P, p0, fma(R[0][0], dt[0], zero), fma(R[PPT - 1][0], dt[PPT - 1], zero), two, VEC);
         }
       } else {
 #pragma unroll
         for (int k = 0; k <= KMAX; ++k)
-          store_pair(a.out + ((int64_t)k * a.J + j) * a.P, p0, R[0][k], R[1][k], two, VEC);
+          store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, R[0][k], R[PPT - 1][k], two, VEC);
       }
     }
   };
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(WalkArgs a) {
     const double* row = tab + (size_t)(kHeaderRows + N) * kRow;
     const double A = row[0], B = row[1], A2 = row[2], zero = row[7];
 #pragma unroll
-    for (int i = 0; i < kPPT; ++i) {
+    for (int i = 0; i < PPT; ++i) {
       const double g = fma(A, u[i], -B);
       double nw[KMAX + 1];
       nw[0] = fma(g, S[i][0], -T[i][0]);
@@ -314,19 +326,26 @@ __global__ void __launch_bounds__(kThreads) per_mode_kernel(const Column* cols, 
   }
 }
 
-template <int KMAX, bool ANG>
-cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, size_t smem, bool vec, bool dup, cudaStream_t st) {
+template <int KMAX, bool ANG, int TPB>
+cudaError_t launch_walk_tpb(const WalkArgs& a, dim3 grid, size_t smem, bool vec, bool dup, cudaStream_t st) {
   if (ANG && dup) {
     if (vec)
-      walk_kernel<KMAX, ANG, true, true><<<grid, kThreads, smem, st>>>(a);
+      walk_kernel<KMAX, ANG, true, true, TPB><<<grid, TPB, smem, st>>>(a);
     else
-      walk_kernel<KMAX, ANG, false, true><<<grid, kThreads, smem, st>>>(a);
+      walk_kernel<KMAX, ANG, false, true, TPB><<<grid, TPB, smem, st>>>(a);
   } else if (vec) {
-    walk_kernel<KMAX, ANG, true><<<grid, kThreads, smem, st>>>(a);
+    walk_kernel<KMAX, ANG, true, false, TPB><<<grid, TPB, smem, st>>>(a);
   } else {
-    walk_kernel<KMAX, ANG, false><<<grid, kThreads, smem, st>>>(a);
+    walk_kernel<KMAX, ANG, false, false, TPB><<<grid, TPB, smem, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+template <int KMAX, bool ANG>
+cudaError_t launch_walk_t(const WalkArgs& a, dim3 grid, bool small, size_t smem, bool vec, bool dup,
+                          cudaStream_t st) {
+  return small ? launch_walk_tpb<KMAX, ANG, kThreadsSmall>(a, grid, smem, vec, dup, st)
+               : launch_walk_tpb<KMAX, ANG, kThreads>(a, grid, smem, vec, dup, st);
 }
 
 }  // namespace
@@ -379,9 +398,17 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
   a.J = plan->n_modes;
   a.out = out;
   a.out_dtheta = out_dtheta;
-  const int64_t blocks_x = (n_points + kPointsPerBlock - 1) / kPointsPerBlock;
+  // Short launches (fewer than eight 128-thread blocks per SM) take 32-thread blocks of one
+  // point per thread: more, shorter warps over more SMs.
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n_cols = (int64_t)plan->cols.size();
+  const bool small = ((n_points + kThreads * kPPT - 1) / (kThreads * kPPT)) * n_cols < 8 * (int64_t)sms;
+  const int64_t per_block = small ? kThreadsSmall : kThreads * kPPT;
+  const int64_t blocks_x = (n_points + per_block - 1) / per_block;
   if (blocks_x > 0x7fffffffLL) return set_error(ZP_ERR_INVALID_ARG, "n_points too large for one launch");
-  dim3 grid((unsigned)blocks_x, (unsigned)plan->cols.size());
+  dim3 grid((unsigned)blocks_x, (unsigned)n_cols);
   const size_t smem = (size_t)(kHeaderRows + plan->max_steps) * kRow * sizeof(double) +
                       (size_t)(plan->max_steps + 1) * sizeof(int32_t);
   const bool vec = (n_points % 2 == 0) && ((uintptr_t)out % 16 == 0) &&
@@ -414,10 +441,10 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
   bool dup = false;
   for (size_t i = 0; i + 1 < plan->slot_ptr.size() && !dup; ++i) dup = plan->slot_ptr[i + 1] - plan->slot_ptr[i] > 2;
   switch (max_deriv) {
-    case 0: e = ang ? launch_walk_t<0, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<0, false>(a, grid, smem, vec, dup, stream); break;
-    case 1: e = ang ? launch_walk_t<1, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<1, false>(a, grid, smem, vec, dup, stream); break;
-    case 2: e = ang ? launch_walk_t<2, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<2, false>(a, grid, smem, vec, dup, stream); break;
-    case 3: e = ang ? launch_walk_t<3, true>(a, grid, smem, vec, dup, stream) : launch_walk_t<3, false>(a, grid, smem, vec, dup, stream); break;
+    case 0: e = ang ? launch_walk_t<0, true>(a, grid, small, smem, vec, dup, stream) : launch_walk_t<0, false>(a, grid, small, smem, vec, dup, stream); break;
+    case 1: e = ang ? launch_walk_t<1, true>(a, grid, small, smem, vec, dup, stream) : launch_walk_t<1, false>(a, grid, small, smem, vec, dup, stream); break;
+    case 2: e = ang ? launch_walk_t<2, true>(a, grid, small, smem, vec, dup, stream) : launch_walk_t<2, false>(a, grid, small, smem, vec, dup, stream); break;
+    case 3: e = ang ? launch_walk_t<3, true>(a, grid, small, smem, vec, dup, stream) : launch_walk_t<3, false>(a, grid, small, smem, vec, dup, stream); break;
     default: return set_error(ZP_ERR_DERIV_ORDER, "max_deriv outside 0..3");
   }
   if (e != cudaSuccess) return cuda_error(e, "walk_kernel launch");
