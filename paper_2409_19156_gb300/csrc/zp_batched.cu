@@ -338,6 +338,9 @@ __global__ void batched_column_kernel(BatchArgs a, int max_slots) {
             }
           }
           const int sb = sp[N], se = sp[N + 1];
+          double rq[PPT];  // R = w_N Q, shared by the step's outputs
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) rq[k] = row[3] * q[k];
           for (int s = sb; s < se; ++s) {
             const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
             const bool is_sin = (code >> 31) != 0;
@@ -346,7 +349,7 @@ __global__ void batched_column_kernel(BatchArgs a, int max_slots) {
             for (int i = 0; i < kSC; ++i) v[i] = 0.0;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              const double z = row[3] * q[k] * (is_sin ? sm[k] : cm[k]);
+              const double z = rq[k] * (is_sin ? sm[k] : cm[k]);
 #pragma unroll
               for (int i = 0; i < kSC; ++i) v[i] = fma(z, G[k][i], v[i]);
             }
