@@ -74,7 +74,9 @@ typedef enum {
                          coefficient set whose entries span many orders of magnitude keeps
                          fewer bits on its small entries than the FP64 path.  An infinity or
                          NaN in a coefficient set (or in a point's basis row) makes that set's
-                         (point's) outputs NaN */
+                         (point's) outputs NaN.  Scratch (stream-ordered): the slices of C and
+                         of a slab of points and the slab's int32 diagonal sums, about 4.5 GB at
+                         most */
 } zp_precision;
 
 /* Largest radial order accepted (recursion tables live in shared memory). */

@@ -423,7 +423,14 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
   if (n_points >= 8192 && plan->cols.size() >= 4 && m_max <= 128) {
     const int pw_max = m_max + 2;
     const size_t rows = (size_t)(pw_max + 1) + (ang ? 2 * (size_t)(m_max + 1) : 0);
-    ZP_TRY(tables.alloc(rows * (size_t)n_points * sizeof(double), stream));
+    // The tables are an optimisation: without the memory for them the walk computes its seeds.
+    if (tables.alloc(rows * (size_t)n_points * sizeof(double), stream) != ZP_OK) {
+      cudaGetLastError();
+      clear_error();
+    }
+  }
+  if (tables.ptr) {
+    const int pw_max = m_max + 2;
     double* pw = (double*)tables.ptr;
     double* cs = ang ? pw + (size_t)(pw_max + 1) * n_points : nullptr;
     double* sn = ang ? cs + (size_t)(m_max + 1) * n_points : nullptr;
