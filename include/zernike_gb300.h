@@ -52,7 +52,7 @@ typedef enum {
   ZP_ERR_DERIV_ORDER = 3,   /* derivative order outside 0..3 */
   ZP_ERR_CUDA = 4,          /* a CUDA runtime or cuBLAS call failed */
   ZP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-  ZP_ERR_UNSUPPORTED = 6,   /* valid request this build does not support (e.g. wrong GPU) */
+  ZP_ERR_UNSUPPORTED = 6,   /* valid request the library cannot serve (e.g. wrong GPU) */
   ZP_ERR_NO_MEMORY = 7      /* a device allocation failed */
 } zp_status;
 
