@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--series-only", action="store_true",
                     help="run only the mixed_n32 series measurement (profiling captures)")
     ap.add_argument("--series-points", type=int, default=1_000_000)
+    ap.add_argument("--series-sets", type=int, default=None,
+                    help="with --series-only: fewer coefficient sets (profiling captures of the basis kernel)")
     ap.add_argument("--series-emulated", action="store_true",
                     help="with --series-only: also time the emulated float64 contraction")
     ap.add_argument("--adjoint-only", action="store_true",
@@ -481,7 +483,7 @@ def _events_ms(stream, fn, steps):
 
 
 def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_fp64: bool = True,
-                   with_emulated_only: bool = False) -> dict:
+                   with_emulated_only: bool = False, n_sets: int | None = None) -> dict:
     """mixed_n32: 561 modes, 1e6 points r = sqrt(U), 4096 coefficient sets.  The split-precision
     tensor-core series (per-phase CUDA-event times recorded by the library on the launching
     stream) against the plain float64 basis-then-DGEMM form on the same inputs."""
@@ -497,6 +499,8 @@ def measure_series(dev, peaks, steps: int = 3, n_points: int = 1_000_000, with_f
     r, th = inputs.sqrt_uniform_points(cfg["n_points"], cfg["seed"])
     r, th = r[:n_points], th[:n_points]
     C = inputs.scaled_normal_coeffs(ns, cfg["n_sets"], cfg["seed"])
+    if n_sets is not None:
+        C = C[:, :n_sets].copy()
     J, P, S = len(ns), len(r), C.shape[1]
     plan = zp.Plan(ns, ms, device=dev)
     rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
@@ -857,7 +861,7 @@ def main():
 
         torch.cuda.set_device(0)
         res = measure_series(torch.device("cuda", 0), {}, steps=args.steps, n_points=args.series_points,
-                             with_fp64=False, with_emulated_only=args.series_emulated)
+                             with_fp64=False, with_emulated_only=args.series_emulated, n_sets=args.series_sets)
         print(json.dumps({"series_only": res}), flush=True)
         return
     if args.impl == "reference":

@@ -570,7 +570,7 @@ zp_status zp_batch_create(const zp_instance* instances, int64_t n_instances, int
   std::vector<size_t> plan_off;
   size_t off = 0;
   for (auto& p : b->plans) {
-    size_t o6[6];
+    size_t o6[kPlanSections];
     plan_off.push_back(off);
     off += align256(plan_device_layout(p.get(), o6));
   }

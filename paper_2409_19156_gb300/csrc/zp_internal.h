@@ -30,6 +30,30 @@ struct Column {
   int32_t slot_base;  // index of (column, N = 0) in slot_ptr
 };
 
+// Step descriptor of the split-precision basis, one per table row (header rows unused):
+//   .x = number of slots of the step | (sin flags of its first 24 slots << 8), or
+//        kStepIrregular when the step has more than 24 slots (then slot_idx is read);
+//   .y = bits of the float32 weight W0_N (the float64 value truncated toward zero).
+constexpr uint32_t kStepIrregular = 255u;
+constexpr int kStepMaxFlags = 24;
+constexpr int kPlanSections = 7;
+
+// float32 bits of a float64 given as its high and low words, by truncating the significand:
+// magnitudes below the float32 normal range give a signed zero, finite ones above it
+// infinity; infinities are kept and NaNs stay NaNs (quiet).  Integer operations only.
+__host__ __device__ inline uint32_t trunc_float_bits(uint32_t hi, uint32_t lo) {
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {
+    // Bits 31..23 of t hold the low 9 exponent bits; subtracting 0x180 there rebiases
+    // 1023 -> 127 for every exponent of the float32 normal range.
+    const uint32_t t = (hi << 3) | (lo >> 29);
+    return (t - 0xC0000000u) | sign;
+  }
+  if (e == 0x7ffu) return sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  return e <= 896u ? sign : (sign | 0x7f800000u);
+}
+
 struct DevicePlanTables {
   Column* cols = nullptr;
   double* table = nullptr;
@@ -37,6 +61,7 @@ struct DevicePlanTables {
   int32_t* slot_idx = nullptr;  // output column j, bit 31 set for the sin (m < 0) factor
   int32_t* mode_col = nullptr;  // [n_modes]: column index of every mode
   int32_t* mode_N = nullptr;    // [n_modes]: Jacobi degree of every mode
+  uint2* split_step = nullptr;  // [table rows]: step descriptors of the split basis
 };
 
 }  // namespace zp
@@ -50,6 +75,7 @@ struct zp_plan {
   std::vector<zp::Column> cols;      // ordered by n_steps, longest first
   std::vector<double> table;         // rows of kRow doubles
   std::vector<int32_t> slot_ptr, slot_idx, mode_col, mode_N;
+  std::vector<uint32_t> split_step;  // 2 words per table row
   zp::DevicePlanTables dev;
   size_t device_bytes = 0;
   void* dev_block = nullptr;  // single allocation backing dev.*
@@ -66,9 +92,9 @@ void clear_error();
 zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out);
 // Host half only: validates and fills the host tables of *p (no device memory touched).
 zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan* p);
-// Byte size of the plan's device tables; offsets[0..5] of cols, table, slot_ptr, slot_idx,
-// mode_col, mode_N inside that block (256-byte aligned sections).
-size_t plan_device_layout(const zp_plan* p, size_t offsets[6]);
+// Byte size of the plan's device tables; offsets[0..6] of cols, table, slot_ptr, slot_idx,
+// mode_col, mode_N, split_step inside that block (256-byte aligned sections).
+size_t plan_device_layout(const zp_plan* p, size_t offsets[kPlanSections]);
 // Points p->dev at `base` (laid out as plan_device_layout) and copies the host tables there,
 // with cudaMemcpyAsync on `stream` when async, else synchronously.
 zp_status plan_upload(zp_plan* p, void* base, cudaStream_t stream, bool async);

@@ -71,45 +71,25 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-template <bool TF32>
-__device__ __forceinline__ void put_elem(uint8_t* chunk, uint32_t row, uint32_t kk, float z) {
-  if constexpr (TF32) {
-    *reinterpret_cast<float*>(chunk + ptx::sw128_offset_b32(row, kk)) = to_tf32(z);
-  } else {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(z);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(z - __bfloat162float(hi));
-    const uint32_t off = ptx::sw128_offset_b16(row, kk);
-    *reinterpret_cast<__nv_bfloat16*>(chunk + off) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(chunk + kAPart + off) = lo;
-  }
-}
-
 // float of a float64 by truncating its significand (integer pipe: the float64 pipe is the
 // scarce one).  Relative error below 2^-23; magnitudes under the float normal range give a
 // signed zero, finite ones above it infinity; infinities and NaNs are kept.  The split
 // operands carry 16 (BF16x3) or 11 (TF32) significant bits, so truncation is harmless.
 __device__ __forceinline__ float float_of_double(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u;
-  const uint32_t e = (hi >> 20) & 0x7ffu;
-  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  uint32_t bits;
-  if (e == 0x7ffu) {
-    bits = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
-  } else if (e <= 896u) {
-    bits = sign;
-  } else if (e >= 896u + 255u) {
-    bits = sign | 0x7f800000u;
-  } else {
-    bits = sign | ((e - 896u) << 23) | mant;
-  }
-  return __uint_as_float(bits);
+  return __uint_as_float(trunc_float_bits((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x)));
+}
+
+// Two floats rounded to bfloat16 (nearest even) in one 32-bit word, `lo` in the low half.
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 struct BasisArgs {
   const Column* cols;
   int n_cols;
   const double* table;
+  const uint2* steps;  // per table row: slot count and sin flags, float32 weight
   const int32_t* slot_ptr;
   const int32_t* slot_idx;
   const double* r;
@@ -121,15 +101,16 @@ struct BasisArgs {
 };
 
 // Register packing of consecutive K values into one 16-byte unit of the swizzled layout:
-// each push shifts the 128-bit chain w[3]:w[2]:w[1]:w[0] right by one element and inserts
-// the new element at the top, so after a full unit w[0] holds the first element.
+// each push shifts the 128-bit chain w[3]:w[2]:w[1]:w[0] right by one element (two for
+// push32) and inserts the new element(s) at the top, so after a full unit w[0] holds the
+// first element.
 struct Pack16 {
   uint32_t w[4] = {0u, 0u, 0u, 0u};
   __device__ __forceinline__ void push16(uint32_t v) {
-    w[0] = (w[0] >> 16) | (w[1] << 16);
-    w[1] = (w[1] >> 16) | (w[2] << 16);
-    w[2] = (w[2] >> 16) | (w[3] << 16);
-    w[3] = (w[3] >> 16) | (v << 16);
+    w[0] = __funnelshift_r(w[0], w[1], 16);
+    w[1] = __funnelshift_r(w[1], w[2], 16);
+    w[2] = __funnelshift_r(w[2], w[3], 16);
+    w[3] = __funnelshift_r(w[3], v, 16);
   }
   __device__ __forceinline__ void push32(uint32_t v) {
     w[0] = w[1];
@@ -192,31 +173,67 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
   int k = 0;
   Pack16 hi[Q], lo[Q];
 
-  auto push = [&](const float (&z)[Q]) {
+  // Writes the unit that value k - 1 completed.
+  auto flush = [&]() {
+    const int k0 = k - UNIT;
+    uint8_t* chunk = gA + (size_t)(k0 / C::BK) * C::A_CHUNK;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (TF32) {
+        hi[i].store(chunk + ptx::sw128_offset_b32(rowi[i], (uint32_t)(k0 % C::BK)));
+      } else {
+        const uint32_t off = ptx::sw128_offset_b16(rowi[i], (uint32_t)(k0 % C::BK));
+        hi[i].store(chunk + off);
+        lo[i].store(chunk + kAPart + off);
+      }
+    }
+  };
+  // One value at K position k.
+  auto push1 = [&](const float (&z)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if constexpr (TF32) {
         hi[i].push32(__float_as_uint(to_tf32(z[i])));
       } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(z[i]);
-        const __nv_bfloat16 l = __float2bfloat16_rn(z[i] - __bfloat162float(h));
-        hi[i].push16((uint32_t)__bfloat16_as_ushort(h));
-        lo[i].push16((uint32_t)__bfloat16_as_ushort(l));
+        const uint32_t h = bf16x2_bits(z[i], 0.0f) & 0xffffu;
+        const uint32_t l = bf16x2_bits(z[i] - __uint_as_float(h << 16), 0.0f) & 0xffffu;
+        hi[i].push16(h);
+        lo[i].push16(l);
       }
     }
-    if (++k % UNIT == 0) {
-      const int k0 = k - UNIT;
-      uint8_t* chunk = gA + (size_t)(k0 / C::BK) * C::A_CHUNK;
+    if (++k % UNIT == 0) flush();
+  };
+  // BF16x3: two values at K positions k and k + 1, converted in pairs (the same roundings
+  // as two single pushes).
+  auto push2 = [&](const float (&z0)[Q], const float (&z1)[Q]) {
+    uint32_t h2[Q], l2[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      h2[i] = bf16x2_bits(z0[i], z1[i]);
+      l2[i] = bf16x2_bits(z0[i] - __uint_as_float(h2[i] << 16), z1[i] - __uint_as_float(h2[i] & 0xffff0000u));
+    }
+    if ((k & (UNIT - 1)) == UNIT - 1) {  // the first value completes a unit
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        if constexpr (TF32) {
-          hi[i].store(chunk + ptx::sw128_offset_b32(rowi[i], (uint32_t)(k0 % C::BK)));
-        } else {
-          const uint32_t off = ptx::sw128_offset_b16(rowi[i], (uint32_t)(k0 % C::BK));
-          hi[i].store(chunk + off);
-          lo[i].store(chunk + kAPart + off);
-        }
+        hi[i].push16(h2[i] & 0xffffu);
+        lo[i].push16(l2[i] & 0xffffu);
       }
+      ++k;
+      flush();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        hi[i].push16(h2[i] >> 16);
+        lo[i].push16(l2[i] >> 16);
+      }
+      ++k;
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        hi[i].push32(h2[i]);
+        lo[i].push32(l2[i]);
+      }
+      k += 2;
+      if ((k & (UNIT - 1)) == 0) flush();
     }
   };
 
@@ -242,57 +259,80 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
       cf[i] = float_of_double(cm[i]);
       sf[i] = float_of_double(sm[i]);
       T[i] = pm[i];
-      S[i] = fma(h[4], pm[i] * u[i], -(h[8] * pm[i]));
+      S[i] = pm[i] * fma(h[4], u[i], -h[8]);  // R_{m+2}^m = rho^m ((m+2) rho^2 - (m+1))
     }
     m_prev = m;
+    const uint2* st = a.steps + col.table_row + kHeaderRows;
     const int32_t* sp = a.slot_ptr + col.slot_base;
-    // Step N's recursion value is formed before step N - 1's outputs are emitted, so the
-    // float64 latency of the recursion overlaps the conversions, products and packing.  Per
-    // value the float64 pipe sees only the two recursion FMAs: the weight W = k! w_N and the
-    // angular factor are applied in float32 (converted on the integer pipe).
-    double q_prev[Q];
-    float W_prev = 0.0f;
-    int sb_prev = 0, se_prev = 0;
-    auto emit = [&]() {
+    // Outputs of step N: value qv times the weight, times cos or sin per slot.  Per value
+    // the float64 pipe sees only the two recursion FMAs; the weight and the angular factor
+    // are applied in float32 (converted on the integer pipe).
+    auto emit = [&](const double (&qv)[Q], uint2 info, int N) {
       float Rf[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) Rf[i] = float_of_double(q_prev[i]) * W_prev;
-      for (int s = sb_prev; s < se_prev; ++s) {
-        const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+      for (int i = 0; i < Q; ++i) Rf[i] = float_of_double(qv[i]) * __uint_as_float(info.y);
+      uint32_t cnt = info.x & 0xffu, flags = info.x >> 8;
+      if (cnt == kStepIrregular) {
+        for (int s = sp[N]; s < sp[N + 1]; ++s) {
+          const uint32_t code = (uint32_t)__ldg(a.slot_idx + s);
+          float z[Q];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) z[i] = Rf[i] * ((code >> 31) ? sf[i] : cf[i]);
+          push1(z);
+        }
+        return;
+      }
+      if constexpr (!TF32) {
+        for (; cnt >= 2; cnt -= 2, flags >>= 2) {
+          float z0[Q], z1[Q];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            z0[i] = Rf[i] * ((flags & 1u) ? sf[i] : cf[i]);
+            z1[i] = Rf[i] * ((flags & 2u) ? sf[i] : cf[i]);
+          }
+          push2(z0, z1);
+        }
+      }
+      for (; cnt > 0; --cnt, flags >>= 1) {
         float z[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) z[i] = Rf[i] * ((code >> 31) ? sf[i] : cf[i]);
-        push(z);
+        for (int i = 0; i < Q; ++i) z[i] = Rf[i] * ((flags & 1u) ? sf[i] : cf[i]);
+        push1(z);
       }
     };
-    for (int N = 0; N < col.n_steps; ++N) {
-      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
-      const double A = row[0], B = row[1], W = row[3];
-      double q[Q];
+    // Step N's recursion value is formed before step N - 1's outputs are emitted, so the
+    // float64 latency of the recursion overlaps the conversions, products and packing.
+    double qp[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (N == 0) {
-          q[i] = T[i];
-        } else if (N == 1) {
-          q[i] = S[i];
-        } else {
-          const double g = fma(A, u[i], -B);
+    for (int i = 0; i < Q; ++i) qp[i] = T[i];
+    uint2 ip = st[0];
+    if (col.n_steps > 1) {
+      const uint2 in = st[1];
+      emit(qp, ip, 0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) qp[i] = S[i];
+      ip = in;
+      for (int N = 2; N < col.n_steps; ++N) {
+        const double2 AB = *reinterpret_cast<const double2*>(h + (size_t)(kHeaderRows + N) * kRow);
+        const uint2 inN = st[N];
+        double q[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const double g = fma(AB.x, u[i], -AB.y);
           q[i] = fma(g, S[i], -T[i]);
           T[i] = S[i];
           S[i] = q[i];
         }
-      }
-      if (N > 0) emit();
+        emit(qp, ip, N - 1);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) q_prev[i] = q[i];
-      W_prev = float_of_double(W);
-      sb_prev = sp[N];
-      se_prev = sp[N + 1];
+        for (int i = 0; i < Q; ++i) qp[i] = q[i];
+        ip = inN;
+      }
     }
-    if (col.n_steps > 0) emit();
+    emit(qp, ip, col.n_steps - 1);
   }
   const float zeros[Q] = {};
-  while (k % C::BK != 0) push(zeros);
+  while (k % C::BK != 0) push1(zeros);
 }
 
 struct CoeffArgs {
@@ -722,7 +762,8 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   timer.ms = phase_ms;
   timer.stream = stream;
   cudaEvent_t ev0;
-  using C = Cfg<TF32 ? KIND_TF32 : KIND_BF16X3>;
+  constexpr int KIND = TF32 ? KIND_TF32 : KIND_BF16X3;
+  using C = Cfg<KIND>;
   const int64_t J = plan->n_modes;
   const int KC = (int)((J + C::BK - 1) / C::BK);
   const int64_t MT = (P + BM - 1) / BM;
@@ -732,6 +773,18 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   ScratchBuffer bbuf, abuf;
   uint8_t* A = nullptr;
   uint8_t* B = nullptr;
+  // A basis wave: the point tiles whose CTAs are resident at once.  The basis kernel is
+  // latency-bound per CTA, so a launch that ends with a part-filled wave takes nearly as long as
+  // a full one; slabs are therefore whole waves where the scratch allows.
+  GemmShape gs;
+  ZP_TRY(gemm_shape<KIND>(&gs));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_basis_kernel<TF32>, basis_threads<TF32>(), 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t wave = (int64_t)std::max(per_sm, 1) * gs.sms;
   int64_t slab = 0;
   if (preset) {
     // Caller-provided scratch: the B tiles first, then as many point tiles as fit.
@@ -739,26 +792,29 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
       return set_error(ZP_ERR_INVALID_ARG, "split scratch too small for this problem");
     A = preset->a;
     B = preset->b;
-    slab = std::min<int64_t>(MT, (int64_t)(preset->a_bytes / tile_bytes));
+    const int64_t fit = (int64_t)(preset->a_bytes / tile_bytes);
+    slab = std::min<int64_t>(MT, fit >= wave ? fit / wave * wave : fit);
   } else {
-    // Slabs of at most 512 MB of split basis, run back to back on the caller's stream.  (Running
-    // the float64 basis of slab i+1 on a second stream beside the GEMM of slab i was measured
-    // slower on GB300: the GEMM is sensitive to the basis kernel's extra L2 write traffic.)
-    slab = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((512ull << 20) / tile_bytes)));
+    // Slabs of about 512 MB of split basis, rounded to whole waves (at least one, at most 4 GB),
+    // run back to back on the caller's stream.  (Running the float64 basis of slab i+1 on a
+    // second stream beside the GEMM of slab i was measured slower on GB300: the GEMM is
+    // sensitive to the basis kernel's extra L2 write traffic.)
+    const int64_t cap = (int64_t)((512ull << 20) / tile_bytes);
+    const int64_t hard = std::max<int64_t>(1, (int64_t)((4ull << 30) / tile_bytes));
+    int64_t want = std::max<int64_t>(1, (cap + wave / 2) / wave) * wave;
+    if (want > hard) want = hard >= gs.sms ? hard / gs.sms * gs.sms : hard;
+    slab = std::max<int64_t>(1, std::min<int64_t>(MT, want));
     ZP_TRY(bbuf.alloc(b_bytes, stream));
     ZP_TRY(abuf.alloc((size_t)slab * tile_bytes, stream));
     A = (uint8_t*)abuf.ptr;
     B = (uint8_t*)bbuf.ptr;
   }
 
-  constexpr int KIND = TF32 ? KIND_TF32 : KIND_BF16X3;
   const uint32_t coeff_smem = C::B_CHUNK + 1024;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
       cudaSuccess)
     return cuda_error(e, "cudaFuncSetAttribute(split_coeff_kernel)");
-  GemmShape gs;
-  ZP_TRY(gemm_shape<KIND>(&gs));
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
   timer.begin(0, &ev0, stream);
@@ -768,7 +824,8 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 
   for (int64_t mt0 = 0; mt0 < MT; mt0 += slab) {
     const int64_t tiles = std::min<int64_t>(slab, MT - mt0);
-    BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx,
+    BasisArgs ba{plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.split_step, plan->dev.slot_ptr,
+                 plan->dev.slot_idx,
                  r, theta, P, mt0, KC, A};
     timer.begin(1, &ev0, stream);
     split_basis_kernel<TF32><<<(unsigned)tiles, basis_threads<TF32>(), 0, stream>>>(ba, tiles);

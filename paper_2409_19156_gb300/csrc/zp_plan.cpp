@@ -169,26 +169,46 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
     const int32_t pos = p->slot_ptr[s] + fill[s]++;
     p->slot_idx[pos] = (int32_t)((uint32_t)j | (m[j] < 0 ? 0x80000000u : 0u));
   }
+  // Step descriptors of the split basis: slot count and sin flags, and the float32 weight.
+  p->split_step.assign(2 * (size_t)row, 0u);
+  for (const Column& col : p->cols) {
+    for (int32_t N = 0; N < col.n_steps; ++N) {
+      const size_t s = (size_t)col.slot_base + N;
+      const int32_t b = p->slot_ptr[s], cnt = p->slot_ptr[s + 1] - b;
+      uint32_t code = kStepIrregular;
+      if (cnt <= kStepMaxFlags) {
+        code = (uint32_t)cnt;
+        for (int32_t i = 0; i < cnt; ++i) code |= ((uint32_t)p->slot_idx[(size_t)b + i] >> 31) << (8 + i);
+      }
+      const size_t r = (size_t)col.table_row + kHeaderRows + N;
+      uint64_t wbits;
+      std::memcpy(&wbits, &p->table[r * kRow + 3], sizeof(wbits));
+      p->split_step[2 * r] = code;
+      p->split_step[2 * r + 1] = trunc_float_bits((uint32_t)(wbits >> 32), (uint32_t)wbits);
+    }
+  }
   return ZP_OK;
 }
 
-size_t plan_device_layout(const zp_plan* p, size_t offsets[6]) {
+size_t plan_device_layout(const zp_plan* p, size_t offsets[kPlanSections]) {
   const size_t b_cols = align_up(p->cols.size() * sizeof(Column), 256);
   const size_t b_table = align_up(p->table.size() * sizeof(double), 256);
   const size_t b_sptr = align_up(p->slot_ptr.size() * sizeof(int32_t), 256);
   const size_t b_sidx = align_up(std::max<size_t>(p->slot_idx.size(), 1) * sizeof(int32_t), 256);
   const size_t b_mode = align_up(std::max<int64_t>(p->n_modes, 1) * sizeof(int32_t), 256);
+  const size_t b_step = align_up(std::max<size_t>(p->split_step.size(), 2) * sizeof(uint32_t), 256);
   offsets[0] = 0;
   offsets[1] = b_cols;
   offsets[2] = b_cols + b_table;
   offsets[3] = b_cols + b_table + b_sptr;
   offsets[4] = b_cols + b_table + b_sptr + b_sidx;
   offsets[5] = b_cols + b_table + b_sptr + b_sidx + b_mode;
-  return offsets[5] + b_mode;
+  offsets[6] = b_cols + b_table + b_sptr + b_sidx + 2 * b_mode;
+  return offsets[6] + b_step;
 }
 
 zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool async) {
-  size_t off[6];
+  size_t off[kPlanSections];
   plan_device_layout(p, off);
   char* base = (char*)base_ptr;
   p->dev.cols = (Column*)(base + off[0]);
@@ -197,6 +217,7 @@ zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool asyn
   p->dev.slot_idx = (int32_t*)(base + off[3]);
   p->dev.mode_col = (int32_t*)(base + off[4]);
   p->dev.mode_N = (int32_t*)(base + off[5]);
+  p->dev.split_step = (uint2*)(base + off[6]);
   struct Part {
     void* dst;
     const void* src;
@@ -208,6 +229,7 @@ zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool asyn
       {p->dev.slot_idx, p->slot_idx.data(), p->slot_idx.size() * sizeof(int32_t)},
       {p->dev.mode_col, p->mode_col.data(), p->mode_col.size() * sizeof(int32_t)},
       {p->dev.mode_N, p->mode_N.data(), p->mode_N.size() * sizeof(int32_t)},
+      {p->dev.split_step, p->split_step.data(), p->split_step.size() * sizeof(uint32_t)},
   };
   for (const Part& part : parts) {
     if (part.bytes == 0) continue;
@@ -223,7 +245,7 @@ zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_pla
   std::unique_ptr<zp_plan> p(new zp_plan());
   zp_status st = build_plan_host(n, m, n_modes, p.get());
   if (st != ZP_OK) return st;
-  size_t off[6];
+  size_t off[kPlanSections];
   const size_t total = plan_device_layout(p.get(), off);
   cudaError_t e = cudaMalloc(&p->dev_block, total);
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(plan tables)");

@@ -73,7 +73,7 @@ extern "C" zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, i
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
   }
   // Layout of the static array: plan tables | coefficient tiles | basis slab.
-  size_t offsets[6];
+  size_t offsets[kPlanSections];
   const size_t table_bytes = round_up(plan_device_layout(&plan, offsets), 1024);
   size_t b_bytes = 0, tile_bytes = 0;
   const size_t need = table_bytes + round_up(split_scratch_bytes(prec, n_modes, n_sets, &b_bytes, &tile_bytes), 1024);

@@ -107,7 +107,7 @@ def test_mixed_n32_full_size_sampled():
 @pytest.mark.parametrize("prec,code", [("bf16x3", 1), ("tf32", 2)])
 @pytest.mark.parametrize("nmax,P,S", [(20, 20_000, 300), (32, 3_001, 256), (5, 129, 7)])
 def test_slab_size_does_not_change_the_result(prec, code, nmax, P, S):
-    """zp_series_eval (slabs of up to 512 MB of split basis) and zp_series_eval_static (its
+    """zp_series_eval (slabs of whole basis waves, ~512 MB) and zp_series_eval_static (its
     64 MB array: many smaller slabs, other CTA-pair boundaries) compute the same basis values
     and the same MMA sequence per tile, so their outputs are identical, for an odd number of
     point tiles too (a pair's missing second tile)."""
