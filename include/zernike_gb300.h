@@ -338,9 +338,9 @@ ZP_API zp_status zp_batch_tune(zp_batch* batch, int32_t which, zp_precision prec
  * device address (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  The tables travel by cudaMemcpyAsync from pageable host
  * memory on `stream`.
- * Limits: the plan tables, the coefficient tiles (ceil(n_sets/256) * ceil(n_modes/64) * 64 KiB
- * for BF16X3, /32 and 32 KiB for TF32) and one 128-point basis tile (ceil(n_modes/64) * 32 KiB,
- * TF32: ceil(n_modes/32) * 16 KiB) must fit in ZP_STATIC_SCRATCH_BYTES; larger problems are
+ * Limits: the plan tables, the coefficient tiles (ceil(n_sets/256) * ceil(n_modes/32) * 32 KiB)
+ * and one 128-point basis tile (ceil(n_modes/32) * 16 KiB), for either precision, must fit in
+ * ZP_STATIC_SCRATCH_BYTES; larger problems are
  * rejected with ZP_ERR_INVALID_ARG before anything is launched.  Points beyond one tile are
  * processed in slabs, so n_points has no limit of its own.
  */

@@ -9,7 +9,7 @@
 //      Sec. 2 in float64, Algorithm 1's order), rotates cos/sin(m theta) by angle addition
 //      from column to column, splits each Z into bfloat16 hi/lo (or TF32), packs 8 (4)
 //      consecutive K values in registers and writes each 16-byte unit straight to its place
-//      in the tensor core's 128-byte-swizzled K-major layout in a scratch buffer.
+//      in the tensor core's swizzled K-major layout in a scratch buffer.
 //      The K order of the contraction is the plan's slot order (column by column), so a
 //      thread's outputs are consecutive in K; the coefficient rows are permuted to match.
 //  (B) split_gemm_kernel: persistent, warp-specialised tcgen05 GEMM.  Warp 0 streams A
@@ -37,9 +37,7 @@ namespace {
 
 constexpr int BM = 128;  // points per tile (TMEM lanes)
 constexpr int BN = 256;  // coefficient sets per tile (TMEM columns per accumulator)
-constexpr uint32_t kRowBytes = 128;
-constexpr uint32_t kAPart = BM * kRowBytes;  // 16 KB: one 128 x 128-byte K-chunk
-constexpr uint32_t kBPart = BN * kRowBytes;  // 32 KB
+constexpr uint32_t kRingBytes = 192u << 10;  // shared-memory ring of operand stages
 constexpr int kGemmThreads = 192;            // 6 warps: producer, MMA, 4 x epilogue
 constexpr int kCoeffThreads = BN;
 
@@ -47,15 +45,23 @@ constexpr int kCoeffThreads = BN;
 // SLICE (one bf16 product of integer-valued slices, for the emulated-float64 contraction).
 constexpr int KIND_BF16X3 = 0, KIND_TF32 = 1, KIND_SLICE = 2;
 
+// Operand rows: BF16x3 keeps 64-byte rows in the 64-byte swizzle layout (a K chunk of 32
+// values; hi + lo stages of 48 KB, 4 in the ring: with 128-byte rows and 2 stages of 96 KB the
+// bulk copies' latency was exposed to the MMA issue, 8.6 against 8.2 ms at mixed_n32).  TF32
+// and the slice products keep 128-byte rows (48 KB stages, 4 in the ring): with 64-byte rows
+// a stage holds only two MMAs and the per-stage barrier work dominated (TF32 7.3 -> 8.9 ms).
 template <int KIND>
 struct Cfg {
-  static constexpr int BK = KIND == KIND_TF32 ? 32 : 64;  // K elements per 128-byte row
-  static constexpr int PARTS = KIND == KIND_BF16X3 ? 2 : 1;  // hi (+ lo)
-  static constexpr uint32_t A_CHUNK = kAPart * PARTS;
-  static constexpr uint32_t B_CHUNK = kBPart * PARTS;
-  static constexpr int STAGES = PARTS == 2 ? 2 : 4;
+  static constexpr uint32_t ROW = KIND == KIND_BF16X3 ? 64u : 128u;  // bytes per operand row
+  static constexpr int BK = (int)ROW / (KIND == KIND_TF32 ? 4 : 2);  // K elements per row
+  static constexpr int PARTS = KIND == KIND_BF16X3 ? 2 : 1;          // hi (+ lo)
+  static constexpr uint32_t A_PART = BM * ROW;                       // one 128-row K chunk
+  static constexpr uint32_t B_PART = BN * ROW;
+  static constexpr uint32_t A_CHUNK = A_PART * PARTS;
+  static constexpr uint32_t B_CHUNK = B_PART * PARTS;
   static constexpr uint32_t STAGE = A_CHUNK + B_CHUNK;
-  static constexpr int KSTEPS = 4;  // MMA K-steps per chunk (16 bf16 or 8 tf32 = 32 bytes each)
+  static constexpr int STAGES = (int)(kRingBytes / STAGE);
+  static constexpr int KSTEPS = (int)ROW / 32;  // MMA K-steps per chunk (16 bf16 or 8 tf32 = 32 bytes each)
   static constexpr uint32_t SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
@@ -180,11 +186,11 @@ __device__ __forceinline__ void split_basis_tile(const BasisArgs& a, int64_t til
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if constexpr (TF32) {
-        hi[i].store(chunk + ptx::sw128_offset_b32(rowi[i], (uint32_t)(k0 % C::BK)));
+        hi[i].store(chunk + ptx::sw_offset_b32<C::ROW>(rowi[i], (uint32_t)(k0 % C::BK)));
       } else {
-        const uint32_t off = ptx::sw128_offset_b16(rowi[i], (uint32_t)(k0 % C::BK));
+        const uint32_t off = ptx::sw_offset_b16<C::ROW>(rowi[i], (uint32_t)(k0 % C::BK));
         hi[i].store(chunk + off);
-        lo[i].store(chunk + kAPart + off);
+        lo[i].store(chunk + C::A_PART + off);
       }
     }
   };
@@ -360,13 +366,13 @@ __global__ void __launch_bounds__(kCoeffThreads) split_coeff_kernel(CoeffArgs a)
     }
     const float f = (float)v;
     if constexpr (TF32) {
-      *reinterpret_cast<float*>(smem + ptx::sw128_offset_b32(t, kk)) = to_tf32(f);
+      *reinterpret_cast<float*>(smem + ptx::sw_offset_b32<C::ROW>(t, kk)) = to_tf32(f);
     } else {
       const __nv_bfloat16 hi = __float2bfloat16_rn(f);
       const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-      const uint32_t off = ptx::sw128_offset_b16(t, kk);
+      const uint32_t off = ptx::sw_offset_b16<C::ROW>(t, kk);
       *reinterpret_cast<__nv_bfloat16*>(smem + off) = hi;
-      *reinterpret_cast<__nv_bfloat16*>(smem + kBPart + off) = lo;
+      *reinterpret_cast<__nv_bfloat16*>(smem + C::B_PART + off) = lo;
     }
   }
   __syncthreads();
@@ -538,16 +544,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
             const uint32_t koff = ks * 32;
             const uint32_t first = (kk == 0 && ks == 0) ? 0u : 1u;
             if constexpr (TF32) {
-              ptx::mma_tf32(d_tmem, ptx::sw128_kmajor_desc(sA + koff), ptx::sw128_kmajor_desc(sB + koff), idesc,
+              ptx::mma_tf32(d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff), ptx::sw_kmajor_desc<C::ROW>(sB + koff), idesc,
                             first);
             } else if constexpr (KIND == KIND_SLICE) {
-              ptx::mma_bf16(d_tmem, ptx::sw128_kmajor_desc(sA + koff), ptx::sw128_kmajor_desc(sB + koff), idesc,
+              ptx::mma_bf16(d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff), ptx::sw_kmajor_desc<C::ROW>(sB + koff), idesc,
                             first);
             } else {
-              const uint64_t ah = ptx::sw128_kmajor_desc(sA + koff);
-              const uint64_t al = ptx::sw128_kmajor_desc(sA + kAPart + koff);
-              const uint64_t bh = ptx::sw128_kmajor_desc(sB + koff);
-              const uint64_t bl = ptx::sw128_kmajor_desc(sB + kBPart + koff);
+              const uint64_t ah = ptx::sw_kmajor_desc<C::ROW>(sA + koff);
+              const uint64_t al = ptx::sw_kmajor_desc<C::ROW>(sA + C::A_PART + koff);
+              const uint64_t bh = ptx::sw_kmajor_desc<C::ROW>(sB + koff);
+              const uint64_t bl = ptx::sw_kmajor_desc<C::ROW>(sB + C::B_PART + koff);
               ptx::mma_bf16(d_tmem, ah, bh, idesc, first);
               ptx::mma_bf16(d_tmem, ah, bl, idesc, 1u);
               ptx::mma_bf16(d_tmem, al, bh, idesc, 1u);
@@ -861,7 +867,7 @@ constexpr int kSliceOpts = 4;
 constexpr int kSliceBeta[kSliceOpts] = {7, 6, 5, 4};
 constexpr int kSliceS[kSliceOpts] = {8, 9, 11, 14};
 
-// Largest number of 64-element K chunks one batch may hold with slice option o: with
+// Largest number of K chunks (Cfg<KIND_SLICE>::BK values) one batch may hold with slice option o: with
 // |a_1| <= 2^beta and |a_t| <= 2^(beta-1) for t >= 2 (each later digit cuts a remainder of at
 // most 1/2), diagonal d sums K * (2 * 2^beta * 2^(beta-1) + (d-3) * 2^(2 beta - 2)) at most,
 // largest at d = s + 1: K * 2^(2 beta) * (1 + (s-2)/4), which must stay below 2^24.
@@ -873,7 +879,7 @@ int max_batch_chunks(int o) {
 // How K is cut: slice option, chunks per batch, batches, and the recombination's Horner split.
 struct EmuShape {
   SliceParams sp;
-  int KC = 0;            // 64-element K chunks
+  int KC = 0;            // K chunks
   int kc_per_batch = 0;  // chunks per K batch
   int k_batches = 1;
   int split = 0;         // diagonals in the first Horner chain
@@ -1067,15 +1073,16 @@ __device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, u
   }
 }
 
-// Slices of an operand's rows in the tensor core's K-major 128-byte-swizzled chunks: tile
-// (row / ROWS) x K chunk kc at ((tile * KC + kc) * ROWS * 128) bytes, slice t a further
+// Slices of an operand's rows in the tensor core's K-major swizzled chunks: tile
+// (row / ROWS) x K chunk kc at ((tile * KC + kc) * ROWS * Cfg<KIND_SLICE>::ROW) bytes, slice t a further
 // t * slice_stride.  Thread = (row, group of 8 consecutive K), rows fastest.  Rows past `rows`
 // and K past `K` are zero.
 template <int ROWS>
 __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
                                   const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride) {
+  constexpr int BK = Cfg<KIND_SLICE>::BK;
   const int64_t rows_pad = tiles * ROWS;
-  const int64_t total = rows_pad * KC * 8;
+  const int64_t total = rows_pad * KC * (BK / 8);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = i % rows_pad;
     const int64_t k0 = (i / rows_pad) * 8;
@@ -1088,8 +1095,9 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     for (int q = 0; q < 8; ++q) x[q] = (use && k0 + q < K) ? to_fixed(X.x[row * X.sr + (k0 + q) * X.sk], shift) : 0;
     const int64_t tile = row / ROWS;
     const uint32_t r = (uint32_t)(row % ROWS);
-    const int kc = (int)(k0 / 64);
-    uint8_t* d = dst + ((size_t)tile * KC + kc) * (ROWS * kRowBytes) + ptx::sw128_offset_b16(r, (uint32_t)(k0 % 64));
+    const int kc = (int)(k0 / BK);
+    constexpr uint32_t ROW = Cfg<KIND_SLICE>::ROW;
+    uint8_t* d = dst + ((size_t)tile * KC + kc) * (ROWS * ROW) + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
     cut_slices(x, sp.beta, sp.s, d, slice_stride);
   }
 }

@@ -135,11 +135,15 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout (rows of
-// 128 bytes, 8-row groups 1024 bytes apart), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor: K-major operand in the ROW-byte swizzle layout (rows of ROW
+// bytes, 8-row groups 8 * ROW bytes apart; ROW = 128 or 64), descriptor version 1.  Layout
+// field: 2 = 128-byte swizzle, 4 = 64-byte swizzle.
+template <uint32_t ROW>
+__device__ __forceinline__ uint64_t sw_kmajor_desc(uint32_t saddr) {
+  static_assert(ROW == 128 || ROW == 64, "128- or 64-byte swizzle");
+  constexpr uint64_t layout = ROW == 128 ? 2u : 4u;
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8u * ROW) >> 4) << 32) |
+         ((uint64_t)1 << 46) | (layout << 61);
 }
 
 // Instruction descriptor for kind::f16 (A, B = bf16; D = f32; both K-major).
@@ -202,16 +206,28 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Byte offset of element (row, k) of a K-major tile of 2-byte elements in the 128-byte
-// swizzle layout (64 elements per 128-byte row; the tile base must be 1024-byte aligned).
-__host__ __device__ __forceinline__ uint32_t sw128_offset_b16(uint32_t row, uint32_t k) {
-  const uint32_t chunk = (k >> 3) ^ (row & 7u);
-  return (row >> 3) * 1024u + (row & 7u) * 128u + chunk * 16u + (k & 7u) * 2u;
+// Physical 16-byte unit of logical unit `unit` in row `row` of a K-major tile in the ROW-byte
+// swizzle layout: 128 bytes XOR the unit index (3 bits) with row % 8; 64 bytes XOR it (2 bits)
+// with (row / 2) % 4 (address bits 6:4 with 9:7, resp. 5:4 with 8:7).
+template <uint32_t ROW>
+__host__ __device__ __forceinline__ uint32_t sw_unit(uint32_t row, uint32_t unit) {
+  static_assert(ROW == 128 || ROW == 64, "128- or 64-byte swizzle");
+  if constexpr (ROW == 128) {
+    return unit ^ (row & 7u);
+  } else {
+    return unit ^ ((row >> 1) & 3u);
+  }
 }
-// Same for 4-byte elements (32 per 128-byte row).
-__host__ __device__ __forceinline__ uint32_t sw128_offset_b32(uint32_t row, uint32_t k) {
-  const uint32_t chunk = (k >> 2) ^ (row & 7u);
-  return (row >> 3) * 1024u + (row & 7u) * 128u + chunk * 16u + (k & 3u) * 4u;
+// Byte offset of element (row, k) of a K-major tile of 2-byte elements (ROW / 2 per row; the
+// tile base must be 8 * ROW-byte aligned).
+template <uint32_t ROW>
+__host__ __device__ __forceinline__ uint32_t sw_offset_b16(uint32_t row, uint32_t k) {
+  return (row >> 3) * (8u * ROW) + (row & 7u) * ROW + sw_unit<ROW>(row, k >> 3) * 16u + (k & 7u) * 2u;
+}
+// Same for 4-byte elements (ROW / 4 per row).
+template <uint32_t ROW>
+__host__ __device__ __forceinline__ uint32_t sw_offset_b32(uint32_t row, uint32_t k) {
+  return (row >> 3) * (8u * ROW) + (row & 7u) * ROW + sw_unit<ROW>(row, k >> 2) * 16u + (k & 3u) * 4u;
 }
 
 }  // namespace ptx
