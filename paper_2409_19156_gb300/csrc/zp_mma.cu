@@ -1153,32 +1153,51 @@ struct RecombineArgs {
   int64_t ldc;
 };
 
+// VW consecutive int32 diagonal sums (streaming loads), VW in {1, 2, 4}.
+template <int VW>
+__device__ __forceinline__ void load_sums(const int* p, long long (&t)[VW]) {
+  if constexpr (VW == 4) {
+    const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
+    t[0] = v.x, t[1] = v.y, t[2] = v.z, t[3] = v.w;
+  } else if constexpr (VW == 2) {
+    const int2 v = __ldcs(reinterpret_cast<const int2*>(p));
+    t[0] = v.x, t[1] = v.y;
+  } else {
+    t[0] = __ldcs(p);
+  }
+}
+
+// Number of consecutive outputs of one recombination thread (a 16-byte store per two).
+constexpr int kRecombineWidth = 4;
+
 // C[m][n] = sigma_m sigma_n 2^(-beta (ndiag+1)) Nmn with Nmn = sum_d (sum_batches T_d)
 // 2^(beta (ndiag+1-d)), d = 2..ndiag+1, formed exactly: the first `split` diagonals in one
 // int64 Horner chain, the rest in another, joined into 128 bits and rounded once.
-// Block = row m of C (grid-stride), threads across n.
+// Block = row m of C (grid-stride), threads across n, VW consecutive outputs per thread.
+template <int VW>
 __global__ void recombine_kernel(RecombineArgs a) {
   const int lo_shift = a.beta * (a.ndiag - a.split);
   const int e_base = -a.beta * (a.ndiag + 1);
-  // Vector path: int4 loads of T (its rows are 4-aligned when N is) and 16-byte stores of C.
-  const bool vec = (a.N % 4) == 0 && (a.ldc % 2) == 0 && ((uintptr_t)a.C % 16) == 0;
+  // Vector path: VW-wide loads of T (its rows are VW-aligned when N is) and 16-byte stores of C.
+  const bool vec =
+      (a.N % VW) == 0 && (VW == 1 || ((a.ldc % 2) == 0 && ((uintptr_t)a.C % 16) == 0));
   for (int64_t m = blockIdx.x; m < a.rows; m += gridDim.x) {
     const bool row_bad = a.rexp[m] == kNonFiniteRow;
     const int em = a.rexp[m] + e_base;
     const int* trow = a.T + m * a.N;
     double* crow = a.C + m * a.ldc;
     if (vec) {
-      for (int64_t n4 = (int64_t)threadIdx.x * 4; n4 < a.N; n4 += (int64_t)blockDim.x * 4) {
-        long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+      for (int64_t n0 = (int64_t)threadIdx.x * VW; n0 < a.N; n0 += (int64_t)blockDim.x * VW) {
+        long long hi[VW] = {}, lo[VW] = {};
         if (a.k_batches == 1) {
           // One batch: the diagonal loads are independent, unrolled so they are all in flight.
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             if (q < a.ndiag) {
-              const int4 v = __ldcs(reinterpret_cast<const int4*>(trow + q * a.diag_stride + n4));
-              const long long t[4] = {v.x, v.y, v.z, v.w};
+              long long t[VW];
+              load_sums<VW>(trow + q * a.diag_stride + n0, t);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
+              for (int k = 0; k < VW; ++k) {
                 if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
                 else lo[k] = horner(lo[k], a.beta, t[k]);
               }
@@ -1186,30 +1205,36 @@ __global__ void recombine_kernel(RecombineArgs a) {
           }
         } else {
           for (int q = 0; q < a.ndiag; ++q) {
-            long long t[4] = {0, 0, 0, 0};
+            long long t[VW] = {};
             for (int kb = 0; kb < a.k_batches; ++kb) {
-              const int4 v =
-                  __ldcs(reinterpret_cast<const int4*>(trow + kb * a.batch_stride + q * a.diag_stride + n4));
-              t[0] += v.x, t[1] += v.y, t[2] += v.z, t[3] += v.w;
+              long long v[VW];
+              load_sums<VW>(trow + kb * a.batch_stride + q * a.diag_stride + n0, v);
+#pragma unroll
+              for (int k = 0; k < VW; ++k) t[k] += v[k];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < VW; ++k) {
               if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
               else lo[k] = horner(lo[k], a.beta, t[k]);
             }
           }
         }
-        const int4 ce = *reinterpret_cast<const int4*>(a.cexp + n4);
-        const int e[4] = {ce.x, ce.y, ce.z, ce.w};
-        double v[4];
+        double v[VW];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          v[k] = (row_bad || e[k] == kNonFiniteRow)
+        for (int k = 0; k < VW; ++k) {
+          const int ec = a.cexp[n0 + k];
+          v[k] = (row_bad || ec == kNonFiniteRow)
                      ? __longlong_as_double(0x7ff8000000000000ll)
                      : int128_to_double((__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k],
-                                        em + e[k]);
-        __stcs(reinterpret_cast<double2*>(crow + n4), make_double2(v[0], v[1]));
-        __stcs(reinterpret_cast<double2*>(crow + n4 + 2), make_double2(v[2], v[3]));
+                                        em + ec);
+        }
+        if constexpr (VW == 1) {
+          __stcs(crow + n0, v[0]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < VW; k += 2)
+            __stcs(reinterpret_cast<double2*>(crow + n0 + k), make_double2(v[k], v[k + 1]));
+        }
       }
     } else {
       for (int64_t n = threadIdx.x; n < a.N; n += blockDim.x) {
@@ -1238,6 +1263,7 @@ struct EmuGemm {
   int sms = 0;
   GemmShape gs;
   int64_t slab_tiles = 0;  // row tiles per slab
+  int64_t recombine_blocks = 0;
   ScratchBuffer bsl, cexp, asl, rexp, tbuf, maxbits;
   int64_t a_stride = 0, b_stride = 0;
 
@@ -1250,6 +1276,14 @@ struct EmuGemm {
     const int64_t MT = (M + BM - 1) / BM;
     ZP_TRY(gemm_shape<KIND_SLICE>(&gs));
     sms = gs.sms;
+    // One resident wave of recombination blocks, grid-striding over the rows.
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recombine_kernel<kRecombineWidth>, 256, 0) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 4;
+    }
+    recombine_blocks = (int64_t)std::max(per_sm, 1) * sms;
     if (!choose_emu_shape(K, MT * NT, sms, &sh))
       return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");
     // Slab: int32 sums (k_batches x s x rows x N x 4 B) within about 4 GB.
@@ -1294,7 +1328,7 @@ struct EmuGemm {
     }
     RecombineArgs ra{(const int*)tbuf.ptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
                      sh.sp.beta, (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
-    recombine_kernel<<<(unsigned)std::min<int64_t>(rows, 8 * (int64_t)sms), 256, 0, stream>>>(ra);
+    recombine_kernel<kRecombineWidth><<<(unsigned)std::min<int64_t>(rows, recombine_blocks), 256, 0, stream>>>(ra);
     e = cudaGetLastError();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "recombine_kernel launch");
   }
