@@ -143,3 +143,34 @@ def test_split_long_column_plan():
         bound = REL[prec] * (z.T @ Ct.abs()) + 1e-6
         wait_ok()
         assert bool(((F - F64).abs() <= bound).all())
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_split_step_descriptors_irregular_and_odd_steps(prec):
+    """Recursion steps of every slot shape the basis kernel's per-step descriptors take: one
+    slot, odd counts with mixed cos/sin flags, exactly 24 slots (the most a descriptor's flags
+    hold), and 26 and 40 slots (beyond them: the slots are read one by one), in caller order
+    with duplicates; against the oracle."""
+    ns, ms = [], []
+    ns += [10, 10] * 13                  # one step with 26 slots (alternating cos / sin)
+    ms += [2, -2] * 13
+    ns += [7] * 24                       # exactly 24 slots, mixed flags
+    ms += [3, -3, -3, 3, 3, 3, -3, -3] * 3
+    ns += [6, 6, 6]                      # three cos slots (odd count)
+    ms += [0, 0, 0]
+    ns += [8, 8, 8]                      # odd count, mixed flags
+    ms += [4, -4, -4]
+    ns += [12] * 40                      # 40 sin slots
+    ms += [-6] * 40
+    ns += [5, 3, 1, 9, 0, 11]            # single-slot steps in other columns
+    ms += [1, -1, 1, -9, 0, 11]
+    order = np.random.default_rng(5).permutation(len(ns))
+    ns = [ns[i] for i in order]
+    ms = [ms[i] for i in order]
+    r, th = inputs.uniform_points(150, 44)
+    C = inputs.scaled_normal_coeffs(ns, 37, 44)
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), prec).cpu().numpy()
+    wait_ok()
+    want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
+    tol = REL[prec] * abs_sum(ns, ms, r, th, C) + 1e-6
+    assert (np.abs(F - want) <= tol).all()
