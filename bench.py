@@ -67,6 +67,8 @@ def parse_args():
                     help="run only the series_n24 forward / adjoint / fit measurement (profiling captures)")
     ap.add_argument("--adjoint-emulated-only", action="store_true",
                     help="run only the series_n24 emulated-float64 adjoint (profiling captures)")
+    ap.add_argument("--paper-shapes-only", action="store_true",
+                    help="run only the paper-shapes measurement (Algorithm 2, Fig. 3 grid, duplicated modes)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
@@ -849,6 +851,13 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"adjoint_emulated_only": measure_adjoint_emulated(torch.device("cuda", 0),
                                                                             steps=args.steps)}), flush=True)
+        return
+    if args.paper_shapes_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"paper_shapes_only": measure_paper_shapes(torch.device("cuda", 0), steps=args.steps)}),
+              flush=True)
         return
     if args.adjoint_only:
         import torch
