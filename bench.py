@@ -147,6 +147,22 @@ def _oracle_chunk(args):
     return len(ns) * len(rs) * 4 + 0 * len(tab)
 
 
+def _oracle_parity_chunk(args):
+    """Exact oracle values at a few points against the GPU's values there: per derivative
+    order k, the largest absolute error and the largest error over the tolerance
+    1e-11 max(n, 1)^(2k)."""
+    ns, ms, rs, gpu = args
+    import numpy as np
+
+    from oracle import radial as oradial
+
+    want = np.array(oradial.radial_table(ns, ms, rs, 3))  # [4][modes][points]
+    err = np.abs(np.asarray(gpu) - want)
+    n1 = np.maximum(np.asarray(ns, dtype=np.float64), 1.0)
+    tol = np.stack([1e-11 * n1 ** (2 * k) for k in range(4)])[:, :, None]
+    return err.max(axis=(1, 2)).tolist(), float((err / tol).max())
+
+
 class OraclePool:
     """A spawn-started process pool over the host cores that times the exact CPU oracle on a
     sample of the workload's points (all modes, k = 0..3)."""
@@ -172,6 +188,21 @@ class OraclePool:
         return {"value": vals / dt, "unit": UNIT, "cores": len(chunks), "kind": "oracle",
                 "sample": f"{len(pts)} of the 100000 points x all 2601 modes x k=0..3 "
                           f"({vals} exact-rational values in {dt:.2f} s)"}
+
+    def parity(self, rs, gpu) -> dict:
+        """The GPU output of the timed workload (gpu: [4][modes][len(rs)] at the points rs)
+        against the exact oracle, the points dealt over the pool."""
+        import numpy as np
+
+        gpu = np.asarray(gpu)
+        parts = [list(range(i, len(rs), self.cores)) for i in range(self.cores)]
+        parts = [q for q in parts if q]
+        res = self.pool.map(_oracle_parity_chunk, [(self.ns, self.ms, [float(rs[i]) for i in q], gpu[:, :, q])
+                                                   for q in parts])
+        max_abs = [max(r[0][k] for r in res) for k in range(4)]
+        worst = max(r[1] for r in res)
+        return {"points": len(rs), "values": int(gpu.size), "max_abs_err_k0_k3": max_abs,
+                "max_err_over_tol": worst, "tol": "1e-11 * max(n,1)^(2k)", "ok": worst <= 1.0}
 
     def time_alg1_numpy(self, chunk: int = 8192) -> dict:
         """The numpy restatement of Algorithm 1 on the whole workload (all 100000 points, all
@@ -327,6 +358,10 @@ def run_ours(args) -> None:
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # Sampled output of the timed steps (every point index spread over [0, 1] and both ends),
+    # checked against the exact oracle in the CPU-baseline leg below.
+    parity_idx = np.unique(np.concatenate([[0, P - 1], np.linspace(0, P - 1, 62).astype(int)]))
+    parity_gpu = out[:, :, torch.as_tensor(parity_idx, device=dev)].cpu().numpy()
     total_ms = max_over_ranks(sum(ms_steps), dist, dev)
     ms_per_step = total_ms / args.steps
     values_per_step = P * J * K
@@ -436,6 +471,7 @@ def run_ours(args) -> None:
         pool = OraclePool()
         try:
             cpu = pool.time(args.cpu_sample_points)
+            cpu["parity_of_the_timed_output"] = pool.parity(np.asarray(r)[parity_idx], parity_gpu)
             cpu_alg1 = pool.time_alg1_numpy()
         finally:
             pool.close()
