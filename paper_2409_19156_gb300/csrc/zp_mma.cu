@@ -1075,17 +1075,19 @@ __device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, u
 
 // Slices of an operand's rows in the tensor core's K-major swizzled chunks: tile
 // (row / ROWS) x K chunk kc at ((tile * KC + kc) * ROWS * Cfg<KIND_SLICE>::ROW) bytes, slice t a further
-// t * slice_stride.  Thread = (row, group of 8 consecutive K), rows fastest.  Rows past `rows`
-// and K past `K` are zero.
-template <int ROWS>
+// t * slice_stride.  Thread = (row, group of 8 consecutive K): rows fastest when an operand's
+// rows are contiguous (KFAST = false), K groups fastest when its K is (coalesced loads either
+// way).  Rows past `rows` and K past `K` are zero.
+template <int ROWS, bool KFAST>
 __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
                                   const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride) {
   constexpr int BK = Cfg<KIND_SLICE>::BK;
   const int64_t rows_pad = tiles * ROWS;
-  const int64_t total = rows_pad * KC * (BK / 8);
+  const int64_t groups = (int64_t)KC * (BK / 8);
+  const int64_t total = rows_pad * groups;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i % rows_pad;
-    const int64_t k0 = (i / rows_pad) * 8;
+    const int64_t row = KFAST ? i / groups : i % rows_pad;
+    const int64_t k0 = (KFAST ? i % groups : i / rows_pad) * 8;
     const bool valid = row < rows;
     const int ex = valid ? expo[row] : 0;
     const bool use = valid && ex != kNonFiniteRow;
@@ -1143,6 +1145,7 @@ __device__ __forceinline__ long long horner(long long acc, int beta, long long t
 
 struct RecombineArgs {
   const int* T;            // [k_batches][ndiag][rows][N] int32 diagonal sums
+  const long long* T64;    // or [ndiag][rows][N] int64 sums of all batches (then k_batches = 1)
   int64_t diag_stride;     // rows * N
   int64_t batch_stride;    // ndiag * rows * N
   int k_batches, ndiag, split, beta;
@@ -1153,7 +1156,7 @@ struct RecombineArgs {
   int64_t ldc;
 };
 
-// VW consecutive int32 diagonal sums (streaming loads), VW in {1, 2, 4}.
+// VW consecutive diagonal sums (streaming loads), VW in {1, 2, 4}.
 template <int VW>
 __device__ __forceinline__ void load_sums(const int* p, long long (&t)[VW]) {
   if constexpr (VW == 4) {
@@ -1166,16 +1169,53 @@ __device__ __forceinline__ void load_sums(const int* p, long long (&t)[VW]) {
     t[0] = __ldcs(p);
   }
 }
+template <int VW>
+__device__ __forceinline__ void load_sums(const long long* p, long long (&t)[VW]) {
+#pragma unroll
+  for (int k = 0; k < VW; k += 2) {
+    if (k + 1 < VW) {
+      const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(p + k));
+      t[k] = v.x, t[k + 1] = v.y;
+    } else {
+      t[k] = __ldcs(p + k);
+    }
+  }
+}
+
+// Sums the K batches' int32 diagonal sums of every element of a batch plane into int64 `acc`
+// (zeroed by the caller), `per` batches per thread: many threads share a long batch list, and
+// the integer atomics make the result exact and independent of their order.
+__global__ void sum_batches_kernel(const int* __restrict__ T, int64_t batch_stride, int k_batches, int per,
+                                   long long* __restrict__ acc) {
+  const int64_t groups = (k_batches + per - 1) / per;
+  const int64_t total = batch_stride * groups;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i % batch_stride;
+    const int kb0 = (int)(i / batch_stride) * per;
+    const int kb1 = kb0 + per < k_batches ? kb0 + per : k_batches;
+    long long sum = 0;
+    for (int kb = kb0; kb < kb1; ++kb) sum += __ldcs(T + kb * batch_stride + e);
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc + e), (unsigned long long)sum);
+  }
+}
 
 // Number of consecutive outputs of one recombination thread (a 16-byte store per two).
 constexpr int kRecombineWidth = 4;
+// From this many K batches on, the batches are pre-summed in parallel before recombining.
+constexpr int kPreReduceBatches = 8;
 
 // C[m][n] = sigma_m sigma_n 2^(-beta (ndiag+1)) Nmn with Nmn = sum_d (sum_batches T_d)
 // 2^(beta (ndiag+1-d)), d = 2..ndiag+1, formed exactly: the first `split` diagonals in one
 // int64 Horner chain, the rest in another, joined into 128 bits and rounded once.
 // Block = row m of C (grid-stride), threads across n, VW consecutive outputs per thread.
-template <int VW>
+template <int VW, typename TT>
 __global__ void recombine_kernel(RecombineArgs a) {
+  const TT* Tbase;
+  if constexpr (sizeof(TT) == 8) {
+    Tbase = a.T64;
+  } else {
+    Tbase = a.T;
+  }
   const int lo_shift = a.beta * (a.ndiag - a.split);
   const int e_base = -a.beta * (a.ndiag + 1);
   // Vector path: VW-wide loads of T (its rows are VW-aligned when N is) and 16-byte stores of C.
@@ -1184,7 +1224,7 @@ __global__ void recombine_kernel(RecombineArgs a) {
   for (int64_t m = blockIdx.x; m < a.rows; m += gridDim.x) {
     const bool row_bad = a.rexp[m] == kNonFiniteRow;
     const int em = a.rexp[m] + e_base;
-    const int* trow = a.T + m * a.N;
+    const TT* trow = Tbase + m * a.N;
     double* crow = a.C + m * a.ldc;
     if (vec) {
       for (int64_t n0 = (int64_t)threadIdx.x * VW; n0 < a.N; n0 += (int64_t)blockDim.x * VW) {
@@ -1264,6 +1304,7 @@ struct EmuGemm {
   GemmShape gs;
   int64_t slab_tiles = 0;  // row tiles per slab
   int64_t recombine_blocks = 0;
+  ScratchBuffer accbuf;  // int64 batch sums (runs with many K batches)
   ScratchBuffer bsl, cexp, asl, rexp, tbuf, maxbits;
   int64_t a_stride = 0, b_stride = 0;
 
@@ -1278,7 +1319,7 @@ struct EmuGemm {
     sms = gs.sms;
     // One resident wave of recombination blocks, grid-striding over the rows.
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recombine_kernel<kRecombineWidth>, 256, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recombine_kernel<kRecombineWidth, int>, 256, 0) !=
         cudaSuccess) {
       cudaGetLastError();
       per_sm = 4;
@@ -1296,9 +1337,15 @@ struct EmuGemm {
     ZP_TRY(asl.alloc((size_t)sh.sp.s * a_stride, stream));
     ZP_TRY(rexp.alloc((size_t)slab_tiles * BM * sizeof(int), stream));
     ZP_TRY(tbuf.alloc((size_t)slab_tiles * t_tile, stream));
+    if (sh.k_batches >= kPreReduceBatches)
+      ZP_TRY(accbuf.alloc((size_t)sh.sp.s * slab_tiles * BM * N * sizeof(long long), stream));
     ZP_TRY(maxbits.alloc((size_t)std::max<int64_t>(N, slab_tiles * BM) * sizeof(unsigned long long), stream));
     ZP_TRY(scale_rows(B, N, K, (unsigned long long*)maxbits.ptr, (int*)cexp.ptr, stream));
-    slice_rows_kernel<BN><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+    if (B.sk == 1 && B.sr != 1)
+      slice_rows_kernel<BN, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                           (uint8_t*)bsl.ptr, b_stride);
+    else
+      slice_rows_kernel<BN, false><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
                                                     (uint8_t*)bsl.ptr, b_stride);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "B slicing launch");
@@ -1309,8 +1356,12 @@ struct EmuGemm {
     using C = Cfg<KIND_SLICE>;
     const int64_t tiles = (rows + BM - 1) / BM;
     ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
-    slice_rows_kernel<BM><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
-                                                    (uint8_t*)asl.ptr, a_stride);
+    if (A.sk == 1 && A.sr != 1)
+      slice_rows_kernel<BM, true><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
+                                                           (uint8_t*)asl.ptr, a_stride);
+    else
+      slice_rows_kernel<BM, false><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
+                                                            (uint8_t*)asl.ptr, a_stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "A slicing launch");
     const int64_t trows = slab_tiles * BM;
@@ -1326,9 +1377,26 @@ struct EmuGemm {
       ga.t_batch_stride = batch_stride;
       ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, gs, stream));
     }
-    RecombineArgs ra{(const int*)tbuf.ptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
+    RecombineArgs ra{(const int*)tbuf.ptr, nullptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
                      sh.sp.beta, (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
-    recombine_kernel<kRecombineWidth><<<(unsigned)std::min<int64_t>(rows, recombine_blocks), 256, 0, stream>>>(ra);
+    const unsigned rblocks = (unsigned)std::min<int64_t>(rows, recombine_blocks);
+    if (sh.k_batches >= kPreReduceBatches) {
+      // Many K batches (a small output cut along a long K): the batches are first summed into
+      // int64 planes by many threads, then recombined as one batch.
+      if ((e = cudaMemsetAsync(accbuf.ptr, 0, (size_t)batch_stride * sizeof(long long), stream)) != cudaSuccess)
+        return cuda_error(e, "cudaMemsetAsync");
+      const int per = 8;
+      const int64_t work = batch_stride * ((sh.k_batches + per - 1) / per);
+      sum_batches_kernel<<<(unsigned)std::min<int64_t>((work + 255) / 256, 8 * (int64_t)sms), 256, 0, stream>>>(
+          (const int*)tbuf.ptr, batch_stride, sh.k_batches, per, (long long*)accbuf.ptr);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "sum_batches_kernel launch");
+      ra.T = nullptr;
+      ra.T64 = (const long long*)accbuf.ptr;
+      ra.k_batches = 1;
+      recombine_kernel<kRecombineWidth, long long><<<rblocks, 256, 0, stream>>>(ra);
+    } else {
+      recombine_kernel<kRecombineWidth, int><<<rblocks, 256, 0, stream>>>(ra);
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "recombine_kernel launch");
   }
