@@ -6,9 +6,9 @@
 // Steps: the basis by the walk kernel (float64, into scratch), the rows scaled by sqrt(w) when
 // weights are given, the Gram matrix and the right-hand side by cuBLAS DGEMM (or by the
 // float64-accurate tensor-core GEMM of zp_mma.cu for ZP_PREC_FP64_EMULATED), the
-// ridge added on the diagonal, a Cholesky factorisation and solve by cuSOLVER, and a DGEAM
-// transpose into the caller's row-major [J][S] output.  The call synchronises its stream at
-// the end to read the factorisation status.
+// ridge added on the diagonal, a Cholesky factorisation and solve (the library's own blocked
+// kernels up to 640 modes, cuSOLVER beyond), and a DGEAM transpose into the caller's row-major
+// [J][S] output.  The call synchronises its stream at the end to read the factorisation status.
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
@@ -65,6 +65,247 @@ __global__ void pivot_range_kernel(const double* L, int64_t J, double* out) {
     out[0] = smin[0];
     out[1] = smax[0];
   }
+}
+
+// ---- Cholesky factorisation and solve for small normal matrices (J <= kCholMaxJ) ----------
+// cuSOLVER's potrf / potrs take 1.3 + 0.9 ms for J = 325 (latency-bound panel kernels); these
+// kernels do the same in a few tens of launches without grid-wide waits.  A is column-major
+// J x J, lower triangle; every element is written by one thread in a fixed order (the results
+// are deterministic).
+constexpr int kNb = 32;          // panel width
+constexpr int kCholMaxJ = 640;   // shared-memory staging limit of the solve kernel
+constexpr int kSolveCols = 2;    // right-hand sides per CTA of the solve kernel
+
+// Pivot d = sqrt(v) and its reciprocal.  In the float32 range: the reciprocal square root by
+// Newton-Raphson iteration (r <- r (3 - v r^2) / 2, quadratic convergence) from the float32
+// estimate rsqrtf, two steps to float64 precision, d = v r; one thread's dependent float64 chain
+// is much shorter this way than a float64 sqrt and a division.  Elsewhere (and for v <= 0 or NaN,
+// which the caller reports): sqrt and a division.
+__device__ __forceinline__ void pivot_sqrt(double v, double* d, double* rd) {
+  if (v > 1e-30 && v < 1e30) {
+    double r = (double)rsqrtf((float)v);
+    r = r * fma(-0.5 * v, r * r, 1.5);
+    r = r * fma(-0.5 * v, r * r, 1.5);
+    *rd = r;
+    *d = v * r;
+  } else {
+    *d = sqrt(v);
+    *rd = 1.0 / *d;
+  }
+}
+
+// Panel k0 (columns k0 .. k0 + nb - 1, the updates of earlier panels already applied): every
+// CTA factors the nb x nb diagonal block in shared memory (identical arithmetic, so the copies
+// agree bitwise); CTA 0 writes the factor back, CTA b >= 1 solves rows k0 + 32 b ... of the
+// panel against it (L_rows = A_rows L_kk^-T).  info[0]: 1 + the first column whose pivot is not
+// positive (left 0 when there is none).
+__global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int J, int k0, int* info) {
+  __shared__ double D[kNb][kNb + 1];
+  __shared__ double R[kNb][kNb + 1];
+  __shared__ double rd[kNb];
+  const int nb = min(kNb, J - k0);
+  const int tid = threadIdx.x;
+  const int tx = tid % kNb, ty = tid / kNb;  // 256 threads: 8 rows of 32
+#pragma unroll
+  for (int c = ty; c < kNb; c += 8)
+    D[tx][c] = (tx < nb && c < nb && tx >= c) ? A[(size_t)(k0 + tx) + (size_t)(k0 + c) * J] : 0.0;
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (tid == 0) {
+      const double v = D[c][c];
+      if (!(v > 0.0) && blockIdx.x == 0) atomicCAS(info, 0, k0 + c + 1);
+      double d, r;
+      pivot_sqrt(v, &d, &r);
+      D[c][c] = d;
+      rd[c] = r;
+    }
+    __syncthreads();
+    if (tid > c && tid < nb) D[tid][c] *= rd[c];
+    __syncthreads();
+    // Trailing block: (r, q) = (tx, q) with c < q <= r < nb.
+#pragma unroll
+    for (int q = ty; q < kNb; q += 8)
+      if (q > c && q <= tx && tx < nb) D[tx][q] = fma(-D[tx][c], D[q][c], D[tx][q]);
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int r = e % nb, c = e / nb;
+      if (r >= c) A[(size_t)(k0 + r) + (size_t)(k0 + c) * J] = D[r][c];
+    }
+    return;
+  }
+  const int i0 = k0 + nb + ((int)blockIdx.x - 1) * kNb;
+  const int rows = min(kNb, J - i0);
+  if (rows <= 0) return;
+  for (int e = tid; e < rows * nb; e += blockDim.x) {
+    const int r = e % rows, c = e / rows;
+    R[r][c] = A[(size_t)(i0 + r) + (size_t)(k0 + c) * J];
+  }
+  __syncthreads();
+  // Rows below the diagonal block exist only for full-width panels (nb = 32): the row is solved
+  // in registers, fully unrolled (a shared-memory row would serialise on store-load ordering).
+  if (tid < rows) {
+    double x[kNb];
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) x[c] = R[tid][c];
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) {
+      x[c] *= rd[c];
+#pragma unroll
+      for (int q = c + 1; q < kNb; ++q) x[q] = fma(-x[c], D[q][c], x[q]);
+    }
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) R[tid][c] = x[c];
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * nb; e += blockDim.x) {
+    const int r = e % rows, c = e / rows;
+    A[(size_t)(i0 + r) + (size_t)(k0 + c) * J] = R[r][c];
+  }
+}
+
+// Trailing update after panel k0: A[i][j] -= sum_u L[i][k0+u] L[j][k0+u] for k0 + 32 <= j <= i,
+// one 32 x 32 tile (tile row ti >= tile column tj) per CTA, 4 outputs per thread.
+__global__ void __launch_bounds__(256) chol_update_kernel(double* A, int J, int k0) {
+  __shared__ double Li[kNb][kNb + 1], Lj[kNb][kNb + 1];
+  const int k1 = k0 + kNb;
+  const int t = (int)blockIdx.x;
+  int ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int i0 = k1 + ti * kNb, j0 = k1 + tj * kNb;
+  const int ri = min(kNb, J - i0), rj = min(kNb, J - j0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+    const int r = e % kNb, c = e / kNb;
+    Li[r][c] = r < ri ? A[(size_t)(i0 + r) + (size_t)(k0 + c) * J] : 0.0;
+    Lj[r][c] = r < rj ? A[(size_t)(j0 + r) + (size_t)(k0 + c) * J] : 0.0;
+  }
+  __syncthreads();
+  const int r = tid % kNb;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = tid / kNb + 8 * q;
+    const int i = i0 + r, j = j0 + c;
+    if (r < ri && c < rj && i >= j) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int u = 0; u < kNb; ++u) acc = fma(Li[r][u], Lj[c][u], acc);
+      A[(size_t)i + (size_t)j * J] -= acc;
+    }
+  }
+}
+
+// Solves L L^T X = B in place for kSolveCols columns of B per CTA (B column-major J x S): the
+// forward substitution L y = b walks the columns of L, the backward one L^T x = y its rows; L
+// is staged in shared memory 32 columns (rows) at a time.  Shared memory: (32 + 2 kSolveCols +
+// 1) J doubles.
+__global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ L, int J, double* B, int S) {
+  extern __shared__ double sm[];
+  double* Lb = sm;                       // [32][J]
+  double* y = Lb + (size_t)kNb * J;      // [kSolveCols][J] working right-hand sides
+  double* z = y + (size_t)kSolveCols * J;  // [kSolveCols][J] forward solution
+  double* rdg = z + (size_t)kSolveCols * J;  // [J] reciprocals of the pivots
+  const int tid = threadIdx.x;
+  const int s0 = (int)blockIdx.x * kSolveCols;
+  const int ns = min(kSolveCols, S - s0);
+  for (int e = tid; e < J; e += blockDim.x) rdg[e] = 1.0 / L[(size_t)e + (size_t)e * J];
+  for (int e = tid; e < kSolveCols * J; e += blockDim.x) {
+    const int k = e / J, t = e % J;
+    y[e] = k < ns ? B[(size_t)t + (size_t)(s0 + k) * J] : 0.0;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < J; c0 += kNb) {
+    const int nc = min(kNb, J - c0);
+    // Eight loads in flight per thread (the staged block comes from L2).
+    for (int base = tid; base < nc * J; base += 8 * (int)blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = base + q * (int)blockDim.x, u = e / J, t = e % J;
+        v[q] = (e < nc * J && t > c0 + u) ? L[(size_t)t + (size_t)(c0 + u) * J] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = base + q * (int)blockDim.x;
+        if (e < nc * J) Lb[(size_t)(e / J) * J + e % J] = v[q];
+      }
+    }
+    __syncthreads();
+    for (int u = 0; u < nc; ++u) {
+      const int c = c0 + u;
+      double yc[kSolveCols];
+#pragma unroll
+      for (int k = 0; k < kSolveCols; ++k) yc[k] = y[(size_t)k * J + c] * rdg[c];
+      if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < kSolveCols; ++k) z[(size_t)k * J + c] = yc[k];
+      }
+      for (int t = c + 1 + tid; t < J; t += blockDim.x) {
+        const double l = Lb[(size_t)u * J + t];
+#pragma unroll
+        for (int k = 0; k < kSolveCols; ++k) y[(size_t)k * J + t] = fma(-l, yc[k], y[(size_t)k * J + t]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i0 = (J - 1) / kNb * kNb; i0 >= 0; i0 -= kNb) {
+    const int nr = min(kNb, J - i0);
+    for (int base = tid; base < nr * (i0 + nr); base += 8 * (int)blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = base + q * (int)blockDim.x, u = e % nr, t = e / nr;
+        v[q] = (e < nr * (i0 + nr) && t < i0 + u) ? L[(size_t)(i0 + u) + (size_t)t * J] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = base + q * (int)blockDim.x;
+        if (e < nr * (i0 + nr)) Lb[(size_t)(e % nr) * J + e / nr] = v[q];
+      }
+    }
+    __syncthreads();
+    for (int u = nr - 1; u >= 0; --u) {
+      const int i = i0 + u;
+      double xi[kSolveCols];
+#pragma unroll
+      for (int k = 0; k < kSolveCols; ++k) xi[k] = z[(size_t)k * J + i] * rdg[i];
+      if (tid == 0) {
+        for (int k = 0; k < ns; ++k) B[(size_t)i + (size_t)(s0 + k) * J] = xi[k];
+      }
+      for (int t = tid; t < i; t += blockDim.x) {
+        const double l = Lb[(size_t)u * J + t];
+#pragma unroll
+        for (int k = 0; k < kSolveCols; ++k) z[(size_t)k * J + t] = fma(-l, xi[k], z[(size_t)k * J + t]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Factors the J x J normal matrix (J <= kCholMaxJ) in place and solves for the J x S
+// right-hand sides in place; info[0] as in chol_panel_kernel (zeroed here).
+zp_status small_cholesky_solve(double* A, int J, double* B, int S, int* info, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+  for (int k0 = 0; k0 < J; k0 += kNb) {
+    const int nb = std::min(kNb, J - k0);
+    const int below = J - k0 - nb;
+    chol_panel_kernel<<<1 + (below + kNb - 1) / kNb, 256, 0, stream>>>(A, J, k0, info);
+    if (below > 0) {
+      const int nt = (below + kNb - 1) / kNb;
+      chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, stream>>>(A, J, k0);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "Cholesky panel launch");
+  }
+  const size_t smem = (size_t)(kNb + 2 * kSolveCols + 1) * J * sizeof(double);
+  if ((e = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute(chol_solve_kernel)");
+  chol_solve_kernel<<<(S + kSolveCols - 1) / kSolveCols, 256, smem, stream>>>(A, J, B, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "chol_solve_kernel launch");
+  return ZP_OK;
 }
 
 struct SolverHandles {
@@ -137,20 +378,26 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
     add_ridge_kernel<<<(unsigned)((J + 255) / 256), 256, 0, stream>>>((double*)gram.ptr, J, ridge);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "add_ridge_kernel launch");
   }
-  int lwork = 0;
-  if (cusolverDnDpotrf_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, &lwork) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf_bufferSize failed");
   ScratchBuffer work;
-  ZP_TRY(work.alloc((size_t)std::max(lwork, 1) * sizeof(double), stream));
-  if (cusolverDnDpotrf(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, (double*)work.ptr, lwork,
-                       (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf failed");
-  pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
-  if (cusolverDnDpotrs(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (int)S, (double*)gram.ptr, (int)J, (double*)rhs.ptr,
-                       (int)J, (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cusolverDnDpotrs failed");
+  if (J <= kCholMaxJ && S <= (int64_t)INT32_MAX) {
+    ZP_TRY(small_cholesky_solve((double*)gram.ptr, (int)J, (double*)rhs.ptr, (int)S, (int*)info.ptr, stream));
+    pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
+  } else {
+    int lwork = 0;
+    if (cusolverDnDpotrf_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, &lwork) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf_bufferSize failed");
+    ZP_TRY(work.alloc((size_t)std::max(lwork, 1) * sizeof(double), stream));
+    if (cusolverDnDpotrf(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, (double*)work.ptr, lwork,
+                         (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf failed");
+    pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
+    if (cusolverDnDpotrs(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (int)S, (double*)gram.ptr, (int)J, (double*)rhs.ptr,
+                         (int)J, (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrs failed");
+  }
   // coeffs row-major [J][S] = column-major S x J = transpose of the J x S solution.
   if (cublasDgeam(blas, CUBLAS_OP_T, CUBLAS_OP_N, (int)S, (int)J, &one, (double*)rhs.ptr, (int)J, &zero, coeffs,
                   (int)S, coeffs, (int)S) != CUBLAS_STATUS_SUCCESS)

@@ -67,3 +67,19 @@ def test_singular_fit_is_reported_and_ridge_fixes_it():
     assert "positive definite" in str(e.value)
     C = zp.series_fit(ns, ms, dev(r), dev(th), dev(Y), ridge=1e-3)
     assert bool(torch.isfinite(C).all())
+
+
+@pytest.mark.parametrize("n_max,S", [(7, 3), (34, 5), (35, 1)])
+def test_fit_round_trip_across_solver_sizes(n_max, S):
+    """Round trips through zp_series_eval on an exact polar quadrature for 36 modes (two
+    32-column panels, ragged), 630 modes (the library's own blocked Cholesky near its 640-mode
+    limit) and 666 modes (beyond it: cuSOLVER), with odd set counts."""
+    ns, ms = inputs.full_zernike_modes(n_max)
+    r, th, w = polar_quadrature(n_max // 2 + 3, 2 * n_max + 4)
+    C = np.random.default_rng(n_max).standard_normal((len(ns), S))
+    plan = zp.Plan(ns, ms)
+    rt, tt = dev(r), dev(th)
+    Y = zp.series_eval(None, None, rt, tt, dev(C), plan=plan)
+    for prec in ("fp64", "fp64emu"):
+        got = zp.series_fit(None, None, rt, tt, Y, weights=dev(w), plan=plan, prec=prec).cpu().numpy()
+        assert np.max(np.abs(got - C)) < 1e-9, (prec, np.max(np.abs(got - C)))
