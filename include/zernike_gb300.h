@@ -237,7 +237,8 @@ ZP_API zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double*
  * Least-squares fit of series coefficients (the "fit" counterpart of zp_series_eval):
  *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
  * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 throughout (basis by
- * the recursion walk, Gram matrix and right-hand side by DGEMM, Cholesky by cuSOLVER).
+ * the recursion walk, Gram matrix and right-hand side by DGEMM, Cholesky factorisation and
+ * solve by the library's own blocked kernels up to 640 modes, by cuSOLVER beyond).
  *   weights: DEVICE float64 [n_points] (w_p >= 0) or NULL (all 1).
  *   samples: DEVICE float64 [n_points][n_sets] (Y, row-major).
  *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
@@ -258,8 +259,7 @@ ZP_API zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const 
  * zp_series_fit_plan with a choice of arithmetic for the Gram matrix Z W Z^T and the
  * right-hand side Z W Y: ZP_PREC_FP64 (cuBLAS DGEMM) or ZP_PREC_FP64_EMULATED (the
  * float64-accurate tensor-core GEMM, error about n_points 2^-54 times the largest magnitudes
- * of the rows involved).  The Cholesky factorisation and solve are float64 (cuSOLVER) either
- * way.  Other precisions: ZP_ERR_INVALID_ARG.
+ * of the rows involved).  The Cholesky factorisation and solve are float64 either way.  Other precisions: ZP_ERR_INVALID_ARG.
  */
 ZP_API zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta,
                                          const double* weights, int64_t n_points, const double* samples,
