@@ -359,6 +359,16 @@ ZP_API zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64
 ZP_API zp_status zp_device_wait_status(int32_t reset);
 
 /*
+ * Returns the library's retained scratch memory on the current device to the system.  The
+ * series, adjoint and fit calls draw their scratch from a library-owned stream-ordered memory
+ * pool per device that keeps up to 16 GiB of freed scratch reserved across synchronisations
+ * (so that calls which synchronise do not map their scratch again each time).  Memory still
+ * in use by pending work is kept: synchronise the streams that used the library first.
+ * ZP_OK when the device has no pool yet.
+ */
+ZP_API zp_status zp_release_scratch(void);
+
+/*
  * Failure-detection self-test: launches (asynchronously, on `stream`) one thread that waits on
  * a device barrier nothing arrives on, with the same bounded wait the tensor-core kernels use,
  * giving up after limit_ms (1..2000).  A following zp_device_wait_status then reports

@@ -41,6 +41,7 @@ SIGNATURES = {
     "zp_series_adjoint": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
                                          ctypes.c_int64, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_device_wait_status": (ctypes.c_int, [ctypes.c_int32]),
+    "zp_release_scratch": (ctypes.c_int, []),
     "zp_series_point_hessian": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, ctypes.c_int64, c_dp,
                                                ctypes.c_int64, c_dp, c_dp, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_series_point_hessian_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,

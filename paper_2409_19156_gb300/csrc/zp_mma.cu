@@ -711,18 +711,21 @@ int max_active_clusters(int sms) {
 
 template <int KIND>
 zp_status gemm_shape(GemmShape* g) {
-  using C = Cfg<KIND>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
-  }
-  g->pairs = max_active_clusters<KIND, 2>(g->sms);
-  if (g->pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
-  return ZP_OK;
+  static DeviceMemo<GemmShape> memo;
+  return memo.get(g, [](GemmShape* x) -> zp_status {
+    using C = Cfg<KIND>;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+    }
+    x->pairs = max_active_clusters<KIND, 2>(x->sms);
+    if (x->pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
+    return ZP_OK;
+  });
 }
 
 template <int KIND, int CL>
@@ -785,11 +788,18 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
   GemmShape gs;
   ZP_TRY(gemm_shape<KIND>(&gs));
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_basis_kernel<TF32>, basis_threads<TF32>(), 0) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
+  static DeviceMemo<int> basis_per_sm;
+  ZP_TRY(basis_per_sm.get(&per_sm, [](int* x) -> zp_status {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(x, split_basis_kernel<TF32>, basis_threads<TF32>(), 0) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      *x = 1;
+    }
+    // The coefficient kernel's shared memory limit, set once per device.
+    const cudaError_t e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(Cfg<TF32 ? KIND_TF32 : KIND_BF16X3>::B_CHUNK + 1024));
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaFuncSetAttribute(split_coeff_kernel)");
+  }));
   const int64_t wave = (int64_t)std::max(per_sm, 1) * gs.sms;
   int64_t slab = 0;
   if (preset) {
@@ -818,9 +828,6 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 
   const uint32_t coeff_smem = C::B_CHUNK + 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(split_coeff_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, coeff_smem)) !=
-      cudaSuccess)
-    return cuda_error(e, "cudaFuncSetAttribute(split_coeff_kernel)");
 
   CoeffArgs ca{coeffs, plan->dev.slot_idx, J, S, KC, B};
   timer.begin(0, &ev0, stream);
@@ -1319,11 +1326,15 @@ struct EmuGemm {
     sms = gs.sms;
     // One resident wave of recombination blocks, grid-striding over the rows.
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recombine_kernel<kRecombineWidth, int>, 256, 0) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      per_sm = 4;
-    }
+    static DeviceMemo<int> recombine_per_sm;
+    ZP_TRY(recombine_per_sm.get(&per_sm, [](int* x) -> zp_status {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(x, recombine_kernel<kRecombineWidth, int>, 256, 0) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        *x = 4;
+      }
+      return ZP_OK;
+    }));
     recombine_blocks = (int64_t)std::max(per_sm, 1) * sms;
     if (!choose_emu_shape(K, MT * NT, sms, &sh))
       return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");

@@ -1,9 +1,38 @@
 // Declarations shared by the series translation units.
 #pragma once
 
+#include <mutex>
+
 #include "zp_internal.h"
 
 namespace zp {
+
+// Per-device memo of a host-side launch parameter that never changes for a device (occupancy
+// queries, function attributes), computed on the device's first use: these queries cost far
+// more host time than a launch, and the library's calls are often issued back to back.
+template <typename T>
+struct DeviceMemo {
+  std::mutex mu;
+  bool have[64] = {};
+  T val[64] = {};
+  template <typename F>
+  zp_status get(T* out, F&& compute) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return compute(out);
+    std::lock_guard<std::mutex> lock(mu);
+    if (have[dev]) {
+      *out = val[dev];
+      return ZP_OK;
+    }
+    const zp_status st = compute(out);
+    if (st != ZP_OK) return st;
+    val[dev] = *out;
+    have[dev] = true;
+    return ZP_OK;
+  }
+};
 
 // Stream-ordered scratch: cudaMallocAsync on `stream`, cudaFreeAsync on the same stream
 // when the object goes out of scope (after the work that uses it has been enqueued).

@@ -85,3 +85,24 @@ def test_plan_entry_points_capture_in_a_cuda_graph(P):
     torch.cuda.synchronize()
     ref2, _ = zp.basis(None, None, rt, tt, 2, plan=plan)
     assert torch.equal(out, ref2)
+
+
+def test_release_scratch_returns_ok_and_calls_keep_working():
+    """zp_release_scratch trims the library's scratch pool after a synchronisation; a call that
+    needs scratch afterwards allocates again and gives the same result."""
+    import numpy as np
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import _lib, inputs
+
+    ns, ms = inputs.full_zernike_modes(12)
+    r, th = inputs.uniform_points(3000, 3)
+    C = np.random.default_rng(3).standard_normal((len(ns), 8))
+    rt, tt, Ct = (torch.as_tensor(x, device="cuda:0") for x in (r, th, C))
+    before = zp.series_eval(ns, ms, rt, tt, Ct, "fp64emu")
+    torch.cuda.synchronize()
+    lib = _lib.load()
+    assert lib.zp_release_scratch() == 0
+    after = zp.series_eval(ns, ms, rt, tt, Ct, "fp64emu")
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    assert lib.zp_release_scratch() == 0
