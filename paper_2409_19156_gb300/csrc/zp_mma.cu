@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
         ptx::tmem_ld_32x32b_x32(tmem_base + ((q * 32u) << 16) + acc * BN + (uint32_t)c0, v);
-        ptx::tmem_ld_wait();
+        ptx::tmem_ld_wait(v);
         if constexpr (KIND == KIND_SLICE) {
           // Slice products sum to integers below 2^24 (exact in float32): store them as int32.
 #pragma unroll
