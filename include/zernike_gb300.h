@@ -159,8 +159,10 @@ ZP_API zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_
  *   out:    DEVICE [n_points][n_sets] row-major; float64 for ZP_PREC_FP64, float32 for
  *           ZP_PREC_BF16X3 / ZP_PREC_TF32.
  * The float64 form writes the basis to scratch device memory (allocated stream-ordered on
- * `stream` and released before return) and contracts with cuBLAS DGEMM.  The split forms
- * run the float64 recursion into tensor-core tiles (tcgen05) with float32 accumulation.
+ * `stream` from the library's scratch pool, see zp_release_scratch, and released to it before
+ * return) and contracts with cuBLAS DGEMM.  The split forms run the float64 recursion into
+ * tensor-core operand tiles in scratch (slabs of whole waves of point tiles) and contract them
+ * with tcgen05 MMAs and float32 accumulation.
  */
 ZP_API zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes,
                          const double* r, const double* theta, int64_t n_points,
