@@ -102,9 +102,12 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
     }
     n_max = std::max(n_max, nj);
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  // The host tables need no device; without one (device -1) the later upload fails instead.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = -1;
+  }
 
   p->device = dev;
   p->n_modes = n_modes;
