@@ -88,3 +88,22 @@ def test_negative_sizes_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.zp_plan_create(pn, pm, -1, ctypes.byref(h)) == 1
     assert lib.zp_plan_create(None, None, 3, ctypes.byref(h)) == 1
+
+
+def test_no_cpu_fallback_anywhere(monkeypatch, tmp_path):
+    """The Python layer refuses host tensors instead of computing on the CPU, and a missing
+    shared library raises instead of falling back."""
+    torch = pytest.importorskip("torch")
+    import paper_2409_19156_gb300 as zp
+
+    r = torch.linspace(0, 1, 8, dtype=torch.float64)
+    for call in (lambda: zp.radial([2], [0], r, 1),
+                 lambda: zp.basis([2], [0], r, r, 0),
+                 lambda: zp.series_eval([2], [0], r, r, torch.ones(1, 3, dtype=torch.float64), "bf16x3"),
+                 lambda: zp.series_fit([2], [0], r, r, torch.ones(8, 3, dtype=torch.float64))):
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call()
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(zbuild, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()
