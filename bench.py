@@ -415,6 +415,13 @@ def run_ours(args) -> None:
             if st:
                 _lib.check("zp_radial_plan", st)
 
+        def e2e_host_buffers_step():
+            # one C-ABI call on host buffers: the kernels read r from pinned host memory and write
+            # the result into pinned host memory, both across the host link
+            st = lib.zp_radial_plan(plan.handle, r_host.data_ptr(), P, 3, out_host.data_ptr(), sp)
+            if st:
+                _lib.check("zp_radial_plan", st)
+
         def time_e2e(fn):
             fn()
             barrier()
@@ -452,11 +459,15 @@ def run_ours(args) -> None:
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
         t_mapped = time_e2e(e2e_mapped_step)
         assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
-        best, how = min((t_copy, "device kernel + D2H copy"), (t_multi, "device kernel + D2H on four copy streams"),
-                        (t_mapped, "kernel writes pinned host memory directly"))
+        out_host.zero_()
+        t_host = time_e2e(e2e_host_buffers_step)
+        assert float(out_host[3, J - 1, P - 1]) == float(out[3, J - 1, P - 1].item())
+        # The end-to-end figure is the C-ABI call on host buffers; the other forms are context.
+        best, how = t_host, "one C-ABI call on pinned host buffers (r read and result written across the link)"
         e2e = {"value": aggregate_value(values_per_step, world, best), "unit": UNIT,
                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": out_bytes, "ms_per_step": best, "how": how,
-               "ms_per_step_copy": t_copy, "ms_per_step_copy4": t_multi, "ms_per_step_mapped": t_mapped}
+               "ms_per_step_copy": t_copy, "ms_per_step_copy4": t_multi, "ms_per_step_mapped": t_mapped,
+               "ms_per_step_host_buffers": t_host}
 
     extras = None
     if rank == 0 and not args.no_extras:
