@@ -17,7 +17,10 @@
  *  - Point arrays r[] (and theta[]) are DEVICE float64 arrays of length n_points.  r is
  *    evaluated as the polynomial it is: values outside [0, 1] are not clamped.
  *  - Outputs are DEVICE arrays owned and allocated by the caller; the library never keeps a
- *    pointer to them after the call returns.  Layouts are row-major with the point index
+ *    pointer to them after the call returns.
+ *  - DEVICE means reachable by the current device at that address: its own memory, managed
+ *    memory, or pinned host memory mapped at the same address (cudaHostAlloc, cudaHostRegister
+ *    under unified addressing), which the kernels then read or write across the host link.  Layouts are row-major with the point index
  *    fastest unless stated.
  *  - Arguments are validated on the host before anything is launched.  On any error the
  *    call returns a non-zero zp_status, launches nothing and leaves outputs untouched;

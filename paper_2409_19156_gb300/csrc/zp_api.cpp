@@ -26,7 +26,11 @@ zp_status check_device_array(const void* ptr, const char* name, size_t align) {
     }
     return ZP_OK;
   }
-  if (attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr) return ZP_OK;
+  // Pinned host memory mapped at the same address (cudaHostAlloc / cudaHostRegister under
+  // unified addressing): the kernels read or write it across the host link.
+  if (attr.type == cudaMemoryTypeHost && attr.devicePointer == ptr) return ZP_OK;
+  if (attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr)
+    return set_error(ZP_ERR_INVALID_ARG, std::string(name) + " is pinned host memory mapped at another device address");
   return set_error(ZP_ERR_INVALID_ARG, std::string(name) + " is not device-accessible memory");
 }
 
