@@ -31,17 +31,21 @@ if ROOT not in sys.path:
 METRIC = "Zernike basis values/s (FP64, points x modes x derivs)"
 UNIT = "values/s"
 WORKLOAD = "radial_n100"
-# Float64 issue roofline: GB300 issues 2 float64 lanes per SM per clock (1.25 TFLOP/s
-# nominal = 152 SMs x 2 lanes x 2 flop x 2.07 GHz); one FMA or MUL = one op.
+# Float64 roofline of the walk.  Nominal: 2 float64 lanes per SM per clock (152 SMs x 2 lanes
+# x 2 flop x 2.07 GHz = 1.259 TFLOP/s).  The peak the line reports is measured in the run by
+# the library's float64 probe (zp_probe_fp64: one wave of independent FMA chains, CUDA events).
 SMS, DP_LANES_PER_SM, SM_MAX_MHZ = 152, 2, 2070.0
-DP_OPS_PEAK = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
-# float64 operations per (point, mode) of the k <= 3 walk: 1 (g) + 1 (g') + 1 + 2 + 3 + 3
-# (Taylor lanes 0..3) + 4 (stores scaled by k! w_N).
+DP_OPS_PEAK_NOMINAL = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
+# Algorithmic work per (point, mode) of the k <= 3 radial workload: 14 FMA = 28 flop (the
+# unscaled recursion and its three derivative lanes).  The kernel's rescaled form issues 15
+# float64 operations per (point, mode): 1 (g) + 1 (g') + 1 + 2 + 3 + 3 (Taylor lanes 0..3) + 4
+# (stores scaled by k! w_N), every one as an FMA.
+FLOP_PER_VALUE_TUPLE = 28
 DP_OPS_PER_VALUE_TUPLE = 15
-# DRAM bytes (read + write) of one walk_kernel<3,false,true> launch at 20000 points, from the
-# ncu capture in profiles/walk_kernel_radial_n100.md (1.604159 GB written + 17.184 MB read:
-# the output and one read of the power table), scaled to 100000 points (both proportional to
-# the point count).
+# DRAM bytes (read + write) of one walk_kernel<3,false,true> launch at 20000 points, from one
+# ncu capture of that kernel (dram__bytes_write.sum 1.604159 GB + dram__bytes_read.sum
+# 17.184 MB: the output and one read of the power table), scaled to 100000 points (both
+# proportional to the point count).  The walk kernel has not changed since that capture.
 WALK_TRAFFIC_20000 = 1.604159e9 + 17.184256e6
 
 
@@ -381,9 +385,23 @@ def run_ours(args) -> None:
         prep_ms.append(phase[0])
         walk_ms.append(phase[1])
     dp_ops = DP_OPS_PER_VALUE_TUPLE * P * J
+    flops = FLOP_PER_VALUE_TUPLE * P * J
     kernel_ms = statistics.mean(walk_ms)
     achieved = dp_ops / (kernel_ms * 1e-3)
+    achieved_flops = flops / (kernel_ms * 1e-3)
     out_bytes = values_per_step * 8
+    # The float64 peak, measured now on this GPU: best of three probe launches per operation.
+    probe = {}
+    for op, name in ((0, "fma"), (1, "mul"), (2, "add")):
+        best = None
+        for _ in range(3):
+            res = (ctypes.c_double * 6)()
+            _lib.check("zp_probe_fp64", lib.zp_probe_fp64(op, 20000, sp, res))
+            if best is None or res[2] > best[2]:
+                best = list(res)
+        probe[name] = {"ops_per_s": best[2], "lanes_per_sm_clk": best[3], "implied_sm_mhz": best[4], "ms": best[1]}
+    fma_ops = probe["fma"]["ops_per_s"]
+    peak_flops = 2.0 * fma_ops
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -470,7 +488,9 @@ def run_ours(args) -> None:
                "ms_per_step_host_buffers": t_host}
 
     extras = None
-    if rank == 0 and not args.no_extras:
+    # The secondary workloads run only in a single-GPU job: under torchrun every rank runs the
+    # headline workload alone.
+    if world == 1 and not args.no_extras:
         del out
         torch.cuda.empty_cache()
         extras = {"series": measure_series(dev, peaks), "adjoint": measure_adjoint(dev),
@@ -495,13 +515,20 @@ def run_ours(args) -> None:
             "config": {"workload": WORKLOAD, "modes": J, "n_max": 100, "points": P, "derivs": K,
                        "points_dist": "Chebyshev-Gauss nodes mapped to [0,1]", "parallelism": f"replicas{world}",
                        "l2": "256 MB write between steps, outside the per-step CUDA events; each step writes 8.3 GB"},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": DP_OPS_PEAK / 1e9,
-                         "unit": "G float64 ops/s", "frac": achieved / DP_OPS_PEAK,
+            "roofline": {"bound": "alu", "achieved": achieved_flops / 1e12, "peak": peak_flops / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved_flops / peak_flops,
                          "traffic": WALK_TRAFFIC_20000 * P / 20000 if WALK_TRAFFIC_20000 else None,
                          "traffic_note": "ncu dram__bytes_read+write of a 20000-point launch scaled by points",
-                         "kernel": "walk_kernel<3,false,true>", "ops_per_launch": dp_ops,
+                         "kernel": "walk_kernel<3,false,true>", "flop_per_launch": flops,
+                         "flop_per_unit": FLOP_PER_VALUE_TUPLE, "units_per_launch": P * J,
                          "kernel_ms": kernel_ms, "point_prep_kernel_ms": statistics.mean(prep_ms),
-                         "peak_source": "2 float64 lanes/SM/clk x 152 SMs x 2070 MHz (probe measured 1.91)",
+                         "peak_source": "measured in this run: zp_probe_fp64 float64 FMA rate x 2 flop "
+                                        "(best of 3 one-wave launches, CUDA events)",
+                         "fp64_probe": probe,
+                         "peak_nominal": DP_OPS_PEAK_NOMINAL * 2 / 1e12,
+                         "frac_of_nominal": achieved_flops / (2 * DP_OPS_PEAK_NOMINAL),
+                         "issued_ops_per_unit": DP_OPS_PER_VALUE_TUPLE,
+                         "issued_ops_frac_of_measured_fma_rate": achieved / fma_ops,
                          "hbm_write_gbs": out_bytes / (kernel_ms * 1e-3) / 1e9,
                          "hbm_frac_of_measured_copy": out_bytes / (kernel_ms * 1e-3) / 1e9 / hbm_peak},
             "e2e": e2e,
@@ -641,12 +668,13 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     plan = zp.Plan(ns, ms, device=dev)
     rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
     stream = torch.cuda.current_stream(dev)
-    zp.series_eval(None, None, rt, tt, Ct, plan=plan)
-    zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
-    fwd = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, plan=plan), steps)
+    # "fp64": the plain basis-then-DGEMM baseline; "fp64emu": the library's default float64 path.
+    zp.series_eval(None, None, rt, tt, Ct, "fp64", plan=plan)
+    zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64")
+    fwd = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, "fp64", plan=plan), steps)
     zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan)
     fwd_emu = _events_ms(stream, lambda: zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan), steps)
-    adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan), steps)
+    adj = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64"), steps)
     zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu")
     adj_emu = _events_ms(stream, lambda: zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu"),
                          steps)
@@ -657,10 +685,10 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
     _, wgl = np.polynomial.legendre.leggauss(cfg["n_r"])
     w = torch.as_tensor(np.repeat(0.25 * wgl, cfg["n_theta"]) * (2.0 * math.pi / cfg["n_theta"]), device=dev)
     Y = zp.series_eval(None, None, rt, tt, Ct, plan=plan)
-    Cfit = zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
+    Cfit = zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64")
     t0 = time.perf_counter()
     for _ in range(steps):
-        zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan)
+        zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64")
     fit_ms = (time.perf_counter() - t0) * 1e3 / steps  # the fit synchronises its stream
     Cfit_emu = zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64emu")
     t0 = time.perf_counter()
@@ -668,6 +696,7 @@ def measure_adjoint(dev, steps: int = 5) -> dict:
         zp.series_fit(None, None, rt, tt, Y, weights=w, plan=plan, prec="fp64emu")
     fit_emu_ms = (time.perf_counter() - t0) * 1e3 / steps
     return {"workload": "series_n24", "modes": len(ns), "points": len(r), "sets": C.shape[1],
+            "baseline": "fp64_* = float64 basis then cuBLAS DGEMM; fp64_emulated_* = the default path",
             "fp64_forward_ms": fwd, "fp64_emulated_forward_ms": fwd_emu, "fp64_adjoint_ms": adj,
             "fp64_emulated_adjoint_ms": adj_emu, "fp64_fit_ms": fit_ms, "fp64_emulated_fit_ms": fit_emu_ms,
             "fit_roundtrip_max_abs_err": float((Cfit - Ct).abs().max()),

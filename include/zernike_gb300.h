@@ -60,7 +60,9 @@ typedef enum {
 } zp_status;
 
 typedef enum {
-  ZP_PREC_FP64 = 0,   /* float64 throughout; outputs float64 */
+  ZP_PREC_FP64 = 0,   /* the plain float64 basis-then-GEMM form, kept as the baseline: the basis
+                         is written to scratch and contracted by cuBLAS DGEMM; outputs float64.
+                         The library's default float64 path is ZP_PREC_FP64_EMULATED */
   ZP_PREC_BF16X3 = 1, /* float64 basis, contraction on tensor cores as hi*hi + hi*lo + lo*hi
                          with bfloat16 halves and float32 accumulation; outputs float32 */
   ZP_PREC_TF32 = 2,   /* float64 basis rounded to TF32, tensor-core contraction with float32
@@ -161,9 +163,10 @@ ZP_API zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_
  *   coeffs: DEVICE float64 [n_modes][n_sets] row-major.
  *   out:    DEVICE [n_points][n_sets] row-major; float64 for ZP_PREC_FP64, float32 for
  *           ZP_PREC_BF16X3 / ZP_PREC_TF32.
- * The float64 form writes the basis to scratch device memory (allocated stream-ordered on
- * `stream` from the library's scratch pool, see zp_release_scratch, and released to it before
- * return) and contracts with cuBLAS DGEMM.  The split forms run the float64 recursion into
+ * ZP_PREC_FP64_EMULATED is the float64-accurate form to use; ZP_PREC_FP64 is the plain
+ * baseline: it writes the basis to scratch device memory (allocated stream-ordered on `stream`
+ * from the library's scratch pool, see zp_release_scratch, and released to it before return)
+ * and contracts with cuBLAS DGEMM.  The split forms run the float64 recursion into
  * tensor-core operand tiles in scratch (slabs of whole waves of point tiles) and contract them
  * with tcgen05 MMAs and float32 accumulation.
  */
@@ -187,12 +190,14 @@ ZP_API zp_status zp_series_eval_timed(const zp_plan* plan, const double* r, cons
 
 /*
  * Adjoint of the series (the reverse-mode derivative that Sec. 3 provides by a custom
- * rule), float64 throughout.  With G = grad_out (DEVICE float64 [n_points][n_sets]):
+ * rule), float64 results.  With G = grad_out (DEVICE float64 [n_points][n_sets]):
  *   grad_coeffs[j, s] = sum_p Z_j(p) G[p, s]                         ([n_modes][n_sets])
  *   grad_r[p]         = sum_j dZ_j/drho(p)   sum_s coeffs[j, s] G[p, s]      ([n_points])
  *   grad_theta[p]     = sum_j dZ_j/dtheta(p) sum_s coeffs[j, s] G[p, s]      ([n_points])
  * Any of the three outputs may be NULL (not computed).  The basis is recomputed, never
  * read from a previous forward call.  Reductions are deterministic (no float atomics).
+ * The contractions grad_coeffs = Z G and H = C G^T run on the float64-accurate tensor-core
+ * GEMM of ZP_PREC_FP64_EMULATED (zp_series_adjoint_plan_prec selects the DGEMM baseline).
  */
 ZP_API zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes,
                             const double* r, const double* theta, int64_t n_points,
@@ -204,8 +209,8 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
                                  const double* grad_out, double* grad_coeffs, double* grad_r,
                                  double* grad_theta, void* stream);
 /*
- * zp_series_adjoint_plan with a choice of contraction arithmetic: ZP_PREC_FP64 (cuBLAS
- * DGEMM, as above) or ZP_PREC_FP64_EMULATED (grad_coeffs = Z G and H = C G^T by the
+ * zp_series_adjoint_plan with a choice of contraction arithmetic: ZP_PREC_FP64 (the cuBLAS
+ * DGEMM baseline) or ZP_PREC_FP64_EMULATED (the default: grad_coeffs = Z G and H = C G^T by the
  * float64-accurate tensor-core GEMM of ZP_PREC_FP64_EMULATED, with the scale-relative error
  * bound stated there: about K 2^-54 times the largest operand magnitudes of the row and
  * column, K = n_points for grad_coeffs and n_sets for H).  grad_r and grad_theta are then
@@ -224,7 +229,8 @@ ZP_API zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* 
  *   grad_r[p]  = dL/dr_p,        grad_theta[p] = dL/dtheta_p,
  *   hess_rr[p] = d2L/dr_p^2,     hess_rt[p] = d2L/dr_p dtheta_p,     hess_tt[p] = d2L/dtheta_p^2.
  * Any output may be NULL.  grad_out = G, DEVICE float64 [n_points][n_sets].  Same basis
- * recomputation and reduction as zp_series_adjoint (one extra Taylor lane).
+ * recomputation and reduction as zp_series_adjoint (one extra Taylor lane; H = C G^T on the
+ * float64-accurate tensor-core GEMM).
  */
 ZP_API zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes,
                                          const double* r, const double* theta, int64_t n_points,
@@ -239,11 +245,26 @@ ZP_API zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double*
                                               double* hess_tt, void* stream);
 
 /*
+ * Hessian-vector product of L = sum_{p,s} F[p,s] G[p,s] in the point coordinates for a
+ * tangent (v_r, v_theta) (DEVICE float64 [n_points] each): with the per-point blocks of
+ * zp_series_point_hessian,
+ *   hv_r[p]     = hess_rr[p] v_r[p] + hess_rt[p] v_theta[p],
+ *   hv_theta[p] = hess_rt[p] v_r[p] + hess_tt[p] v_theta[p]
+ * (the Hessian is block diagonal, so the product is per point), formed inside the same kernel
+ * without storing the blocks.  Either output may be NULL.
+ */
+ZP_API zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, const double* theta,
+                                          int64_t n_points, const double* coeffs, int64_t n_sets,
+                                          const double* grad_out, const double* v_r, const double* v_theta,
+                                          double* hv_r, double* hv_theta, void* stream);
+
+/*
  * Least-squares fit of series coefficients (the "fit" counterpart of zp_series_eval):
  *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
- * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 throughout (basis by
- * the recursion walk, Gram matrix and right-hand side by DGEMM, Cholesky factorisation and
- * solve by the library's own blocked kernels up to 640 modes, by cuSOLVER beyond).
+ * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 results (basis by the
+ * recursion walk, Gram matrix and right-hand side by the float64-accurate tensor-core GEMM of
+ * ZP_PREC_FP64_EMULATED, Cholesky factorisation and solve by the library's own blocked kernels
+ * up to 640 modes, by cuSOLVER potrf/potrs beyond).
  *   weights: DEVICE float64 [n_points] (w_p >= 0) or NULL (all 1).
  *   samples: DEVICE float64 [n_points][n_sets] (Y, row-major).
  *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
@@ -262,8 +283,8 @@ ZP_API zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const 
                                     int64_t n_sets, double ridge, double* coeffs, void* stream);
 /*
  * zp_series_fit_plan with a choice of arithmetic for the Gram matrix Z W Z^T and the
- * right-hand side Z W Y: ZP_PREC_FP64 (cuBLAS DGEMM) or ZP_PREC_FP64_EMULATED (the
- * float64-accurate tensor-core GEMM, error about n_points 2^-54 times the largest magnitudes
+ * right-hand side Z W Y: ZP_PREC_FP64 (the cuBLAS DGEMM baseline) or ZP_PREC_FP64_EMULATED (the
+ * default: the float64-accurate tensor-core GEMM, error about n_points 2^-54 times the largest magnitudes
  * of the rows involved).  The Cholesky factorisation and solve are float64 either way.  Other precisions: ZP_ERR_INVALID_ARG.
  */
 ZP_API zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta,
@@ -340,13 +361,16 @@ ZP_API zp_status zp_batch_tune(zp_batch* batch, int32_t which, zp_precision prec
  * rewrites everything it reads, so nothing needs clearing.  Calls that overlap on the GPU
  * (different streams, or different host threads) race on the array: serialise them, for
  * example by issuing them on one stream.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The tables travel by cudaMemcpyAsync from pageable host
- * memory on `stream`.
+ * device address (cudaGetSymbolAddress, with that device current).  Under CUDA's default lazy
+ * module loading the array's memory is committed when the library's module is first loaded
+ * on a device, which may be that first call: a caller that will later be unable to allocate
+ * should make one small call first (or run with CUDA_MODULE_LOADING=EAGER).  The tables
+ * travel by cudaMemcpyAsync from pageable host memory on `stream`, so the call cannot be
+ * captured in a CUDA graph: on a capturing stream it returns ZP_ERR_INVALID_ARG.
  * Limits: the plan tables, the coefficient tiles (ceil(n_sets/256) * ceil(n_modes/32) * 32 KiB)
  * and one 128-point basis tile (ceil(n_modes/32) * 16 KiB), for either precision, must fit in
- * ZP_STATIC_SCRATCH_BYTES; larger problems are
- * rejected with ZP_ERR_INVALID_ARG before anything is launched.  Points beyond one tile are
+ * ZP_STATIC_SCRATCH_BYTES (n_modes * n_sets is bounded before any size is multiplied); larger
+ * problems are rejected with ZP_ERR_INVALID_ARG before anything is launched.  Points beyond one tile are
  * processed in slabs, so n_points has no limit of its own.
  */
 #define ZP_STATIC_SCRATCH_BYTES (64u << 20)
@@ -354,6 +378,19 @@ ZP_API zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64
                                        const double* r, const double* theta, int64_t n_points,
                                        const double* coeffs, int64_t n_sets, zp_precision prec,
                                        float* out, void* stream);
+
+/*
+ * Float64 issue-rate probe (measurement service; the paper has no counterpart: it states its
+ * hardware's float64 rate, GB300's has to be measured).  Runs one wave of CTAs on the current
+ * device in which every thread issues `iters` rounds of 16 independent dependent chains of one
+ * float64 operation, op = 0 (fused multiply-add), 1 (multiply) or 2 (add), after a short
+ * warm-up launch, and synchronises `stream`.  result[6] (HOST) receives: [0] operations
+ * issued, [1] milliseconds (CUDA events around the launch), [2] operations per second, [3]
+ * lanes per SM per clock (from the SM cycle counter, independent of the clock the GPU ran
+ * at), [4] the SM clock implied by cycles over time (MHz), [5] the SM count.  iters: a
+ * multiple of 4 in 4..2^24.  Allocates a few KB of stream-ordered scratch.
+ */
+ZP_API zp_status zp_probe_fp64(int32_t op, int32_t iters, void* stream, double* result);
 
 /*
  * Reads (and optionally clears) the library's device-side wait-status word on the current

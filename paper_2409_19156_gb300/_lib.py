@@ -46,12 +46,15 @@ SIGNATURES = {
                                                ctypes.c_int64, c_dp, c_dp, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_series_point_hessian_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
                                                     c_dp, c_dp, c_dp, c_dp, c_dp, c_dp, c_dp]),
+    "zp_series_point_hvp_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
+                                                c_dp, c_dp, c_dp, c_dp, c_dp, c_dp]),
     "zp_series_fit": (ctypes.c_int, [c_i32p, c_i32p, ctypes.c_int64, c_dp, c_dp, c_dp, ctypes.c_int64, c_dp,
                                      ctypes.c_int64, ctypes.c_double, c_dp, c_dp]),
     "zp_series_fit_plan": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
                                           ctypes.c_double, c_dp, c_dp]),
     "zp_series_fit_plan_prec": (ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_dp, ctypes.c_int64, c_dp, ctypes.c_int64,
                                                ctypes.c_double, c_dp, ctypes.c_int, c_dp]),
+    "zp_probe_fp64": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, c_dp, ctypes.POINTER(ctypes.c_double)]),
     "zp_device_wait_selftest": (ctypes.c_int, [ctypes.c_int32, c_dp]),
     "zp_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
     "zp_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),

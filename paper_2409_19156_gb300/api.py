@@ -8,6 +8,10 @@ Functions mirror the C ABI (include/zernike_gb300.h):
     series_adjoint(n, m, r, theta, C, G)  -> (grad_C, grad_r, grad_theta)
 `n`, `m` are host integer sequences; r, theta, C, G are CUDA float64 tensors.  Work is
 enqueued on torch's current stream of the tensors' device.
+
+Precisions: "fp64emu" (the default for float64 results: contractions on the library's
+float64-accurate tensor-core GEMM), "fp64" (the plain basis-then-cuBLAS-DGEMM baseline),
+"bf16x3" and "tf32" (split-precision tensor-core contraction, float32 results).
 """
 from __future__ import annotations
 
@@ -113,7 +117,7 @@ def radial_per_mode(plan: Plan, r: torch.Tensor) -> torch.Tensor:
     return out
 
 
-def series_eval(n, m, r, theta, coeffs, prec: str = "fp64", plan: Plan | None = None) -> torch.Tensor:
+def series_eval(n, m, r, theta, coeffs, prec: str = "fp64emu", plan: Plan | None = None) -> torch.Tensor:
     r = _dev_f64(r, "r")
     theta = _dev_f64(theta, "theta")
     coeffs = _dev_f64(coeffs, "coeffs")
@@ -136,9 +140,10 @@ def series_eval(n, m, r, theta, coeffs, prec: str = "fp64", plan: Plan | None = 
 
 
 def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), plan: Plan | None = None,
-                   prec: str = "fp64"):
+                   prec: str = "fp64emu"):
     """(grad_coeffs [J][S], grad_r [P], grad_theta [P]) for upstream grad_out [P][S]; prec
-    "fp64" (DGEMM contractions) or "fp64emu" (float64-accurate tensor-core contractions)."""
+    "fp64emu" (float64-accurate tensor-core contractions, the default) or "fp64" (the DGEMM
+    baseline)."""
     if prec not in ("fp64", "fp64emu"):
         raise ValueError("series_adjoint takes prec 'fp64' or 'fp64emu'")
     r = _dev_f64(r, "r")
@@ -156,7 +161,7 @@ def series_adjoint(n, m, r, theta, coeffs, grad_out, need=(True, True, True), pl
     gt = torch.empty(P, dtype=torch.float64, device=dev) if need[2] else None
     st = _stream(dev)
     with torch.cuda.device(dev):
-        if plan is None and prec == "fp64":
+        if plan is None and prec == "fp64emu":
             _lib.call("zp_series_adjoint", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(), P,
                       coeffs.data_ptr(), S, grad_out.data_ptr(), _lib.ptr(gC), _lib.ptr(gr), _lib.ptr(gt), st)
         else:
@@ -190,18 +195,34 @@ def series_point_hessian(n, m, r, theta, coeffs, grad_out, plan: Plan | None = N
     return tuple(outs)
 
 
-def point_hvp(hess, v_r, v_theta):
-    """Hessian-vector product with the block-diagonal point Hessian from series_point_hessian:
-    returns (Hv)_r, (Hv)_theta for tangent vectors v_r, v_theta over the points."""
-    _, _, hrr, hrt, htt = hess
-    return hrr * v_r + hrt * v_theta, hrt * v_r + htt * v_theta
+def series_point_hvp(n, m, r, theta, coeffs, grad_out, v_r, v_theta, plan: Plan | None = None):
+    """Hessian-vector product of L = <grad_out, F> in the point coordinates for the tangent
+    (v_r, v_theta): returns ((Hv)_r, (Hv)_theta), each [P] float64, formed in the library's
+    point kernel (the Hessian is block diagonal, one 2x2 block per point)."""
+    r = _dev_f64(r, "r")
+    theta = _dev_f64(theta, "theta")
+    coeffs = _dev_f64(coeffs, "coeffs")
+    G = _dev_f64(grad_out, "grad_out")
+    v_r = _dev_f64(v_r, "v_r")
+    v_theta = _dev_f64(v_theta, "v_theta")
+    P, S = r.numel(), coeffs.shape[1]
+    if G.shape != (P, S) or v_r.numel() != P or v_theta.numel() != P:
+        raise ValueError("grad_out must be [n_points, n_sets] and v_r, v_theta [n_points]")
+    pl = plan if plan is not None else Plan(n, m, device=r.device)
+    hv_r = torch.empty(P, dtype=torch.float64, device=r.device)
+    hv_t = torch.empty(P, dtype=torch.float64, device=r.device)
+    with torch.cuda.device(r.device):
+        _lib.call("zp_series_point_hvp_plan", pl.handle, r.data_ptr(), theta.data_ptr(), P, coeffs.data_ptr(), S,
+                  G.data_ptr(), v_r.data_ptr(), v_theta.data_ptr(), hv_r.data_ptr(), hv_t.data_ptr(),
+                  _stream(r.device))
+    return hv_r, hv_t
 
 
 def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: Plan | None = None,
-               prec: str = "fp64"):
+               prec: str = "fp64emu"):
     """Least-squares coefficients C [J][S] with sum_j Z_j(p) C[j, s] ~ samples[p, s] (weighted,
-    optional ridge); float64 throughout, the Gram matrix and right-hand side by DGEMM ("fp64")
-    or by the float64-accurate tensor-core GEMM ("fp64emu")."""
+    optional ridge); float64 results, the Gram matrix and right-hand side by the float64-accurate
+    tensor-core GEMM ("fp64emu", the default) or by the DGEMM baseline ("fp64")."""
     if prec not in ("fp64", "fp64emu"):
         raise ValueError("series_fit takes prec 'fp64' or 'fp64emu'")
     r = _dev_f64(r, "r")
@@ -216,7 +237,7 @@ def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: 
     out = torch.empty((J, S), dtype=torch.float64, device=r.device)
     st = _stream(r.device)
     with torch.cuda.device(r.device):
-        if plan is None and prec == "fp64":
+        if plan is None and prec == "fp64emu":
             _lib.call("zp_series_fit", _lib.i32_ptr(nn), _lib.i32_ptr(mm), J, r.data_ptr(), theta.data_ptr(),
                       _lib.ptr(w), P, Y.data_ptr(), S, float(ridge), out.data_ptr(), st)
         else:
@@ -228,12 +249,12 @@ def series_fit(n, m, r, theta, samples, weights=None, ridge: float = 0.0, plan: 
 
 class ZernikeSeries(torch.autograd.Function):
     """F = Z(r, theta) C with gradients for C, r and theta from the library's adjoint
-    (basis recomputed in the backward pass, never stored).  float64 throughout; prec "fp64"
-    (DGEMM contractions) or "fp64emu" (float64-accurate tensor-core contractions) for both
-    passes."""
+    (basis recomputed in the backward pass, never stored).  float64 results; prec "fp64emu"
+    (float64-accurate tensor-core contractions, the default) or "fp64" (the DGEMM baseline)
+    for both passes."""
 
     @staticmethod
-    def forward(ctx, r, theta, coeffs, plan: Plan, prec: str = "fp64"):
+    def forward(ctx, r, theta, coeffs, plan: Plan, prec: str = "fp64emu"):
         if prec not in ("fp64", "fp64emu"):
             raise ValueError("zernike_series takes prec 'fp64' or 'fp64emu'")
         ctx.plan = plan
@@ -252,7 +273,7 @@ class ZernikeSeries(torch.autograd.Function):
         return gr, gt, gC, None, None
 
 
-def zernike_series(r, theta, coeffs, plan: Plan, prec: str = "fp64") -> torch.Tensor:
+def zernike_series(r, theta, coeffs, plan: Plan, prec: str = "fp64emu") -> torch.Tensor:
     """Differentiable float64 series F[p, s] = sum_j Z_j(r_p, theta_p) coeffs[j, s]."""
     return ZernikeSeries.apply(r, theta, coeffs, plan, prec)
 

@@ -7,8 +7,9 @@
 // weights are given, the Gram matrix and the right-hand side by cuBLAS DGEMM (or by the
 // float64-accurate tensor-core GEMM of zp_mma.cu for ZP_PREC_FP64_EMULATED), the
 // ridge added on the diagonal, a Cholesky factorisation and solve (the library's own blocked
-// kernels up to 640 modes, cuSOLVER beyond), and a DGEAM transpose into the caller's row-major
-// [J][S] output.  The call synchronises its stream at the end to read the factorisation status.
+// kernels up to 640 modes, whose solve stores straight into the caller's row-major [J][S]
+// output; cuSOLVER beyond, followed by the library's transpose kernel).  The call synchronises
+// its stream at the end to read the factorisation status.
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
@@ -207,11 +208,12 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* A, int J, int 
   }
 }
 
-// Solves L L^T X = B in place for kSolveCols columns of B per CTA (B column-major J x S): the
-// forward substitution L y = b walks the columns of L, the backward one L^T x = y its rows; L
-// is staged in shared memory 32 columns (rows) at a time.  Shared memory: (32 + 2 kSolveCols +
-// 1) J doubles.
-__global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ L, int J, double* B, int S) {
+// Solves L L^T X = B for kSolveCols columns of B per CTA (B column-major J x S) and stores X
+// row-major [J][S] (the caller's coefficient layout): the forward substitution L y = b walks
+// the columns of L, the backward one L^T x = y its rows; L is staged in shared memory 32
+// columns (rows) at a time.  Shared memory: (32 + 2 kSolveCols + 1) J doubles.
+__global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ L, int J,
+                                                         const double* __restrict__ B, int S, double* __restrict__ X) {
   extern __shared__ double sm[];
   double* Lb = sm;                       // [32][J]
   double* y = Lb + (size_t)kNb * J;      // [kSolveCols][J] working right-hand sides
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
 #pragma unroll
       for (int k = 0; k < kSolveCols; ++k) xi[k] = z[(size_t)k * J + i] * rdg[i];
       if (tid == 0) {
-        for (int k = 0; k < ns; ++k) B[(size_t)i + (size_t)(s0 + k) * J] = xi[k];
+        for (int k = 0; k < ns; ++k) X[(size_t)i * S + (size_t)(s0 + k)] = xi[k];
       }
       for (int t = tid; t < i; t += blockDim.x) {
         const double l = Lb[(size_t)u * J + t];
@@ -295,8 +297,9 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
 }
 
 // Factors the J x J normal matrix (J <= kCholMaxJ) in place and solves for the J x S
-// right-hand sides in place; info[0] as in chol_panel_kernel (zeroed here).
-zp_status small_cholesky_solve(double* A, int J, double* B, int S, int* info, cudaStream_t stream) {
+// right-hand sides B (column-major), storing the solution row-major [J][S] in X; info[0] as in
+// chol_panel_kernel (zeroed here).
+zp_status small_cholesky_solve(double* A, int J, const double* B, int S, double* X, int* info, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), stream);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
   for (int k0 = 0; k0 < J; k0 += kNb) {
@@ -317,9 +320,25 @@ zp_status small_cholesky_solve(double* A, int J, double* B, int S, int* info, cu
     const cudaError_t err = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *x);
     return err == cudaSuccess ? ZP_OK : cuda_error(err, "cudaFuncSetAttribute(chol_solve_kernel)");
   }));
-  chol_solve_kernel<<<(S + kSolveCols - 1) / kSolveCols, 256, smem, stream>>>(A, J, B, S);
+  chol_solve_kernel<<<(S + kSolveCols - 1) / kSolveCols, 256, smem, stream>>>(A, J, B, S, X);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "chol_solve_kernel launch");
   return ZP_OK;
+}
+
+// out row-major [J][S] from in column-major J x S (32 x 32 tiles through shared memory).
+__global__ void __launch_bounds__(256) transpose_kernel(const double* __restrict__ in, int64_t J, int64_t S,
+                                                        double* __restrict__ out) {
+  __shared__ double t[32][33];
+  const int64_t s0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int jj = e % 32, ss = e / 32;
+    if (j0 + jj < J && s0 + ss < S) t[ss][jj] = in[(j0 + jj) + (s0 + ss) * J];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int ss = e % 32, jj = e / 32;
+    if (j0 + jj < J && s0 + ss < S) out[(j0 + jj) * S + (s0 + ss)] = t[ss][jj];
+  }
 }
 
 struct SolverHandles {
@@ -399,7 +418,8 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
   }
   ScratchBuffer work;
   if (J <= kCholMaxJ && S <= (int64_t)INT32_MAX) {
-    ZP_TRY(small_cholesky_solve((double*)gram.ptr, (int)J, (double*)rhs.ptr, (int)S, (int*)info.ptr, stream));
+    ZP_TRY(small_cholesky_solve((double*)gram.ptr, (int)J, (const double*)rhs.ptr, (int)S, coeffs, (int*)info.ptr,
+                                stream));
     pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
   } else {
@@ -416,11 +436,11 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
     if (cusolverDnDpotrs(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (int)S, (double*)gram.ptr, (int)J, (double*)rhs.ptr,
                          (int)J, (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
       return set_error(ZP_ERR_CUDA, "cusolverDnDpotrs failed");
+    // coeffs row-major [J][S] from the column-major J x S solution.
+    transpose_kernel<<<dim3((unsigned)((S + 31) / 32), (unsigned)((J + 31) / 32)), 256, 0, stream>>>(
+        (const double*)rhs.ptr, J, S, coeffs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "transpose_kernel launch");
   }
-  // coeffs row-major [J][S] = column-major S x J = transpose of the J x S solution.
-  if (cublasDgeam(blas, CUBLAS_OP_T, CUBLAS_OP_N, (int)S, (int)J, &one, (double*)rhs.ptr, (int)J, &zero, coeffs,
-                  (int)S, coeffs, (int)S) != CUBLAS_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cublasDgeam failed");
   double h_info[4] = {0, 0, 0, 0};
   if ((e = cudaMemcpyAsync(h_info, info.ptr, sizeof(h_info), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(stream)) != cudaSuccess)
@@ -446,8 +466,8 @@ extern "C" {
 zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta, const double* weights,
                              int64_t n_points, const double* samples, int64_t n_sets, double ridge, double* coeffs,
                              void* stream) {
-  return zp_series_fit_plan_prec(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, ZP_PREC_FP64,
-                                 stream);
+  return zp_series_fit_plan_prec(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs,
+                                 ZP_PREC_FP64_EMULATED, stream);
 }
 
 zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta, const double* weights,

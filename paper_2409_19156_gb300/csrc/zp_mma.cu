@@ -30,6 +30,7 @@
 #include "zp_device.cuh"
 #include "zp_api_common.h"
 #include "zp_ptx.cuh"
+#include "zp_emu_device.cuh"
 #include "zp_emu_shape.h"
 #include "zp_series_internal.h"
 
@@ -403,12 +404,9 @@ struct GemmArgs {
   int64_t t_batch_stride = 0;
 };
 
-// CL = 1: one CTA per tile.  CL = 2: CTA pairs (a cluster of two) work on two point tiles of
-// the same coefficient tile; each CTA loads its own A chunk and one half of the B chunk, which
-// a cluster-multicast bulk copy writes into both CTAs' shared memory, so B crosses L2 once per
-// pair.  A stage is refilled only after both CTAs' MMAs have released it (the MMA commit
-// arrives on the "empty" barrier of both CTAs).
-template <int KIND, int CL>
+// One CTA per output tile at a time (persistent over tiles); every operand chunk is brought
+// from global memory into this CTA's own shared memory by a plain bulk copy.
+template <int KIND>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a) {
   using C = Cfg<KIND>;
   constexpr bool TF32 = KIND == KIND_TF32;
@@ -422,19 +420,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t rank = CL > 1 ? ptx::cluster_ctarank() : 0u;
-  const int64_t cid = blockIdx.x / CL, nclusters = gridDim.x / CL;
-  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
-  // Cluster geometry: CL point tiles x one set tile; this CTA holds point tile mi of the group.
-  constexpr int CM = CL, CN = 1;
-  const uint32_t mi = rank, ni = 0u;
-  // CTAs whose bulk copies write into this CTA's stages: each of their MMA commits frees a stage.
-  constexpr uint32_t kWriters = (uint32_t)CL;
-  const uint16_t commit_mask = (uint16_t)0x3;
+  const int64_t cid = blockIdx.x, nctas = gridDim.x;
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::STAGES; ++i) {
       ptx::mbar_init(&full[i], 1);
-      ptx::mbar_init(&empty[i], kWriters);
+      ptx::mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tmem_full[i], 1);
@@ -449,15 +439,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if constexpr (CL > 1) ptx::cluster_sync();  // peers' barriers exist before any multicast
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
 
-  // Tile t of this cluster: k batch t / per_batch, then point-tile group (CM point tiles) and
-  // set-tile group (CN set tiles), set-tile group fastest.
-  const int64_t groups = (a.m_tiles + CM - 1) / CM;
-  const int64_t groups_n = (a.n_tiles + CN - 1) / CN;
-  const int64_t per_batch = groups * groups_n;
+  // Tile t: k batch t / per_batch, then point tile and set tile, set tile fastest.
+  const int64_t groups_n = a.n_tiles;
+  const int64_t per_batch = a.m_tiles * groups_n;
   const int64_t total = per_batch * a.k_batches;
   const int kcb = a.kc_per_batch > 0 ? a.kc_per_batch : a.KC;
   // K chunks [kc0, kc0 + nkc) of tile t.
@@ -475,18 +462,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters) {
+      for (int64_t t = cid; t < total && !*abort_flag; t += nctas) {
         const int64_t tm = t % per_batch;
-        const int64_t mt = (tm / groups_n) * CM + mi;
-        const int nt = (int)((tm % groups_n) * CN + ni);
+        const int64_t mt = tm / groups_n;
+        const int nt = (int)(tm % groups_n);
         int kc0, nkc;
         k_range(t, kc0, nkc);
-        // A group's tiles past the slab end (or the last set tile) reuse the last valid tile's
-        // data (their outputs are never stored); they still take part in the shared loads.
-        const int64_t mt_src = mt < a.m_tiles ? mt : a.m_tiles - 1;
-        const int nt_src = nt < a.n_tiles ? nt : a.n_tiles - 1;
-        const uint8_t* gA0 = a.A + (size_t)mt_src * a.KC * C::A_CHUNK;
-        const uint8_t* gB0 = a.B + (size_t)nt_src * a.KC * C::B_CHUNK;
+        const uint8_t* gA0 = a.A + (size_t)mt * a.KC * C::A_CHUNK;
+        const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
         for (int kk = 0; kk < a.npairs * nkc; ++kk) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
@@ -497,15 +480,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride;
           uint8_t* sA = smem + stage * C::STAGE;
           ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
-          if constexpr (CL == 1) {
-            ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
-            ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
-          } else {
-            constexpr uint32_t HALF = C::B_CHUNK / 2;
-            ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
-            ptx::bulk_g2s_multicast(sA + C::A_CHUNK + rank * HALF, gB + (size_t)kc * C::B_CHUNK + rank * HALF, HALF,
-                                    &full[stage], (uint16_t)0x3);
-          }
+          ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
+          ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -519,7 +495,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       int stage = 0;
       uint32_t phase = 0;
       int64_t local = 0;
-      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters, ++local) {
+      for (int64_t t = cid; t < total && !*abort_flag; t += nctas, ++local) {
         const uint32_t acc = (uint32_t)(local & 1);
         const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
         if (!ptx::mbar_wait(&tmem_empty[acc], acc_phase ^ 1u, abort_flag)) {
@@ -560,11 +536,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
               ptx::mma_bf16(d_tmem, al, bh, idesc, 1u);
             }
           }
-          if constexpr (CL == 1) {
-            ptx::mma_commit(&empty[stage]);
-          } else {
-            ptx::mma_commit_multicast(&empty[stage], commit_mask);
-          }
+          ptx::mma_commit(&empty[stage]);
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -579,7 +551,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     const uint32_t q = (uint32_t)(warp & 3);
     const uint32_t row = q * 32 + lane;
     int64_t local = 0;
-    for (int64_t t = cid; t < total; t += nclusters, ++local) {
+    for (int64_t t = cid; t < total; t += nctas, ++local) {
       const uint32_t acc = (uint32_t)(local & 1);
       const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
       // One lane per warp polls the barrier; the shuffle hands its answer to the warp.
@@ -591,10 +563,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       }
       ptx::tc_fence_after();
       const int64_t tm = t % per_batch;
-      const int64_t mt_local = (tm / groups_n) * CM + mi;
-      const int nt = (int)((tm % groups_n) * CN + ni);
-      const bool valid_tile = mt_local < a.m_tiles && nt < a.n_tiles;
-      const int64_t mt = a.mt_base + mt_local;
+      const int64_t mt = a.mt_base + tm / groups_n;
+      const int nt = (int)(tm % groups_n);
       const int64_t p = mt * BM + row;
       const int64_t col0 = (int64_t)nt * BN;
       float* frow = a.F + (t / per_batch) * a.t_batch_stride + p * a.S;
@@ -609,7 +579,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
         }
-        if (valid_tile && p < a.P) {
+        if (p < a.P) {
           const int64_t cbase = col0 + c0;
           if (vec && cbase + 32 <= a.S) {
             float4* dst = reinterpret_cast<float4*>(frow + cbase);
@@ -630,8 +600,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
   }
   ptx::tc_fence_before();
   __syncthreads();
-  // No CTA of a cluster leaves while a peer may still multicast into it or arrive on its barriers.
-  if constexpr (CL > 1) ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, 512);
@@ -676,39 +644,11 @@ struct PhaseTimer {
   }
 };
 
-// Co-scheduling of the GEMM's CTA pairs (point-tile pairs sharing B): how many fit on the GPU
-// at once (0: pairs cannot run).  (2 x 2 clusters sharing A as well were built and measured
-// 2-3 % slower on GB300, so the kernel keeps pairs.)
+// Launch geometry of the persistent GEMM: one CTA per SM (the ring fills most of the
+// shared memory).
 struct GemmShape {
-  int sms = 0, pairs = 0;
+  int sms = 0;
 };
-
-template <int KIND, int CL>
-int max_active_clusters(int sms) {
-  using C = Cfg<KIND>;
-  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  int n = 0;
-  cudaLaunchConfig_t q = {};
-  q.gridDim = dim3(CL * (unsigned)sms);
-  q.blockDim = dim3(kGemmThreads);
-  q.dynamicSmemBytes = C::SMEM;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  q.attrs = at;
-  q.numAttrs = 1;
-  if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<KIND, CL>, &q) != cudaSuccess) {
-    cudaGetLastError();
-    n = 0;
-  }
-  return n;
-}
 
 template <int KIND>
 zp_status gemm_shape(GemmShape* g) {
@@ -718,50 +658,23 @@ zp_status gemm_shape(GemmShape* g) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+    if (cudaFuncSetAttribute(split_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
         cudaSuccess) {
       cudaGetLastError();
       return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
     }
-    x->pairs = max_active_clusters<KIND, 2>(x->sms);
-    if (x->pairs < 0) return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
     return ZP_OK;
   });
 }
 
-template <int KIND, int CL>
-cudaError_t launch_clustered(const GemmArgs& ga, unsigned clusters, cudaStream_t stream) {
-  using C = Cfg<KIND>;
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(CL * clusters);
-  lc.blockDim = dim3(kGemmThreads);
-  lc.dynamicSmemBytes = C::SMEM;
-  lc.stream = stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  lc.attrs = at;
-  lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, CL>, ga);
-}
-
-// Persistent launch over `tiles` point tiles x NT set tiles (x K batches): CTA pairs when they
-// can run and there are two point tiles, else single CTAs; at most as many as are co-resident.
+// Persistent launch over `tiles` point tiles x NT set tiles (x K batches), at most one CTA per SM.
 template <int KIND>
 zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, const GemmShape& g, cudaStream_t stream) {
   using C = Cfg<KIND>;
   const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
-  cudaError_t e;
-  if (g.pairs > 0 && tiles >= 2) {
-    const int64_t groups = ((tiles + 1) / 2) * NT * kb;
-    e = launch_clustered<KIND, 2>(ga, (unsigned)std::min<int64_t>(groups, g.pairs), stream);
-  } else {
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, g.sms);
-    split_gemm_kernel<KIND, 1><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
-    e = cudaGetLastError();
-  }
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, g.sms);
+  split_gemm_kernel<KIND><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "split_gemm_kernel launch");
 }
 
@@ -868,20 +781,6 @@ zp_status run_split(const zp_plan* plan, const double* r, const double* theta, i
 
 static_assert(Cfg<KIND_SLICE>::BK == kSliceBK, "slice chunk width shared with zp_emu_shape.h");
 
-// Row exponent marking a row that holds an infinity or a NaN: its slices are zero and every
-// output that involves it is NaN.
-constexpr int kNonFiniteRow = 1 << 20;
-
-// Exponent e with 2^e > |x| for the largest |x| given as its float64 bits with the sign
-// cleared (positive doubles order like their bit patterns, infinities and NaNs above all
-// finite values); 0 for zero, -1022 for subnormals, kNonFiniteRow for a non-finite row.
-__device__ __forceinline__ int scale_exponent(unsigned long long max_abs_bits) {
-  if (max_abs_bits == 0) return 0;
-  const int ef = (int)(max_abs_bits >> 52);
-  if (ef == 0x7ff) return kNonFiniteRow;
-  return ef ? ef - 1022 : -1022;
-}
-
 // A float64 operand read with strides: X(row, k) = x[row * sr + k * sk].
 struct Operand {
   const double* x;
@@ -952,29 +851,6 @@ zp_status scale_rows(Operand X, int64_t rows, int64_t K, unsigned long long* bit
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "row scale launch");
 }
 
-// X = round-half-even(z * 2^shift) for shift = beta * s - e, i.e. x = z 2^(-e) in [-1, 1] as a
-// fixed-point integer with beta * s fraction bits (|X| <= 2^(beta s) <= 2^56), from z's bits.
-__device__ __forceinline__ long long to_fixed(double z, int shift) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(z);
-  const int ef = (int)((b >> 52) & 0x7ff);
-  const unsigned long long frac = b & 0xfffffffffffffull;
-  const unsigned long long m = ef ? (frac | (1ull << 52)) : frac;  // |z| = m 2^(max(ef,1) - 1075)
-  const int sh = (ef ? ef : 1) - 1075 + shift;
-  unsigned long long mag;
-  if (sh >= 0) {
-    mag = m << sh;  // |z| < 2^e keeps this below 2^(beta s)
-  } else if (sh <= -64) {
-    mag = 0;  // m 2^sh < 2^-11
-  } else {
-    const int r = -sh;
-    mag = m >> r;
-    const unsigned long long rem = m & ((1ull << r) - 1);
-    const unsigned long long half = 1ull << (r - 1);
-    if (rem > half || (rem == half && (mag & 1))) ++mag;
-  }
-  return (b >> 63) ? -(long long)mag : (long long)mag;
-}
-
 // Cuts 8 fixed-point values X[0..7] (beta * s fraction bits) into s balanced base-2^beta digits
 // and writes slice t's 16-byte unit of bf16 integers at `dst + t * slice_stride`.  Digits are
 // taken from the least significant end: a = X mod 2^beta moved into [-2^(beta-1), 2^(beta-1)),
@@ -1035,45 +911,6 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     uint8_t* d = dst + ((size_t)tile * KC + kc) * (ROWS * ROW) + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
     cut_slices(x, sp.beta, sp.s, d, slice_stride);
   }
-}
-
-// Correctly rounded float64 of N * 2^e2 (round half to even), N a signed 128-bit integer.
-// The mantissa and exponent are assembled on the integer pipe; results outside the normal
-// range go through ldexp.
-__device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
-  if (N == 0) return 0.0;
-  const bool neg = N < 0;
-  const unsigned __int128 M = neg ? (unsigned __int128)0 - (unsigned __int128)N : (unsigned __int128)N;
-  const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;
-  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-  unsigned long long mant;
-  if (nbits <= 53) {
-    mant = lo << (53 - nbits);
-  } else {
-    const int r = nbits - 53;
-    const unsigned __int128 q = M >> r;
-    mant = (unsigned long long)q;
-    const unsigned __int128 rem = M - (q << r);
-    const unsigned __int128 half = (unsigned __int128)1 << (r - 1);
-    if (rem > half || (rem == half && (mant & 1))) ++mant;
-  }
-  int ex = nbits - 1 + e2;  // N 2^e2 = (mant / 2^52) 2^ex
-  if (mant == (1ull << 53)) {
-    mant >>= 1;
-    ++ex;
-  }
-  if (ex < -1022 || ex > 1023) {
-    const double v = ldexp((double)mant, ex - 52);
-    return neg ? -v : v;
-  }
-  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
-                                  (mant & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
-}
-
-// Horner step acc * 2^beta + t in two's-complement int64 (the true value fits; see `split`).
-__device__ __forceinline__ long long horner(long long acc, int beta, long long t) {
-  return (long long)(((unsigned long long)acc << beta) + (unsigned long long)t);
 }
 
 struct RecombineArgs {

@@ -1,8 +1,9 @@
-// Series of Zernike functions and its adjoint, float64 ("plain basis-then-GEMM" form).
+// Series of Zernike functions and its adjoint, float64.
 //
 //   F = Z^T C                     (Z: basis [J][P] written by the walk kernel to scratch)
-//   grad_C = Z G                  (cuBLAS DGEMM)
-//   H = C G^T  -> [J][P]          (cuBLAS DGEMM, point-fastest so the next kernel coalesces)
+//   grad_C = Z G                  (float64-accurate tensor-core GEMM of zp_mma.cu by default;
+//                                  cuBLAS DGEMM for ZP_PREC_FP64, the plain baseline form)
+//   H = C G^T  -> [J][P]          (the same, point-fastest so the next kernel coalesces)
 //   grad_r[p]     = sum_j dZ_j/drho(p)   H[j][p]
 //   grad_theta[p] = sum_j dZ_j/dtheta(p) H[j][p]
 // The last two are one kernel that regenerates the basis derivatives in registers (the
@@ -29,15 +30,17 @@ constexpr int kRedThreads = 128;
 // accumulates, with H[j][p] = sum_s C[j, s] G[p, s],
 //   grad_r  = sum_j dZ_j/drho H,        grad_theta = sum_j dZ_j/dtheta H,
 //   and with HESS the point's 2x2 Hessian block of L = <G, F>:
-//   hess_rr = sum_j d2Z_j/drho2 H,  hess_rt = sum_j d2Z_j/drho dtheta H,  hess_tt = sum_j d2Z_j/dtheta2 H.
+//   hess_rr = sum_j d2Z_j/drho2 H,  hess_rt = sum_j d2Z_j/drho dtheta H,  hess_tt = sum_j d2Z_j/dtheta2 H,
+//   and, given a tangent (v_r, v_theta), the Hessian-vector product
+//   hv_r = hess_rr v_r + hess_rt v_theta,  hv_theta = hess_rt v_r + hess_tt v_theta.
 // (The Hessian of L in the point coordinates is block diagonal: r_p and theta_p only enter row p.)
+
 template <bool HESS>
 __global__ void __launch_bounds__(kRedThreads)
 adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* __restrict__ table,
                      const int32_t* __restrict__ slot_ptr, const int32_t* __restrict__ slot_idx,
                      const double* __restrict__ r, const double* __restrict__ theta, int64_t P,
-                     const double* __restrict__ H, double* grad_r, double* grad_theta, double* hess_rr,
-                     double* hess_rt, double* hess_tt) {
+                     const double* __restrict__ H, double* grad_r, double* grad_theta, HessOut ho) {
   const int64_t p = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
   if (p >= P) return;
   const double rho = r[p], u = rho * rho, th = theta[p];
@@ -123,9 +126,14 @@ adjoint_point_kernel(const Column* __restrict__ cols, int n_cols, const double* 
   if (grad_r) grad_r[p] = acc_r;
   if (grad_theta) grad_theta[p] = acc_t;
   if constexpr (HESS) {
-    if (hess_rr) hess_rr[p] = acc_rr;
-    if (hess_rt) hess_rt[p] = acc_rt;
-    if (hess_tt) hess_tt[p] = acc_tt;
+    if (ho.rr) ho.rr[p] = acc_rr;
+    if (ho.rt) ho.rt[p] = acc_rt;
+    if (ho.tt) ho.tt[p] = acc_tt;
+    if (ho.v_r) {
+      const double vr = ho.v_r[p], vt = ho.v_theta[p];
+      if (ho.hv_r) ho.hv_r[p] = fma(acc_rr, vr, acc_rt * vt);
+      if (ho.hv_theta) ho.hv_theta[p] = fma(acc_rt, vr, acc_tt * vt);
+    }
   }
 }
 
@@ -259,10 +267,9 @@ zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* t
 
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs, double* grad_r,
-                              double* grad_theta, cudaStream_t stream, double* hess_rr, double* hess_rt,
-                              double* hess_tt, bool emulated) {
+                              double* grad_theta, cudaStream_t stream, const HessOut& ho, bool emulated) {
   const int64_t J = plan->n_modes;
-  const bool need_h = grad_r || grad_theta || hess_rr || hess_rt || hess_tt;
+  const bool need_h = grad_r || grad_theta || ho.any();
   ScratchBuffer z, hbuf;
   CublasLock cl;
   if (grad_coeffs) {
@@ -290,14 +297,14 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
       ZP_TRY(dgemm(cl.h, true, false, P, J, S, G, S, coeffs, S, (double*)hbuf.ptr, P));
     }
     const int64_t blocks = (P + kRedThreads - 1) / kRedThreads;
-    if (hess_rr || hess_rt || hess_tt)
+    if (ho.any())
       adjoint_point_kernel<true><<<(unsigned)blocks, kRedThreads, 0, stream>>>(
           plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
-          (const double*)hbuf.ptr, grad_r, grad_theta, hess_rr, hess_rt, hess_tt);
+          (const double*)hbuf.ptr, grad_r, grad_theta, ho);
     else
       adjoint_point_kernel<false><<<(unsigned)blocks, kRedThreads, 0, stream>>>(
           plan->dev.cols, (int)plan->cols.size(), plan->dev.table, plan->dev.slot_ptr, plan->dev.slot_idx, r, theta, P,
-          (const double*)hbuf.ptr, grad_r, grad_theta, nullptr, nullptr, nullptr);
+          (const double*)hbuf.ptr, grad_r, grad_theta, HessOut());
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "adjoint_point_kernel launch");
   }
@@ -372,7 +379,7 @@ zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const dou
                                  const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_coeffs,
                                  double* grad_r, double* grad_theta, void* stream) {
   return zp_series_adjoint_plan_prec(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r,
-                                     grad_theta, ZP_PREC_FP64, stream);
+                                     grad_theta, ZP_PREC_FP64_EMULATED, stream);
 }
 
 zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
@@ -397,8 +404,8 @@ zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, cons
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
   }
   ZP_TRY(check_device_array(grad_out, "grad_out", 8));
-  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st, nullptr,
-                             nullptr, nullptr, prec == ZP_PREC_FP64_EMULATED);
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, grad_coeffs, grad_r, grad_theta, st, HessOut(),
+                             prec == ZP_PREC_FP64_EMULATED);
 }
 
 zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
@@ -423,8 +430,40 @@ zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, con
     return ZP_OK;
   }
   ZP_TRY(check_device_array(grad_out, "grad_out", 8));
-  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, nullptr, grad_r, grad_theta, st, hess_rr, hess_rt,
-                             hess_tt);
+  HessOut ho;
+  ho.rr = hess_rr;
+  ho.rt = hess_rt;
+  ho.tt = hess_tt;
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, nullptr, grad_r, grad_theta, st, ho,
+                             /*emulated=*/true);
+}
+
+zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                   const double* coeffs, int64_t n_sets, const double* grad_out, const double* v_r,
+                                   const double* v_theta, double* hv_r, double* hv_theta, void* stream) {
+  clear_error();
+  ZP_TRY(series_args(plan, r, theta, n_points, coeffs, n_sets));
+  if (hv_r) ZP_TRY(check_device_array(hv_r, "hv_r", 8));
+  if (hv_theta) ZP_TRY(check_device_array(hv_theta, "hv_theta", 8));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t J = plan->n_modes, P = n_points, S = n_sets;
+  if (P == 0 || (!hv_r && !hv_theta)) return ZP_OK;
+  if (J == 0 || S == 0) {
+    cudaError_t e = cudaSuccess;
+    if (hv_r) e = cudaMemsetAsync(hv_r, 0, (size_t)P * 8, st);
+    if (e == cudaSuccess && hv_theta) e = cudaMemsetAsync(hv_theta, 0, (size_t)P * 8, st);
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
+  }
+  ZP_TRY(check_device_array(grad_out, "grad_out", 8));
+  ZP_TRY(check_device_array(v_r, "v_r", 8));
+  ZP_TRY(check_device_array(v_theta, "v_theta", 8));
+  HessOut ho;
+  ho.v_r = v_r;
+  ho.v_theta = v_theta;
+  ho.hv_r = hv_r;
+  ho.hv_theta = hv_theta;
+  return series_adjoint_fp64(plan, r, theta, P, coeffs, S, grad_out, nullptr, nullptr, nullptr, st, ho,
+                             /*emulated=*/true);
 }
 
 zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,

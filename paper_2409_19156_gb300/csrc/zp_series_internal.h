@@ -48,12 +48,24 @@ struct ScratchBuffer {
 
 zp_status series_eval_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                            const double* coeffs, int64_t S, double* out, cudaStream_t stream);
-// hess_*: NULL, or [P] outputs of the per-point Hessian blocks of L = <G, F>.
+// Optional per-point second-order outputs of the adjoint for L = <G, F>: the 2x2 Hessian
+// blocks (rr, rt, tt: NULL or [P]) and, for a tangent (v_r, v_theta) ([P] each, both or
+// neither), the Hessian-vector product (hv_r, hv_theta: NULL or [P]).
+struct HessOut {
+  double* rr = nullptr;
+  double* rt = nullptr;
+  double* tt = nullptr;
+  const double* v_r = nullptr;
+  const double* v_theta = nullptr;
+  double* hv_r = nullptr;
+  double* hv_theta = nullptr;
+  bool any() const { return rr || rt || tt || hv_r || hv_theta; }
+};
+// emulated: the contractions on the float64-accurate tensor-core GEMM (else cuBLAS DGEMM).
 zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs,
-                              double* grad_r, double* grad_theta, cudaStream_t stream,
-                              double* hess_rr = nullptr, double* hess_rt = nullptr, double* hess_tt = nullptr,
-                              bool emulated = false);
+                              double* grad_r, double* grad_theta, cudaStream_t stream, const HessOut& ho,
+                              bool emulated);
 // Split-precision tensor-core series (BF16x3 or TF32, float32 output).
 // Float64-accurate series by error-free slicing on the tensor cores (float64 output).
 zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const double* theta, int64_t P,

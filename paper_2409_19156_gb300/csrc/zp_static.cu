@@ -10,6 +10,11 @@
 // Host code must not use the array's name as a device address (in host code it names a
 // host-side stand-in).  The device address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, and passed to the kernels.
+//
+// Under CUDA's default lazy module loading the array's device memory is committed when the
+// library's module is first loaded on a device, which can be this entry point's first call
+// there: a caller that must not allocate at all later should make one small call (or set
+// CUDA_MODULE_LOADING=EAGER) while allocation is still allowed.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -59,6 +64,25 @@ extern "C" zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, i
   if (prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32)
     return set_error(ZP_ERR_INVALID_ARG, "zp_series_eval_static supports ZP_PREC_BF16X3 and ZP_PREC_TF32 only");
   if (n_points < 0 || n_sets < 0) return set_error(ZP_ERR_INVALID_ARG, "negative size");
+  // Size bounds before any product of sizes is formed: the array bounds the coefficient tiles
+  // (at least 64 bytes per mode and set) and so n_modes * n_sets; the output memset and the
+  // kernels' int64 index arithmetic bound n_points * n_sets.
+  if (n_modes > (int64_t)(ZP_STATIC_SCRATCH_BYTES / 64) || n_sets > (int64_t)(ZP_STATIC_SCRATCH_BYTES / 64) ||
+      (n_modes > 0 && n_sets > (int64_t)(ZP_STATIC_SCRATCH_BYTES / 64) / n_modes))
+    return set_error(ZP_ERR_INVALID_ARG, "n_modes * n_sets exceeds what ZP_STATIC_SCRATCH_BYTES can hold; use "
+                                         "zp_series_eval instead");
+  if (n_sets > 0 && n_points > (int64_t)(INT64_MAX / 16) / n_sets)
+    return set_error(ZP_ERR_INVALID_ARG, "n_points * n_sets too large");
+  // The call copies its plan tables from host memory that is freed on return, which a captured
+  // graph would read again at every replay: stream capture is refused.
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+      return set_error(ZP_ERR_INVALID_ARG, "zp_series_eval_static cannot be captured in a CUDA graph (its tables "
+                                           "come from host memory freed on return); call it outside capture");
+  }
   // Host half of a plan: validation, columns, tables (host memory only).
   zp_plan plan;
   ZP_TRY(build_plan_host(n, m, n_modes, &plan));

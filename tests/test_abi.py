@@ -107,3 +107,17 @@ def test_no_cpu_fallback_anywhere(monkeypatch, tmp_path):
     monkeypatch.setattr(zbuild, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load()
+
+
+def test_probe_and_static_entry_validate_on_the_host(lib):
+    res = (ctypes.c_double * 6)()
+    assert lib.zp_probe_fp64(3, 100, None, res) == 1  # unknown operation
+    assert lib.zp_probe_fp64(0, 0, None, res) == 1  # no iterations
+    assert lib.zp_probe_fp64(0, 100, None, None) == 1
+    pn, keep_n = _i32([0, 1])
+    pm, keep_m = _i32([0, 1])
+    # Sizes whose products would wrap around in 64 bits are refused before anything else.
+    for sets in (1 << 40, (1 << 62) // 3):
+        assert lib.zp_series_eval_static(pn, pm, 2, None, None, 10, None, sets, 1, None, None) == 1
+        assert b"ZP_STATIC_SCRATCH_BYTES" in lib.zp_last_error()
+    assert lib.zp_series_eval_static(pn, pm, 2, None, None, 10, None, 4, 0, None, None) == 1  # float64

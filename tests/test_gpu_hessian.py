@@ -42,7 +42,11 @@ def test_hvp_matches_gradient_differences():
     hess = zp.series_point_hessian(None, None, rt, tt, C, G, plan=plan)
     rng = np.random.default_rng(10)
     vr, vt = dev(rng.standard_normal(500)), dev(rng.standard_normal(500))
-    hv_r, hv_t = zp.point_hvp(hess, vr, vt)
+    hv_r, hv_t = zp.series_point_hvp(None, None, rt, tt, C, G, vr, vt, plan=plan)
+    # the product formed in the kernel equals the blocks applied to the tangent
+    _, _, hrr, hrt, htt = hess
+    assert float((hv_r - (hrr * vr + hrt * vt)).abs().max()) <= 1e-13 * (1 + float(hv_r.abs().max()))
+    assert float((hv_t - (hrt * vr + htt * vt)).abs().max()) <= 1e-13 * (1 + float(hv_t.abs().max()))
     eps = 1e-6
     gp = zp.series_point_hessian(None, None, rt + eps * vr, tt + eps * vt, C, G, plan=plan)
     gm = zp.series_point_hessian(None, None, rt - eps * vr, tt - eps * vt, C, G, plan=plan)

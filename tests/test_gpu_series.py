@@ -1,5 +1,6 @@
 """Parity of the float64 series and its adjoint (zp_series_eval / zp_series_adjoint) with the
-oracle, and the autograd wrapper against central finite differences."""
+oracle, and the autograd wrapper against central finite differences.  The default float64 path
+is the emulated tensor-core contraction; the small cases also run the DGEMM baseline."""
 import numpy as np
 import pytest
 
@@ -18,29 +19,31 @@ def dev(x):
 
 
 def abs_bound(ns, ms, r, th, C, G=None):
-    """Sum of |terms| of each output: float64 rounding bound scale (see DESIGN: tolerance)."""
+    """Sum of |terms| of each output: the scale of the float64 rounding bound."""
     Z = np.abs(np.array(obasis.basis_table(ns, ms, r, th, 0)[0][0]))  # [J][P]
     if G is None:
         return Z.T @ np.abs(C)  # [P][S]
     return Z @ np.abs(G)  # [J][S]
 
 
-def test_series_eval_fp64_small():
+@pytest.mark.parametrize("prec", ["fp64emu", "fp64"])
+def test_series_eval_fp64_small(prec):
     ns, ms = inputs.full_zernike_modes(8)
     r, th = inputs.uniform_points(300, 21)
     C = inputs.scaled_normal_coeffs(ns, 5, 21)
-    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C)).cpu().numpy()
+    F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), prec).cpu().numpy()
     want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
     tol = 1e-13 * (1.0 + abs_bound(ns, ms, r, th, C))
     assert (np.abs(F - want) <= tol).all()
 
 
-def test_series_adjoint_fp64_small():
+@pytest.mark.parametrize("prec", ["fp64emu", "fp64"])
+def test_series_adjoint_fp64_small(prec):
     ns, ms = inputs.full_zernike_modes(7)
     r, th = inputs.uniform_points(90, 22)
     C = inputs.scaled_normal_coeffs(ns, 4, 22)
     G = np.random.default_rng(5).standard_normal((90, 4))
-    gC, gr, gt = zp.series_adjoint(ns, ms, dev(r), dev(th), dev(C), dev(G))
+    gC, gr, gt = zp.series_adjoint(ns, ms, dev(r), dev(th), dev(C), dev(G), prec=prec)
     wC, wr, wt = oseries.series_adjoint(ns, ms, r, th, C.tolist(), G.tolist())
     tolC = 1e-13 * (1.0 + abs_bound(ns, ms, r, th, C, G))
     assert (np.abs(gC.cpu().numpy() - np.array(wC)) <= tolC).all()
@@ -48,7 +51,7 @@ def test_series_adjoint_fp64_small():
     assert (np.abs(gr.cpu().numpy() - np.array(wr)) <= 1e-12 * scale).all()
     assert (np.abs(gt.cpu().numpy() - np.array(wt)) <= 1e-12 * scale).all()
     # Outputs may be requested individually
-    gC2, gr2, gt2 = zp.series_adjoint(ns, ms, dev(r), dev(th), dev(C), dev(G), need=(False, True, False))
+    gC2, gr2, gt2 = zp.series_adjoint(ns, ms, dev(r), dev(th), dev(C), dev(G), need=(False, True, False), prec=prec)
     assert gC2 is None and gt2 is None
     assert torch.equal(gr2, gr)
 

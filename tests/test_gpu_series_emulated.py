@@ -131,7 +131,7 @@ def test_emulated_adjoint_series_n24_full_size_against_fp64():
     G = torch.randn((len(r), C.shape[1]), dtype=torch.float64, device=DEV,
                     generator=torch.Generator(DEV).manual_seed(3))
     e = zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64emu")
-    f = zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan)
+    f = zp.series_adjoint(None, None, rt, tt, Ct, G, plan=plan, prec="fp64")
     Z = zp.basis(None, None, rt, tt, 0, plan=plan)[0][0]
     bC = 1e-12 * (1.0 + Z.abs() @ G.abs()) + len(r) * 2.0 ** -48 * torch.outer(Z.abs().amax(1), G.abs().amax(0))
     assert bool(((e[0] - f[0]).abs() <= bC).all())
