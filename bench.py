@@ -73,6 +73,9 @@ def parse_args():
                     help="run only the series_n24 emulated-float64 adjoint (profiling captures)")
     ap.add_argument("--paper-shapes-only", action="store_true",
                     help="run only the paper-shapes measurement (Algorithm 2, Fig. 3 grid, duplicated modes)")
+    ap.add_argument("--fused-only", action="store_true",
+                    help="run only the fused float64-accurate series measurement (profiling captures)")
+    ap.add_argument("--fused-points", type=int, default=1_000_000)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
@@ -495,6 +498,7 @@ def run_ours(args) -> None:
         torch.cuda.empty_cache()
         extras = {"series": measure_series(dev, peaks), "adjoint": measure_adjoint(dev),
                   "basis": measure_basis_latency(dev), "batched": measure_batched(dev),
+                  "fused_series": measure_fused_series(dev, peaks),
                   "paper_shapes": measure_paper_shapes(dev)}
 
     cpu = cpu_alg1 = None
@@ -723,6 +727,68 @@ def measure_adjoint_emulated(dev, steps: int = 2) -> dict:
     return {"workload": "series_n24", "fp64_emulated_adjoint_ms": ms_}
 
 
+def fused_fp64_ops(ns, ms) -> int:
+    """float64 operations per point of the fused kernel's walk: per column step N >= 2 the
+    recursion (2), per step with outputs the weight product (1), per output the angular product
+    (1); per column the angle addition (4)."""
+    cols = {}
+    for n, m in zip(ns, ms):
+        cols.setdefault(abs(int(m)), {}).setdefault((int(n) - abs(int(m))) // 2, 0)
+        cols[abs(int(m))][(int(n) - abs(int(m))) // 2] += 1
+    ops = 0
+    for m, steps in cols.items():
+        n_steps = max(steps) + 1
+        ops += 4 + 2 * max(0, n_steps - 2)
+        ops += sum(1 + c for c in steps.values())
+    return ops
+
+
+def measure_fused_series(dev, peaks, steps: int = 5, n_points: int = 1_000_000) -> dict:
+    """The fused float64-accurate series (basis on chip, 16 sets) on the mixed_n32 points (561
+    modes, 1e6 points r = sqrt(U)) against the plain float64 basis-then-DGEMM form, with the
+    fused kernel's float64 roofline (its walk issues fused_fp64_ops per point)."""
+    import ctypes
+
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import _lib, inputs
+
+    cfg = inputs.WORKLOADS["mixed_n32"]
+    ns, ms = inputs.full_zernike_modes(cfg["n_max"])
+    r, th = inputs.sqrt_uniform_points(n_points, cfg["seed"])
+    S = 16
+    C = inputs.scaled_normal_coeffs(ns, S, cfg["seed"])
+    plan = zp.Plan(ns, ms, device=dev)
+    rt, tt, Ct = (torch.as_tensor(x, device=dev) for x in (r, th, C))
+    stream = torch.cuda.current_stream(dev)
+    lib = _lib.load()
+    out = torch.empty((n_points, S), dtype=torch.float64, device=dev)
+    out64 = torch.empty_like(out)
+    sp = stream.cuda_stream
+
+    def run(code, o):
+        _lib.check("zp_series_eval_plan", lib.zp_series_eval_plan(plan.handle, rt.data_ptr(), tt.data_ptr(), n_points,
+                                                                   Ct.data_ptr(), S, code, o.data_ptr(), sp))
+
+    run(4, out)
+    t_fused = _events_ms(stream, lambda: run(4, out), steps)
+    run(0, out64)
+    t_dgemm = _events_ms(stream, lambda: run(0, out64), 2)
+    ops = fused_fp64_ops(ns, ms) * n_points
+    probe = (ctypes.c_double * 6)()
+    _lib.check("zp_probe_fp64", lib.zp_probe_fp64(0, 20000, sp, probe))
+    diff = float((out - out64).abs().max())
+    return {"workload": "mixed_n32 points, 16 sets", "modes": len(ns), "points": n_points, "sets": S,
+            "fp64emu_fused_ms": t_fused, "fp64_basis_then_dgemm_ms": t_dgemm,
+            "speedup_fused_vs_basis_then_dgemm": t_dgemm / t_fused,
+            "max_abs_diff_vs_dgemm": diff, "max_abs_value": float(out64.abs().max()),
+            "roofline": {"bound": "alu", "kernel": "fused_emu_kernel (includes the coefficient digit kernels)",
+                         "fp64_ops": ops, "achieved_ops_per_s": ops / (t_fused * 1e-3),
+                         "peak_ops_per_s": probe[2], "frac": ops / (t_fused * 1e-3) / probe[2],
+                         "peak_source": "zp_probe_fp64 float64 FMA rate measured in this run"}}
+
+
 def measure_paper_shapes(dev, steps: int = 50) -> dict:
     """The paper's own timing shapes.  (1) Algorithm 2 (one recursion per mode) against the
     per-column walk (Algorithm 1's decomposition) on the 2601-mode radial set, k = 0, 100000
@@ -871,6 +937,24 @@ def measure_batched(dev, steps: int = 3, n_instances: int = 512, point_scale: fl
     out["tuned_forward_cfg"] = list(cfg64)
     out["tuned_adjoint_cfg"] = list(cfg_adj)
     out["fp64_forward_basis_values_per_s"] = basis_values / (t_graph * 1e-3)
+    # The fused float64-accurate forward on the tensor cores (basis generated inside the MMA
+    # kernel), also as a CUDA-graph replay, against the float64 CUDA-core contraction above.
+    ref = [rec["out"].clone() for rec in b.instances]
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g2, stream=side):
+            b.forward("fp64emu")
+    stream.wait_stream(side)
+    g2.replay()
+    t_fused = _events_ms(stream, g2.replay, steps)
+    diff = max(float((rec["out"] - r0).abs().max()) for rec, r0 in zip(b.instances, ref) if r0.numel())
+    mag = max(float(r0.abs().max()) for r0 in ref if r0.numel())
+    out["fp64emu_fused_forward_graph_ms"] = t_fused
+    out["fp64emu_fused_forward_basis_values_per_s"] = basis_values / (t_fused * 1e-3)
+    out["fp64emu_fused_max_abs_diff_vs_fp64"] = diff
+    out["fp64emu_fused_max_abs_value"] = mag
+    out["speedup_fused_vs_fp64_forward"] = t_graph / t_fused
+    del ref
     b.close()
     b32 = zp.Batch(inst, S, out_dtype=torch.float32, with_adjoint=False)
     cfg32 = b32.tune("forward", "fp32", reps=1)[0] if tune else b32.config()
@@ -920,6 +1004,13 @@ def main():
         res = measure_batched(torch.device("cuda", 0), steps=args.steps, n_instances=args.batched_instances,
                               point_scale=args.batched_point_scale, tune=False)
         print(json.dumps({"batched_only": res}), flush=True)
+        return
+    if args.fused_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"fused_only": measure_fused_series(torch.device("cuda", 0), {}, steps=args.steps,
+                                                             n_points=args.fused_points)}), flush=True)
         return
     if args.adjoint_emulated_only:
         import torch

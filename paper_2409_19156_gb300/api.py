@@ -323,8 +323,14 @@ class Batch:
         self.handle = handle
         self._arr = arr
 
-    def forward(self, prec: str = "fp64"):
-        code = {"fp64": 0, "fp32": 3}[prec]
+    def forward(self, prec: str = "fp64emu"):
+        """F for every instance: "fp64emu" (the fused float64-accurate tensor-core kernel, at most
+        16 sets and 5041 modes per instance), "fp64" (float64 contraction on the CUDA cores) or
+        "fp32" (float32 contraction, float32 outputs)."""
+        code = {"fp64": 0, "fp32": 3, "fp64emu": 4}[prec]
+        want = torch.float32 if prec == "fp32" else torch.float64
+        if self.out_dtype != want:
+            raise TypeError(f"forward({prec!r}) writes {want}, the batch's outputs are {self.out_dtype}")
         _lib.call("zp_batch_forward", self.handle, code, _stream(torch.device("cuda", torch.cuda.current_device())))
 
     def forward_per_instance(self):
@@ -345,7 +351,7 @@ class Batch:
     def tune(self, which: str = "forward", prec: str = "fp64", reps: int = 2):
         cfg = (ctypes.c_int32 * 4)()
         best = ctypes.c_float()
-        code = {"fp64": 0, "fp32": 3}[prec]
+        code = {"fp64": 0, "fp32": 3, "fp64emu": 4}[prec]
         _lib.call("zp_batch_tune", self.handle, 0 if which == "forward" else 1, code, reps,
                   _stream(torch.device("cuda", torch.cuda.current_device())), cfg, ctypes.byref(best))
         return tuple(cfg), best.value

@@ -25,6 +25,7 @@
 
 #include "zp_device.cuh"
 #include "zp_api_common.h"
+#include "zp_fused.h"
 #include "zp_series_internal.h"
 
 namespace zp {
@@ -406,6 +407,15 @@ struct zp_batch {
   // launch configuration (autotuned): point-tile size, CTAs per SM, column-kernel PPT/threads
   int tp = 128, ctas_per_sm = 4, col_ppt = 2, col_threads = 128;
   std::vector<int64_t> inst_item_begin, inst_item_end;  // point items per instance
+  // Fused float64-accurate forward on the tensor cores (ZP_PREC_FP64_EMULATED), available when
+  // n_sets <= 16 and every instance has at most 5041 modes: instance descriptors, 128-point
+  // items ordered by cost, the instance of every 32-mode chunk, coefficient digits and scales.
+  bool fused_ok = false;
+  void* fused_block = nullptr;
+  zp::FusedInst* d_finst = nullptr;
+  zp::FusedItem* d_fitems = nullptr;
+  int32_t* d_fchunk = nullptr;
+  int64_t n_fitems = 0, n_fchunks = 0;
 };
 
 namespace zp {
@@ -501,7 +511,84 @@ zp_status launch_columns(const zp_batch* b, cudaStream_t st) {
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "batched_column_kernel launch");
 }
 
+// Descriptors, items and buffers of the fused forward (see zp_batch::fused_ok).
+zp_status build_fused(zp_batch* b) {
+  if (b->n_sets > kFusedMaxSets || b->n_sets == 0) return ZP_OK;
+  for (auto& in : b->inst)
+    if (in.n_modes > kFusedMaxModes) return ZP_OK;
+  const int64_t n = (int64_t)b->inst.size();
+  std::vector<FusedInst> fi(n);
+  std::vector<int32_t> chunk_inst;
+  std::vector<std::pair<int64_t, int32_t>> order;  // (modes, instance): costliest tiles first
+  int64_t kc_total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const zp_instance& in = b->inst[i];
+    const zp_plan* p = b->plans[b->inst_plan[i]].get();
+    FusedInst& d = fi[i];
+    d.cols = p->dev.cols;
+    d.table = p->dev.table;
+    d.steps = p->dev.split_step;
+    d.slot_ptr = p->dev.slot_ptr;
+    d.slot_idx = p->dev.slot_idx;
+    d.n_cols = (int32_t)p->cols.size();
+    d.KC = (int32_t)((in.n_modes + 31) / 32);
+    d.kc_base = kc_total;
+    d.J = in.n_modes;
+    d.P = in.n_points;
+    d.S = b->n_sets;
+    d.r = in.r;
+    d.theta = in.theta;
+    d.coeffs = in.coeffs;
+    d.out = (double*)in.out;
+    kc_total += d.KC;
+    for (int32_t c = 0; c < d.KC; ++c) chunk_inst.push_back((int32_t)i);
+    if (in.n_modes > 0 && in.n_points > 0) order.push_back({in.n_modes, (int32_t)i});
+  }
+  std::stable_sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
+  std::vector<FusedItem> items;
+  for (auto& o : order)
+    for (int64_t t = 0; t * 128 < b->inst[o.second].n_points; ++t) items.push_back(FusedItem{o.second, (int32_t)t});
+  const size_t inst_b = align256(std::max<int64_t>(n, 1) * sizeof(FusedInst));
+  const size_t item_b = align256(std::max<size_t>(items.size(), 1) * sizeof(FusedItem));
+  const size_t chunk_b = align256(std::max<int64_t>(kc_total, 1) * sizeof(int32_t));
+  const size_t cexp_b = align256(std::max<int64_t>(n, 1) * kFusedMaxSets * sizeof(int));
+  const size_t dig_b = (size_t)std::max<int64_t>(kc_total, 1) * kFusedBChunk;
+  cudaError_t e = cudaMalloc(&b->fused_block, inst_b + item_b + chunk_b + cexp_b + dig_b);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fused batch)");
+  char* base = (char*)b->fused_block;
+  int* cexp = (int*)(base + inst_b + item_b + chunk_b);
+  uint8_t* dig = (uint8_t*)(base + inst_b + item_b + chunk_b + cexp_b);
+  for (int64_t i = 0; i < n; ++i) {
+    fi[i].cexp = cexp + i * kFusedMaxSets;
+    fi[i].bdig = dig + (size_t)fi[i].kc_base * kFusedBChunk;
+  }
+  b->d_finst = (FusedInst*)base;
+  b->d_fitems = (FusedItem*)(base + inst_b);
+  b->d_fchunk = (int32_t*)(base + inst_b + item_b);
+  e = cudaMemcpy(b->d_finst, fi.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(b->d_fitems, items.data(), items.size() * sizeof(FusedItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && kc_total > 0)
+    e = cudaMemcpy(b->d_fchunk, chunk_inst.data(), kc_total * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "copy of fused batch descriptors");
+  b->n_fitems = (int64_t)items.size();
+  b->n_fchunks = kc_total;
+  b->fused_ok = true;
+  return ZP_OK;
+}
+
 zp_status batch_forward(zp_batch* b, zp_precision prec, cudaStream_t st) {
+  if (prec == ZP_PREC_FP64_EMULATED) {
+    if (!b->fused_ok)
+      return set_error(ZP_ERR_UNSUPPORTED, "the emulated float64 batched forward takes at most 16 sets and 5041 "
+                                           "modes per instance");
+    FusedArgs a;
+    a.insts = b->d_finst;
+    a.items = b->d_fitems;
+    a.n_items = b->n_fitems;
+    if (b->n_fitems == 0) return ZP_OK;
+    return fused_launch(a, (int64_t)b->inst.size(), b->d_fchunk, b->n_fchunks, st);
+  }
   if (b->n_pitems == 0) return ZP_OK;
   if (prec == ZP_PREC_FP32) {
     if (b->coeff32_total > 0) {
@@ -658,8 +745,10 @@ zp_status zp_batch_create(const zp_instance* instances, int64_t n_instances, int
   }
   zp_status st = build_point_items(b.get(), nullptr);
   if (st == ZP_OK) st = set_column_attributes(b.get());
+  if (st == ZP_OK) st = build_fused(b.get());
   if (st != ZP_OK) {
     cudaFree(b->dev_block);
+    if (b->fused_block) cudaFree(b->fused_block);
     return st;
   }
   *out = b.release();
@@ -674,6 +763,7 @@ zp_status zp_batch_destroy(zp_batch* b) {
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   if (b->dev_block) cudaFree(b->dev_block);
+  if (b->fused_block) cudaFree(b->fused_block);
   cudaSetDevice(cur);
   delete b;
   return ZP_OK;
@@ -682,8 +772,9 @@ zp_status zp_batch_destroy(zp_batch* b) {
 zp_status zp_batch_forward(zp_batch* b, zp_precision prec, void* stream) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
-  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP32)
-    return set_error(ZP_ERR_INVALID_ARG, "batched forward supports ZP_PREC_FP64 and ZP_PREC_FP32");
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP32 && prec != ZP_PREC_FP64_EMULATED)
+    return set_error(ZP_ERR_INVALID_ARG,
+                     "batched forward supports ZP_PREC_FP64_EMULATED, ZP_PREC_FP64 and ZP_PREC_FP32");
   for (size_t i = 0; i < b->inst.size(); ++i)
     if (b->inst[i].n_points > 0 && b->n_sets > 0 && !b->inst[i].out)
       return set_error(ZP_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": out is NULL");
@@ -785,7 +876,10 @@ zp_status zp_batch_tune(zp_batch* b, int32_t which, zp_precision prec, int32_t r
   const int tps[] = {64, 128, 256};
   const int ctas[] = {2, 4, 8};
   std::vector<std::array<int, 4>> cands;
-  if (which == 0) {
+  if (which == 0 && prec == ZP_PREC_FP64_EMULATED) {
+    // The fused forward takes none of these parameters: one timing of the current configuration.
+    cands.push_back({b->tp, b->ctas_per_sm, b->col_ppt, b->col_threads});
+  } else if (which == 0) {
     for (int tp : tps)
       for (int c : ctas) cands.push_back({tp, c, b->col_ppt, b->col_threads});
   } else {

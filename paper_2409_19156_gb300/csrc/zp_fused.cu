@@ -1,0 +1,631 @@
+// Fused float64-accurate Zernike series for up to 16 coefficient sets: the basis is built on
+// chip and fed straight to the tensor cores; no basis value, digit or partial sum is written
+// to global memory.
+//
+//   F[p, s] = sum_j Z_j(p) C[j, s],   s < 16,
+//
+// contracted by error-free slicing (Ozaki et al., a published scheme, written here from its
+// definition): every Z_j(p) is scaled by 2^-e_p (e_p = 1 for 0 <= r <= 1, where |Z| <= 1;
+// else from a first pass over the point's modes), rounded to a fixed-point integer with 55
+// fraction bits and cut into 11 balanced base-32 digits a_1..a_11 (integers of at most 6 bits,
+// exact in bfloat16); the coefficients are cut the same way per set (b_1..b_11, scale 2^-e_s).
+// Then Z C = 2^(e_p + e_s) sum_d T_d 2^(-5 d) with T_d = sum_{t+u=d} sum_j a_t b_u, kept for
+// d <= 12 (the dropped pairs weigh below 2^-60 of the scales).
+//
+// One persistent CTA per SM works through 128-point tiles:
+//  - warps 0-3 (one thread per point) walk every |m| column of the plan with the float64
+//    recursion of Sec. 2 (Algorithm 1's column order, cos/sin(m theta) by angle addition
+//    between consecutive columns), form each value, cut it into its 11 digits on the integer
+//    pipe and write them into 11 digit tiles in shared memory (the tensor core's 64-byte
+//    swizzled K-major layout, 32 K values per stage, two stages);
+//  - warp 4 issues the tcgen05 MMAs: per K step and A digit t, one MMA of N = 176 against the
+//    coefficient digit tile shifted by t blocks of 16 rows (zero blocks in front), so that
+//    every MMA adds a_t b_u into the TMEM columns of diagonal t + u for all u at once; every
+//    diagonal sum is an integer below 2^24 (at most 5041 modes), hence exact in float32;
+//  - warps 5-8 take each finished tile's 11 x 16 diagonal sums out of TMEM, recombine them
+//    exactly in integers (two Horner chains joined into 128 bits) and round once to float64.
+// The K order of the contraction is the plan's slot order, so the coefficient digits are
+// prepared per call in that order (fused_coeff_kernel).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "zp_api_common.h"
+#include "zp_device.cuh"
+#include "zp_emu_device.cuh"
+#include "zp_fused.h"
+#include "zp_ptx.cuh"
+#include "zp_series_internal.h"
+
+namespace zp {
+namespace {
+
+constexpr int kBeta = kFusedBeta;   // digit width (bits)
+constexpr int kDig = kFusedDigits;  // digits per value
+constexpr int FM = 128;             // points per tile (TMEM lanes)
+constexpr int FBK = 32;             // K values per stage (64-byte bf16 rows)
+constexpr int FNS = kFusedMaxSets;  // sets per digit block (rows of a B block, TMEM columns)
+constexpr uint32_t kRowBytes = 64;
+constexpr uint32_t kASlice = FM * kRowBytes;                 // one digit tile of A: 8 KB
+constexpr uint32_t kABytes = kDig * kASlice;                 // 88 KB
+constexpr uint32_t kBBlock = FNS * kRowBytes;                // one digit block of B: 1 KB
+constexpr uint32_t kBPadBytes = (2 * kDig - 1) * kBBlock;    // 10 zero blocks + 11 digit blocks
+constexpr uint32_t kBCopyOffset = (kDig - 1) * kBBlock;
+constexpr uint32_t kStageBytes = kABytes + kBPadBytes;       // 109.5 KB
+constexpr int kStages = 2;
+constexpr int kAccCols = kDig * FNS;                         // 176 TMEM columns per tile
+constexpr int kAccStride = 256;                              // two accumulators in 512 columns
+constexpr int kProducerWarps = 4, kMmaWarp = 4, kEpiWarps = 4;  // warps 5-8: epilogue
+constexpr int kThreads = 32 * (kProducerWarps + 1 + kEpiWarps);  // 288
+constexpr int kSplit = 5;  // diagonals d = 2..6 in the first Horner chain, 7..12 in the second
+constexpr uint32_t kAux = 2048;
+constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + kAux;
+static_assert(kBPadBytes % 1024 == 0 && kABytes % 1024 == 0, "1024-byte aligned operand tiles");
+static_assert(kSmem <= 232448, "shared memory per CTA");
+static_assert(kAccCols <= kAccStride, "accumulator fits its TMEM half");
+
+constexpr long long kBias = fused_bias();
+
+__device__ unsigned int g_fused_error = 0;  // set when a bounded wait gives up
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// bf16 bit patterns (in the high half of a float's bits) of the 11 digits of fixed-point X,
+// most significant first: word[t] holds digit a_{t+1} of the value.  Balanced digits come from
+// the biased word's bit fields; a small integer d is exact as float(2^23 + d) - 2^23.
+__device__ __forceinline__ void digits_of(long long X, uint32_t (&f)[kDig]) {
+  const long long Y = X + kBias;
+  f[0] = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y, 0)) - 12582912.0f);
+#pragma unroll
+  for (int t = 1; t < kDig; ++t)
+    f[t] = __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y, t)) - 8388624.0f);  // 2^23+16
+}
+
+// Two values' digits joined per digit into one 32-bit word of two bf16 (value 0 low).
+__device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t (&w)[kDig]) {
+  uint32_t f0[kDig], f1[kDig];
+  digits_of(X0, f0);
+  digits_of(X1, f1);
+#pragma unroll
+  for (int t = 0; t < kDig; ++t) w[t] = __byte_perm(f0[t], f1[t], 0x7632);
+}
+
+struct Barriers {
+  uint64_t full[kStages];   // producer warps (4 arrivals)
+  uint64_t bfull[kStages];  // coefficient digit copy (1 arrival + bytes)
+  uint64_t empty[kStages];  // MMA commit
+  uint64_t tfull[2];        // MMA commit after a tile's last stage
+  uint64_t tempty[2];       // epilogue warps (4 arrivals)
+  uint64_t rfull[2];        // row exponents written (4 producer warps)
+  uint64_t rempty[2];       // row exponents read (4 epilogue warps)
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+  int row_exp[2][FM];
+};
+static_assert(sizeof(Barriers) <= kAux, "barrier block");
+
+// Bounded wait by one lane of the warp; the others learn the outcome by a shuffle.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int lane) {
+  bool ok = true;
+  if (lane == 0) ok = ptx::mbar_wait(bar, parity, abort_flag);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+__device__ __forceinline__ void fail(volatile int* abort_flag) {
+  *abort_flag = 1;
+  atomicOr(&g_fused_error, 1u);
+}
+
+// The float64 walk of one point over every column of its plan (Sec. 2 recursion, rescaled as
+// in the plan's tables: Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2}, R = W0_N Q_N), calling
+// emit(z) for every output slot in the plan's slot order.
+template <typename Emit>
+__device__ __forceinline__ void walk_point(const FusedInst& d, double rho, double th, Emit&& emit) {
+  const double u = rho * rho;
+  double s1, c1;
+  sincos(th, &s1, &c1);
+  double cm = 1.0, sm = 0.0, pm = 1.0;
+  int m_prev = 0;
+  for (int c = 0; c < d.n_cols; ++c) {
+    const Column col = d.cols[c];
+    const int m = col.m;
+    if (c > 0 && m == m_prev + 1) {
+      const double cn = fma(cm, c1, -sm * s1);
+      sm = fma(sm, c1, cm * s1);
+      cm = cn;
+      pm *= rho;
+    } else if (c == 0 || m != m_prev) {
+      cm = 1.0;
+      sm = 0.0;
+      if (m != 0) sincos((double)m * th, &sm, &cm);
+      pm = pow_uint(rho, m);
+    }
+    m_prev = m;
+    const double* h = d.table + (size_t)col.table_row * kRow;
+    const uint2* st = d.steps + col.table_row + kHeaderRows;
+    const int32_t* sp = d.slot_ptr + col.slot_base;
+    double T = pm, S = pm * fma(h[4], u, -h[8]);
+    for (int N = 0; N < col.n_steps; ++N) {
+      const double* row = h + (size_t)(kHeaderRows + N) * kRow;
+      double q;
+      if (N == 0) {
+        q = T;
+      } else if (N == 1) {
+        q = S;
+      } else {
+        const double g = fma(row[0], u, -row[1]);
+        q = fma(g, S, -T);
+        T = S;
+        S = q;
+      }
+      const uint32_t info = st[N].x;
+      uint32_t cnt = info & 0xffu, flags = info >> 8;
+      if (cnt == 0) continue;
+      const double R = q * row[3];
+      if (cnt == kStepIrregular) {
+        for (int s = sp[N]; s < sp[N + 1]; ++s) {
+          const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
+          emit(R * ((code >> 31) ? sm : cm));
+        }
+      } else {
+        for (; cnt > 0; --cnt, flags >>= 1) emit(R * ((flags & 1u) ? sm : cm));
+      }
+    }
+  }
+}
+
+// Item `it` of the launch: instance and first point.
+__device__ __forceinline__ void item_of(const FusedArgs& a, int64_t it, int& inst, int64_t& p0) {
+  if (a.items) {
+    const FusedItem w = a.items[it];
+    inst = w.inst;
+    p0 = (int64_t)w.tile * FM;
+  } else {
+    inst = 0;
+    p0 = it * FM;
+  }
+}
+
+__device__ __forceinline__ const FusedInst& inst_of(const FusedArgs& a, int inst) {
+  return a.insts ? a.insts[inst] : a.single;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  Barriers* bar = reinterpret_cast<Barriers*>(smem + kStages * kStageBytes);
+  volatile int* abort_flag = &bar->abort_flag;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      ptx::mbar_init(&bar->full[i], kProducerWarps);
+      ptx::mbar_init(&bar->bfull[i], 1);
+      ptx::mbar_init(&bar->empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&bar->tfull[i], 1);
+      ptx::mbar_init(&bar->tempty[i], kEpiWarps);
+      ptx::mbar_init(&bar->rfull[i], kProducerWarps);
+      ptx::mbar_init(&bar->rempty[i], kEpiWarps);
+    }
+    ptx::mbar_init(&bar->drain, 1);
+    bar->abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  // The zero blocks in front of each stage's coefficient digits (never overwritten).
+  for (uint32_t i = threadIdx.x; i < kStages * kBCopyOffset / 16; i += kThreads) {
+    const uint32_t st = i / (kBCopyOffset / 16), o = i % (kBCopyOffset / 16);
+    reinterpret_cast<uint4*>(smem + st * kStageBytes + kABytes)[o] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  ptx::fence_proxy_async_smem();
+  if (warp == kMmaWarp) {
+    ptx::tmem_alloc(&bar->tmem_base, 2 * kAccStride);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = bar->tmem_base;
+
+  if (warp < kProducerWarps) {
+    // ---------------------------------------------------------------- producers
+    const uint32_t row = (uint32_t)threadIdx.x;  // point row of the tile (TMEM lane)
+    int stage = 0;
+    uint32_t sphase = 0;
+    uint32_t b_issued0 = 0u, b_issued1 = 0u;  // coefficient copies issued per stage (warp 0, lane 0)
+    static_assert(kStages == 2, "two stages");
+    bool ok = true;
+    int64_t local = 0;
+    for (int64_t it = blockIdx.x; it < a.n_items && ok; it += gridDim.x, ++local) {
+      int ii;
+      int64_t p0;
+      item_of(a, it, ii, p0);
+      const FusedInst& d = inst_of(a, ii);
+      const int64_t p = p0 + row;
+      const bool valid = p < d.P;
+      const double rho = valid ? d.r[p] : 0.0, th = valid ? d.theta[p] : 0.0;
+      // Row exponent: |Z| <= 1 on the unit disc; elsewhere the point's largest |Z| decides.
+      int ep = 1;
+      if (!(rho >= 0.0 && rho <= 1.0 && fabs(th) <= 1.79e308)) {
+        unsigned long long mx = 0;
+        walk_point(d, rho, th, [&](double z) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(z) & 0x7fffffffffffffffull;
+          mx = b > mx ? b : mx;
+        });
+        ep = scale_exponent(mx);
+      }
+      const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
+      if (!warp_wait(&bar->rempty[acc], use ^ 1u, abort_flag, lane)) {
+        fail(abort_flag);
+        ok = false;
+        break;
+      }
+      bar->row_exp[acc][row] = ep;
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&bar->rfull[acc]);
+      const bool zero_row = ep == kNonFiniteRow;
+      const int shift = kBeta * kDig - (zero_row ? 0 : ep);
+
+      int k = 0;  // K position within the tile
+      uint32_t w[kDig][4];
+      double pending = 0.0;
+      bool have_pending = false;
+      uint8_t* sA = smem + stage * kStageBytes;
+      // Stores the 16-byte unit completed at K position k (a multiple of 8), opening the stage
+      // (waiting for it to be free, starting its coefficient copy) at its first unit and
+      // handing it to the MMA warp after its last.
+      auto flush_unit = [&]() -> bool {
+        const int kk = (k - 8) % FBK;
+        if (kk == 0) {
+          if (!warp_wait(&bar->empty[stage], sphase ^ 1u, abort_flag, lane)) return false;
+          sA = smem + stage * kStageBytes;
+          if (warp == 0 && lane == 0) {
+            const int kc = (k - 8) / FBK;
+            ptx::mbar_arrive_expect_tx(&bar->bfull[stage], kFusedBChunk);
+            ptx::bulk_g2s(sA + kABytes + kBCopyOffset, d.bdig + (size_t)kc * kFusedBChunk, kFusedBChunk,
+                          &bar->bfull[stage]);
+            if (stage == 0) ++b_issued0;
+            else ++b_issued1;
+          }
+        }
+        const uint32_t off = ptx::sw_offset_b16<kRowBytes>(row, (uint32_t)kk);
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          *reinterpret_cast<uint4*>(sA + t * kASlice + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+        if (kk == FBK - 8) {
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&bar->full[stage]);
+          if (++stage == kStages) {
+            stage = 0;
+            sphase ^= 1u;
+          }
+        }
+        return true;
+      };
+      // Two consecutive K values (k even): digits, packed in pairs, placed at the unit's word.
+      auto push_pair = [&](double z0, double z1) -> bool {
+        const long long X0 = zero_row ? 0 : to_fixed(z0, shift);
+        const long long X1 = zero_row ? 0 : to_fixed(z1, shift);
+        uint32_t pw[kDig];
+        digit_pair(X0, X1, pw);
+        switch ((k >> 1) & 3) {
+          case 0:
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) w[t][0] = pw[t];
+            break;
+          case 1:
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) w[t][1] = pw[t];
+            break;
+          case 2:
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) w[t][2] = pw[t];
+            break;
+          default:
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) w[t][3] = pw[t];
+            break;
+        }
+        k += 2;
+        if ((k & 7) == 0) return flush_unit();
+        return true;
+      };
+      walk_point(d, rho, th, [&](double z) {
+        if (!ok) return;
+        if (!have_pending) {
+          pending = z;
+          have_pending = true;
+        } else {
+          have_pending = false;
+          ok = push_pair(pending, z);
+        }
+      });
+      if (ok && have_pending) ok = push_pair(pending, 0.0);
+      while (ok && (k % FBK) != 0) ok = push_pair(0.0, 0.0);
+      if (!ok) {
+        fail(abort_flag);
+        break;
+      }
+    }
+    // Every coefficient copy this CTA issued has landed before the CTA may exit (a wait that
+    // ignores the abort flag, still bounded).
+    if (warp == 0 && lane == 0) {
+      int never = 0;
+      if (b_issued0 && !ptx::mbar_wait(&bar->bfull[0], (b_issued0 - 1u) & 1u, &never)) atomicOr(&g_fused_error, 1u);
+      if (b_issued1 && !ptx::mbar_wait(&bar->bfull[1], (b_issued1 - 1u) & 1u, &never)) atomicOr(&g_fused_error, 1u);
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(FM, kAccCols);
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t local = 0;
+      for (int64_t it = blockIdx.x; it < a.n_items && !*abort_flag; it += gridDim.x, ++local) {
+        int ii;
+        int64_t p0;
+        item_of(a, it, ii, p0);
+        const int KC = inst_of(a, ii).KC;
+        const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
+        if (!ptx::mbar_wait(&bar->tempty[acc], use ^ 1u, abort_flag)) {
+          fail(abort_flag);
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * kAccStride;
+        bool ok = true;
+        for (int kc = 0; kc < KC; ++kc) {
+          if (!ptx::mbar_wait(&bar->full[stage], phase, abort_flag) ||
+              !ptx::mbar_wait(&bar->bfull[stage], phase, abort_flag)) {
+            fail(abort_flag);
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sA = ptx::smem_u32(smem + stage * kStageBytes);
+          const uint32_t sB = sA + kABytes;
+#pragma unroll
+          for (int ks = 0; ks < FBK / 16; ++ks) {
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) {
+              // A digit t+1 times the coefficient digits shifted down by t blocks: block
+              // (t+1) + u - 2 of the accumulator (diagonal t+1+u) receives a_{t+1} b_u.
+              const uint64_t adesc = ptx::sw_kmajor_desc<kRowBytes>(sA + t * kASlice + ks * 32);
+              const uint64_t bdesc = ptx::sw_kmajor_desc<kRowBytes>(sB + (kDig - 1 - t) * kBBlock + ks * 32);
+              ptx::mma_bf16(d_tmem, adesc, bdesc, idesc, (kc == 0 && ks == 0 && t == 0) ? 0u : 1u);
+            }
+          }
+          ptx::mma_commit(&bar->empty[stage]);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&bar->tfull[acc]);
+      }
+      // Every MMA this thread issued has completed before TMEM is released (a wait that
+      // ignores the abort flag, still bounded).
+      ptx::mma_commit(&bar->drain);
+      int never = 0;
+      if (!ptx::mbar_wait(&bar->drain, 0u, &never)) atomicOr(&g_fused_error, 1u);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const uint32_t q = (uint32_t)(warp & 3);  // TMEM lane quadrant this warp may read
+    const uint32_t row = q * 32 + lane;
+    int64_t local = 0;
+    for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x, ++local) {
+      int ii;
+      int64_t p0;
+      item_of(a, it, ii, p0);
+      const FusedInst& d = inst_of(a, ii);
+      const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
+      if (!warp_wait(&bar->tfull[acc], use, abort_flag, lane) || !warp_wait(&bar->rfull[acc], use, abort_flag, lane)) {
+        fail(abort_flag);
+        break;
+      }
+      ptx::tc_fence_after();
+      const int ep = bar->row_exp[acc][row];
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&bar->rempty[acc]);
+      const int64_t p = p0 + row;
+      const bool store = p < d.P;
+      const int e_base = ep - kBeta * (kDig + 1);
+#pragma unroll 1
+      for (int h = 0; h < FNS / 8; ++h) {
+        long long hi[8] = {}, lo[8] = {};
+#pragma unroll
+        for (int db = 0; db < kDig; ++db) {
+          uint32_t v[8];
+          ptx::tmem_ld_32x32b_x8(tmem_base + ((q * 32u) << 16) + acc * kAccStride + (uint32_t)(db * FNS + h * 8), v);
+          ptx::tmem_ld_wait(v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const long long tv = (long long)__float2int_rn(__uint_as_float(v[i]));
+            if (db < kSplit) hi[i] = horner(hi[i], kBeta, tv);
+            else lo[i] = horner(lo[i], kBeta, tv);
+          }
+        }
+        if (store) {
+          double out[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int ec = d.cexp[h * 8 + i];
+            out[i] = (ep == kNonFiniteRow || ec == kNonFiniteRow)
+                         ? __longlong_as_double(0x7ff8000000000000ll)
+                         : int128_to_double(
+                               (__int128)((unsigned __int128)(__int128)hi[i] << (kBeta * (kDig - kSplit))) +
+                                   (__int128)lo[i],
+                               e_base + ec);
+          }
+          double* orow = d.out + p * d.S;
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (h * 8 + i < d.S) orow[h * 8 + i] = out[i];
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&bar->tempty[acc]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 2 * kAccStride);
+  }
+}
+
+// Set scale exponents: cexp[s] = e with 2^e > max_j |C[j][s]| (kNonFiniteRow for a set holding
+// an infinity or a NaN), one block per instance, sets past S get 0.
+__global__ void __launch_bounds__(256) fused_cexp_kernel(FusedArgs a, int64_t n_inst) {
+  __shared__ unsigned long long red[FNS][8];
+  const int64_t inst = blockIdx.x;
+  if (inst >= n_inst) return;
+  const FusedInst& d = inst_of(a, (int)inst);
+  unsigned long long mx[FNS];
+#pragma unroll
+  for (int s = 0; s < FNS; ++s) mx[s] = 0;
+  for (int64_t j = threadIdx.x; j < d.J; j += blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < FNS; ++s) {
+      if (s < d.S) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(d.coeffs[j * d.S + s]) & 0x7fffffffffffffffull;
+        mx[s] = b > mx[s] ? b : mx[s];
+      }
+    }
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int s = 0; s < FNS; ++s) {
+    unsigned long long v = mx[s];
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (lane == 0) red[s][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < FNS) {
+    unsigned long long v = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v = red[threadIdx.x][w] > v ? red[threadIdx.x][w] : v;
+    d.cexp[threadIdx.x] = (int)threadIdx.x < d.S ? scale_exponent(v) : 0;
+  }
+}
+
+// Coefficient digits in the plan's slot order: thread = (chunk, set, group of 8 modes); the
+// 8 values' 11 digits are written as one 16-byte unit into each digit block's row for the set.
+__global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int32_t* chunk_inst, int64_t n_chunks) {
+  const int64_t total = n_chunks * FNS * (FBK / 8);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = i / (FNS * (FBK / 8));
+    const int s = (int)((i / (FBK / 8)) % FNS);
+    const int q = (int)(i % (FBK / 8));
+    const int inst = chunk_inst ? chunk_inst[g] : 0;
+    const FusedInst& d = inst_of(a, inst);
+    const int64_t kc = g - d.kc_base;
+    const int ec = s < d.S ? d.cexp[s] : 0;
+    const bool use = s < d.S && ec != kNonFiniteRow;
+    long long X[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t k = kc * FBK + q * 8 + e;
+      X[e] = 0;
+      if (use && k < d.J) {
+        const int64_t j = (int64_t)((uint32_t)__ldg(d.slot_idx + k) & 0x7fffffffu);
+        X[e] = to_fixed(d.coeffs[j * d.S + s], kBeta * kDig - ec);
+      }
+    }
+    uint32_t w[kDig][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t pw[kDig];
+      digit_pair(X[2 * e], X[2 * e + 1], pw);
+#pragma unroll
+      for (int t = 0; t < kDig; ++t) w[t][e] = pw[t];
+    }
+    uint8_t* chunk = d.bdig + (size_t)kc * kFusedBChunk;
+#pragma unroll
+    for (int t = 0; t < kDig; ++t)
+      *reinterpret_cast<uint4*>(chunk + ptx::sw_offset_b16<kRowBytes>((uint32_t)(t * FNS + s), (uint32_t)(q * 8))) =
+          make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+  }
+}
+
+}  // namespace
+
+zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
+                       cudaStream_t stream) {
+  if (a.n_items == 0) return ZP_OK;
+  static DeviceMemo<int> sms_memo;
+  int sms = 0;
+  ZP_TRY(sms_memo.get(&sms, [](int* x) -> zp_status {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(x, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused kernel set-up");
+  }));
+  fused_cexp_kernel<<<(unsigned)n_inst, 256, 0, stream>>>(a, n_inst);
+  const int64_t threads = n_chunks * FNS * (FBK / 8);
+  fused_coeff_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 8 * (int64_t)sms)), 256,
+                       0, stream>>>(a, chunk_inst, n_chunks);
+  const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, sms);
+  fused_emu_kernel<<<grid, kThreads, kSmem, stream>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused series launch");
+}
+
+zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                            int64_t S, double* out, cudaStream_t stream) {
+  const int64_t J = plan->n_modes;
+  if (S > kFusedMaxSets || J > kFusedMaxModes)
+    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 modes");
+  FusedArgs a;
+  FusedInst& d = a.single;
+  d.cols = plan->dev.cols;
+  d.table = plan->dev.table;
+  d.steps = plan->dev.split_step;
+  d.slot_ptr = plan->dev.slot_ptr;
+  d.slot_idx = plan->dev.slot_idx;
+  d.n_cols = (int32_t)plan->cols.size();
+  d.KC = (int32_t)((J + FBK - 1) / FBK);
+  d.kc_base = 0;
+  d.J = J;
+  d.P = P;
+  d.S = S;
+  d.r = r;
+  d.theta = theta;
+  d.coeffs = coeffs;
+  d.out = out;
+  ScratchBuffer buf;
+  const size_t bbytes = (size_t)d.KC * kFusedBChunk;
+  ZP_TRY(buf.alloc(bbytes + 256, stream));
+  d.bdig = (uint8_t*)buf.ptr;
+  d.cexp = (int*)((uint8_t*)buf.ptr + bbytes);
+  a.n_items = (P + FM - 1) / FM;
+  return fused_launch(a, 1, nullptr, d.KC, stream);
+}
+
+zp_status fused_error_word(unsigned int* value, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_fused_error, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyFromSymbol");
+  if (reset) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyToSymbol(g_fused_error, &zero, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyToSymbol");
+  }
+  return ZP_OK;
+}
+
+}  // namespace zp

@@ -1,0 +1,85 @@
+// Host-side interface of the fused float64-accurate series for few coefficient sets
+// (zp_fused.cu): the basis is generated inside the tensor-core kernel and never written out.
+#pragma once
+
+#include <cstdint>
+
+#include "zp_internal.h"
+
+namespace zp {
+
+constexpr int kFusedBeta = 5;       // bits per digit
+constexpr int kFusedDigits = 11;    // digits per value: 55 fraction bits
+constexpr int kFusedMaxSets = 16;   // coefficient sets per launch
+// Longest contraction whose diagonal sums stay exact integers in float32:
+// K * 2^(2 beta) * (1 + (digits - 2) / 4) < 2^24.
+constexpr int64_t kFusedMaxModes = 5041;
+// Bytes of one 32-mode chunk of coefficient digits: 11 digit blocks of 16 sets x 64 bytes, each
+// row the tensor core's 64-byte swizzled K-major layout.
+constexpr uint32_t kFusedBChunk = (uint32_t)kFusedDigits * kFusedMaxSets * 64u;
+
+// Balanced base-32 digits of a fixed-point value X (|X| < 2^55), most significant first:
+// Y = X + fused_bias() holds, for the 10 low positions, the unsigned fields f_t = d_t + 16 of
+// the balanced digits d_t in [-16, 16); the most significant digit is Y >> 50 itself (at most
+// 33 in magnitude), so that X = sum_t d_t 2^(5 (10 - t)) with d_0 the top digit.
+__host__ __device__ constexpr long long fused_bias() {
+  long long b = 0;
+  for (int t = 0; t < kFusedDigits - 1; ++t) b += (long long)(1 << (kFusedBeta - 1)) << (kFusedBeta * t);
+  return b;
+}
+// Digit t of the biased word Y: t = 0 the signed top digit, else the unsigned field.
+__host__ __device__ inline int fused_digit_field(long long Y, int t) {
+  return t == 0 ? (int)(Y >> (kFusedBeta * (kFusedDigits - 1)))
+                : (int)((unsigned long long)(Y >> (kFusedBeta * (kFusedDigits - 1 - t))) & 31u);
+}
+
+// One series instance of the fused kernel (device pointers).
+struct FusedInst {
+  const Column* cols = nullptr;
+  const double* table = nullptr;
+  const uint2* steps = nullptr;  // the plan's per-step slot counts and sin flags
+  const int32_t* slot_ptr = nullptr;
+  const int32_t* slot_idx = nullptr;
+  int32_t n_cols = 0;
+  int32_t KC = 0;        // 32-mode chunks of the contraction
+  int64_t kc_base = 0;   // first chunk of this instance in the launch's chunk numbering
+  int64_t J = 0, P = 0, S = 0;
+  const double* r = nullptr;
+  const double* theta = nullptr;
+  const double* coeffs = nullptr;  // [J][S]
+  uint8_t* bdig = nullptr;         // [KC][kFusedBChunk] coefficient digits (written per call)
+  int* cexp = nullptr;             // [kFusedMaxSets] set scale exponents (written per call)
+  double* out = nullptr;           // [P][S]
+};
+
+// A 128-point tile of one instance.
+struct FusedItem {
+  int32_t inst;
+  int32_t tile;
+};
+
+// Launch description: `insts` and `items` in device memory, or (both NULL) one instance
+// passed by value whose tiles are the items in order.
+struct FusedArgs {
+  const FusedInst* insts = nullptr;
+  const FusedItem* items = nullptr;
+  int64_t n_items = 0;
+  FusedInst single;
+};
+
+// Coefficient scales and digits of every instance (n_inst instances, chunk_inst[g] = instance of
+// global chunk g, n_chunks chunks in total; chunk_inst NULL for the single-instance form), then the
+// fused kernel over all items: stream-ordered, no host synchronisation (capturable).
+zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
+                       cudaStream_t stream);
+
+// F = Z C for one plan with S <= kFusedMaxSets and n_modes <= kFusedMaxModes (scratch for the
+// coefficient digits from the library's pool).
+zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                            int64_t S, double* out, cudaStream_t stream);
+
+// Reads and optionally clears the fused kernel's wait-status word (non-zero: a bounded wait
+// gave up).
+zp_status fused_error_word(unsigned int* value, bool reset);
+
+}  // namespace zp

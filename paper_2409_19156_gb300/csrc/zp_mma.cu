@@ -32,6 +32,7 @@
 #include "zp_ptx.cuh"
 #include "zp_emu_device.cuh"
 #include "zp_emu_shape.h"
+#include "zp_fused.h"
 #include "zp_series_internal.h"
 
 namespace zp {
@@ -1285,8 +1286,9 @@ extern "C" zp_status zp_device_wait_selftest(int32_t limit_ms, void* stream) {
 
 extern "C" zp_status zp_device_wait_status(int32_t reset) {
   zp::clear_error();
-  unsigned int v = 0;
+  unsigned int v = 0, f = 0;
   ZP_TRY(zp::split_error_word(&v, reset != 0));
-  if (v) return zp::set_error(ZP_ERR_TIMEOUT, "a bounded device wait in the tensor-core series kernel gave up");
+  ZP_TRY(zp::fused_error_word(&f, reset != 0));
+  if (v || f) return zp::set_error(ZP_ERR_TIMEOUT, "a bounded device wait in a tensor-core series kernel gave up");
   return ZP_OK;
 }

@@ -19,6 +19,7 @@
 
 #include "zp_device.cuh"
 #include "zp_api_common.h"
+#include "zp_fused.h"
 #include "zp_series_internal.h"
 
 namespace zp {
@@ -345,8 +346,12 @@ zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaMemsetAsync");
   }
   if (prec == ZP_PREC_FP64) return series_eval_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
-  if (prec == ZP_PREC_FP64_EMULATED)
+  if (prec == ZP_PREC_FP64_EMULATED) {
+    // Few sets: the fused kernel (basis generated on chip, no basis or partial sums in HBM).
+    if (n_sets <= kFusedMaxSets && plan->n_modes <= kFusedMaxModes)
+      return fused_series_eval(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
     return series_eval_emulated_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
+  }
   return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, st);
 }
 
