@@ -514,8 +514,8 @@ zp_status launch_columns(const zp_batch* b, cudaStream_t st) {
 // Descriptors, items and buffers of the fused forward (see zp_batch::fused_ok).
 zp_status build_fused(zp_batch* b) {
   if (b->n_sets > kFusedMaxSets || b->n_sets == 0) return ZP_OK;
-  for (auto& in : b->inst)
-    if (in.n_modes > kFusedMaxModes) return ZP_OK;
+  for (size_t i = 0; i < b->inst.size(); ++i)
+    if (b->plans[b->inst_plan[i]]->fused_kpad > kFusedMaxModes) return ZP_OK;
   const int64_t n = (int64_t)b->inst.size();
   std::vector<FusedInst> fi(n);
   std::vector<int32_t> chunk_inst;
@@ -530,8 +530,15 @@ zp_status build_fused(zp_batch* b) {
     d.steps = p->dev.split_step;
     d.slot_ptr = p->dev.slot_ptr;
     d.slot_idx = p->dev.slot_idx;
+    d.fcols = p->dev.fused_col;
+  d.scols = (const int32_t*)(p->dev.fused_col + p->cols.size());
+  d.ncols_s[0] = p->fused_ncols[0];
+  d.ncols_s[1] = p->fused_ncols[1];
+  d.units = p->fused_units;
+    d.kperm = p->dev.fused_kperm;
+    d.Kp = in.n_modes > 0 ? p->fused_kpad : 0;
     d.n_cols = (int32_t)p->cols.size();
-    d.KC = (int32_t)((in.n_modes + 31) / 32);
+    d.KC = (int32_t)((d.Kp + 31) / 32);
     d.kc_base = kc_total;
     d.J = in.n_modes;
     d.P = in.n_points;

@@ -24,12 +24,15 @@
 //    diagonal sum is an integer below 2^24 (at most 5041 modes), hence exact in float32;
 //  - warps 5-8 take each finished tile's 11 x 16 diagonal sums out of TMEM, recombine them
 //    exactly in integers (two Horner chains joined into 128 bits) and round once to float64.
-// The K order of the contraction is the plan's slot order, so the coefficient digits are
-// prepared per call in that order (fused_coeff_kernel).
+// The K order of the contraction is the plan's slot order with every column padded to a
+// multiple of 8 positions (so a column's steps fill whole 16-byte operand units in unrolled
+// straight-line code), and the coefficient digits are prepared per call in that order
+// (fused_coeff_kernel).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "zp_api_common.h"
@@ -57,8 +60,10 @@ constexpr uint32_t kStageBytes = kABytes + kBPadBytes;       // 109.5 KB
 constexpr int kStages = 2;
 constexpr int kAccCols = kDig * FNS;                         // 176 TMEM columns per tile
 constexpr int kAccStride = 256;                              // two accumulators in 512 columns
-constexpr int kProducerWarps = 4, kMmaWarp = 4, kEpiWarps = 4;  // warps 5-8: epilogue
-constexpr int kThreads = 32 * (kProducerWarps + 1 + kEpiWarps);  // 288
+// Warps 0-7 produce (warp w: point rows 32 (w % 4) .. + 31, stream w / 4) and also drain the
+// accumulator of the previous tile (warp w: its rows, sets 8 (w / 4) .. + 7); warp 8 issues MMAs.
+constexpr int kProducerWarps = 8, kMmaWarp = 8;
+constexpr int kThreads = 32 * (kProducerWarps + 1);  // 288
 constexpr int kSplit = 5;  // diagonals d = 2..6 in the first Horner chain, 7..12 in the second
 constexpr uint32_t kAux = 2048;
 constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + kAux;
@@ -95,25 +100,35 @@ __device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t 
 }
 
 struct Barriers {
-  uint64_t full[kStages];   // producer warps (4 arrivals)
+  uint64_t full[kStages];   // producer warps (8 arrivals)
   uint64_t bfull[kStages];  // coefficient digit copy (1 arrival + bytes)
   uint64_t empty[kStages];  // MMA commit
   uint64_t tfull[2];        // MMA commit after a tile's last stage
-  uint64_t tempty[2];       // epilogue warps (4 arrivals)
-  uint64_t rfull[2];        // row exponents written (4 producer warps)
-  uint64_t rempty[2];       // row exponents read (4 epilogue warps)
+  uint64_t tempty[2];       // producer warps after draining the accumulator (8 arrivals)
   uint64_t drain;
   uint32_t tmem_base;
   int abort_flag;
-  int row_exp[2][FM];
 };
 static_assert(sizeof(Barriers) <= kAux, "barrier block");
 
-// Bounded wait by one lane of the warp; the others learn the outcome by a shuffle.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int lane) {
+// Bounded wait by one lane of the warp; the others learn the outcome by a shuffle.  Roles that
+// mostly wait for the producers (the epilogue) poll with a sleep in between.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int lane,
+                                          bool sleepy = false) {
   bool ok = true;
-  if (lane == 0) ok = ptx::mbar_wait(bar, parity, abort_flag);
+  if (lane == 0) ok = sleepy ? ptx::mbar_wait_sleepy(bar, parity, abort_flag, 500) : ptx::mbar_wait(bar, parity, abort_flag);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// round-half-even(z * 2^shift) as an int64 (|z| 2^shift < 2^55): the scaling is an integer add
+// to the exponent field (exact while the result stays normal; anything that would leave the
+// normal range rounds to 0 anyway) and the conversion one float64 -> int64 instruction, which
+// the conversion unit issues far faster than GB300's float64 pipe.  z must be finite.
+__device__ __forceinline__ long long to_fixed_fast(double z, int shift) {
+  const long long b = __double_as_longlong(z);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  const long long sb = (ef + shift > 0) ? b + ((long long)shift << 52) : 0ll;
+  return __double2ll_rn(__longlong_as_double(sb));
 }
 
 __device__ __forceinline__ void fail(volatile int* abort_flag) {
@@ -195,6 +210,40 @@ __device__ __forceinline__ const FusedInst& inst_of(const FusedArgs& a, int inst
   return a.insts ? a.insts[inst] : a.single;
 }
 
+// Drains accumulator `acc` of a finished tile for this thread's row and 8 sets (h): 11 diagonal
+// sums per output out of TMEM, recombined exactly (two Horner chains joined into 128 bits) and
+// rounded once to float64.
+__device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint32_t tmem_base, uint32_t acc, uint32_t q,
+                                           uint32_t row, int h, int ep) {
+  const int64_t p = p0 + row;
+  long long hi[8] = {}, lo[8] = {};
+#pragma unroll
+  for (int db = 0; db < kDig; ++db) {
+    uint32_t v[8];
+    ptx::tmem_ld_32x32b_x8(tmem_base + ((q * 32u) << 16) + acc * kAccStride + (uint32_t)(db * FNS + h * 8), v);
+    ptx::tmem_ld_wait(v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long tv = (long long)__float2int_rn(__uint_as_float(v[i]));
+      if (db < kSplit) hi[i] = horner(hi[i], kBeta, tv);
+      else lo[i] = horner(lo[i], kBeta, tv);
+    }
+  }
+  if (p >= d.P) return;
+  const int e_base = ep - kBeta * (kDig + 1);
+  double* orow = d.out + p * d.S;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (h * 8 + i >= d.S) break;
+    const int ec = d.cexp[h * 8 + i];
+    orow[h * 8 + i] = (ep == kNonFiniteRow || ec == kNonFiniteRow)
+                          ? __longlong_as_double(0x7ff8000000000000ll)
+                          : int128_to_double(
+                                (__int128)((unsigned __int128)(__int128)hi[i] << (kBeta * (kDig - kSplit))) + (__int128)lo[i],
+                                e_base + ec);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -210,9 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&bar->tfull[i], 1);
-      ptx::mbar_init(&bar->tempty[i], kEpiWarps);
-      ptx::mbar_init(&bar->rfull[i], kProducerWarps);
-      ptx::mbar_init(&bar->rempty[i], kEpiWarps);
+      ptx::mbar_init(&bar->tempty[i], kProducerWarps);
     }
     ptx::mbar_init(&bar->drain, 1);
     bar->abort_flag = 0;
@@ -234,14 +281,29 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
   const uint32_t tmem_base = bar->tmem_base;
 
   if (warp < kProducerWarps) {
-    // ---------------------------------------------------------------- producers
-    const uint32_t row = (uint32_t)threadIdx.x;  // point row of the tile (TMEM lane)
+    // ------------------------------------------------------- producers (and accumulator drain)
+    const uint32_t q = (uint32_t)(warp & 3);          // TMEM lane quadrant of this warp
+    const uint32_t row = q * 32 + (uint32_t)lane;     // point row of the tile (TMEM lane)
+    const int strm = warp >> 2;                       // column stream of this thread
     int stage = 0;
     uint32_t sphase = 0;
     uint32_t b_issued0 = 0u, b_issued1 = 0u;  // coefficient copies issued per stage (warp 0, lane 0)
     static_assert(kStages == 2, "two stages");
     bool ok = true;
     int64_t local = 0;
+    // The previous tile, drained after this thread produced the next one.
+    int prev_inst = -1, prev_ep = 0;
+    int64_t prev_p0 = 0;
+    auto drain_prev = [&]() -> bool {
+      const uint32_t pacc = (uint32_t)((local - 1) & 1), puse = (uint32_t)(((local - 1) >> 1) & 1);
+      if (!warp_wait(&bar->tfull[pacc], puse, abort_flag, lane)) return false;
+      ptx::tc_fence_after();
+      drain_tile(inst_of(a, prev_inst), prev_p0, tmem_base, pacc, q, row, strm, prev_ep);
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&bar->tempty[pacc]);
+      return true;
+    };
     for (int64_t it = blockIdx.x; it < a.n_items && ok; it += gridDim.x, ++local) {
       int ii;
       int64_t p0;
@@ -250,9 +312,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       const int64_t p = p0 + row;
       const bool valid = p < d.P;
       const double rho = valid ? d.r[p] : 0.0, th = valid ? d.theta[p] : 0.0;
-      // Row exponent: |Z| <= 1 on the unit disc; elsewhere the point's largest |Z| decides.
+      // Row exponent: |Z| <= 1 on the unit disc; elsewhere the point's largest |Z| decides (both
+      // threads of the point walk all of its columns for it).
       int ep = 1;
-      if (!(rho >= 0.0 && rho <= 1.0 && fabs(th) <= 1.79e308)) {
+      if (!(rho >= 0.0 && rho <= 1.0 && isfinite(th))) {
         unsigned long long mx = 0;
         walk_point(d, rho, th, [&](double z) {
           const unsigned long long b = (unsigned long long)__double_as_longlong(z) & 0x7fffffffffffffffull;
@@ -260,33 +323,22 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         });
         ep = scale_exponent(mx);
       }
-      const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
-      if (!warp_wait(&bar->rempty[acc], use ^ 1u, abort_flag, lane)) {
-        fail(abort_flag);
-        ok = false;
-        break;
-      }
-      bar->row_exp[acc][row] = ep;
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&bar->rfull[acc]);
       const bool zero_row = ep == kNonFiniteRow;
       const int shift = kBeta * kDig - (zero_row ? 0 : ep);
 
-      int k = 0;  // K position within the tile
+      int unit = 0;  // this stream's next unit; its global unit is 2 unit + strm
       uint32_t w[kDig][4];
-      double pending = 0.0;
-      bool have_pending = false;
       uint8_t* sA = smem + stage * kStageBytes;
-      // Stores the 16-byte unit completed at K position k (a multiple of 8), opening the stage
-      // (waiting for it to be free, starting its coefficient copy) at its first unit and
-      // handing it to the MMA warp after its last.
-      auto flush_unit = [&]() -> bool {
-        const int kk = (k - 8) % FBK;
-        if (kk == 0) {
-          if (!warp_wait(&bar->empty[stage], sphase ^ 1u, abort_flag, lane)) return false;
+      // This stream's next unit in shared memory (its byte offset within digit tile 0), opening
+      // the stage at the stream's first unit in it: waiting for the stage to be free, stream 0
+      // starting its coefficient copy.  -1 when a bounded wait gave up.
+      auto open_unit = [&]() -> int {
+        const int slot = ((2 * unit + strm) & 3);  // unit slot within the stage (0..3)
+        if (slot == strm) {
+          if (!warp_wait(&bar->empty[stage], sphase ^ 1u, abort_flag, lane)) return -1;
           sA = smem + stage * kStageBytes;
           if (warp == 0 && lane == 0) {
-            const int kc = (k - 8) / FBK;
+            const int kc = unit / 2;
             ptx::mbar_arrive_expect_tx(&bar->bfull[stage], kFusedBChunk);
             ptx::bulk_g2s(sA + kABytes + kBCopyOffset, d.bdig + (size_t)kc * kFusedBChunk, kFusedBChunk,
                           &bar->bfull[stage]);
@@ -294,11 +346,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             else ++b_issued1;
           }
         }
-        const uint32_t off = ptx::sw_offset_b16<kRowBytes>(row, (uint32_t)kk);
-#pragma unroll
-        for (int t = 0; t < kDig; ++t)
-          *reinterpret_cast<uint4*>(sA + t * kASlice + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
-        if (kk == FBK - 8) {
+        return (int)ptx::sw_offset_b16<kRowBytes>(row, (uint32_t)(slot * 8));
+      };
+      // The unit is written: hand the stage to the MMA warp after the stream's last unit in it.
+      auto finish_unit = [&]() {
+        const int slot = ((2 * unit + strm) & 3);
+        ++unit;
+        if (slot == 2 + strm) {
           ptx::fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&bar->full[stage]);
@@ -307,53 +361,183 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             sphase ^= 1u;
           }
         }
+      };
+      auto store_unit = [&]() -> bool {
+        const int off = open_unit();
+        if (off < 0) return false;
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          *reinterpret_cast<uint4*>(sA + t * kASlice + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+        finish_unit();
         return true;
       };
-      // Two consecutive K values (k even): digits, packed in pairs, placed at the unit's word.
-      auto push_pair = [&](double z0, double z1) -> bool {
-        const long long X0 = zero_row ? 0 : to_fixed(z0, shift);
-        const long long X1 = zero_row ? 0 : to_fixed(z1, shift);
-        uint32_t pw[kDig];
-        digit_pair(X0, X1, pw);
-        switch ((k >> 1) & 3) {
-          case 0:
+      // Digits of two consecutive K values into word `word` of the unit (word 0..3): per digit,
+      // the two values' bf16 patterns joined into one 32-bit word.
+      auto put_pair_const = [&](auto word_c, double z0, double z1) {
+        constexpr int word = decltype(word_c)::value;
+        const long long Y0 = (zero_row ? 0 : to_fixed_fast(z0, shift)) + kBias;
+        const long long Y1 = (zero_row ? 0 : to_fixed_fast(z1, shift)) + kBias;
 #pragma unroll
-            for (int t = 0; t < kDig; ++t) w[t][0] = pw[t];
-            break;
-          case 1:
-#pragma unroll
-            for (int t = 0; t < kDig; ++t) w[t][1] = pw[t];
-            break;
-          case 2:
-#pragma unroll
-            for (int t = 0; t < kDig; ++t) w[t][2] = pw[t];
-            break;
-          default:
-#pragma unroll
-            for (int t = 0; t < kDig; ++t) w[t][3] = pw[t];
-            break;
+        for (int t = 0; t < kDig; ++t) {
+          const uint32_t f0 = t == 0 ? __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y0, 0)) - 12582912.0f)
+                                     : __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y0, t)) -
+                                                       8388624.0f);
+          const uint32_t f1 = t == 0 ? __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y1, 0)) - 12582912.0f)
+                                     : __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y1, t)) -
+                                                       8388624.0f);
+          w[t][word] = __byte_perm(f0, f1, 0x7632);
         }
-        k += 2;
-        if ((k & 7) == 0) return flush_unit();
-        return true;
       };
-      walk_point(d, rho, th, [&](double z) {
-        if (!ok) return;
-        if (!have_pending) {
-          pending = z;
-          have_pending = true;
+      // The walk of this stream's columns (Sec. 2 recursion in the plan's rescaled form, Algorithm
+      // 1's column order within the stream).  The recursion runs uniformly from the seeds
+      // q_{-2} = -rho^m, q_{-1} = 0 with (A_0, B_0) = (0, 0) and (A_1, B_1) = ((m+2), (m+1)), so
+      // unrolled steps need no cases; cos/sin(m theta) and rho^m advance by one or two columns
+      // by angle addition and products.
+      const double u = rho * rho;
+      double s1, c1;
+      sincos(th, &s1, &c1);
+      const double c2 = fma(c1, c1, -s1 * s1), s2 = 2.0 * s1 * c1;
+      double cm = 1.0, sm = 0.0, pm = 1.0;
+      int m_prev = -100;
+      const int ncs = d.ncols_s[strm];
+      const int32_t* scol = d.scols + (strm ? d.ncols_s[0] : 0);
+      for (int ci = 0; ci < ncs && ok; ++ci) {
+        const int c = scol[ci];
+        const Column col = d.cols[c];
+        const int m = col.m;
+        if (m == m_prev + 1) {
+          const double cn = fma(cm, c1, -sm * s1);
+          sm = fma(sm, c1, cm * s1);
+          cm = cn;
+          pm *= rho;
+        } else if (m == m_prev + 2) {
+          const double cn = fma(cm, c2, -sm * s2);
+          sm = fma(sm, c2, cm * s2);
+          cm = cn;
+          pm *= u;
+        } else if (m != m_prev) {
+          cm = 1.0;
+          sm = 0.0;
+          if (m != 0) sincos((double)m * th, &sm, &cm);
+          pm = pow_uint(rho, m);
+        }
+        m_prev = m;
+        const double* h = d.table + (size_t)col.table_row * kRow;
+        const int n_steps = col.n_steps;
+        const int4 fc = d.fcols[c];
+        const int kind = fc.x & 255;
+        const double fa = (fc.x >> 8) & 1 ? sm : cm, fb = (fc.x >> 9) & 1 ? sm : cm;
+        double S = 0.0, T = -pm, W = 0.0;
+        // One recursion step N (>= n_steps: a padding step on the last row, its output unused).
+        auto step = [&](int N) -> double {
+          const int Nc = N < n_steps ? N : n_steps - 1;
+          const double* rw = h + (size_t)(kHeaderRows + Nc) * kRow;
+          const double A = N >= 2 ? rw[0] : (N == 1 ? h[4] : 0.0);
+          const double B = N >= 2 ? rw[1] : (N == 1 ? h[8] : 0.0);
+          const double g = fma(A, u, -B);
+          const double qv = fma(g, S, -T);
+          T = S;
+          S = qv;
+          W = rw[3];
+          return qv;
+        };
+        if (kind == kFusedKindTwo) {
+          // Two outputs per step: four steps fill one unit.
+          for (int N0 = 0; N0 < n_steps && ok; N0 += 4) {
+            auto one = [&](auto ic) {
+              constexpr int i = decltype(ic)::value;
+              const double qv = step(N0 + i);
+              const bool live = N0 + i < n_steps;
+              const double R = qv * W;
+              put_pair_const(ic, live ? R * fa : 0.0, live ? R * fb : 0.0);
+            };
+            one(std::integral_constant<int, 0>{});
+            one(std::integral_constant<int, 1>{});
+            one(std::integral_constant<int, 2>{});
+            one(std::integral_constant<int, 3>{});
+            ok = store_unit();
+          }
+        } else if (kind == kFusedKindOne) {
+          // One output per step: eight steps fill one unit.
+          for (int N0 = 0; N0 < n_steps && ok; N0 += 8) {
+            auto two = [&](auto ic) {
+              constexpr int i = decltype(ic)::value;
+              const double q0 = step(N0 + 2 * i);
+              const double R0 = q0 * W;
+              const double q1 = step(N0 + 2 * i + 1);
+              const double R1 = q1 * W;
+              put_pair_const(ic, N0 + 2 * i < n_steps ? R0 * fa : 0.0, N0 + 2 * i + 1 < n_steps ? R1 * fa : 0.0);
+            };
+            two(std::integral_constant<int, 0>{});
+            two(std::integral_constant<int, 1>{});
+            two(std::integral_constant<int, 2>{});
+            two(std::integral_constant<int, 3>{});
+            ok = store_unit();
+          }
         } else {
-          have_pending = false;
-          ok = push_pair(pending, z);
+          // Any other step pattern: outputs one at a time in slot order, each pair of values
+          // written into the open unit as one 32-bit word per digit.
+          const uint2* st = d.steps + col.table_row + kHeaderRows;
+          const int32_t* sp = d.slot_ptr + col.slot_base;
+          int kin = 0, off = 0;  // K position within the open unit, its byte offset
+          double pending = 0.0;
+          bool have = false;
+          auto emit = [&](double z) {
+            if (!have) {
+              pending = z;
+              have = true;
+              return;
+            }
+            have = false;
+            if (!ok) return;
+            if (kin == 0) {
+              off = open_unit();
+              if (off < 0) {
+                ok = false;
+                return;
+              }
+            }
+            uint32_t pw[kDig];
+            digit_pair(zero_row ? 0 : to_fixed_fast(pending, shift), zero_row ? 0 : to_fixed_fast(z, shift), pw);
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) *reinterpret_cast<uint32_t*>(sA + t * kASlice + off + kin * 2) = pw[t];
+            kin += 2;
+            if (kin == 8) {
+              kin = 0;
+              finish_unit();
+            }
+          };
+          for (int N = 0; N < n_steps; ++N) {
+            const double qv = step(N);
+            const uint32_t info = st[N].x;
+            uint32_t cnt = info & 0xffu, flags = info >> 8;
+            if (cnt == 0) continue;
+            const double R = qv * W;
+            if (cnt == kStepIrregular) {
+              for (int sl = sp[N]; sl < sp[N + 1]; ++sl) emit(R * (((uint32_t)__ldg(d.slot_idx + sl) >> 31) ? sm : cm));
+            } else {
+              for (; cnt > 0; --cnt, flags >>= 1) emit(R * ((flags & 1u) ? sm : cm));
+            }
+          }
+          if (have) emit(0.0);
+          while (kin != 0) emit(0.0), emit(0.0);
         }
-      });
-      if (ok && have_pending) ok = push_pair(pending, 0.0);
-      while (ok && (k % FBK) != 0) ok = push_pair(0.0, 0.0);
+      }
+      // Zero units up to the tile's unit count (the same for both streams, whole stages).
+#pragma unroll
+      for (int t = 0; t < kDig; ++t) w[t][0] = w[t][1] = w[t][2] = w[t][3] = 0u;
+      while (ok && unit < d.units) ok = store_unit();
+      // Drain the previous tile's accumulator now that this one is on its way.
+      if (ok && prev_inst >= 0) ok = drain_prev();
       if (!ok) {
         fail(abort_flag);
         break;
       }
+      prev_inst = ii;
+      prev_p0 = p0;
+      prev_ep = ep;
     }
+    if (ok && prev_inst >= 0 && !drain_prev()) fail(abort_flag);
     // Every coefficient copy this CTA issued has landed before the CTA may exit (a wait that
     // ignores the abort flag, still bounded).
     if (warp == 0 && lane == 0) {
@@ -374,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         item_of(a, it, ii, p0);
         const int KC = inst_of(a, ii).KC;
         const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
-        if (!ptx::mbar_wait(&bar->tempty[acc], use ^ 1u, abort_flag)) {
+        if (!ptx::mbar_wait_sleepy(&bar->tempty[acc], use ^ 1u, abort_flag, 200)) {
           fail(abort_flag);
           break;
         }
@@ -382,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         const uint32_t d_tmem = tmem_base + acc * kAccStride;
         bool ok = true;
         for (int kc = 0; kc < KC; ++kc) {
-          if (!ptx::mbar_wait(&bar->full[stage], phase, abort_flag) ||
+          if (!ptx::mbar_wait_sleepy(&bar->full[stage], phase, abort_flag, 200) ||
               !ptx::mbar_wait(&bar->bfull[stage], phase, abort_flag)) {
             fail(abort_flag);
             ok = false;
@@ -416,65 +600,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       ptx::mma_commit(&bar->drain);
       int never = 0;
       if (!ptx::mbar_wait(&bar->drain, 0u, &never)) atomicOr(&g_fused_error, 1u);
-    }
-  } else {
-    // ---------------------------------------------------------------- epilogue
-    const uint32_t q = (uint32_t)(warp & 3);  // TMEM lane quadrant this warp may read
-    const uint32_t row = q * 32 + lane;
-    int64_t local = 0;
-    for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x, ++local) {
-      int ii;
-      int64_t p0;
-      item_of(a, it, ii, p0);
-      const FusedInst& d = inst_of(a, ii);
-      const uint32_t acc = (uint32_t)(local & 1), use = (uint32_t)((local >> 1) & 1);
-      if (!warp_wait(&bar->tfull[acc], use, abort_flag, lane) || !warp_wait(&bar->rfull[acc], use, abort_flag, lane)) {
-        fail(abort_flag);
-        break;
-      }
-      ptx::tc_fence_after();
-      const int ep = bar->row_exp[acc][row];
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&bar->rempty[acc]);
-      const int64_t p = p0 + row;
-      const bool store = p < d.P;
-      const int e_base = ep - kBeta * (kDig + 1);
-#pragma unroll 1
-      for (int h = 0; h < FNS / 8; ++h) {
-        long long hi[8] = {}, lo[8] = {};
-#pragma unroll
-        for (int db = 0; db < kDig; ++db) {
-          uint32_t v[8];
-          ptx::tmem_ld_32x32b_x8(tmem_base + ((q * 32u) << 16) + acc * kAccStride + (uint32_t)(db * FNS + h * 8), v);
-          ptx::tmem_ld_wait(v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const long long tv = (long long)__float2int_rn(__uint_as_float(v[i]));
-            if (db < kSplit) hi[i] = horner(hi[i], kBeta, tv);
-            else lo[i] = horner(lo[i], kBeta, tv);
-          }
-        }
-        if (store) {
-          double out[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int ec = d.cexp[h * 8 + i];
-            out[i] = (ep == kNonFiniteRow || ec == kNonFiniteRow)
-                         ? __longlong_as_double(0x7ff8000000000000ll)
-                         : int128_to_double(
-                               (__int128)((unsigned __int128)(__int128)hi[i] << (kBeta * (kDig - kSplit))) +
-                                   (__int128)lo[i],
-                               e_base + ec);
-          }
-          double* orow = d.out + p * d.S;
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (h * 8 + i < d.S) orow[h * 8 + i] = out[i];
-        }
-      }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&bar->tempty[acc]);
     }
   }
   ptx::tc_fence_before();
@@ -523,7 +648,8 @@ __global__ void __launch_bounds__(256) fused_cexp_kernel(FusedArgs a, int64_t n_
   }
 }
 
-// Coefficient digits in the plan's slot order: thread = (chunk, set, group of 8 modes); the
+// Coefficient digits in the fused layout's K order (the plan's slot order, each column padded to
+// a multiple of 8 positions): thread = (chunk, set, group of 8 positions); the
 // 8 values' 11 digits are written as one 16-byte unit into each digit block's row for the set.
 __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int32_t* chunk_inst, int64_t n_chunks) {
   const int64_t total = n_chunks * FNS * (FBK / 8);
@@ -541,8 +667,9 @@ __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int
     for (int e = 0; e < 8; ++e) {
       const int64_t k = kc * FBK + q * 8 + e;
       X[e] = 0;
-      if (use && k < d.J) {
-        const int64_t j = (int64_t)((uint32_t)__ldg(d.slot_idx + k) & 0x7fffffffu);
+      const int32_t slot = (use && k < d.Kp) ? __ldg(d.kperm + k) : -1;
+      if (slot >= 0) {
+        const int64_t j = (int64_t)((uint32_t)__ldg(d.slot_idx + slot) & 0x7fffffffu);
         X[e] = to_fixed(d.coeffs[j * d.S + s], kBeta * kDig - ec);
       }
     }
@@ -589,8 +716,8 @@ zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_
 zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
                             int64_t S, double* out, cudaStream_t stream) {
   const int64_t J = plan->n_modes;
-  if (S > kFusedMaxSets || J > kFusedMaxModes)
-    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 modes");
+  if (S > kFusedMaxSets || plan->fused_kpad > kFusedMaxModes)
+    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 padded modes");
   FusedArgs a;
   FusedInst& d = a.single;
   d.cols = plan->dev.cols;
@@ -598,8 +725,15 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.steps = plan->dev.split_step;
   d.slot_ptr = plan->dev.slot_ptr;
   d.slot_idx = plan->dev.slot_idx;
+  d.fcols = plan->dev.fused_col;
+  d.scols = (const int32_t*)(plan->dev.fused_col + plan->cols.size());
+  d.ncols_s[0] = plan->fused_ncols[0];
+  d.ncols_s[1] = plan->fused_ncols[1];
+  d.units = plan->fused_units;
+  d.kperm = plan->dev.fused_kperm;
+  d.Kp = plan->fused_kpad;
   d.n_cols = (int32_t)plan->cols.size();
-  d.KC = (int32_t)((J + FBK - 1) / FBK);
+  d.KC = (int32_t)((plan->fused_kpad + FBK - 1) / FBK);
   d.kc_base = 0;
   d.J = J;
   d.P = P;

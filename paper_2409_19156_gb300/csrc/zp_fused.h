@@ -11,8 +11,8 @@ namespace zp {
 constexpr int kFusedBeta = 5;       // bits per digit
 constexpr int kFusedDigits = 11;    // digits per value: 55 fraction bits
 constexpr int kFusedMaxSets = 16;   // coefficient sets per launch
-// Longest contraction whose diagonal sums stay exact integers in float32:
-// K * 2^(2 beta) * (1 + (digits - 2) / 4) < 2^24.
+// Longest contraction (K positions of the fused layout, padding included) whose diagonal sums
+// stay exact integers in float32: K * 2^(2 beta) * (1 + (digits - 2) / 4) < 2^24.
 constexpr int64_t kFusedMaxModes = 5041;
 // Bytes of one 32-mode chunk of coefficient digits: 11 digit blocks of 16 sets x 64 bytes, each
 // row the tensor core's 64-byte swizzled K-major layout.
@@ -40,8 +40,14 @@ struct FusedInst {
   const uint2* steps = nullptr;  // the plan's per-step slot counts and sin flags
   const int32_t* slot_ptr = nullptr;
   const int32_t* slot_idx = nullptr;
+  const int4* fcols = nullptr;       // the plan's fused contraction layout per column
+  const int32_t* scols = nullptr;    // columns of stream 0, then of stream 1 (walk order)
+  const int32_t* kperm = nullptr;    // slot of every K position of that layout, -1 for padding
+  int64_t Kp = 0;                    // K positions of that layout
+  int32_t ncols_s[2] = {0, 0};       // columns per stream
+  int32_t units = 0;                 // 8-value units per stream
   int32_t n_cols = 0;
-  int32_t KC = 0;        // 32-mode chunks of the contraction
+  int32_t KC = 0;        // 32-position chunks of the contraction
   int64_t kc_base = 0;   // first chunk of this instance in the launch's chunk numbering
   int64_t J = 0, P = 0, S = 0;
   const double* r = nullptr;
@@ -73,8 +79,8 @@ struct FusedArgs {
 zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
                        cudaStream_t stream);
 
-// F = Z C for one plan with S <= kFusedMaxSets and n_modes <= kFusedMaxModes (scratch for the
-// coefficient digits from the library's pool).
+// F = Z C for one plan with S <= kFusedMaxSets and plan->fused_kpad <= kFusedMaxModes (scratch
+// for the coefficient digits from the library's pool).
 zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
                             int64_t S, double* out, cudaStream_t stream);
 

@@ -36,7 +36,16 @@ struct Column {
 //   .y = bits of the float32 weight W0_N (the float64 value truncated toward zero).
 constexpr uint32_t kStepIrregular = 255u;
 constexpr int kStepMaxFlags = 24;
-constexpr int kPlanSections = 7;
+constexpr int kPlanSections = 9;
+
+// Contraction layout of the fused float64-accurate series: the columns are dealt to two streams
+// (two producer threads per point); a column's outputs fill whole 8-value units (16-byte
+// operand units, zero padded), and unit j of stream s is the global unit 2 j + s.  Per column
+// (int4): x = kind | (sin flag of the step's first output) << 8 | (of its second) << 9 (kind 1:
+// every step has one output, kind 2: every step has two outputs in the same cos/sin order,
+// kind 0: anything else), y = stream, z = first unit within the stream, w = number of outputs.
+// The columns of stream 0 then of stream 1, in walk order, follow the n_columns records.
+constexpr int kFusedKindGeneric = 0, kFusedKindOne = 1, kFusedKindTwo = 2;
 
 // float32 bits of a float64 given as its high and low words, by truncating the significand:
 // magnitudes below the float32 normal range give a signed zero, finite ones above it
@@ -62,6 +71,8 @@ struct DevicePlanTables {
   int32_t* mode_col = nullptr;  // [n_modes]: column index of every mode
   int32_t* mode_N = nullptr;    // [n_modes]: Jacobi degree of every mode
   uint2* split_step = nullptr;  // [table rows]: step descriptors of the split basis
+  int4* fused_col = nullptr;    // [columns]: fused contraction layout (see kFusedKind*)
+  int32_t* fused_kperm = nullptr;  // [fused_kpad]: slot of every K position, -1 for padding
 };
 
 }  // namespace zp
@@ -76,6 +87,11 @@ struct zp_plan {
   std::vector<double> table;         // rows of kRow doubles
   std::vector<int32_t> slot_ptr, slot_idx, mode_col, mode_N;
   std::vector<uint32_t> split_step;  // 2 words per table row
+  std::vector<int32_t> fused_col;    // 4 words per column, then the streams' column lists
+  std::vector<int32_t> fused_kperm;
+  int64_t fused_kpad = 0;            // K positions of the fused layout (multiple of 32)
+  int32_t fused_ncols[2] = {0, 0};   // columns per stream
+  int32_t fused_units = 0;           // 8-value units per stream (even)
   zp::DevicePlanTables dev;
   size_t device_bytes = 0;
   void* dev_block = nullptr;  // single allocation backing dev.*
@@ -92,8 +108,9 @@ void clear_error();
 zp_status build_plan(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan** out);
 // Host half only: validates and fills the host tables of *p (no device memory touched).
 zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, zp_plan* p);
-// Byte size of the plan's device tables; offsets[0..6] of cols, table, slot_ptr, slot_idx,
-// mode_col, mode_N, split_step inside that block (256-byte aligned sections).
+// Byte size of the plan's device tables; offsets[0..8] of cols, table, slot_ptr, slot_idx,
+// mode_col, mode_N, split_step, fused_col, fused_kperm inside that block (256-byte aligned
+// sections).
 size_t plan_device_layout(const zp_plan* p, size_t offsets[kPlanSections]);
 // Points p->dev at `base` (laid out as plan_device_layout) and copies the host tables there,
 // with cudaMemcpyAsync on `stream` when async, else synchronously.

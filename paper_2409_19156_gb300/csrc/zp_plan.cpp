@@ -190,6 +190,63 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
       p->split_step[2 * r + 1] = trunc_float_bits((uint32_t)(wbits >> 32), (uint32_t)wbits);
     }
   }
+  // Fused contraction layout.  The columns are dealt to two streams (two producer threads per
+  // point) in walk order, each column to the stream with fewer 8-value units so far; each
+  // column's outputs fill whole units (slot order, zero padded), and the K order interleaves
+  // the streams unit by unit: unit j of stream s is global unit 2 j + s.
+  const size_t nc = p->cols.size();
+  p->fused_col.assign(5 * nc, 0);
+  int32_t units[2] = {0, 0};
+  std::vector<int32_t> scol[2];
+  std::vector<int32_t> col_first(nc, 0), col_stream(nc, 0);
+  for (size_t c = 0; c < nc; ++c) {
+    const Column& col = p->cols[c];
+    const int32_t first = p->slot_ptr[col.slot_base], last = p->slot_ptr[(size_t)col.slot_base + col.n_steps];
+    int kind = -1;
+    uint32_t fa = 0, fb = 0;
+    for (int32_t N = 0; N < col.n_steps; ++N) {
+      const size_t s = (size_t)col.slot_base + N;
+      const int32_t b = p->slot_ptr[s], cnt = p->slot_ptr[s + 1] - b;
+      const uint32_t a0 = cnt > 0 ? (uint32_t)p->slot_idx[b] >> 31 : 0u;
+      const uint32_t a1 = cnt > 1 ? (uint32_t)p->slot_idx[(size_t)b + 1] >> 31 : 0u;
+      const int k = (cnt == 1) ? kFusedKindOne : (cnt == 2 ? kFusedKindTwo : kFusedKindGeneric);
+      if (N == 0) {
+        kind = k;
+        fa = a0;
+        fb = a1;
+      } else if (k != kind || a0 != fa || (k == kFusedKindTwo && a1 != fb)) {
+        kind = kFusedKindGeneric;
+      }
+    }
+    if (kind < 0) kind = kFusedKindGeneric;
+    const int32_t nvals = last - first;
+    const int st = units[1] < units[0] ? 1 : 0;
+    col_stream[c] = st;
+    col_first[c] = units[st];
+    p->fused_col[4 * c] = kind | (int32_t)(fa << 8) | (int32_t)(fb << 9);
+    p->fused_col[4 * c + 1] = st;
+    p->fused_col[4 * c + 2] = units[st];
+    p->fused_col[4 * c + 3] = nvals;
+    units[st] += (nvals + 7) / 8;
+    scol[st].push_back((int32_t)c);
+  }
+  for (int st = 0; st < 2; ++st)
+    for (size_t i = 0; i < scol[st].size(); ++i) p->fused_col[4 * nc + (st ? scol[0].size() : 0) + i] = scol[st][i];
+  p->fused_ncols[0] = (int32_t)scol[0].size();
+  p->fused_ncols[1] = (int32_t)scol[1].size();
+  // Units per stream: the larger count, rounded so that both streams fill whole 4-unit stages.
+  p->fused_units = std::max(units[0], units[1]);
+  p->fused_units += p->fused_units & 1;
+  p->fused_kperm.assign((size_t)p->fused_units * 2 * 8, -1);
+  for (size_t c = 0; c < nc; ++c) {
+    const Column& col = p->cols[c];
+    const int32_t first = p->slot_ptr[col.slot_base];
+    for (int32_t i = 0; i < p->fused_col[4 * c + 3]; ++i) {
+      const int32_t unit = 2 * (col_first[c] + i / 8) + col_stream[c];
+      p->fused_kperm[(size_t)unit * 8 + i % 8] = first + i;
+    }
+  }
+  p->fused_kpad = (int64_t)p->fused_kperm.size();
   return ZP_OK;
 }
 
@@ -200,6 +257,8 @@ size_t plan_device_layout(const zp_plan* p, size_t offsets[kPlanSections]) {
   const size_t b_sidx = align_up(std::max<size_t>(p->slot_idx.size(), 1) * sizeof(int32_t), 256);
   const size_t b_mode = align_up(std::max<int64_t>(p->n_modes, 1) * sizeof(int32_t), 256);
   const size_t b_step = align_up(std::max<size_t>(p->split_step.size(), 2) * sizeof(uint32_t), 256);
+  const size_t b_fcol = align_up(std::max<size_t>(p->fused_col.size(), 4) * sizeof(int32_t), 256);
+  const size_t b_fperm = align_up(std::max<size_t>(p->fused_kperm.size(), 1) * sizeof(int32_t), 256);
   offsets[0] = 0;
   offsets[1] = b_cols;
   offsets[2] = b_cols + b_table;
@@ -207,7 +266,9 @@ size_t plan_device_layout(const zp_plan* p, size_t offsets[kPlanSections]) {
   offsets[4] = b_cols + b_table + b_sptr + b_sidx;
   offsets[5] = b_cols + b_table + b_sptr + b_sidx + b_mode;
   offsets[6] = b_cols + b_table + b_sptr + b_sidx + 2 * b_mode;
-  return offsets[6] + b_step;
+  offsets[7] = offsets[6] + b_step;
+  offsets[8] = offsets[7] + b_fcol;
+  return offsets[8] + b_fperm;
 }
 
 zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool async) {
@@ -221,6 +282,8 @@ zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool asyn
   p->dev.mode_col = (int32_t*)(base + off[4]);
   p->dev.mode_N = (int32_t*)(base + off[5]);
   p->dev.split_step = (uint2*)(base + off[6]);
+  p->dev.fused_col = (int4*)(base + off[7]);
+  p->dev.fused_kperm = (int32_t*)(base + off[8]);
   struct Part {
     void* dst;
     const void* src;
@@ -233,6 +296,8 @@ zp_status plan_upload(zp_plan* p, void* base_ptr, cudaStream_t stream, bool asyn
       {p->dev.mode_col, p->mode_col.data(), p->mode_col.size() * sizeof(int32_t)},
       {p->dev.mode_N, p->mode_N.data(), p->mode_N.size() * sizeof(int32_t)},
       {p->dev.split_step, p->split_step.data(), p->split_step.size() * sizeof(uint32_t)},
+      {p->dev.fused_col, p->fused_col.data(), p->fused_col.size() * sizeof(int32_t)},
+      {p->dev.fused_kperm, p->fused_kperm.data(), p->fused_kperm.size() * sizeof(int32_t)},
   };
   for (const Part& part : parts) {
     if (part.bytes == 0) continue;

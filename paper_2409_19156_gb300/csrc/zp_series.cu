@@ -348,7 +348,7 @@ zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double
   if (prec == ZP_PREC_FP64) return series_eval_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
   if (prec == ZP_PREC_FP64_EMULATED) {
     // Few sets: the fused kernel (basis generated on chip, no basis or partial sums in HBM).
-    if (n_sets <= kFusedMaxSets && plan->n_modes <= kFusedMaxModes)
+    if (n_sets <= kFusedMaxSets && plan->fused_kpad <= kFusedMaxModes)
       return fused_series_eval(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
     return series_eval_emulated_fp64(plan, r, theta, n_points, coeffs, n_sets, (double*)out, st);
   }
