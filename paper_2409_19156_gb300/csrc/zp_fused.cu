@@ -6,9 +6,10 @@
 //
 // contracted by error-free slicing (Ozaki et al., a published scheme, written here from its
 // definition): every Z_j(p) is scaled by 2^-e_p (e_p = 1 for 0 <= r <= 1, where |Z| <= 1;
-// else from a first pass over the point's modes), rounded to a fixed-point integer with 55
+// else from a first pass over the point's modes), truncated to a fixed-point integer with 55
 // fraction bits and cut into 11 balanced base-32 digits a_1..a_11 (integers of at most 6 bits,
-// exact in bfloat16); the coefficients are cut the same way per set (b_1..b_11, scale 2^-e_s).
+// exact in bfloat16); the coefficients are rounded to the same fixed point and cut the same way
+// per set (b_1..b_11, scale 2^-e_s).
 // Then Z C = 2^(e_p + e_s) sum_d T_d 2^(-5 d) with T_d = sum_{t+u=d} sum_j a_t b_u, kept for
 // d <= 12 (the dropped pairs weigh below 2^-60 of the scales).
 //
@@ -120,15 +121,18 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// round-half-even(z * 2^shift) as an int64 (|z| 2^shift < 2^55): the scaling is an integer add
-// to the exponent field (exact while the result stays normal; anything that would leave the
-// normal range rounds to 0 anyway) and the conversion one float64 -> int64 instruction, which
-// the conversion unit issues far faster than GB300's float64 pipe.  z must be finite.
-__device__ __forceinline__ long long to_fixed_fast(double z, int shift) {
-  const long long b = __double_as_longlong(z);
-  const int ef = (int)((b >> 52) & 0x7ff);
-  const long long sb = (ef + shift > 0) ? b + ((long long)shift << 52) : 0ll;
-  return __double2ll_rn(__longlong_as_double(sb));
+// z * 2^shift truncated toward zero to an int64 (|z| 2^shift < 2^55, z finite), from z's bits
+// on the integer pipe: the float64 -> int64 conversion instruction issues on GB300's float64
+// pipe, the one this kernel is bound by.  Truncation instead of rounding leaves an error below
+// 2^-shift per value (one unit of the last of the 55 fraction bits).
+__device__ __forceinline__ long long to_fixed_trunc(double z, int shift) {
+  const uint32_t hi = (uint32_t)__double2hiint(z), lo = (uint32_t)__double2loint(z);
+  const int ef = (int)((hi >> 20) & 0x7ffu);
+  const int sh = ef - 1075 + shift;  // |z| 2^shift = m 2^sh with m the 53-bit significand
+  const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+  unsigned long long mag = sh >= 0 ? (m << (sh & 63)) : (m >> (-sh < 63 ? -sh : 63));
+  mag = ef == 0 ? 0ull : mag;  // zero (and subnormals, far below the last fraction bit)
+  return (hi >> 31) ? -(long long)mag : (long long)mag;
 }
 
 __device__ __forceinline__ void fail(volatile int* abort_flag) {
@@ -375,8 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       // the two values' bf16 patterns joined into one 32-bit word.
       auto put_pair_const = [&](auto word_c, double z0, double z1) {
         constexpr int word = decltype(word_c)::value;
-        const long long Y0 = (zero_row ? 0 : to_fixed_fast(z0, shift)) + kBias;
-        const long long Y1 = (zero_row ? 0 : to_fixed_fast(z1, shift)) + kBias;
+        const long long Y0 = (zero_row ? 0 : to_fixed_trunc(z0, shift)) + kBias;
+        const long long Y1 = (zero_row ? 0 : to_fixed_trunc(z1, shift)) + kBias;
 #pragma unroll
         for (int t = 0; t < kDig; ++t) {
           const uint32_t f0 = t == 0 ? __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y0, 0)) - 12582912.0f)
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
               }
             }
             uint32_t pw[kDig];
-            digit_pair(zero_row ? 0 : to_fixed_fast(pending, shift), zero_row ? 0 : to_fixed_fast(z, shift), pw);
+            digit_pair(zero_row ? 0 : to_fixed_trunc(pending, shift), zero_row ? 0 : to_fixed_trunc(z, shift), pw);
 #pragma unroll
             for (int t = 0; t < kDig; ++t) *reinterpret_cast<uint32_t*>(sA + t * kASlice + off + kin * 2) = pw[t];
             kin += 2;
