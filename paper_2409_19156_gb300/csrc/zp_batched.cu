@@ -530,11 +530,14 @@ zp_status build_fused(zp_batch* b) {
     d.steps = p->dev.split_step;
     d.slot_ptr = p->dev.slot_ptr;
     d.slot_idx = p->dev.slot_idx;
+    d.mode_col = p->dev.mode_col;
+    d.mode_N = p->dev.mode_N;
     d.fcols = p->dev.fused_col;
   d.scols = (const int32_t*)(p->dev.fused_col + p->cols.size());
   d.ncols_s[0] = p->fused_ncols[0];
   d.ncols_s[1] = p->fused_ncols[1];
   d.units = p->fused_units;
+    d.ep_disc = p->fused_ep;
     d.kperm = p->dev.fused_kperm;
     d.Kp = in.n_modes > 0 ? p->fused_kpad : 0;
     d.n_cols = (int32_t)p->cols.size();

@@ -142,7 +142,8 @@ __device__ __forceinline__ void fail(volatile int* abort_flag) {
 
 // The float64 walk of one point over every column of its plan (Sec. 2 recursion, rescaled as
 // in the plan's tables: Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2}, R = W0_N Q_N), calling
-// emit(z) for every output slot in the plan's slot order.
+// emit(Q_N cos/sin(m theta)) for every output slot in the plan's slot order: the values this
+// kernel digitises (the weight W0_N travels with the coefficients).
 template <typename Emit>
 __device__ __forceinline__ void walk_point(const FusedInst& d, double rho, double th, Emit&& emit) {
   const double u = rho * rho;
@@ -185,14 +186,13 @@ __device__ __forceinline__ void walk_point(const FusedInst& d, double rho, doubl
       const uint32_t info = st[N].x;
       uint32_t cnt = info & 0xffu, flags = info >> 8;
       if (cnt == 0) continue;
-      const double R = q * row[3];
       if (cnt == kStepIrregular) {
         for (int s = sp[N]; s < sp[N + 1]; ++s) {
           const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
-          emit(R * ((code >> 31) ? sm : cm));
+          emit(q * ((code >> 31) ? sm : cm));
         }
       } else {
-        for (; cnt > 0; --cnt, flags >>= 1) emit(R * ((flags & 1u) ? sm : cm));
+        for (; cnt > 0; --cnt, flags >>= 1) emit(q * ((flags & 1u) ? sm : cm));
       }
     }
   }
@@ -316,16 +316,19 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       const int64_t p = p0 + row;
       const bool valid = p < d.P;
       const double rho = valid ? d.r[p] : 0.0, th = valid ? d.theta[p] : 0.0;
-      // Row exponent: |Z| <= 1 on the unit disc; elsewhere the point's largest |Z| decides (both
-      // threads of the point walk all of its columns for it).
-      int ep = 1;
+      // Row exponent: on the unit disc |R| <= 1, so |Q cos/sin| <= 1 / w_N < 2^ep_disc; elsewhere
+      // the point's largest digitised value decides (both threads of the point walk all of its
+      // columns for it).
+      int ep = d.ep_disc;
       if (!(rho >= 0.0 && rho <= 1.0 && isfinite(th))) {
         unsigned long long mx = 0;
+        bool bad = false;
         walk_point(d, rho, th, [&](double z) {
           const unsigned long long b = (unsigned long long)__double_as_longlong(z) & 0x7fffffffffffffffull;
           mx = b > mx ? b : mx;
+          bad |= !isfinite(z);
         });
-        ep = scale_exponent(mx);
+        ep = bad ? kNonFiniteRow : scale_exponent(mx);
       }
       const bool zero_row = ep == kNonFiniteRow;
       const int shift = kBeta * kDig - (zero_row ? 0 : ep);
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         const int4 fc = d.fcols[c];
         const int kind = fc.x & 255;
         const double fa = (fc.x >> 8) & 1 ? sm : cm, fb = (fc.x >> 9) & 1 ? sm : cm;
-        double S = 0.0, T = -pm, W = 0.0;
+        double S = 0.0, T = -pm;
         // One recursion step N (>= n_steps: a padding step on the last row, its output unused).
         auto step = [&](int N) -> double {
           const int Nc = N < n_steps ? N : n_steps - 1;
@@ -442,7 +445,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           const double qv = fma(g, S, -T);
           T = S;
           S = qv;
-          W = rw[3];
           return qv;
         };
         if (kind == kFusedKindTwo) {
@@ -452,8 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
               constexpr int i = decltype(ic)::value;
               const double qv = step(N0 + i);
               const bool live = N0 + i < n_steps;
-              const double R = qv * W;
-              put_pair_const(ic, live ? R * fa : 0.0, live ? R * fb : 0.0);
+              put_pair_const(ic, live ? qv * fa : 0.0, live ? qv * fb : 0.0);
             };
             one(std::integral_constant<int, 0>{});
             one(std::integral_constant<int, 1>{});
@@ -467,10 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             auto two = [&](auto ic) {
               constexpr int i = decltype(ic)::value;
               const double q0 = step(N0 + 2 * i);
-              const double R0 = q0 * W;
               const double q1 = step(N0 + 2 * i + 1);
-              const double R1 = q1 * W;
-              put_pair_const(ic, N0 + 2 * i < n_steps ? R0 * fa : 0.0, N0 + 2 * i + 1 < n_steps ? R1 * fa : 0.0);
+              // m = 0: the angular factor is 1 (no product)
+              const double z0 = m == 0 ? q0 : q0 * fa, z1 = m == 0 ? q1 : q1 * fa;
+              put_pair_const(ic, N0 + 2 * i < n_steps ? z0 : 0.0, N0 + 2 * i + 1 < n_steps ? z1 : 0.0);
             };
             two(std::integral_constant<int, 0>{});
             two(std::integral_constant<int, 1>{});
@@ -516,11 +517,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             const uint32_t info = st[N].x;
             uint32_t cnt = info & 0xffu, flags = info >> 8;
             if (cnt == 0) continue;
-            const double R = qv * W;
             if (cnt == kStepIrregular) {
-              for (int sl = sp[N]; sl < sp[N + 1]; ++sl) emit(R * (((uint32_t)__ldg(d.slot_idx + sl) >> 31) ? sm : cm));
+              for (int sl = sp[N]; sl < sp[N + 1]; ++sl) emit(qv * (((uint32_t)__ldg(d.slot_idx + sl) >> 31) ? sm : cm));
             } else {
-              for (; cnt > 0; --cnt, flags >>= 1) emit(R * ((flags & 1u) ? sm : cm));
+              for (; cnt > 0; --cnt, flags >>= 1) emit(qv * ((flags & 1u) ? sm : cm));
             }
           }
           if (have) emit(0.0);
@@ -614,8 +614,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
   }
 }
 
-// Set scale exponents: cexp[s] = e with 2^e > max_j |C[j][s]| (kNonFiniteRow for a set holding
-// an infinity or a NaN), one block per instance, sets past S get 0.
+// The recursion weight W0_N of mode j (the plan's table): the fused kernel digitises Q_N trig and
+// contracts it with W0_N C[j][s].
+__device__ __forceinline__ double mode_weight(const FusedInst& d, int64_t j) {
+  const Column col = d.cols[d.mode_col[j]];
+  return d.table[((size_t)col.table_row + kHeaderRows + d.mode_N[j]) * kRow + 3];
+}
+
+// Set scale exponents: cexp[s] = e with 2^e > max_j |W0_N(j) C[j][s]| (kNonFiniteRow for a set
+// holding an infinity or a NaN), one block per instance, sets past S get 0.
 __global__ void __launch_bounds__(256) fused_cexp_kernel(FusedArgs a, int64_t n_inst) {
   __shared__ unsigned long long red[FNS][8];
   const int64_t inst = blockIdx.x;
@@ -625,11 +632,12 @@ __global__ void __launch_bounds__(256) fused_cexp_kernel(FusedArgs a, int64_t n_
 #pragma unroll
   for (int s = 0; s < FNS; ++s) mx[s] = 0;
   for (int64_t j = threadIdx.x; j < d.J; j += blockDim.x) {
+    const double wj = mode_weight(d, j);
 #pragma unroll
     for (int s = 0; s < FNS; ++s) {
       if (s < d.S) {
         const unsigned long long b =
-            (unsigned long long)__double_as_longlong(d.coeffs[j * d.S + s]) & 0x7fffffffffffffffull;
+            (unsigned long long)__double_as_longlong(wj * d.coeffs[j * d.S + s]) & 0x7fffffffffffffffull;
         mx[s] = b > mx[s] ? b : mx[s];
       }
     }
@@ -674,7 +682,7 @@ __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int
       const int32_t slot = (use && k < d.Kp) ? __ldg(d.kperm + k) : -1;
       if (slot >= 0) {
         const int64_t j = (int64_t)((uint32_t)__ldg(d.slot_idx + slot) & 0x7fffffffu);
-        X[e] = to_fixed(d.coeffs[j * d.S + s], kBeta * kDig - ec);
+        X[e] = to_fixed(mode_weight(d, j) * d.coeffs[j * d.S + s], kBeta * kDig - ec);
       }
     }
     uint32_t w[kDig][4];
@@ -729,11 +737,14 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.steps = plan->dev.split_step;
   d.slot_ptr = plan->dev.slot_ptr;
   d.slot_idx = plan->dev.slot_idx;
+  d.mode_col = plan->dev.mode_col;
+  d.mode_N = plan->dev.mode_N;
   d.fcols = plan->dev.fused_col;
   d.scols = (const int32_t*)(plan->dev.fused_col + plan->cols.size());
   d.ncols_s[0] = plan->fused_ncols[0];
   d.ncols_s[1] = plan->fused_ncols[1];
   d.units = plan->fused_units;
+  d.ep_disc = plan->fused_ep;
   d.kperm = plan->dev.fused_kperm;
   d.Kp = plan->fused_kpad;
   d.n_cols = (int32_t)plan->cols.size();

@@ -40,12 +40,15 @@ struct FusedInst {
   const uint2* steps = nullptr;  // the plan's per-step slot counts and sin flags
   const int32_t* slot_ptr = nullptr;
   const int32_t* slot_idx = nullptr;
+  const int32_t* mode_col = nullptr;  // column of every mode
+  const int32_t* mode_N = nullptr;    // Jacobi degree of every mode
   const int4* fcols = nullptr;       // the plan's fused contraction layout per column
   const int32_t* scols = nullptr;    // columns of stream 0, then of stream 1 (walk order)
   const int32_t* kperm = nullptr;    // slot of every K position of that layout, -1 for padding
   int64_t Kp = 0;                    // K positions of that layout
   int32_t ncols_s[2] = {0, 0};       // columns per stream
   int32_t units = 0;                 // 8-value units per stream
+  int32_t ep_disc = 1;               // row scale exponent for points on the unit disc
   int32_t n_cols = 0;
   int32_t KC = 0;        // 32-position chunks of the contraction
   int64_t kc_base = 0;   // first chunk of this instance in the launch's chunk numbering

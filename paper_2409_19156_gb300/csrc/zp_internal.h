@@ -92,6 +92,7 @@ struct zp_plan {
   int64_t fused_kpad = 0;            // K positions of the fused layout (multiple of 32)
   int32_t fused_ncols[2] = {0, 0};   // columns per stream
   int32_t fused_units = 0;           // 8-value units per stream (even)
+  int32_t fused_ep = 1;              // row scale exponent of the fused kernel on the unit disc
   zp::DevicePlanTables dev;
   size_t device_bytes = 0;
   void* dev_block = nullptr;  // single allocation backing dev.*

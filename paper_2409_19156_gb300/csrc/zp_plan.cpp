@@ -12,6 +12,7 @@
 //   Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2},  A_N = 2 a_N w_{N-1}/w_N, B_N = (a_N+b_N) w_{N-1}/w_N
 // and saves one multiply per derivative lane per step; stores multiply by W_k = k! w_N.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -247,6 +248,20 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
     }
   }
   p->fused_kpad = (int64_t)p->fused_kperm.size();
+  // The fused kernel digitises Q_N cos/sin(m theta) and carries the weight w_N on the
+  // coefficient side; on the unit disc |R| <= 1, so |Q| <= 1 / w_N: the row scale 2^e covers
+  // the largest 1 / w_N of the plan's outputs (with a margin for the recursion's rounding).
+  double inv_w = 1.0;
+  for (const Column& col : p->cols)
+    for (int32_t N = 0; N < col.n_steps; ++N) {
+      const size_t s = (size_t)col.slot_base + N;
+      if (p->slot_ptr[s + 1] == p->slot_ptr[s]) continue;
+      const double w = p->table[((size_t)col.table_row + kHeaderRows + N) * kRow + 3];
+      inv_w = std::max(inv_w, 1.0 / w);
+    }
+  int e = 0;
+  while (std::ldexp(1.0, e) <= inv_w * (1.0 + 1e-9)) ++e;
+  p->fused_ep = e;
   return ZP_OK;
 }
 

@@ -73,13 +73,16 @@ def test_fused_points_off_the_disc_and_non_finite():
     r[10:20] = np.linspace(1.0, 1.4, 10)
     r[20:25] = -np.linspace(0.1, 0.9, 5)
     r[7] = np.nan
-    th[8] = np.nan
+    th[8] = np.inf
+    th[9] = np.nan
+    th[30] = 1e300  # finite: evaluated, by angle addition from cos/sin(theta)
     C = inputs.scaled_normal_coeffs(ns, 6, 9)
     C[4, 1] = np.inf
     F = zp.series_eval(ns, ms, dev(r), dev(th), dev(C), "fp64emu").cpu().numpy()
     check_waits()
-    assert np.isnan(F[7]).all() and np.isnan(F[8]).all() and np.isnan(F[:, 1]).all()
-    ok_rows = np.array([p for p in range(300) if p not in (7, 8)])
+    assert np.isnan(F[7]).all() and np.isnan(F[8]).all() and np.isnan(F[9]).all() and np.isnan(F[:, 1]).all()
+    assert np.isfinite(F[30, [0, 2, 3, 4, 5]]).all()
+    ok_rows = np.array([p for p in range(300) if p not in (7, 8, 9, 30)])
     cols = [0, 2, 3, 4, 5]
     Cg = C[:, cols]
     want = np.array(oseries.series_eval(ns, ms, r[ok_rows], th[ok_rows], Cg.tolist()))
