@@ -31,6 +31,11 @@
  *  - The mode-list entry points build (and cache, keyed by the exact mode list and device)
  *    a plan on first use; that first call copies small tables to the device synchronously.
  *    Inside CUDA-graph capture use the *_plan variants with a plan created beforehand.
+ *  - Every compute entry point opens an NVTX range named after itself (visible in Nsight
+ *    timelines).  The environment variable ZP_DEBUG (read once per process) adds checks: 1
+ *    synchronises the caller's stream at the end of each compute call (outside stream capture)
+ *    and turns an asynchronous CUDA error or a bounded device wait that gave up into that call's
+ *    status; 2 also prints one line per call to stderr.  The default (unset, 0) adds nothing.
  */
 #ifndef ZERNIKE_GB300_H
 #define ZERNIKE_GB300_H
@@ -263,8 +268,8 @@ ZP_API zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, 
  *   minimise sum_p w_p || sum_j Z_j(r_p, theta_p) C[j, :] - Y[p, :] ||^2 + ridge ||C||^2
  * through the normal equations (Z W Z^T + ridge I) C = Z W Y, float64 results (basis by the
  * recursion walk, Gram matrix and right-hand side by the float64-accurate tensor-core GEMM of
- * ZP_PREC_FP64_EMULATED, Cholesky factorisation and solve by the library's own blocked kernels
- * up to 640 modes, by cuSOLVER potrf/potrs beyond).
+ * ZP_PREC_FP64_EMULATED, Cholesky factorisation and the two triangular solves by the library's
+ * own blocked kernels).
  *   weights: DEVICE float64 [n_points] (w_p >= 0) or NULL (all 1).
  *   samples: DEVICE float64 [n_points][n_sets] (Y, row-major).
  *   coeffs:  DEVICE float64 [n_modes][n_sets] (output, row-major).
@@ -343,7 +348,11 @@ ZP_API zp_status zp_batch_get_config(const zp_batch* batch, int32_t* cfg);
 /* Autotuner: times each candidate configuration on this batch (which = 0: forward with
  * `prec`, 1: adjoint), one warm-up then `reps` timed runs with CUDA events on `stream`, and
  * keeps the fastest; cfg[4] (may be NULL) and *best_ms receive the result.  Synchronises
- * `stream`; outputs hold the result of the last candidate run. */
+ * `stream`; outputs hold the result of the last candidate run.  Results are kept per GPU
+ * (compute capability, SM count) and batch shape (instances, points, modes, largest n, sets,
+ * pass, precision): a later tune of the same key applies the kept configuration without
+ * launching anything.  When the environment variable ZP_TUNE_CACHE names a file, results are
+ * appended there (one line per key) and read back by later processes. */
 ZP_API zp_status zp_batch_tune(zp_batch* batch, int32_t which, zp_precision prec, int32_t reps,
                                void* stream, int32_t* cfg, float* best_ms);
 

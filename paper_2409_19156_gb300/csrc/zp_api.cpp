@@ -55,10 +55,16 @@ static zp_status radial_common(const zp_plan* plan, const double* r, const doubl
 
 extern "C" {
 
-zp_status zp_radial_plan(const zp_plan* plan, const double* r, int64_t n_points, int32_t max_deriv, double* out,
+static zp_status zp_radial_plan_impl(const zp_plan* plan, const double* r, int64_t n_points, int32_t max_deriv, double* out,
                          void* stream) {
   clear_error();
   return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false);
+}
+
+zp_status zp_radial_plan(const zp_plan* plan, const double* r, int64_t n_points, int32_t max_deriv, double* out,
+                         void* stream) {
+  zp::NvtxRange zp_range_("zp_radial_plan");
+  return zp::entry_finish("zp_radial_plan", stream, zp_radial_plan_impl(plan, r, n_points, max_deriv, out, stream));
 }
 
 zp_status zp_radial_plan_timed(const zp_plan* plan, const double* r, int64_t n_points, int32_t max_deriv, double* out,
@@ -68,7 +74,7 @@ zp_status zp_radial_plan_timed(const zp_plan* plan, const double* r, int64_t n_p
   return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false, phase_ms);
 }
 
-zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, int64_t n_points,
+static zp_status zp_radial_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, int64_t n_points,
                     int32_t max_deriv, double* out, void* stream) {
   clear_error();
   if (max_deriv < 0 || max_deriv > 3) return set_error(ZP_ERR_DERIV_ORDER, "max_deriv must be 0..3");
@@ -79,13 +85,25 @@ zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes, const d
   return radial_common(plan, r, nullptr, n_points, max_deriv, out, nullptr, stream, false);
 }
 
-zp_status zp_basis_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+zp_status zp_radial(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, int64_t n_points,
+                    int32_t max_deriv, double* out, void* stream) {
+  zp::NvtxRange zp_range_("zp_radial");
+  return zp::entry_finish("zp_radial", stream, zp_radial_impl(n, m, n_modes, r, n_points, max_deriv, out, stream));
+}
+
+static zp_status zp_basis_plan_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                         int32_t max_deriv, double* out, double* out_dtheta, void* stream) {
   clear_error();
   return radial_common(plan, r, theta, n_points, max_deriv, out, out_dtheta, stream, true);
 }
 
-zp_status zp_basis(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+zp_status zp_basis_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                        int32_t max_deriv, double* out, double* out_dtheta, void* stream) {
+  zp::NvtxRange zp_range_("zp_basis_plan");
+  return zp::entry_finish("zp_basis_plan", stream, zp_basis_plan_impl(plan, r, theta, n_points, max_deriv, out, out_dtheta, stream));
+}
+
+static zp_status zp_basis_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
                    int64_t n_points, int32_t max_deriv, double* out, double* out_dtheta, void* stream) {
   clear_error();
   if (max_deriv < 0 || max_deriv > 3) return set_error(ZP_ERR_DERIV_ORDER, "max_deriv must be 0..3");
@@ -96,7 +114,13 @@ zp_status zp_basis(const int32_t* n, const int32_t* m, int64_t n_modes, const do
   return radial_common(plan, r, theta, n_points, max_deriv, out, out_dtheta, stream, true);
 }
 
-zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out, void* stream) {
+zp_status zp_basis(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+                   int64_t n_points, int32_t max_deriv, double* out, double* out_dtheta, void* stream) {
+  zp::NvtxRange zp_range_("zp_basis");
+  return zp::entry_finish("zp_basis", stream, zp_basis_impl(n, m, n_modes, r, theta, n_points, max_deriv, out, out_dtheta, stream));
+}
+
+static zp_status zp_radial_per_mode_impl(const zp_plan* plan, const double* r, int64_t n_points, double* out, void* stream) {
   clear_error();
   ZP_TRY(check_plan_device(plan));
   if (n_points < 0) return set_error(ZP_ERR_INVALID_ARG, "n_points < 0");
@@ -104,6 +128,11 @@ zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_t n_poi
   ZP_TRY(check_device_array(r, "r", 8));
   ZP_TRY(check_device_array(out, "out", 8));
   return launch_per_mode(plan, r, n_points, out, (cudaStream_t)stream);
+}
+
+zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out, void* stream) {
+  zp::NvtxRange zp_range_("zp_radial_per_mode");
+  return zp::entry_finish("zp_radial_per_mode", stream, zp_radial_per_mode_impl(plan, r, n_points, out, stream));
 }
 
 }  // extern "C"

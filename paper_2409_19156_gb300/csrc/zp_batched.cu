@@ -18,8 +18,13 @@
 #include <algorithm>
 #include <array>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -779,7 +784,7 @@ zp_status zp_batch_destroy(zp_batch* b) {
   return ZP_OK;
 }
 
-zp_status zp_batch_forward(zp_batch* b, zp_precision prec, void* stream) {
+static zp_status zp_batch_forward_impl(zp_batch* b, zp_precision prec, void* stream) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
   if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP32 && prec != ZP_PREC_FP64_EMULATED)
@@ -791,7 +796,12 @@ zp_status zp_batch_forward(zp_batch* b, zp_precision prec, void* stream) {
   return batch_forward(b, prec, (cudaStream_t)stream);
 }
 
-zp_status zp_batch_forward_per_instance(zp_batch* b, zp_precision prec, void* stream) {
+zp_status zp_batch_forward(zp_batch* b, zp_precision prec, void* stream) {
+  zp::NvtxRange zp_range_("zp_batch_forward");
+  return zp::entry_finish("zp_batch_forward", stream, zp_batch_forward_impl(b, prec, stream));
+}
+
+static zp_status zp_batch_forward_per_instance_impl(zp_batch* b, zp_precision prec, void* stream) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
   if (prec != ZP_PREC_FP64) return set_error(ZP_ERR_INVALID_ARG, "per-instance comparison runs float64 only");
@@ -809,7 +819,12 @@ zp_status zp_batch_forward_per_instance(zp_batch* b, zp_precision prec, void* st
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "per-instance launches");
 }
 
-zp_status zp_batch_adjoint(zp_batch* b, void* stream) {
+zp_status zp_batch_forward_per_instance(zp_batch* b, zp_precision prec, void* stream) {
+  zp::NvtxRange zp_range_("zp_batch_forward_per_instance");
+  return zp::entry_finish("zp_batch_forward_per_instance", stream, zp_batch_forward_per_instance_impl(b, prec, stream));
+}
+
+static zp_status zp_batch_adjoint_impl(zp_batch* b, void* stream) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -837,6 +852,11 @@ zp_status zp_batch_adjoint(zp_batch* b, void* stream) {
   if (need_pt && b->n_pitems) ZP_TRY(launch_points<ADJ>(b, st));
   if (need_c && b->n_citems) ZP_TRY(launch_columns(b, st));
   return ZP_OK;
+}
+
+zp_status zp_batch_adjoint(zp_batch* b, void* stream) {
+  zp::NvtxRange zp_range_("zp_batch_adjoint");
+  return zp::entry_finish("zp_batch_adjoint", stream, zp_batch_adjoint_impl(b, stream));
 }
 
 zp_status zp_batch_set_config(zp_batch* b, int32_t tile_points, int32_t ctas_per_sm, int32_t col_ppt,
@@ -872,10 +892,98 @@ zp_status zp_batch_get_config(const zp_batch* b, int32_t* cfg) {
 // run, then the mean of `reps` runs, CUDA events on `stream`) and keeps the fastest.
 // which: 0 = forward (precision prec), 1 = adjoint.  Writes the chosen configuration to cfg[4]
 // and the best time in ms to *best_ms.  Synchronises `stream`.
+}  // extern "C"
+
+namespace zp {
+namespace {
+// Tuning results kept for the process and, when the environment variable ZP_TUNE_CACHE names a
+// file, across processes: one line per key, "key tile ctas ppt threads best_ms".  The key holds
+// what decides the best launch: the GPU (compute capability, SM count) and the batch's shape
+// (instances, points, modes, largest n, sets), the pass and the precision.
+struct TuneCache {
+  std::mutex mu;
+  bool loaded = false;
+  std::map<std::string, std::array<float, 5>> entries;
+};
+TuneCache& tune_cache() {
+  static TuneCache c;
+  return c;
+}
+const char* tune_cache_path() { return std::getenv("ZP_TUNE_CACHE"); }
+
+std::string tune_key(const zp_batch* b, int32_t which, zp_precision prec) {
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t points = 0, modes = 0;
+  int32_t n_max = 0;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    points += b->inst[i].n_points;
+    modes += b->inst[i].n_modes;
+    n_max = std::max(n_max, b->plans[b->inst_plan[i]]->n_max);
+  }
+  std::ostringstream k;
+  k << "sm" << major << minor << "x" << sms << "/inst" << b->inst.size() << "/pts" << points << "/modes" << modes
+    << "/nmax" << n_max << "/sets" << b->n_sets << "/pass" << which << "/prec" << (int)prec;
+  return k.str();
+}
+
+void tune_cache_load_locked(TuneCache& c) {
+  if (c.loaded) return;
+  c.loaded = true;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    std::istringstream ls(line);
+    std::string key;
+    std::array<float, 5> v{};
+    if (ls >> key >> v[0] >> v[1] >> v[2] >> v[3] >> v[4]) c.entries[key] = v;
+  }
+}
+
+bool tune_cache_get(const std::string& key, std::array<float, 5>* v) {
+  TuneCache& c = tune_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  tune_cache_load_locked(c);
+  auto it = c.entries.find(key);
+  if (it == c.entries.end()) return false;
+  *v = it->second;
+  return true;
+}
+
+void tune_cache_put(const std::string& key, const std::array<float, 5>& v) {
+  TuneCache& c = tune_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  tune_cache_load_locked(c);
+  c.entries[key] = v;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  std::ofstream out(path, std::ios::app);
+  if (out) out << key << " " << v[0] << " " << v[1] << " " << v[2] << " " << v[3] << " " << v[4] << "\n";
+}
+}  // namespace
+}  // namespace zp
+
+extern "C" {
+
 zp_status zp_batch_tune(zp_batch* b, int32_t which, zp_precision prec, int32_t reps, void* stream, int32_t* cfg,
                         float* best_ms) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
+  // A configuration tuned before for this GPU and batch shape (this process or the cache file).
+  const std::string key = tune_key(b, which, prec);
+  std::array<float, 5> hit{};
+  if (tune_cache_get(key, &hit)) {
+    ZP_TRY(zp_batch_set_config(b, (int32_t)hit[0], (int32_t)hit[1], (int32_t)hit[2], (int32_t)hit[3]));
+    if (cfg)
+      for (int k = 0; k < 4; ++k) cfg[k] = (int32_t)hit[k];
+    if (best_ms) *best_ms = hit[4];
+    return ZP_OK;
+  }
   if (reps < 1) reps = 1;
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
@@ -933,6 +1041,7 @@ zp_status zp_batch_tune(zp_batch* b, int32_t which, zp_precision prec, int32_t r
   if (cfg)
     for (int k = 0; k < 4; ++k) cfg[k] = best_cfg[k];
   if (best_ms) *best_ms = best;
+  tune_cache_put(key, {(float)best_cfg[0], (float)best_cfg[1], (float)best_cfg[2], (float)best_cfg[3], best});
   return ZP_OK;
 }
 

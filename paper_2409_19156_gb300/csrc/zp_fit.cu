@@ -6,13 +6,13 @@
 // Steps: the basis by the walk kernel (float64, into scratch), the rows scaled by sqrt(w) when
 // weights are given, the Gram matrix and the right-hand side by cuBLAS DGEMM (or by the
 // float64-accurate tensor-core GEMM of zp_mma.cu for ZP_PREC_FP64_EMULATED), the
-// ridge added on the diagonal, a Cholesky factorisation and solve (the library's own blocked
-// kernels up to 640 modes, whose solve stores straight into the caller's row-major [J][S]
-// output; cuSOLVER beyond, followed by the library's transpose kernel).  The call synchronises
-// its stream at the end to read the factorisation status.
+// ridge added on the diagonal, a right-looking blocked Cholesky factorisation in the library's
+// own kernels, and the two triangular solves (up to 640 modes one kernel that stages L in shared
+// memory and stores straight into the caller's row-major [J][S] output; beyond, blocked solves
+// of 32 rows at a time and a transpose kernel).  The call synchronises its stream at the end to
+// read the factorisation status.
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cstring>
@@ -296,10 +296,84 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
   }
 }
 
-// Factors the J x J normal matrix (J <= kCholMaxJ) in place and solves for the J x S
-// right-hand sides B (column-major), storing the solution row-major [J][S] in X; info[0] as in
-// chol_panel_kernel (zeroed here).
-zp_status small_cholesky_solve(double* A, int J, const double* B, int S, double* X, int* info, cudaStream_t stream) {
+// Blocked triangular solves for normal matrices beyond the solve kernel's shared-memory limit,
+// 32 rows (one diagonal block) at a time: a diagonal-block kernel solves the block's rows for 32
+// right-hand sides per CTA, an update kernel subtracts the solved block from the rows still to
+// be solved (tiles of 32 rows x 32 right-hand sides).  B is column-major J x S, solved in place;
+// every element is written by one thread in a fixed order (deterministic).
+// FWD: L y = b (rows k0 .. k0+31 after the rows above are folded in); else L^T x = y (rows
+// k0 .. k0+31 after the rows below are folded in).
+template <bool FWD>
+__global__ void __launch_bounds__(256) trsm_diag_kernel(const double* __restrict__ L, int J, double* B, int S, int k0) {
+  __shared__ double D[kNb][kNb + 1];
+  __shared__ double X[kNb][kNb + 1];  // [row][rhs]
+  const int nb = min(kNb, J - k0);
+  const int s0 = (int)blockIdx.x * kNb;
+  const int ns = min(kNb, S - s0);
+  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+    const int r = e % kNb, c = e / kNb;
+    D[r][c] = (r < nb && c < nb) ? L[(size_t)(k0 + r) + (size_t)(k0 + c) * J] : 0.0;
+    X[r][c] = (r < nb && c < ns) ? B[(size_t)(k0 + r) + (size_t)(s0 + c) * J] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNb && (int)threadIdx.x < ns) {
+    const int c = threadIdx.x;
+    if constexpr (FWD) {
+      for (int r = 0; r < nb; ++r) {
+        double v = X[r][c];
+        for (int q = 0; q < r; ++q) v = fma(-D[r][q], X[q][c], v);
+        X[r][c] = v / D[r][r];
+      }
+    } else {
+      for (int r = nb - 1; r >= 0; --r) {
+        double v = X[r][c];
+        for (int q = r + 1; q < nb; ++q) v = fma(-D[q][r], X[q][c], v);
+        X[r][c] = v / D[r][r];
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nb * ns; e += blockDim.x) {
+    const int r = e % nb, c = e / nb;
+    B[(size_t)(k0 + r) + (size_t)(s0 + c) * J] = X[r][c];
+  }
+}
+
+// FWD: rows i >= k0 + 32 of B minus L[i][k0..k0+31] times the solved block; else rows i < k0
+// minus L[k0..k0+31][i] (= L^T[i][k0..]) times it.  One 32 x 32 tile of (row, rhs) per CTA.
+template <bool FWD>
+__global__ void __launch_bounds__(256) trsm_update_kernel(const double* __restrict__ L, int J, double* B, int S, int k0) {
+  __shared__ double Lt[kNb][kNb + 1];  // [row of the tile][q]
+  __shared__ double Xs[kNb][kNb + 1];  // [q][rhs]
+  const int nb = min(kNb, J - k0);
+  const int i0 = FWD ? k0 + kNb + (int)blockIdx.y * kNb : (int)blockIdx.y * kNb;
+  const int i1 = FWD ? J : k0;
+  const int s0 = (int)blockIdx.x * kNb;
+  const int nr = min(kNb, i1 - i0), ns = min(kNb, S - s0);
+  if (nr <= 0) return;
+  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+    const int r = e % kNb, q = e / kNb;
+    Lt[r][q] = (r < nr && q < nb) ? (FWD ? L[(size_t)(i0 + r) + (size_t)(k0 + q) * J] : L[(size_t)(k0 + q) + (size_t)(i0 + r) * J])
+                                  : 0.0;
+    Xs[r][q] = (r < nb && q < ns) ? B[(size_t)(k0 + r) + (size_t)(s0 + q) * J] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x % kNb;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = threadIdx.x / kNb + 8 * k;
+    if (r < nr && c < ns) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < kNb; ++q) acc = fma(Lt[r][q], Xs[q][c], acc);
+      B[(size_t)(i0 + r) + (size_t)(s0 + c) * J] -= acc;
+    }
+  }
+}
+
+// Right-looking blocked Cholesky factorisation of the J x J normal matrix in place (lower
+// triangle, column-major); info[0] as in chol_panel_kernel (zeroed here).
+zp_status cholesky_factor(double* A, int J, int* info, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), stream);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
   for (int k0 = 0; k0 < J; k0 += kNb) {
@@ -307,11 +381,24 @@ zp_status small_cholesky_solve(double* A, int J, const double* B, int S, double*
     const int below = J - k0 - nb;
     chol_panel_kernel<<<1 + (below + kNb - 1) / kNb, 256, 0, stream>>>(A, J, k0, info);
     if (below > 0) {
-      const int nt = (below + kNb - 1) / kNb;
-      chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, stream>>>(A, J, k0);
+      const int64_t nt = (below + kNb - 1) / kNb;
+      chol_update_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, stream>>>(A, J, k0);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "Cholesky panel launch");
   }
+  return ZP_OK;
+}
+
+// Solves L L^T X = B for the factor in A: B column-major J x S (overwritten), the solution
+// stored row-major [J][S] in X by the transpose kernel.
+zp_status blocked_cholesky_solve(const double* A, int J, double* B, int S, double* X, cudaStream_t stream);
+
+// Factors the J x J normal matrix (J <= kCholMaxJ) in place and solves for the J x S
+// right-hand sides B (column-major), storing the solution row-major [J][S] in X; info[0] as in
+// chol_panel_kernel (zeroed here).
+zp_status small_cholesky_solve(double* A, int J, const double* B, int S, double* X, int* info, cudaStream_t stream) {
+  ZP_TRY(cholesky_factor(A, J, info, stream));
+  cudaError_t e;
   const size_t smem = (size_t)(kNb + 2 * kSolveCols + 1) * J * sizeof(double);
   static DeviceMemo<int> attr;  // the largest solve's shared memory, allowed once per device
   int dummy = 0;
@@ -341,13 +428,31 @@ __global__ void __launch_bounds__(256) transpose_kernel(const double* __restrict
   }
 }
 
-struct SolverHandles {
+zp_status blocked_cholesky_solve(const double* A, int J, double* B, int S, double* X, cudaStream_t stream) {
+  const unsigned cols = (unsigned)((S + kNb - 1) / kNb);
+  cudaError_t e;
+  for (int k0 = 0; k0 < J; k0 += kNb) {
+    trsm_diag_kernel<true><<<cols, 256, 0, stream>>>(A, J, B, S, k0);
+    const int below = J - k0 - kNb;
+    if (below > 0) trsm_update_kernel<true><<<dim3(cols, (unsigned)((below + kNb - 1) / kNb)), 256, 0, stream>>>(A, J, B, S, k0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "forward substitution launch");
+  }
+  for (int k0 = (J - 1) / kNb * kNb; k0 >= 0; k0 -= kNb) {
+    trsm_diag_kernel<false><<<cols, 256, 0, stream>>>(A, J, B, S, k0);
+    if (k0 > 0) trsm_update_kernel<false><<<dim3(cols, (unsigned)((k0 + kNb - 1) / kNb)), 256, 0, stream>>>(A, J, B, S, k0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "backward substitution launch");
+  }
+  transpose_kernel<<<dim3((unsigned)((S + 31) / 32), (unsigned)((J + 31) / 32)), 256, 0, stream>>>(B, J, S, X);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "transpose_kernel launch");
+  return ZP_OK;
+}
+
+struct BlasHandles {
   std::mutex mu;
-  std::vector<cusolverDnHandle_t> solver;
   std::vector<cublasHandle_t> blas;
 };
-SolverHandles& solver_handles() {
-  static SolverHandles h;
+BlasHandles& blas_handles() {
+  static BlasHandles h;
   return h;
 }
 
@@ -360,20 +465,19 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-  SolverHandles& hs = solver_handles();
-  std::lock_guard<std::mutex> lock(hs.mu);
-  if ((int)hs.solver.size() <= dev) {
-    hs.solver.resize(dev + 1, nullptr);
-    hs.blas.resize(dev + 1, nullptr);
+  // cuBLAS only for the DGEMM baseline (ZP_PREC_FP64).
+  BlasHandles& hs = blas_handles();
+  std::unique_lock<std::mutex> lock(hs.mu, std::defer_lock);
+  cublasHandle_t blas = nullptr;
+  if (!emulated) {
+    lock.lock();
+    if ((int)hs.blas.size() <= dev) hs.blas.resize(dev + 1, nullptr);
+    if (!hs.blas[dev] && cublasCreate(&hs.blas[dev]) != CUBLAS_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "cublasCreate failed");
+    blas = hs.blas[dev];
+    if (cublasSetStream(blas, stream) != CUBLAS_STATUS_SUCCESS)
+      return set_error(ZP_ERR_CUDA, "setting the stream of the cuBLAS handle failed");
   }
-  if (!hs.solver[dev] && cusolverDnCreate(&hs.solver[dev]) != CUSOLVER_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cusolverDnCreate failed");
-  if (!hs.blas[dev] && cublasCreate(&hs.blas[dev]) != CUBLAS_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "cublasCreate failed");
-  cusolverDnHandle_t sol = hs.solver[dev];
-  cublasHandle_t blas = hs.blas[dev];
-  if (cusolverDnSetStream(sol, stream) != CUSOLVER_STATUS_SUCCESS || cublasSetStream(blas, stream) != CUBLAS_STATUS_SUCCESS)
-    return set_error(ZP_ERR_CUDA, "setting the stream of the solver handles failed");
 
   ScratchBuffer zbuf, ybuf, gram, rhs, info;
   ZP_TRY(zbuf.alloc((size_t)J * P * sizeof(double), stream));
@@ -416,31 +520,15 @@ zp_status series_fit_fp64(const zp_plan* plan, const double* r, const double* th
     add_ridge_kernel<<<(unsigned)((J + 255) / 256), 256, 0, stream>>>((double*)gram.ptr, J, ridge);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "add_ridge_kernel launch");
   }
-  ScratchBuffer work;
-  if (J <= kCholMaxJ && S <= (int64_t)INT32_MAX) {
+  if (J <= kCholMaxJ) {
     ZP_TRY(small_cholesky_solve((double*)gram.ptr, (int)J, (const double*)rhs.ptr, (int)S, coeffs, (int*)info.ptr,
                                 stream));
-    pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
   } else {
-    int lwork = 0;
-    if (cusolverDnDpotrf_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, &lwork) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf_bufferSize failed");
-    ZP_TRY(work.alloc((size_t)std::max(lwork, 1) * sizeof(double), stream));
-    if (cusolverDnDpotrf(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (double*)gram.ptr, (int)J, (double*)work.ptr, lwork,
-                         (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
-      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrf failed");
-    pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
-    if (cusolverDnDpotrs(sol, CUBLAS_FILL_MODE_LOWER, (int)J, (int)S, (double*)gram.ptr, (int)J, (double*)rhs.ptr,
-                         (int)J, (int*)info.ptr) != CUSOLVER_STATUS_SUCCESS)
-      return set_error(ZP_ERR_CUDA, "cusolverDnDpotrs failed");
-    // coeffs row-major [J][S] from the column-major J x S solution.
-    transpose_kernel<<<dim3((unsigned)((S + 31) / 32), (unsigned)((J + 31) / 32)), 256, 0, stream>>>(
-        (const double*)rhs.ptr, J, S, coeffs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "transpose_kernel launch");
+    ZP_TRY(cholesky_factor((double*)gram.ptr, (int)J, (int*)info.ptr, stream));
+    ZP_TRY(blocked_cholesky_solve((const double*)gram.ptr, (int)J, (double*)rhs.ptr, (int)S, coeffs, stream));
   }
+  pivot_range_kernel<<<1, 256, 0, stream>>>((const double*)gram.ptr, J, (double*)info.ptr + 2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "pivot_range_kernel launch");
   double h_info[4] = {0, 0, 0, 0};
   if ((e = cudaMemcpyAsync(h_info, info.ptr, sizeof(h_info), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(stream)) != cudaSuccess)
@@ -463,14 +551,21 @@ using namespace zp;
 
 extern "C" {
 
-zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta, const double* weights,
+static zp_status zp_series_fit_plan_impl(const zp_plan* plan, const double* r, const double* theta, const double* weights,
                              int64_t n_points, const double* samples, int64_t n_sets, double ridge, double* coeffs,
                              void* stream) {
   return zp_series_fit_plan_prec(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs,
                                  ZP_PREC_FP64_EMULATED, stream);
 }
 
-zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta, const double* weights,
+zp_status zp_series_fit_plan(const zp_plan* plan, const double* r, const double* theta, const double* weights,
+                             int64_t n_points, const double* samples, int64_t n_sets, double ridge, double* coeffs,
+                             void* stream) {
+  zp::NvtxRange zp_range_("zp_series_fit_plan");
+  return zp::entry_finish("zp_series_fit_plan", stream, zp_series_fit_plan_impl(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, stream));
+}
+
+static zp_status zp_series_fit_plan_prec_impl(const zp_plan* plan, const double* r, const double* theta, const double* weights,
                                   int64_t n_points, const double* samples, int64_t n_sets, double ridge,
                                   double* coeffs, zp_precision prec, void* stream) {
   clear_error();
@@ -493,7 +588,14 @@ zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const do
                          prec == ZP_PREC_FP64_EMULATED);
 }
 
-zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, const double* theta, const double* weights,
+                                  int64_t n_points, const double* samples, int64_t n_sets, double ridge,
+                                  double* coeffs, zp_precision prec, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_fit_plan_prec");
+  return zp::entry_finish("zp_series_fit_plan_prec", stream, zp_series_fit_plan_prec_impl(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, prec, stream));
+}
+
+static zp_status zp_series_fit_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
                         const double* weights, int64_t n_points, const double* samples, int64_t n_sets, double ridge,
                         double* coeffs, void* stream) {
   clear_error();
@@ -501,6 +603,13 @@ zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes, con
   ZP_TRY(cached_plan(n, m, n_modes, &held));
   const zp_plan* plan = held.get();
   return zp_series_fit_plan(plan, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, stream);
+}
+
+zp_status zp_series_fit(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+                        const double* weights, int64_t n_points, const double* samples, int64_t n_sets, double ridge,
+                        double* coeffs, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_fit");
+  return zp::entry_finish("zp_series_fit", stream, zp_series_fit_impl(n, m, n_modes, r, theta, weights, n_points, samples, n_sets, ridge, coeffs, stream));
 }
 
 }  // extern "C"

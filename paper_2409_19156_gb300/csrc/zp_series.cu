@@ -330,7 +330,7 @@ static zp_status series_args(const zp_plan* plan, const double* r, const double*
 
 extern "C" {
 
-zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+static zp_status zp_series_eval_plan_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                               const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream) {
   clear_error();
   if (prec != ZP_PREC_FP64 && prec != ZP_PREC_BF16X3 && prec != ZP_PREC_TF32 && prec != ZP_PREC_FP64_EMULATED)
@@ -355,6 +355,12 @@ zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double
   return series_eval_split(plan, r, theta, n_points, coeffs, n_sets, prec, (float*)out, st);
 }
 
+zp_status zp_series_eval_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                              const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_eval_plan");
+  return zp::entry_finish("zp_series_eval_plan", stream, zp_series_eval_plan_impl(plan, r, theta, n_points, coeffs, n_sets, prec, out, stream));
+}
+
 zp_status zp_series_eval_timed(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                const double* coeffs, int64_t n_sets, zp_precision prec, void* out, void* stream,
                                float* phase_ms) {
@@ -370,7 +376,7 @@ zp_status zp_series_eval_timed(const zp_plan* plan, const double* r, const doubl
                            phase_ms);
 }
 
-zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+static zp_status zp_series_eval_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
                          int64_t n_points, const double* coeffs, int64_t n_sets, zp_precision prec, void* out,
                          void* stream) {
   clear_error();
@@ -380,14 +386,28 @@ zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, co
   return zp_series_eval_plan(plan, r, theta, n_points, coeffs, n_sets, prec, out, stream);
 }
 
-zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r, const double* theta,
+                         int64_t n_points, const double* coeffs, int64_t n_sets, zp_precision prec, void* out,
+                         void* stream) {
+  zp::NvtxRange zp_range_("zp_series_eval");
+  return zp::entry_finish("zp_series_eval", stream, zp_series_eval_impl(n, m, n_modes, r, theta, n_points, coeffs, n_sets, prec, out, stream));
+}
+
+static zp_status zp_series_adjoint_plan_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                  const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_coeffs,
                                  double* grad_r, double* grad_theta, void* stream) {
   return zp_series_adjoint_plan_prec(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r,
                                      grad_theta, ZP_PREC_FP64_EMULATED, stream);
 }
 
-zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                 const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_coeffs,
+                                 double* grad_r, double* grad_theta, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_adjoint_plan");
+  return zp::entry_finish("zp_series_adjoint_plan", stream, zp_series_adjoint_plan_impl(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta, stream));
+}
+
+static zp_status zp_series_adjoint_plan_prec_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                       const double* coeffs, int64_t n_sets, const double* grad_out,
                                       double* grad_coeffs, double* grad_r, double* grad_theta, zp_precision prec,
                                       void* stream) {
@@ -413,7 +433,15 @@ zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, cons
                              prec == ZP_PREC_FP64_EMULATED);
 }
 
-zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                      const double* coeffs, int64_t n_sets, const double* grad_out,
+                                      double* grad_coeffs, double* grad_r, double* grad_theta, zp_precision prec,
+                                      void* stream) {
+  zp::NvtxRange zp_range_("zp_series_adjoint_plan_prec");
+  return zp::entry_finish("zp_series_adjoint_plan_prec", stream, zp_series_adjoint_plan_prec_impl(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta, prec, stream));
+}
+
+static zp_status zp_series_point_hessian_plan_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                        const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_r,
                                        double* grad_theta, double* hess_rr, double* hess_rt, double* hess_tt,
                                        void* stream) {
@@ -443,7 +471,15 @@ zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, con
                              /*emulated=*/true);
 }
 
-zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+zp_status zp_series_point_hessian_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                       const double* coeffs, int64_t n_sets, const double* grad_out, double* grad_r,
+                                       double* grad_theta, double* hess_rr, double* hess_rt, double* hess_tt,
+                                       void* stream) {
+  zp::NvtxRange zp_range_("zp_series_point_hessian_plan");
+  return zp::entry_finish("zp_series_point_hessian_plan", stream, zp_series_point_hessian_plan_impl(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_r, grad_theta, hess_rr, hess_rt, hess_tt, stream));
+}
+
+static zp_status zp_series_point_hvp_plan_impl(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                                    const double* coeffs, int64_t n_sets, const double* grad_out, const double* v_r,
                                    const double* v_theta, double* hv_r, double* hv_theta, void* stream) {
   clear_error();
@@ -471,7 +507,14 @@ zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, const d
                              /*emulated=*/true);
 }
 
-zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+zp_status zp_series_point_hvp_plan(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
+                                   const double* coeffs, int64_t n_sets, const double* grad_out, const double* v_r,
+                                   const double* v_theta, double* hv_r, double* hv_theta, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_point_hvp_plan");
+  return zp::entry_finish("zp_series_point_hvp_plan", stream, zp_series_point_hvp_plan_impl(plan, r, theta, n_points, coeffs, n_sets, grad_out, v_r, v_theta, hv_r, hv_theta, stream));
+}
+
+static zp_status zp_series_point_hessian_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
                                   const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
                                   const double* grad_out, double* grad_r, double* grad_theta, double* hess_rr,
                                   double* hess_rt, double* hess_tt, void* stream) {
@@ -483,7 +526,15 @@ zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_
                                       hess_rt, hess_tt, stream);
 }
 
-zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+zp_status zp_series_point_hessian(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+                                  const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
+                                  const double* grad_out, double* grad_r, double* grad_theta, double* hess_rr,
+                                  double* hess_rt, double* hess_tt, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_point_hessian");
+  return zp::entry_finish("zp_series_point_hessian", stream, zp_series_point_hessian_impl(n, m, n_modes, r, theta, n_points, coeffs, n_sets, grad_out, grad_r, grad_theta, hess_rr, hess_rt, hess_tt, stream));
+}
+
+static zp_status zp_series_adjoint_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
                             const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
                             const double* grad_out, double* grad_coeffs, double* grad_r, double* grad_theta,
                             void* stream) {
@@ -493,6 +544,14 @@ zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes,
   const zp_plan* plan = held.get();
   return zp_series_adjoint_plan(plan, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta,
                                 stream);
+}
+
+zp_status zp_series_adjoint(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+                            const double* theta, int64_t n_points, const double* coeffs, int64_t n_sets,
+                            const double* grad_out, double* grad_coeffs, double* grad_r, double* grad_theta,
+                            void* stream) {
+  zp::NvtxRange zp_range_("zp_series_adjoint");
+  return zp::entry_finish("zp_series_adjoint", stream, zp_series_adjoint_impl(n, m, n_modes, r, theta, n_points, coeffs, n_sets, grad_out, grad_coeffs, grad_r, grad_theta, stream));
 }
 
 }  // extern "C"

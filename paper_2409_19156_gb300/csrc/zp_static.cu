@@ -57,7 +57,7 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 using namespace zp;
 
-extern "C" zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+static zp_status zp_series_eval_static_impl(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
                                            const double* theta, int64_t n_points, const double* coeffs,
                                            int64_t n_sets, zp_precision prec, float* out, void* stream) {
   clear_error();
@@ -121,4 +121,11 @@ extern "C" zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, i
   // Every byte of the coefficient tiles and of each basis tile is written before it is read
   // within this call, so nothing left by an earlier call needs clearing.
   return series_eval_split(&plan, r, theta, n_points, coeffs, n_sets, prec, out, st, nullptr, &sc);
+}
+
+extern "C" zp_status zp_series_eval_static(const int32_t* n, const int32_t* m, int64_t n_modes, const double* r,
+                                           const double* theta, int64_t n_points, const double* coeffs,
+                                           int64_t n_sets, zp_precision prec, float* out, void* stream) {
+  zp::NvtxRange zp_range_("zp_series_eval_static");
+  return zp::entry_finish("zp_series_eval_static", stream, zp_series_eval_static_impl(n, m, n_modes, r, theta, n_points, coeffs, n_sets, prec, out, stream));
 }

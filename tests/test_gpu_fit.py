@@ -69,11 +69,12 @@ def test_singular_fit_is_reported_and_ridge_fixes_it():
     assert bool(torch.isfinite(C).all())
 
 
-@pytest.mark.parametrize("n_max,S", [(7, 3), (34, 5), (35, 1)])
+@pytest.mark.parametrize("n_max,S", [(7, 3), (34, 5), (35, 1), (44, 33)])
 def test_fit_round_trip_across_solver_sizes(n_max, S):
     """Round trips through zp_series_eval on an exact polar quadrature for 36 modes (two
-    32-column panels, ragged), 630 modes (the library's own blocked Cholesky near its 640-mode
-    limit) and 666 modes (beyond it: cuSOLVER), with odd set counts."""
+    32-column panels, ragged), 630 modes (the one-kernel solve near its 640-mode shared-memory
+    limit), 666 and 1035 modes (beyond it: the blocked triangular solves, ragged blocks and more
+    than 32 right-hand sides), with odd set counts."""
     ns, ms = inputs.full_zernike_modes(n_max)
     r, th, w = polar_quadrature(n_max // 2 + 3, 2 * n_max + 4)
     C = np.random.default_rng(n_max).standard_normal((len(ns), S))

@@ -106,3 +106,48 @@ def test_release_scratch_returns_ok_and_calls_keep_working():
     torch.cuda.synchronize()
     assert torch.equal(before, after)
     assert lib.zp_release_scratch() == 0
+
+
+def test_tuner_cache_persists_across_calls(tmp_path, monkeypatch):
+    """zp_batch_tune keeps its result per GPU and batch shape: with ZP_TUNE_CACHE naming a file,
+    the key and configuration are written there, and a second tune of the same batch returns
+    the stored configuration without timing again."""
+    import time
+
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("ZP_TUNE_CACHE", str(path))
+    rng = np.random.default_rng(4)
+    inst = []
+    for k, (n_max, P) in enumerate([(6, 300), (11, 257), (3, 40)]):
+        ns, ms = inputs.full_zernike_modes(n_max)
+        r, th = inputs.uniform_points(P, 40 + k)
+        inst.append({"n": ns, "m": ms, "r": torch.as_tensor(r, device=DEV), "theta": torch.as_tensor(th, device=DEV),
+                     "coeffs": torch.as_tensor(rng.standard_normal((len(ns), 5)), device=DEV)})
+    b = zp.Batch(inst, 5, with_adjoint=False)
+    cfg1, ms1 = b.tune("forward", "fp64", reps=1)
+    text = path.read_text()
+    assert "/inst3/" in text and "/sets5/" in text
+    t0 = time.perf_counter()
+    cfg2, ms2 = b.tune("forward", "fp64", reps=1)
+    assert time.perf_counter() - t0 < 0.05  # no candidate launched
+    assert cfg2 == cfg1 and ms2 == ms1
+    assert b.config() == cfg1
+
+
+def test_debug_level_checks_and_logs_every_call(tmp_path):
+    """ZP_DEBUG=2: every compute entry point synchronises, checks and logs one line."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import torch, paper_2409_19156_gb300 as zp\n"
+            "r = torch.linspace(0, 1, 64, dtype=torch.float64, device='cuda:0')\n"
+            "zp.radial([2, 3], [0, 1], r, 1)\n"
+            "zp.series_eval([2, 3], [0, 1], r, r, torch.ones(2, 3, dtype=torch.float64, device='cuda:0'))\n"
+            "torch.cuda.synchronize()\n")
+    env = dict(os.environ, ZP_DEBUG="2", PYTHONPATH=root)
+    res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr
+    assert "[zp] zp_radial -> 0" in res.stderr
+    assert "[zp] zp_series_eval -> 0" in res.stderr
