@@ -43,10 +43,10 @@ DP_OPS_PEAK_NOMINAL = SMS * DP_LANES_PER_SM * SM_MAX_MHZ * 1e6
 FLOP_PER_VALUE_TUPLE = 28
 DP_OPS_PER_VALUE_TUPLE = 15
 # DRAM bytes (read + write) of one walk_kernel<3,false,true> launch at 20000 points, from one
-# ncu capture of that kernel (dram__bytes_write.sum 1.604159 GB + dram__bytes_read.sum
-# 17.184 MB: the output and one read of the power table), scaled to 100000 points (both
+# ncu capture of that kernel (dram__bytes_write.sum 1.603462 GB + dram__bytes_read.sum
+# 17.015 MB: the output and one read of the power table), scaled to 100000 points (both
 # proportional to the point count).  The walk kernel has not changed since that capture.
-WALK_TRAFFIC_20000 = 1.604159e9 + 17.184256e6
+WALK_TRAFFIC_20000 = 1.603462e9 + 17.015296e6
 
 
 def parse_args():
@@ -73,6 +73,8 @@ def parse_args():
                     help="run only the series_n24 emulated-float64 adjoint (profiling captures)")
     ap.add_argument("--paper-shapes-only", action="store_true",
                     help="run only the paper-shapes measurement (Algorithm 2, Fig. 3 grid, duplicated modes)")
+    ap.add_argument("--fp64-probe-only", action="store_true",
+                    help="run only the float64 issue-rate probe (FMA, MUL, ADD) and print its results")
     ap.add_argument("--fused-only", action="store_true",
                     help="run only the fused float64-accurate series measurement (profiling captures)")
     ap.add_argument("--fused-points", type=int, default=1_000_000)
@@ -1004,6 +1006,25 @@ def main():
         res = measure_batched(torch.device("cuda", 0), steps=args.steps, n_instances=args.batched_instances,
                               point_scale=args.batched_point_scale, tune=False)
         print(json.dumps({"batched_only": res}), flush=True)
+        return
+    if args.fp64_probe_only:
+        import ctypes
+
+        import torch
+
+        from paper_2409_19156_gb300 import _lib
+
+        torch.cuda.set_device(0)
+        lib = _lib.load()
+        sp = torch.cuda.current_stream().cuda_stream
+        out = []
+        for op, name in ((0, "fma"), (1, "mul"), (2, "add")):
+            for iters in (4000, 20000):
+                res = (ctypes.c_double * 6)()
+                _lib.check("zp_probe_fp64", lib.zp_probe_fp64(op, iters, sp, res))
+                out.append({"op": name, "iters": iters, "ops_per_s": res[2], "lanes_per_sm_clk": res[3],
+                            "implied_sm_mhz": res[4], "ms": res[1]})
+        print(json.dumps({"fp64_probe_only": out}), flush=True)
         return
     if args.fused_only:
         import torch

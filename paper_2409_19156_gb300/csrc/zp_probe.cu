@@ -20,20 +20,20 @@ constexpr int kProbeThreads = 256;
 constexpr int kChains = 16;
 constexpr int kUnroll = 4;  // rounds per loop trip (loop overhead off the float64 issue path)
 
-// OP 0: x = fma(x, y, -z); OP 1: x = x * y; OP 2: x = x + y, with y and z per-chain registers
-// (the operand pattern of the recursion kernels; uniform constant operands measured about 10 %
-// slower).  The values keep every chain finite and away from subnormals for any iteration
-// count; the final values go to `sink` so the chains cannot be removed.
+// OP 0: x = fma(a, x, b); OP 1: x = x * a; OP 2: x = x + a, with a and b in registers shared by
+// all chains (the recursion kernels' pattern: a step's coefficient feeds every Taylor lane).
+// Three distinct 64-bit register operands per instruction (per-chain y, z) measured 1.68
+// lanes/SM/clk, a and b from the constant bank 1.69: the register reads, not the float64 pipe,
+// then limit the rate.  The values keep every chain finite and away from subnormals for any
+// iteration count; the final values go to `sink` so the chains cannot be removed.
 template <int OP>
 __global__ void __launch_bounds__(kProbeThreads) fp64_probe_kernel(int iters, double a, double b, double* sink,
                                                                    long long* cycles) {
-  double x[kChains], y[kChains], z[kChains];
+  double x[kChains];
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) {
-    x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
-    y[c] = a * (1.0 + 1e-12 * c);
-    z[c] = -b * (1.0 + 1e-12 * threadIdx.x);
-  }
+  for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  // Runtime values (not foldable into immediates or constant-bank operands).
+  const double ar = a * (1.0 + 1e-15 * (threadIdx.x & 1)), br = b * (1.0 + 1e-15 * (threadIdx.x & 2));
   __syncthreads();
   const long long t0 = clock64();
 #pragma unroll kUnroll
@@ -41,11 +41,11 @@ __global__ void __launch_bounds__(kProbeThreads) fp64_probe_kernel(int iters, do
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
       if constexpr (OP == 0) {
-        x[c] = fma(x[c], y[c], -z[c]);
+        x[c] = fma(ar, x[c], br);
       } else if constexpr (OP == 1) {
-        x[c] = x[c] * y[c];
+        x[c] = x[c] * ar;
       } else {
-        x[c] = x[c] + y[c];
+        x[c] = x[c] + ar;
       }
     }
   }
