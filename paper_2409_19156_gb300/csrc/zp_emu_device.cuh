@@ -45,15 +45,35 @@ __device__ __forceinline__ long long to_fixed(double z, int shift) {
   return (b >> 63) ? -(long long)mag : (long long)mag;
 }
 
+// Leading zero bits of a 64-bit word (64 for zero), on the device and on the host.
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// float64 with the given bit pattern, on the device and on the host.
+__host__ __device__ __forceinline__ double double_of_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  __builtin_memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+
 // Correctly rounded float64 of N * 2^e2 (round half to even), N a signed 128-bit integer.
 // The mantissa and exponent are assembled on the integer pipe; results outside the normal
 // range go through ldexp.
-__device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
+__host__ __device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
   if (N == 0) return 0.0;
   const bool neg = N < 0;
   const unsigned __int128 M = neg ? (unsigned __int128)0 - (unsigned __int128)N : (unsigned __int128)N;
   const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;
-  const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  const int nbits = hi ? 128 - clz64(hi) : 64 - clz64(lo);
   unsigned long long mant;
   if (nbits <= 53) {
     mant = lo << (53 - nbits);
@@ -76,7 +96,56 @@ __device__ __forceinline__ double int128_to_double(__int128 N, int e2) {
   }
   const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
                                   (mant & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
+  return double_of_bits(bits);
+}
+
+// Correctly rounded float64 of (H 2^ls + L) 2^e2 (round half to even), the join of the
+// recombination's two Horner chains, with 64-bit operations only: the part of L above bit ls
+// is carried into H, the sign is taken off (|N| = MH 2^ls + ML, 0 <= ML < 2^ls), and the
+// 53-bit mantissa with its rounding bits is cut from MH and ML.  Values of fewer than 54
+// bits, |H| of 2^62 or more, shifts outside 1..62 and results outside the normal range take
+// the 128-bit path.
+__host__ __device__ __forceinline__ double join_to_double(long long H, long long L, int ls, int e2) {
+  if (ls >= 1 && ls <= 62 && (H >> 62) == (H >> 63)) {
+    const unsigned long long lr = (unsigned long long)L & ((1ull << ls) - 1);
+    const long long hc = H + (L >> ls);
+    const bool neg = hc < 0;
+    const unsigned long long mh = neg ? (unsigned long long)(-(hc + (lr != 0 ? 1 : 0))) : (unsigned long long)hc;
+    const unsigned long long ml = neg && lr != 0 ? (1ull << ls) - lr : lr;
+    const int nb = 64 - clz64(mh);
+    const int r = nb + ls - 53;  // bits below the mantissa
+    if (mh != 0 && r >= 1) {
+      unsigned long long mant;
+      bool up;
+      if (r >= ls) {
+        const int rs = r - ls;  // bits of MH below the mantissa, 0..11
+        mant = mh >> rs;
+        if (rs == 0) {
+          const unsigned long long half = 1ull << (ls - 1);
+          up = ml > half || (ml == half && (mant & 1));
+        } else {
+          const unsigned long long rem = mh & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+          up = rem > half || (rem == half && (ml != 0 || (mant & 1)));
+        }
+      } else {
+        mant = (mh << (ls - r)) | (ml >> r);
+        const unsigned long long rem = ml & ((1ull << r) - 1), half = 1ull << (r - 1);
+        up = rem > half || (rem == half && (mant & 1));
+      }
+      mant += up ? 1 : 0;
+      int ex = nb + ls - 1 + e2;  // |N| 2^e2 lies in [2^ex, 2^(ex+1))
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
+      }
+      if (ex >= -1022 && ex <= 1023) {
+        const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                        (mant & 0xfffffffffffffull);
+        return double_of_bits(bits);
+      }
+    }
+  }
+  return int128_to_double((__int128)((unsigned __int128)(__int128)H << ls) + (__int128)L, e2);
 }
 
 // Horner step acc * 2^beta + t in two's-complement int64 (the true value fits; see `split`).

@@ -36,7 +36,20 @@ struct EmuShape {
   int kc_per_batch = 0;  // chunks per K batch
   int k_batches = 1;
   int split = 0;         // diagonals in the first Horner chain
+  // Paired diagonals: one GEMM launch forms the sums of two neighbouring diagonals (d, d + 1)
+  // and stores T_d 2^beta + T_(d+1) as one int32 (when that cannot overflow), so ceil(s / 2)
+  // planes of sums cross memory instead of s.  Plane q holds diagonals (2q - s % 2, 2q + 1 -
+  // s % 2) (0-based; a diagonal -1 is empty), and consecutive planes differ by 2^(2 beta).
+  bool paired = false;
+  int planes = 0;       // planes of sums (s, or ceil(s / 2) when paired)
+  int plane_split = 0;  // planes in the first Horner chain
 };
+
+// Largest |sum of digit products| of one diagonal over `chunks` K chunks (the bound of
+// max_batch_chunks) with slice option o.
+inline double diagonal_bound(int o, int chunks) {
+  return std::ldexp(1.0, 2 * kSliceBeta[o]) * (1.0 + (kSliceS[o] - 2) / 4.0) * kSliceBK * chunks;
+}
 
 // A large output (M x N tiles filling the GPU twice) takes one K batch with the fewest slice
 // pairs that K allows, since every batch adds a full set of int32 sums to write and read.  A
@@ -85,6 +98,21 @@ inline bool choose_emu_shape(int64_t K, int64_t mn_tiles, int sms, EmuShape* e) 
   e->split = std::min(s, (62 - tb) / beta + 1);
   // The second chain holds s - split diagonals: tb + beta (s - split - 1) + 1 bits.
   if (s > e->split && tb + beta * (s - e->split - 1) + 1 > 63) return false;
+  e->planes = s;
+  e->plane_split = e->split;
+  // Pairs: |T_d 2^beta + T_(d+1)| <= bound (2^beta + 1) must stay below 2^31 in every batch;
+  // a plane summed over the batches then has tp = 31 + ceil(log2 k_batches) bits, and each
+  // Horner step of the recombination shifts by 2 beta.
+  if (diagonal_bound(o, cpb) * (std::ldexp(1.0, beta) + 1.0) < 2147483648.0) {
+    const int planes = (s + 1) / 2;
+    const int tp = tb + 7;
+    const int psplit = std::min(planes, (62 - tp) / (2 * beta) + 1);
+    if (psplit >= 1 && (planes == psplit || tp + 2 * beta * (planes - psplit - 1) + 1 <= 63)) {
+      e->paired = true;
+      e->planes = planes;
+      e->plane_split = psplit;
+    }
+  }
   return true;
 }
 

@@ -242,9 +242,7 @@ __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint3
     const int ec = d.cexp[h * 8 + i];
     orow[h * 8 + i] = (ep == kNonFiniteRow || ec == kNonFiniteRow)
                           ? __longlong_as_double(0x7ff8000000000000ll)
-                          : int128_to_double(
-                                (__int128)((unsigned __int128)(__int128)hi[i] << (kBeta * (kDig - kSplit))) + (__int128)lo[i],
-                                e_base + ec);
+                          : join_to_double(hi[i], lo[i], kBeta * (kDig - kSplit), e_base + ec);
   }
 }
 

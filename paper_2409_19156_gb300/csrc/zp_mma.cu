@@ -403,7 +403,21 @@ struct GemmArgs {
   int k_batches = 1;
   int kc_per_batch = 0;
   int64_t t_batch_stride = 0;
+  // KIND_SLICE with paired diagonals (npairs unused): the tile is 128 points x 128 sets and
+  // covers the diagonals dp and dp + 1 (0-based; dp = -1 leaves only diagonal 0).  B holds per
+  // (set tile, K chunk) all s_slices slices of 128 rows back to back (kSliceBlock bytes each),
+  // so that one N = 256 MMA of A slice t against slices (dp - t, dp + 1 - t) adds into both
+  // diagonals' accumulators (TMEM columns 0-127 and 128-255); A slice dp + 1 meets only B slice
+  // 0 (an N = 128 MMA into columns 128-255).  The epilogue stores T_dp 2^beta + T_(dp+1) as one
+  // int32 (the host checks that it cannot overflow).
+  int paired = 0;
+  int dp = 0;
+  int beta = 0;
+  int s_slices = 0;
 };
+
+// Bytes of one 128-row slice block of the paired B layout.
+constexpr uint32_t kSliceBlock = BM * Cfg<KIND_SLICE>::ROW;
 
 // One CTA per output tile at a time (persistent over tiles); every operand chunk is brought
 // from global memory into this CTA's own shared memory by a plain bulk copy.
@@ -471,18 +485,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         k_range(t, kc0, nkc);
         const uint8_t* gA0 = a.A + (size_t)mt * a.KC * C::A_CHUNK;
         const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
-        for (int kk = 0; kk < a.npairs * nkc; ++kk) {
+        const int items = (KIND == KIND_SLICE && a.paired ? a.dp + 2 : a.npairs) * nkc;
+        for (int kk = 0; kk < items; ++kk) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
             break;
           }
-          const int ts = kk / nkc, kc = kc0 + kk % nkc;  // slice pair (ts, npairs - 1 - ts)
-          const uint8_t* gA = gA0 + (size_t)ts * a.a_slice_stride;
-          const uint8_t* gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride;
+          const int ts = kk / nkc, kc = kc0 + kk % nkc;  // A slice ts
+          const uint8_t* gA = gA0 + (size_t)ts * a.a_slice_stride + (size_t)kc * C::A_CHUNK;
+          const uint8_t* gB;
+          uint32_t b_bytes = C::B_CHUNK;
+          if (KIND == KIND_SLICE && a.paired) {
+            // B slices (dp - ts, dp + 1 - ts), or slice 0 alone for ts = dp + 1.
+            const bool both = ts <= a.dp;
+            gB = a.B + (((size_t)nt * a.KC + kc) * a.s_slices + (both ? a.dp - ts : 0)) * kSliceBlock;
+            b_bytes = both ? 2 * kSliceBlock : kSliceBlock;
+          } else {
+            gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride + (size_t)kc * C::B_CHUNK;
+          }
           uint8_t* sA = smem + stage * C::STAGE;
-          ptx::mbar_arrive_expect_tx(&full[stage], C::STAGE);
-          ptx::bulk_g2s(sA, gA + (size_t)kc * C::A_CHUNK, C::A_CHUNK, &full[stage]);
-          ptx::bulk_g2s(sA + C::A_CHUNK, gB + (size_t)kc * C::B_CHUNK, C::B_CHUNK, &full[stage]);
+          ptx::mbar_arrive_expect_tx(&full[stage], C::A_CHUNK + b_bytes);
+          ptx::bulk_g2s(sA, gA, C::A_CHUNK, &full[stage]);
+          ptx::bulk_g2s(sA + C::A_CHUNK, gB, b_bytes, &full[stage]);
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -508,7 +532,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         int kc0, nkc;
         k_range(t, kc0, nkc);
         bool ok = true;
-        for (int kk = 0; kk < a.npairs * nkc; ++kk) {
+        const int items = (KIND == KIND_SLICE && a.paired ? a.dp + 2 : a.npairs) * nkc;
+        for (int kk = 0; kk < items; ++kk) {
           if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
             fail();
             ok = false;
@@ -517,6 +542,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           ptx::tc_fence_after();
           const uint32_t sA = ptx::smem_u32(smem + stage * C::STAGE);
           const uint32_t sB = sA + C::A_CHUNK;
+          // Paired slice tiles: A slice dp + 1 meets B slice 0 only (diagonal dp + 1, N = 128).
+          const bool half = KIND == KIND_SLICE && a.paired && kk / nkc > a.dp;
 #pragma unroll
           for (int ks = 0; ks < C::KSTEPS; ++ks) {
             const uint32_t koff = ks * 32;
@@ -525,8 +552,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
               ptx::mma_tf32(d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff), ptx::sw_kmajor_desc<C::ROW>(sB + koff), idesc,
                             first);
             } else if constexpr (KIND == KIND_SLICE) {
-              ptx::mma_bf16(d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff), ptx::sw_kmajor_desc<C::ROW>(sB + koff), idesc,
-                            first);
+              constexpr uint32_t idesc_half = ptx::idesc_bf16_f32(BM, BN / 2);
+              ptx::mma_bf16(half ? d_tmem + BN / 2 : d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff),
+                            ptx::sw_kmajor_desc<C::ROW>(sB + koff), half ? idesc_half : idesc, first);
             } else {
               const uint64_t ah = ptx::sw_kmajor_desc<C::ROW>(sA + koff);
               const uint64_t al = ptx::sw_kmajor_desc<C::ROW>(sA + C::A_PART + koff);
@@ -567,18 +595,39 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       const int64_t mt = a.mt_base + tm / groups_n;
       const int nt = (int)(tm % groups_n);
       const int64_t p = mt * BM + row;
-      const int64_t col0 = (int64_t)nt * BN;
+      const bool paired = KIND == KIND_SLICE && a.paired;
+      const int tile_cols = paired ? BN / 2 : BN;
+      const int64_t col0 = (int64_t)nt * tile_cols;
       float* frow = a.F + (t / per_batch) * a.t_batch_stride + p * a.S;
       const bool vec = (a.S % 4) == 0;
+      const uint32_t tacc = tmem_base + ((q * 32u) << 16) + acc * BN;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < tile_cols; c0 += 32) {
         uint32_t v[32];
-        ptx::tmem_ld_32x32b_x32(tmem_base + ((q * 32u) << 16) + acc * BN + (uint32_t)c0, v);
-        ptx::tmem_ld_wait(v);
-        if constexpr (KIND == KIND_SLICE) {
-          // Slice products sum to integers below 2^24 (exact in float32): store them as int32.
+        if (paired) {
+          // T_(dp+1) in columns 128-255, T_dp (none for dp = -1) in columns 0-127.
+          ptx::tmem_ld_32x32b_x32(tacc + BN / 2 + (uint32_t)c0, v);
+          ptx::tmem_ld_wait(v);
+          if (a.dp >= 0) {
+            uint32_t h[32];
+            ptx::tmem_ld_32x32b_x32(tacc + (uint32_t)c0, h);
+            ptx::tmem_ld_wait(h);
+            const int scale = 1 << a.beta;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
+            for (int i = 0; i < 32; ++i)
+              v[i] = (uint32_t)(__float2int_rn(__uint_as_float(h[i])) * scale + __float2int_rn(__uint_as_float(v[i])));
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
+          }
+        } else {
+          ptx::tmem_ld_32x32b_x32(tacc + (uint32_t)c0, v);
+          ptx::tmem_ld_wait(v);
+          if constexpr (KIND == KIND_SLICE) {
+            // Slice products sum to integers below 2^24 (exact in float32): store them as int32.
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
+          }
         }
         if (p < a.P) {
           const int64_t cbase = col0 + c0;
@@ -884,13 +933,15 @@ __device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, u
 }
 
 // Slices of an operand's rows in the tensor core's K-major swizzled chunks: tile
-// (row / ROWS) x K chunk kc at ((tile * KC + kc) * ROWS * Cfg<KIND_SLICE>::ROW) bytes, slice t a further
+// (row / ROWS) x K chunk kc at (tile * KC + kc) * chunk_stride bytes (ROWS * 128 for one slice
+// per chunk, s times that when the slices of a chunk lie back to back), slice t a further
 // t * slice_stride.  Thread = (row, group of 8 consecutive K): rows fastest when an operand's
 // rows are contiguous (KFAST = false), K groups fastest when its K is (coalesced loads either
 // way).  Rows past `rows` and K past `K` are zero.
 template <int ROWS, bool KFAST>
 __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
-                                  const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride) {
+                                  const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride,
+                                  int64_t chunk_stride) {
   constexpr int BK = Cfg<KIND_SLICE>::BK;
   const int64_t rows_pad = tiles * ROWS;
   const int64_t groups = (int64_t)KC * (BK / 8);
@@ -909,17 +960,19 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     const uint32_t r = (uint32_t)(row % ROWS);
     const int kc = (int)(k0 / BK);
     constexpr uint32_t ROW = Cfg<KIND_SLICE>::ROW;
-    uint8_t* d = dst + ((size_t)tile * KC + kc) * (ROWS * ROW) + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
+    uint8_t* d = dst + ((size_t)tile * KC + kc) * chunk_stride + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
     cut_slices(x, sp.beta, sp.s, d, slice_stride);
   }
 }
 
 struct RecombineArgs {
-  const int* T;            // [k_batches][ndiag][rows][N] int32 diagonal sums
+  const int* T;            // [k_batches][ndiag][rows][N] int32 sums (planes of one or two diagonals)
   const long long* T64;    // or [ndiag][rows][N] int64 sums of all batches (then k_batches = 1)
   int64_t diag_stride;     // rows * N
   int64_t batch_stride;    // ndiag * rows * N
-  int k_batches, ndiag, split, beta;
+  int k_batches, ndiag, split;
+  int beta;                // bits between consecutive planes (beta, or 2 beta for paired diagonals)
+  int e_base;              // -beta_slice (s + 1): exponent of the last plane's unit
   const int* rexp;         // [rows]
   const int* cexp;         // [N]
   int64_t rows, N;
@@ -975,11 +1028,14 @@ constexpr int kRecombineWidth = 4;
 // From this many K batches on, the batches are pre-summed in parallel before recombining.
 constexpr int kPreReduceBatches = 8;
 
-// C[m][n] = sigma_m sigma_n 2^(-beta (ndiag+1)) Nmn with Nmn = sum_d (sum_batches T_d)
-// 2^(beta (ndiag+1-d)), d = 2..ndiag+1, formed exactly: the first `split` diagonals in one
-// int64 Horner chain, the rest in another, joined into 128 bits and rounded once.
+// C[m][n] = sigma_m sigma_n 2^e_base Nmn with Nmn = sum_q (sum_batches T_q) 2^(beta (ndiag-1-q))
+// over the planes q (one diagonal each, or two when paired: then beta is twice the slice
+// width), formed exactly: the first `split` planes in one int64 Horner chain, the rest in
+// another, joined into 128 bits and rounded once.
 // Block = row m of C (grid-stride), threads across n, VW consecutive outputs per thread.
-template <int VW, typename TT>
+// SH > 0: the Horner shift is the constant SH (= a.beta), so the 64-bit shifts compile to a
+// fixed instruction pair instead of the general variable-shift sequence.
+template <int VW, typename TT, int SH = 0>
 __global__ void recombine_kernel(RecombineArgs a) {
   const TT* Tbase;
   if constexpr (sizeof(TT) == 8) {
@@ -987,8 +1043,9 @@ __global__ void recombine_kernel(RecombineArgs a) {
   } else {
     Tbase = a.T;
   }
-  const int lo_shift = a.beta * (a.ndiag - a.split);
-  const int e_base = -a.beta * (a.ndiag + 1);
+  const int hsh = SH > 0 ? SH : a.beta;
+  const int lo_shift = hsh * (a.ndiag - a.split);
+  const int e_base = a.e_base;
   // Vector path: VW-wide loads of T (its rows are VW-aligned when N is) and 16-byte stores of C.
   const bool vec =
       (a.N % VW) == 0 && (VW == 1 || ((a.ldc % 2) == 0 && ((uintptr_t)a.C % 16) == 0));
@@ -1002,15 +1059,17 @@ __global__ void recombine_kernel(RecombineArgs a) {
         long long hi[VW] = {}, lo[VW] = {};
         if (a.k_batches == 1) {
           // One batch: the diagonal loads are independent, unrolled so they are all in flight.
+          const TT* tp = trow + n0;
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             if (q < a.ndiag) {
               long long t[VW];
-              load_sums<VW>(trow + q * a.diag_stride + n0, t);
+              load_sums<VW>(tp, t);
+              tp += a.diag_stride;
 #pragma unroll
               for (int k = 0; k < VW; ++k) {
-                if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
-                else lo[k] = horner(lo[k], a.beta, t[k]);
+                if (q < a.split) hi[k] = horner(hi[k], hsh, t[k]);
+                else lo[k] = horner(lo[k], hsh, t[k]);
               }
             }
           }
@@ -1025,8 +1084,8 @@ __global__ void recombine_kernel(RecombineArgs a) {
             }
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
-              if (q < a.split) hi[k] = horner(hi[k], a.beta, t[k]);
-              else lo[k] = horner(lo[k], a.beta, t[k]);
+              if (q < a.split) hi[k] = horner(hi[k], hsh, t[k]);
+              else lo[k] = horner(lo[k], hsh, t[k]);
             }
           }
         }
@@ -1036,8 +1095,7 @@ __global__ void recombine_kernel(RecombineArgs a) {
           const int ec = a.cexp[n0 + k];
           v[k] = (row_bad || ec == kNonFiniteRow)
                      ? __longlong_as_double(0x7ff8000000000000ll)
-                     : int128_to_double((__int128)((unsigned __int128)(__int128)hi[k] << lo_shift) + (__int128)lo[k],
-                                        em + ec);
+                     : join_to_double(hi[k], lo[k], lo_shift, em + ec);
         }
         if constexpr (VW == 1) {
           __stcs(crow + n0, v[0]);
@@ -1053,13 +1111,12 @@ __global__ void recombine_kernel(RecombineArgs a) {
         for (int q = 0; q < a.ndiag; ++q) {
           long long t = 0;
           for (int kb = 0; kb < a.k_batches; ++kb) t += trow[kb * a.batch_stride + q * a.diag_stride + n];
-          if (q < a.split) hi = horner(hi, a.beta, t);
-          else lo = horner(lo, a.beta, t);
+          if (q < a.split) hi = horner(hi, hsh, t);
+          else lo = horner(lo, hsh, t);
         }
         crow[n] = (row_bad || a.cexp[n] == kNonFiniteRow)
                       ? __longlong_as_double(0x7ff8000000000000ll)
-                      : int128_to_double((__int128)((unsigned __int128)(__int128)hi << lo_shift) + (__int128)lo,
-                                         em + a.cexp[n]);
+                      : join_to_double(hi, lo, lo_shift, em + a.cexp[n]);
       }
     }
   }
@@ -1102,26 +1159,39 @@ struct EmuGemm {
     recombine_blocks = (int64_t)std::max(per_sm, 1) * sms;
     if (!choose_emu_shape(K, MT * NT, sms, &sh))
       return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");
-    // Slab: int32 sums (k_batches x s x rows x N x 4 B) within about 4 GB.
-    const size_t t_tile = (size_t)sh.k_batches * sh.sp.s * BM * N * sizeof(int);
+    // Paired diagonals: set tiles of 128 (two diagonals share a tile's 256 accumulator columns).
+    if (sh.paired) NT = (N + BN / 2 - 1) / (BN / 2);
+    // Slab: int32 sums (k_batches x planes x rows x N x 4 B) within about 4 GB.
+    const size_t t_tile = (size_t)sh.k_batches * sh.planes * BM * N * sizeof(int);
     slab_tiles = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / t_tile)));
     a_stride = slab_tiles * sh.KC * (int64_t)C::A_CHUNK;
-    b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;
-    ZP_TRY(bsl.alloc((size_t)sh.sp.s * b_stride, stream));
+    b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;  // a paired B holds NT x KC x s blocks of 16 KB: the same bytes
+    ZP_TRY(bsl.alloc((size_t)sh.sp.s * b_stride / (sh.paired ? 2 : 1), stream));
     ZP_TRY(cexp.alloc((size_t)N * sizeof(int), stream));
     ZP_TRY(asl.alloc((size_t)sh.sp.s * a_stride, stream));
     ZP_TRY(rexp.alloc((size_t)slab_tiles * BM * sizeof(int), stream));
     ZP_TRY(tbuf.alloc((size_t)slab_tiles * t_tile, stream));
     if (sh.k_batches >= kPreReduceBatches)
-      ZP_TRY(accbuf.alloc((size_t)sh.sp.s * slab_tiles * BM * N * sizeof(long long), stream));
+      ZP_TRY(accbuf.alloc((size_t)sh.planes * slab_tiles * BM * N * sizeof(long long), stream));
     ZP_TRY(maxbits.alloc((size_t)std::max<int64_t>(N, slab_tiles * BM) * sizeof(unsigned long long), stream));
     ZP_TRY(scale_rows(B, N, K, (unsigned long long*)maxbits.ptr, (int*)cexp.ptr, stream));
-    if (B.sk == 1 && B.sr != 1)
+    const bool kfast = B.sk == 1 && B.sr != 1;
+    if (sh.paired) {
+      // Per (set tile, K chunk): slices 0..s-1 of 128 rows back to back.
+      const int64_t cs = (int64_t)sh.sp.s * kSliceBlock;
+      if (kfast)
+        slice_rows_kernel<BN / 2, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                                 (uint8_t*)bsl.ptr, kSliceBlock, cs);
+      else
+        slice_rows_kernel<BN / 2, false><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                                  (uint8_t*)bsl.ptr, kSliceBlock, cs);
+    } else if (kfast) {
       slice_rows_kernel<BN, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
-                                                           (uint8_t*)bsl.ptr, b_stride);
-    else
+                                                           (uint8_t*)bsl.ptr, b_stride, C::B_CHUNK);
+    } else {
       slice_rows_kernel<BN, false><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
-                                                    (uint8_t*)bsl.ptr, b_stride);
+                                                            (uint8_t*)bsl.ptr, b_stride, C::B_CHUNK);
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "B slicing launch");
   }
@@ -1133,18 +1203,28 @@ struct EmuGemm {
     ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
     if (A.sk == 1 && A.sr != 1)
       slice_rows_kernel<BM, true><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
-                                                           (uint8_t*)asl.ptr, a_stride);
+                                                           (uint8_t*)asl.ptr, a_stride, C::A_CHUNK);
     else
       slice_rows_kernel<BM, false><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
-                                                            (uint8_t*)asl.ptr, a_stride);
+                                                            (uint8_t*)asl.ptr, a_stride, C::A_CHUNK);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "A slicing launch");
     const int64_t trows = slab_tiles * BM;
-    const int64_t diag_stride = trows * N, batch_stride = (int64_t)sh.sp.s * diag_stride;
-    for (int d = 2; d <= sh.sp.s + 1; ++d) {
+    const int64_t diag_stride = trows * N, batch_stride = (int64_t)sh.planes * diag_stride;
+    const int hsh = sh.paired ? 2 * sh.sp.beta : sh.sp.beta;
+    const int e_base = -sh.sp.beta * (sh.sp.s + 1);
+    for (int q = 0; q < sh.planes; ++q) {
       GemmArgs ga{(const uint8_t*)asl.ptr, (const uint8_t*)bsl.ptr,
-                  (float*)tbuf.ptr + (size_t)(d - 2) * diag_stride, rows, N, 0, tiles, (int)NT, sh.KC};
-      ga.npairs = d - 1;
+                  (float*)tbuf.ptr + (size_t)q * diag_stride, rows, N, 0, tiles, (int)NT, sh.KC};
+      if (sh.paired) {
+        // Plane q: diagonals (2q - s % 2, 2q + 1 - s % 2), 0-based.
+        ga.paired = 1;
+        ga.dp = 2 * q - (sh.sp.s & 1);
+        ga.beta = sh.sp.beta;
+        ga.s_slices = sh.sp.s;
+      } else {
+        ga.npairs = q + 1;  // diagonal q: pairs (t, q - t)
+      }
       ga.a_slice_stride = a_stride;
       ga.b_slice_stride = b_stride;
       ga.k_batches = sh.k_batches;
@@ -1152,8 +1232,9 @@ struct EmuGemm {
       ga.t_batch_stride = batch_stride;
       ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, gs, stream));
     }
-    RecombineArgs ra{(const int*)tbuf.ptr, nullptr, diag_stride, batch_stride, sh.k_batches, sh.sp.s, sh.split,
-                     sh.sp.beta, (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
+    RecombineArgs ra{(const int*)tbuf.ptr, nullptr, diag_stride, batch_stride, sh.k_batches, sh.planes,
+                     sh.plane_split, hsh, e_base,
+                     (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
     const unsigned rblocks = (unsigned)std::min<int64_t>(rows, recombine_blocks);
     if (sh.k_batches >= kPreReduceBatches) {
       // Many K batches (a small output cut along a long K): the batches are first summed into
@@ -1170,7 +1251,14 @@ struct EmuGemm {
       ra.k_batches = 1;
       recombine_kernel<kRecombineWidth, long long><<<rblocks, 256, 0, stream>>>(ra);
     } else {
-      recombine_kernel<kRecombineWidth, int><<<rblocks, 256, 0, stream>>>(ra);
+      // Constant Horner shifts for the slice widths in use (beta, or 2 beta for paired planes).
+      switch (ra.beta) {
+        case 12: recombine_kernel<kRecombineWidth, int, 12><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 14: recombine_kernel<kRecombineWidth, int, 14><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 10: recombine_kernel<kRecombineWidth, int, 10><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 8: recombine_kernel<kRecombineWidth, int, 8><<<rblocks, 256, 0, stream>>>(ra); break;
+        default: recombine_kernel<kRecombineWidth, int><<<rblocks, 256, 0, stream>>>(ra); break;
+      }
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "recombine_kernel launch");

@@ -35,7 +35,7 @@ def test_shapes_are_exact_and_cover_k(driver):
     text = "".join(f"{k} {t} 152\n" for k, t in CASES)
     out = subprocess.run([driver], input=text, capture_output=True, text=True, check=True).stdout.split("\n")
     for (K, tiles), line in zip(CASES, out):
-        ok, beta, s, KC, cpb, nb, split = map(int, line.split())
+        ok, beta, s, KC, cpb, nb, split, paired, planes, psplit = map(int, line.split())
         assert ok, (K, tiles)
         assert KC == -(-K // BK)
         assert beta * s >= 54
@@ -47,10 +47,29 @@ def test_shapes_are_exact_and_cover_k(driver):
         assert tb + beta * (split - 1) + 1 <= 63
         if s > split:
             assert tb + beta * (s - split - 1) + 1 <= 63
+        if paired:
+            # two neighbouring diagonals in one int32: T_d 2^beta + T_(d+1) below 2^31
+            assert cpb * BK * per_k * (2 ** beta + 1) < 2 ** 31, (K, tiles, beta, s, cpb)
+            assert planes == (s + 1) // 2
+            tp = 31 + max(0, math.ceil(math.log2(nb)))  # bits of a plane summed over batches
+            assert 1 <= psplit <= planes
+            assert tp + 2 * beta * (psplit - 1) + 1 <= 63
+            if planes > psplit:
+                assert tp + 2 * beta * (planes - psplit - 1) + 1 <= 63
+        else:
+            assert planes == s and psplit == split
         if tiles >= 2 * 152 and nb == 1:
             # a large output takes one batch with the fewest slice pairs K allows
             assert beta == max(b for b, ss in ((7, 8), (6, 9), (5, 11), (4, 14))
                                if KC * BK * (2 ** (2 * b) + (ss - 2) * 2 ** (2 * b - 2)) < 2 ** 24)
+
+
+def test_mixed_n32_shape_pairs_its_diagonals(driver):
+    """561 modes (K = 576) over many output tiles: beta = 6, s = 9, one batch, and the nine
+    diagonals travel as five int32 planes (the largest pair sum, 9 chunks x 64 x 2^12 x 2.75 x
+    65 = 4.2e8, is far below 2^31)."""
+    out = subprocess.run([driver], input="561 100000 152\n", capture_output=True, text=True, check=True).stdout
+    assert list(map(int, out.split())) == [1, 6, 9, 9, 9, 1, 7, 1, 5, 3]
 
 
 def test_contraction_too_long_is_refused(driver):
