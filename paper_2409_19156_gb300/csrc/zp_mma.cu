@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <utility>
 #include <vector>
 
@@ -41,7 +42,6 @@ namespace {
 constexpr int BM = 128;  // points per tile (TMEM lanes)
 constexpr int BN = 256;  // coefficient sets per tile (TMEM columns per accumulator)
 constexpr uint32_t kRingBytes = 192u << 10;  // shared-memory ring of operand stages
-constexpr int kGemmThreads = 192;            // 6 warps: producer, MMA, 4 x epilogue
 constexpr int kCoeffThreads = BN;
 
 // Operand kinds of the GEMM: BF16x3 (hi/lo halves, three products), TF32 (one product),
@@ -62,10 +62,7 @@ struct Cfg {
   static constexpr uint32_t B_PART = BN * ROW;
   static constexpr uint32_t A_CHUNK = A_PART * PARTS;
   static constexpr uint32_t B_CHUNK = B_PART * PARTS;
-  static constexpr uint32_t STAGE = A_CHUNK + B_CHUNK;
-  static constexpr int STAGES = (int)(kRingBytes / STAGE);
   static constexpr int KSTEPS = (int)ROW / 32;  // MMA K-steps per chunk (16 bf16 or 8 tf32 = 32 bytes each)
-  static constexpr uint32_t SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 __device__ unsigned int g_split_error = 0;  // set when a bounded wait gives up
@@ -419,47 +416,92 @@ struct GemmArgs {
 // Bytes of one 128-row slice block of the paired B layout.
 constexpr uint32_t kSliceBlock = BM * Cfg<KIND_SLICE>::ROW;
 
-// One CTA per output tile at a time (persistent over tiles); every operand chunk is brought
-// from global memory into this CTA's own shared memory by a plain bulk copy.
-template <int KIND>
-__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a) {
+// Threads of the GEMM kernel: producer, MMA and 4 epilogue warps, plus, for a CTA pair, one
+// warp whose thread passes barrier signals between the pair's two CTAs.
+template <int CG>
+constexpr int gemm_threads() {
+  return CG == 2 ? 224 : 192;
+}
+
+// One CTA's shared-memory stage: its A chunk and its share of the B chunk's rows (all of them
+// for a single CTA, half for each CTA of a pair).
+template <int KIND, int CG>
+struct Stage {
   using C = Cfg<KIND>;
+  static constexpr uint32_t B_PART = (uint32_t)(BN / CG) * C::ROW;
+  static constexpr uint32_t B_CHUNK = B_PART * C::PARTS;
+  static constexpr uint32_t BYTES = C::A_CHUNK + B_CHUNK;
+  static constexpr int COUNT = (int)(kRingBytes / BYTES);
+  static constexpr uint32_t SMEM = COUNT * BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+// Persistent GEMM over output tiles; every operand chunk comes from global memory into the
+// CTA's own shared memory by a plain bulk copy.  CG = 1: one CTA per 128-point tile.  CG = 2:
+// a cluster of two CTAs per 256-point tile, multiplied by cta_group::2 MMAs that the even CTA
+// issues: each CTA loads its own 128 points' A chunk and half of the B chunk's rows, the MMA
+// reads both CTAs' halves, and each CTA's tensor memory receives its own points' accumulators,
+// so a B chunk crosses L2 once per pair instead of once per CTA.  The pair's signals are remote
+// mbarrier arrives: the odd CTA's relay thread reports its landed chunks to the even CTA, the
+// even CTA's forwarder thread passes the MMA completions (stage free, accumulator ready) to the
+// odd one, and the odd CTA's epilogue warps report drained accumulators to the even one.
+template <int KIND, int CG>
+__global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmArgs a) {
+  using C = Cfg<KIND>;
+  using S = Stage<KIND, CG>;
   constexpr bool TF32 = KIND == KIND_TF32;
+  constexpr bool PAIR = CG == 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-  uint64_t* empty = full + C::STAGES;
-  uint64_t* tmem_full = empty + C::STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::COUNT * S::BYTES);
+  uint64_t* empty = full + S::COUNT;
+  uint64_t* tmem_full = empty + S::COUNT;
   uint64_t* tmem_empty = tmem_full + 2;
-  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(tmem_empty + 2);
+  uint64_t* drain = tmem_empty + 2;
+  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
+  volatile int* never = abort_flag + 1;  // stays 0: waits that must not be cut short by an abort
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t cid = blockIdx.x, nctas = gridDim.x;
+  const uint32_t rank = PAIR ? ptx::cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
+  const int64_t cid = blockIdx.x / CG, nclusters = gridDim.x / CG;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < C::STAGES; ++i) {
-      ptx::mbar_init(&full[i], 1);
+    for (int i = 0; i < S::COUNT; ++i) {
+      // The pair's even CTA also counts the relay's arrive for the odd CTA's half.
+      ptx::mbar_init(&full[i], PAIR && leader ? 2 : 1);
       ptx::mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tmem_full[i], 1);
-      ptx::mbar_init(&tmem_empty[i], 128);
+      ptx::mbar_init(&tmem_empty[i], 4 * CG);  // one arrive per epilogue warp of each CTA
     }
+    ptx::mbar_init(drain, 1);
     *abort_flag = 0;
+    *never = 0;
     ptx::fence_barrier_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_base_slot, 512);
-    ptx::tmem_relinquish();
+    if constexpr (PAIR) {
+      ptx::tmem_alloc_pair(tmem_base_slot, 512);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(tmem_base_slot, 512);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) {
+    ptx::cluster_sync();  // both CTAs' barriers exist before any remote arrive
+  } else {
+    __syncthreads();
+  }
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
 
-  // Tile t: k batch t / per_batch, then point tile and set tile, set tile fastest.
+  // Tile t: k batch t / per_batch, then group of CG point tiles and set tile, set tile fastest.
   const int64_t groups_n = a.n_tiles;
-  const int64_t per_batch = a.m_tiles * groups_n;
+  const int64_t groups_m = (a.m_tiles + CG - 1) / CG;
+  const int64_t per_batch = groups_m * groups_n;
   const int64_t total = per_batch * a.k_batches;
   const int kcb = a.kc_per_batch > 0 ? a.kc_per_batch : a.KC;
   // K chunks [kc0, kc0 + nkc) of tile t.
@@ -468,6 +510,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     kc0 = kb * kcb;
     nkc = (kc0 + kcb < a.KC ? kc0 + kcb : a.KC) - kc0;
   };
+  // Operand chunks of tile t: per slice pair (or per A slice with paired diagonals) nkc chunks.
+  auto n_items = [&](int nkc) { return (KIND == KIND_SLICE && a.paired ? a.dp + 2 : a.npairs) * nkc; };
+  // This CTA's point tile of tile t, slab-local (past the slab's last tile for the odd CTA of a
+  // half-filled last group: that CTA loads the last tile instead and stores nothing).
+  auto own_mtile = [&](int64_t t) { return ((t % per_batch) / groups_n) * CG + (int64_t)rank; };
   auto fail = [&]() {
     *abort_flag = 1;
     atomicOr(&g_split_error, 1u);
@@ -477,37 +524,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t t = cid; t < total && !*abort_flag; t += nctas) {
-        const int64_t tm = t % per_batch;
-        const int64_t mt = tm / groups_n;
-        const int nt = (int)(tm % groups_n);
+      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters) {
+        const int64_t mt_own = own_mtile(t);
+        const int64_t mt = mt_own < a.m_tiles ? mt_own : a.m_tiles - 1;
+        const int nt = (int)((t % per_batch) % groups_n);
         int kc0, nkc;
         k_range(t, kc0, nkc);
         const uint8_t* gA0 = a.A + (size_t)mt * a.KC * C::A_CHUNK;
         const uint8_t* gB0 = a.B + (size_t)nt * a.KC * C::B_CHUNK;
-        const int items = (KIND == KIND_SLICE && a.paired ? a.dp + 2 : a.npairs) * nkc;
+        const int items = n_items(nkc);
         for (int kk = 0; kk < items; ++kk) {
-          if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+          if (!ptx::mbar_wait<PAIR>(&empty[stage], phase ^ 1u, abort_flag)) {
             fail();
             break;
           }
           const int ts = kk / nkc, kc = kc0 + kk % nkc;  // A slice ts
           const uint8_t* gA = gA0 + (size_t)ts * a.a_slice_stride + (size_t)kc * C::A_CHUNK;
-          const uint8_t* gB;
-          uint32_t b_bytes = C::B_CHUNK;
+          uint8_t* sA = smem + stage * S::BYTES;
+          uint8_t* sB = sA + C::A_CHUNK;
           if (KIND == KIND_SLICE && a.paired) {
-            // B slices (dp - ts, dp + 1 - ts), or slice 0 alone for ts = dp + 1.
+            // B slices (dp - ts, dp + 1 - ts), or slice 0 alone for ts = dp + 1 (an N = 128
+            // MMA); a pair's CTAs hold one slice each, or one half of slice 0's rows each.
             const bool both = ts <= a.dp;
-            gB = a.B + (((size_t)nt * a.KC + kc) * a.s_slices + (both ? a.dp - ts : 0)) * kSliceBlock;
-            b_bytes = both ? 2 * kSliceBlock : kSliceBlock;
+            const uint8_t* blk = a.B + (((size_t)nt * a.KC + kc) * a.s_slices + (both ? a.dp - ts : 0)) * kSliceBlock;
+            const uint32_t b_bytes = (both ? 2 * kSliceBlock : kSliceBlock) / CG;
+            ptx::mbar_arrive_expect_tx(&full[stage], C::A_CHUNK + b_bytes);
+            ptx::bulk_g2s(sA, gA, C::A_CHUNK, &full[stage]);
+            ptx::bulk_g2s(sB, blk + rank * b_bytes, b_bytes, &full[stage]);
           } else {
-            gB = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride + (size_t)kc * C::B_CHUNK;
+            // Rows [rank BN / CG, (rank + 1) BN / CG) of each part of the chunk.
+            const uint8_t* gc = gB0 + (size_t)(a.npairs - 1 - ts) * a.b_slice_stride + (size_t)kc * C::B_CHUNK;
+            ptx::mbar_arrive_expect_tx(&full[stage], S::BYTES);
+            ptx::bulk_g2s(sA, gA, C::A_CHUNK, &full[stage]);
+            if constexpr (C::PARTS == 1 || !PAIR) {
+              ptx::bulk_g2s(sB, gc + rank * S::B_PART, S::B_CHUNK, &full[stage]);
+            } else {
+#pragma unroll
+              for (int part = 0; part < C::PARTS; ++part)
+                ptx::bulk_g2s(sB + part * S::B_PART, gc + part * C::B_PART + rank * S::B_PART, S::B_PART,
+                              &full[stage]);
+            }
           }
-          uint8_t* sA = smem + stage * C::STAGE;
-          ptx::mbar_arrive_expect_tx(&full[stage], C::A_CHUNK + b_bytes);
-          ptx::bulk_g2s(sA, gA, C::A_CHUNK, &full[stage]);
-          ptx::bulk_g2s(sA + C::A_CHUNK, gB, b_bytes, &full[stage]);
-          if (++stage == C::STAGES) {
+          if (++stage == S::COUNT) {
             stage = 0;
             phase ^= 1u;
           }
@@ -515,15 +573,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = TF32 ? ptx::idesc_tf32_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
+    if (lane == 0 && leader) {
+      constexpr uint32_t idesc = TF32 ? ptx::idesc_tf32_f32(BM * CG, BN) : ptx::idesc_bf16_f32(BM * CG, BN);
+      constexpr uint32_t idesc_half = ptx::idesc_bf16_f32(BM * CG, BN / 2);
+      auto mma = [&](uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+        if constexpr (TF32) {
+          if constexpr (PAIR) ptx::mma_tf32_pair(d, ad, bd, id, acc);
+          else ptx::mma_tf32(d, ad, bd, id, acc);
+        } else {
+          if constexpr (PAIR) ptx::mma_bf16_pair(d, ad, bd, id, acc);
+          else ptx::mma_bf16(d, ad, bd, id, acc);
+        }
+      };
+      auto commit = [&](uint64_t* bar) {
+        if constexpr (PAIR) ptx::mma_commit_pair(bar);
+        else ptx::mma_commit(bar);
+      };
       int stage = 0;
       uint32_t phase = 0;
       int64_t local = 0;
-      for (int64_t t = cid; t < total && !*abort_flag; t += nctas, ++local) {
+      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters, ++local) {
         const uint32_t acc = (uint32_t)(local & 1);
         const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
-        if (!ptx::mbar_wait(&tmem_empty[acc], acc_phase ^ 1u, abort_flag)) {
+        if (!ptx::mbar_wait<PAIR>(&tmem_empty[acc], acc_phase ^ 1u, abort_flag)) {
           fail();
           break;
         }
@@ -532,15 +604,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
         int kc0, nkc;
         k_range(t, kc0, nkc);
         bool ok = true;
-        const int items = (KIND == KIND_SLICE && a.paired ? a.dp + 2 : a.npairs) * nkc;
+        const int items = n_items(nkc);
         for (int kk = 0; kk < items; ++kk) {
-          if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
+          if (!ptx::mbar_wait<PAIR>(&full[stage], phase, abort_flag)) {
             fail();
             ok = false;
             break;
           }
           ptx::tc_fence_after();
-          const uint32_t sA = ptx::smem_u32(smem + stage * C::STAGE);
+          const uint32_t sA = ptx::smem_u32(smem + stage * S::BYTES);
           const uint32_t sB = sA + C::A_CHUNK;
           // Paired slice tiles: A slice dp + 1 meets B slice 0 only (diagonal dp + 1, N = 128).
           const bool half = KIND == KIND_SLICE && a.paired && kk / nkc > a.dp;
@@ -548,53 +620,91 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           for (int ks = 0; ks < C::KSTEPS; ++ks) {
             const uint32_t koff = ks * 32;
             const uint32_t first = (kk == 0 && ks == 0) ? 0u : 1u;
-            if constexpr (TF32) {
-              ptx::mma_tf32(d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff), ptx::sw_kmajor_desc<C::ROW>(sB + koff), idesc,
-                            first);
-            } else if constexpr (KIND == KIND_SLICE) {
-              constexpr uint32_t idesc_half = ptx::idesc_bf16_f32(BM, BN / 2);
-              ptx::mma_bf16(half ? d_tmem + BN / 2 : d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff),
-                            ptx::sw_kmajor_desc<C::ROW>(sB + koff), half ? idesc_half : idesc, first);
-            } else {
+            if constexpr (KIND == KIND_BF16X3) {
               const uint64_t ah = ptx::sw_kmajor_desc<C::ROW>(sA + koff);
               const uint64_t al = ptx::sw_kmajor_desc<C::ROW>(sA + C::A_PART + koff);
               const uint64_t bh = ptx::sw_kmajor_desc<C::ROW>(sB + koff);
-              const uint64_t bl = ptx::sw_kmajor_desc<C::ROW>(sB + C::B_PART + koff);
-              ptx::mma_bf16(d_tmem, ah, bh, idesc, first);
-              ptx::mma_bf16(d_tmem, ah, bl, idesc, 1u);
-              ptx::mma_bf16(d_tmem, al, bh, idesc, 1u);
+              const uint64_t bl = ptx::sw_kmajor_desc<C::ROW>(sB + S::B_PART + koff);
+              mma(d_tmem, ah, bh, idesc, first);
+              mma(d_tmem, ah, bl, idesc, 1u);
+              mma(d_tmem, al, bh, idesc, 1u);
+            } else {
+              mma(half ? d_tmem + BN / 2 : d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff),
+                  ptx::sw_kmajor_desc<C::ROW>(sB + koff), half ? idesc_half : idesc, first);
             }
           }
-          ptx::mma_commit(&empty[stage]);
-          if (++stage == C::STAGES) {
+          commit(&empty[stage]);
+          if (++stage == S::COUNT) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (!ok) break;
-        ptx::mma_commit(&tmem_full[acc]);
+        commit(&tmem_full[acc]);
+      }
+      // Every MMA issued here completes before the CTA (and a pair's peer, whose shared and
+      // tensor memory those MMAs use) moves on to leave.
+      commit(drain);
+      if (!ptx::mbar_wait(drain, 0u, never)) atomicOr(&g_split_error, 1u);
+    }
+  } else if (PAIR && warp == 6) {
+    // Pair signals, in the same order as the MMA thread's waits and commits.  Even CTA: each
+    // stage the MMAs freed and each accumulator they filled is passed to the odd CTA.  Odd CTA:
+    // each of its landed chunks is reported to the even CTA's full barrier.
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t local = 0;
+      for (int64_t t = cid; t < total && !*abort_flag; t += nclusters, ++local) {
+        int kc0, nkc;
+        k_range(t, kc0, nkc);
+        const int items = n_items(nkc);
+        bool ok = true;
+        for (int kk = 0; kk < items; ++kk) {
+          uint64_t* bar = leader ? &empty[stage] : &full[stage];
+          if (!ptx::mbar_wait(bar, phase, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          ptx::mbar_arrive_remote(ptx::mapa_shared(bar, leader ? 1u : 0u));
+          if (++stage == S::COUNT) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        if (leader) {
+          const uint32_t acc = (uint32_t)(local & 1);
+          if (!ptx::mbar_wait(&tmem_full[acc], (uint32_t)((local >> 1) & 1), abort_flag)) {
+            fail();
+            break;
+          }
+          ptx::mbar_arrive_remote(ptx::mapa_shared(&tmem_full[acc], 1u));
+        }
       }
     }
-  } else {
-    // Epilogue: warp (2..5) & 3 selects the TMEM lane quadrant it may access.
+  } else if (warp >= 2 && warp <= 5) {
+    // Epilogue: warp & 3 selects the TMEM lane quadrant it may access.
     const uint32_t q = (uint32_t)(warp & 3);
     const uint32_t row = q * 32 + lane;
+    const uint32_t empty_remote = PAIR && !leader ? ptx::mapa_shared(&tmem_empty[0], 0u) : 0u;
     int64_t local = 0;
-    for (int64_t t = cid; t < total; t += nctas, ++local) {
+    for (int64_t t = cid; t < total; t += nclusters, ++local) {
       const uint32_t acc = (uint32_t)(local & 1);
       const uint32_t acc_phase = (uint32_t)((local >> 1) & 1);
       // One lane per warp polls the barrier; the shuffle hands its answer to the warp.
       bool ok = true;
-      if (lane == 0) ok = ptx::mbar_wait(&tmem_full[acc], acc_phase, abort_flag);
+      if (lane == 0) ok = ptx::mbar_wait<PAIR>(&tmem_full[acc], acc_phase, abort_flag);
       if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
         fail();
         break;
       }
       ptx::tc_fence_after();
-      const int64_t tm = t % per_batch;
-      const int64_t mt = a.mt_base + tm / groups_n;
-      const int nt = (int)(tm % groups_n);
-      const int64_t p = mt * BM + row;
+      const int64_t mt_own = own_mtile(t);
+      const int nt = (int)((t % per_batch) % groups_n);
+      const int64_t p = (a.mt_base + mt_own) * BM + row;
+      const bool store = mt_own < a.m_tiles && p < a.P;
       const bool paired = KIND == KIND_SLICE && a.paired;
       const int tile_cols = paired ? BN / 2 : BN;
       const int64_t col0 = (int64_t)nt * tile_cols;
@@ -629,7 +739,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
             for (int i = 0; i < 32; ++i) v[i] = (uint32_t)__float2int_rn(__uint_as_float(v[i]));
           }
         }
-        if (p < a.P) {
+        if (store) {
           const int64_t cbase = col0 + c0;
           if (vec && cbase + 32 <= a.S) {
             float4* dst = reinterpret_cast<float4*>(frow + cbase);
@@ -644,15 +754,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(GemmArgs a)
           }
         }
       }
+      // The warp's loads of this accumulator are done: one arrive per warp (remote for the odd
+      // CTA of a pair, whose accumulators the even CTA's MMAs fill).
       ptx::tc_fence_before();
-      ptx::mbar_arrive(&tmem_empty[acc]);
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR && !leader) ptx::mbar_arrive_remote(empty_remote + acc * (uint32_t)sizeof(uint64_t));
+        else ptx::mbar_arrive(&tmem_empty[acc]);
+      }
     }
   }
   ptx::tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) {
+    ptx::cluster_sync();  // no CTA of a pair leaves while its peer may still signal it
+  } else {
+    __syncthreads();
+  }
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, 512);
+    if constexpr (PAIR) ptx::tmem_dealloc_pair(tmem_base, 512);
+    else ptx::tmem_dealloc(tmem_base, 512);
   }
 }
 
@@ -698,33 +819,88 @@ struct PhaseTimer {
 // shared memory).
 struct GemmShape {
   int sms = 0;
+  int pairs = 0;  // CTA pairs that can be resident at once (0: pairs cannot run)
 };
+
+// CTA pairs of split_gemm_kernel<KIND, 2> that fit on the GPU at once (one per two SMs when
+// the GPCs allow it), after raising the kernel's shared-memory limit.
+template <int KIND>
+int max_pairs() {
+  using S = Stage<KIND, 2>;
+  if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(2);
+  lc.blockDim = dim3(gemm_threads<2>());
+  lc.dynamicSmemBytes = S::SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<KIND, 2>, &lc) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 
 template <int KIND>
 zp_status gemm_shape(GemmShape* g) {
   static DeviceMemo<GemmShape> memo;
   return memo.get(g, [](GemmShape* x) -> zp_status {
-    using C = Cfg<KIND>;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(split_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(split_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Stage<KIND, 1>::SMEM) != cudaSuccess) {
       cudaGetLastError();
       return set_error(ZP_ERR_CUDA, "cudaFuncSetAttribute(split_gemm_kernel)");
     }
+    x->pairs = max_pairs<KIND>();
     return ZP_OK;
   });
 }
 
-// Persistent launch over `tiles` point tiles x NT set tiles (x K batches), at most one CTA per SM.
+// CTA pairs are used unless ZP_GEMM_CTA_PAIRS=0 (read at every launch).
+inline bool pairs_enabled() {
+  const char* v = std::getenv("ZP_GEMM_CTA_PAIRS");
+  return !(v && v[0] == '0');
+}
+
+// Persistent launch over `tiles` point tiles x NT set tiles (x K batches): CTA pairs over
+// 256-point tiles when they can run and there are two point tiles or more, else one CTA per
+// SM over 128-point tiles.
 template <int KIND>
 zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, const GemmShape& g, cudaStream_t stream) {
-  using C = Cfg<KIND>;
   const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, g.sms);
-  split_gemm_kernel<KIND><<<grid, kGemmThreads, C::SMEM, stream>>>(ga);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (g.pairs > 0 && tiles >= 2 && pairs_enabled()) {
+    const int64_t groups = (tiles + 1) / 2 * NT * kb;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(2 * std::min<int64_t>(groups, g.pairs)));
+    lc.blockDim = dim3(gemm_threads<2>());
+    lc.dynamicSmemBytes = Stage<KIND, 2>::SMEM;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelEx(&lc, split_gemm_kernel<KIND, 2>, ga);
+  } else {
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles * NT * kb, g.sms);
+    split_gemm_kernel<KIND, 1><<<grid, gemm_threads<1>(), Stage<KIND, 1>::SMEM, stream>>>(ga);
+    e = cudaGetLastError();
+  }
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "split_gemm_kernel launch");
 }
 

@@ -174,3 +174,23 @@ def test_split_step_descriptors_irregular_and_odd_steps(prec):
     want = np.array(oseries.series_eval(ns, ms, r, th, C.tolist()))
     tol = REL[prec] * abs_sum(ns, ms, r, th, C) + 1e-6
     assert (np.abs(F - want) <= tol).all()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "fp64emu"])
+@pytest.mark.parametrize("nmax,P,S", [(32, 3_001, 300), (20, 129, 256), (8, 20_000, 17)])
+def test_cta_pairs_match_single_ctas(prec, nmax, P, S, monkeypatch):
+    """The GEMM on CTA pairs (256-point tiles, cta_group::2 MMAs, half of B in each CTA) and on
+    single CTAs (ZP_GEMM_CTA_PAIRS=0, read at every launch) run the same MMA sequence for every
+    output: identical results, for odd point-tile counts too (a pair's missing second tile)."""
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.sqrt_uniform_points(P, 140 + nmax)
+    C = inputs.scaled_normal_coeffs(ns, S, 140 + nmax)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    paired = zp.series_eval(ns, ms, rt, tt, Ct, prec)
+    torch.cuda.synchronize()
+    wait_ok()
+    monkeypatch.setenv("ZP_GEMM_CTA_PAIRS", "0")
+    single = zp.series_eval(ns, ms, rt, tt, Ct, prec)
+    torch.cuda.synchronize()
+    wait_ok()
+    assert torch.equal(paired, single)
