@@ -539,8 +539,7 @@ zp_status build_fused(zp_batch* b) {
     d.mode_N = p->dev.mode_N;
     d.fcols = p->dev.fused_col;
   d.scols = (const int32_t*)(p->dev.fused_col + p->cols.size());
-  d.ncols_s[0] = p->fused_ncols[0];
-  d.ncols_s[1] = p->fused_ncols[1];
+  for (int st = 0; st < kFusedStreams; ++st) d.ncols_s[st] = p->fused_ncols[st];
   d.units = p->fused_units;
     d.ep_disc = p->fused_ep;
     d.kperm = p->dev.fused_kperm;

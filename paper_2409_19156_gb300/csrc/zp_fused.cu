@@ -14,17 +14,20 @@
 // d <= 12 (the dropped pairs weigh below 2^-60 of the scales).
 //
 // One persistent CTA per SM works through 128-point tiles:
-//  - warps 0-3 (one thread per point) walk every |m| column of the plan with the float64
-//    recursion of Sec. 2 (Algorithm 1's column order, cos/sin(m theta) by angle addition
-//    between consecutive columns), form each value, cut it into its 11 digits on the integer
-//    pipe and write them into 11 digit tiles in shared memory (the tensor core's 64-byte
-//    swizzled K-major layout, 32 K values per stage, two stages);
-//  - warp 4 issues the tcgen05 MMAs: per K step and A digit t, one MMA of N = 176 against the
+//  - warps 0-11 (three threads per point, each walking one of three streams of |m| columns:
+//    more independent float64 chains per scheduler than two streams give) run the float64
+//    recursion of Sec. 2 (Algorithm 1's column order within a stream, cos/sin(m theta) by
+//    angle addition between consecutive columns), form each value, cut it into its 11 digits
+//    on the integer pipe and write them into 11 digit tiles in shared memory (the tensor
+//    core's 64-byte swizzled K-major layout, 32 K values per stage, two stages, the streams'
+//    8-value units interleaved along K);
+//  - warp 12 issues the tcgen05 MMAs: per K step and A digit t, one MMA of N = 176 against the
 //    coefficient digit tile shifted by t blocks of 16 rows (zero blocks in front), so that
 //    every MMA adds a_t b_u into the TMEM columns of diagonal t + u for all u at once; every
 //    diagonal sum is an integer below 2^24 (at most 5041 modes), hence exact in float32;
-//  - warps 5-8 take each finished tile's 11 x 16 diagonal sums out of TMEM, recombine them
-//    exactly in integers (two Horner chains joined into 128 bits) and round once to float64.
+//  - the warps of streams 0 and 1, after producing a tile, take the previous tile's 11 x 16
+//    diagonal sums out of TMEM, recombine them exactly in integers (two Horner chains joined
+//    into 128 bits) and round once to float64.
 // The K order of the contraction is the plan's slot order with every column padded to a
 // multiple of 8 positions (so a column's steps fill whole 16-byte operand units in unrolled
 // straight-line code), and the coefficient digits are prepared per call in that order
@@ -61,10 +64,13 @@ constexpr uint32_t kStageBytes = kABytes + kBPadBytes;       // 109.5 KB
 constexpr int kStages = 2;
 constexpr int kAccCols = kDig * FNS;                         // 176 TMEM columns per tile
 constexpr int kAccStride = 256;                              // two accumulators in 512 columns
-// Warps 0-7 produce (warp w: point rows 32 (w % 4) .. + 31, stream w / 4) and also drain the
-// accumulator of the previous tile (warp w: its rows, sets 8 (w / 4) .. + 7); warp 8 issues MMAs.
-constexpr int kProducerWarps = 8, kMmaWarp = 8;
-constexpr int kThreads = 32 * (kProducerWarps + 1);  // 288
+// Warps 0 .. 4 kStreams - 1 produce (warp w: point rows 32 (w % 4) .. + 31, stream w / 4); the
+// warps of streams 0 and 1 also drain the accumulator of the previous tile (warp w: its rows,
+// sets 8 (w / 4) .. + 7); the last warp issues MMAs.
+constexpr int kStreams = kFusedStreams;
+constexpr int kProducerWarps = 4 * kStreams, kMmaWarp = kProducerWarps;
+constexpr int kDrainWarps = 8;
+constexpr int kThreads = 32 * (kProducerWarps + 1);  // 416
 constexpr int kSplit = 5;  // diagonals d = 2..6 in the first Horner chain, 7..12 in the second
 constexpr uint32_t kAux = 2048;
 constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + kAux;
@@ -101,11 +107,11 @@ __device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t 
 }
 
 struct Barriers {
-  uint64_t full[kStages];   // producer warps (8 arrivals)
+  uint64_t full[kStages];   // producer warps (one arrival each)
   uint64_t bfull[kStages];  // coefficient digit copy (1 arrival + bytes)
   uint64_t empty[kStages];  // MMA commit
   uint64_t tfull[2];        // MMA commit after a tile's last stage
-  uint64_t tempty[2];       // producer warps after draining the accumulator (8 arrivals)
+  uint64_t tempty[2];       // draining warps after draining the accumulator (8 arrivals)
   uint64_t drain;
   uint32_t tmem_base;
   int abort_flag;
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&bar->tfull[i], 1);
-      ptx::mbar_init(&bar->tempty[i], kProducerWarps);
+      ptx::mbar_init(&bar->tempty[i], kDrainWarps);
     }
     ptx::mbar_init(&bar->drain, 1);
     bar->abort_flag = 0;
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
     int prev_inst = -1, prev_ep = 0;
     int64_t prev_p0 = 0;
     auto drain_prev = [&]() -> bool {
+      if (strm >= 2) return true;  // streams 0 and 1 drain
       const uint32_t pacc = (uint32_t)((local - 1) & 1), puse = (uint32_t)(((local - 1) >> 1) & 1);
       if (!warp_wait(&bar->tfull[pacc], puse, abort_flag, lane)) return false;
       ptx::tc_fence_after();
@@ -331,19 +338,21 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       const bool zero_row = ep == kNonFiniteRow;
       const int shift = kBeta * kDig - (zero_row ? 0 : ep);
 
-      int unit = 0;  // this stream's next unit; its global unit is 2 unit + strm
+      int unit = 0;  // this stream's next unit; its global unit is kStreams unit + strm
       uint32_t w[kDig][4];
       uint8_t* sA = smem + stage * kStageBytes;
       // This stream's next unit in shared memory (its byte offset within digit tile 0), opening
-      // the stage at the stream's first unit in it: waiting for the stage to be free, stream 0
-      // starting its coefficient copy.  -1 when a bounded wait gave up.
+      // the stage at the stream's first unit in it (slot below kStreams: the stream's previous
+      // unit lies in the stage before): waiting for the stage to be free, stream 0 starting its
+      // coefficient copy (every stream has a unit in every stage).  -1 when a bounded wait gave up.
       auto open_unit = [&]() -> int {
-        const int slot = ((2 * unit + strm) & 3);  // unit slot within the stage (0..3)
-        if (slot == strm) {
+        const int g = kStreams * unit + strm;  // global unit
+        const int slot = g & 3;                 // unit slot within the stage (0..3)
+        if (slot < kStreams) {
           if (!warp_wait(&bar->empty[stage], sphase ^ 1u, abort_flag, lane)) return -1;
           sA = smem + stage * kStageBytes;
           if (warp == 0 && lane == 0) {
-            const int kc = unit / 2;
+            const int kc = g >> 2;
             ptx::mbar_arrive_expect_tx(&bar->bfull[stage], kFusedBChunk);
             ptx::bulk_g2s(sA + kABytes + kBCopyOffset, d.bdig + (size_t)kc * kFusedBChunk, kFusedBChunk,
                           &bar->bfull[stage]);
@@ -353,11 +362,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         }
         return (int)ptx::sw_offset_b16<kRowBytes>(row, (uint32_t)(slot * 8));
       };
-      // The unit is written: hand the stage to the MMA warp after the stream's last unit in it.
+      // The unit is written: hand the stage to the MMA warp after the stream's last unit in it
+      // (slot 4 - kStreams or later: the stream's next unit lies in the next stage).
       auto finish_unit = [&]() {
-        const int slot = ((2 * unit + strm) & 3);
+        const int slot = (kStreams * unit + strm) & 3;
         ++unit;
-        if (slot == 2 + strm) {
+        if (slot >= 4 - kStreams) {
           ptx::fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&bar->full[stage]);
@@ -402,10 +412,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       double s1, c1;
       sincos(th, &s1, &c1);
       const double c2 = fma(c1, c1, -s1 * s1), s2 = 2.0 * s1 * c1;
+      // Three streams deal the columns out about three |m| apart: steps of 3 theta too (a step
+      // of 4 as two of 2).  The walk starts from the state of m = 0 (cos = 1, sin = 0, rho^0 = 1).
+      const double c3 = fma(c2, c1, -s2 * s1), s3 = fma(s2, c1, c2 * s1), r3 = u * rho;
       double cm = 1.0, sm = 0.0, pm = 1.0;
-      int m_prev = -100;
+      int m_prev = 0;
       const int ncs = d.ncols_s[strm];
-      const int32_t* scol = d.scols + (strm ? d.ncols_s[0] : 0);
+      int scol0 = 0;
+      for (int sp = 0; sp < strm; ++sp) scol0 += d.ncols_s[sp];
+      const int32_t* scol = d.scols + scol0;
       for (int ci = 0; ci < ncs && ok; ++ci) {
         const int c = scol[ci];
         const Column col = d.cols[c];
@@ -420,6 +435,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           sm = fma(sm, c2, cm * s2);
           cm = cn;
           pm *= u;
+        } else if (m == m_prev + 3) {
+          const double cn = fma(cm, c3, -sm * s3);
+          sm = fma(sm, c3, cm * s3);
+          cm = cn;
+          pm *= r3;
         } else if (m != m_prev) {
           cm = 1.0;
           sm = 0.0;
@@ -525,10 +545,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           while (kin != 0) emit(0.0), emit(0.0);
         }
       }
-      // Zero units up to the tile's unit count (the same for both streams, whole stages).
+      // Zero units up to the tile's unit count (the same for every stream, whole stages).
 #pragma unroll
       for (int t = 0; t < kDig; ++t) w[t][0] = w[t][1] = w[t][2] = w[t][3] = 0u;
-      while (ok && unit < d.units) ok = store_unit();
+      const int my_units = (d.units - strm + kStreams - 1) / kStreams;
+      while (ok && unit < my_units) ok = store_unit();
       // Drain the previous tile's accumulator now that this one is on its way.
       if (ok && prev_inst >= 0) ok = drain_prev();
       if (!ok) {
@@ -739,8 +760,7 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.mode_N = plan->dev.mode_N;
   d.fcols = plan->dev.fused_col;
   d.scols = (const int32_t*)(plan->dev.fused_col + plan->cols.size());
-  d.ncols_s[0] = plan->fused_ncols[0];
-  d.ncols_s[1] = plan->fused_ncols[1];
+  for (int st = 0; st < kFusedStreams; ++st) d.ncols_s[st] = plan->fused_ncols[st];
   d.units = plan->fused_units;
   d.ep_disc = plan->fused_ep;
   d.kperm = plan->dev.fused_kperm;

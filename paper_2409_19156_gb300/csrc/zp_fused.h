@@ -46,8 +46,8 @@ struct FusedInst {
   const int32_t* scols = nullptr;    // columns of stream 0, then of stream 1 (walk order)
   const int32_t* kperm = nullptr;    // slot of every K position of that layout, -1 for padding
   int64_t Kp = 0;                    // K positions of that layout
-  int32_t ncols_s[2] = {0, 0};       // columns per stream
-  int32_t units = 0;                 // 8-value units per stream
+  int32_t ncols_s[kFusedStreams] = {};  // columns per stream
+  int32_t units = 0;                 // global 8-value units of the layout (stream s owns every kFusedStreams-th)
   int32_t ep_disc = 1;               // row scale exponent for points on the unit disc
   int32_t n_cols = 0;
   int32_t KC = 0;        // 32-position chunks of the contraction

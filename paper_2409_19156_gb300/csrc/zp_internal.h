@@ -38,14 +38,16 @@ constexpr uint32_t kStepIrregular = 255u;
 constexpr int kStepMaxFlags = 24;
 constexpr int kPlanSections = 9;
 
-// Contraction layout of the fused float64-accurate series: the columns are dealt to two streams
-// (two producer threads per point); a column's outputs fill whole 8-value units (16-byte
-// operand units, zero padded), and unit j of stream s is the global unit 2 j + s.  Per column
+// Contraction layout of the fused float64-accurate series: the columns are dealt to
+// kFusedStreams streams (that many producer threads per point); a column's outputs fill whole
+// 8-value units (16-byte operand units, zero padded), and unit j of stream s is the global unit
+// kFusedStreams j + s (four global units per 32-position stage).  Per column
 // (int4): x = kind | (sin flag of the step's first output) << 8 | (of its second) << 9 (kind 1:
 // every step has one output, kind 2: every step has two outputs in the same cos/sin order,
 // kind 0: anything else), y = stream, z = first unit within the stream, w = number of outputs.
-// The columns of stream 0 then of stream 1, in walk order, follow the n_columns records.
+// The columns of stream 0, then of stream 1, ..., in walk order, follow the n_columns records.
 constexpr int kFusedKindGeneric = 0, kFusedKindOne = 1, kFusedKindTwo = 2;
+constexpr int kFusedStreams = 3;
 
 // float32 bits of a float64 given as its high and low words, by truncating the significand:
 // magnitudes below the float32 normal range give a signed zero, finite ones above it
@@ -90,8 +92,8 @@ struct zp_plan {
   std::vector<int32_t> fused_col;    // 4 words per column, then the streams' column lists
   std::vector<int32_t> fused_kperm;
   int64_t fused_kpad = 0;            // K positions of the fused layout (multiple of 32)
-  int32_t fused_ncols[2] = {0, 0};   // columns per stream
-  int32_t fused_units = 0;           // 8-value units per stream (even)
+  int32_t fused_ncols[zp::kFusedStreams] = {};  // columns per stream
+  int32_t fused_units = 0;  // global 8-value units G of the layout (whole 4-unit stages); stream s owns (G - s + S - 1) / S
   int32_t fused_ep = 1;              // row scale exponent of the fused kernel on the unit disc
   zp::DevicePlanTables dev;
   size_t device_bytes = 0;

@@ -191,14 +191,17 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
       p->split_step[2 * r + 1] = trunc_float_bits((uint32_t)(wbits >> 32), (uint32_t)wbits);
     }
   }
-  // Fused contraction layout.  The columns are dealt to two streams (two producer threads per
-  // point) in walk order, each column to the stream with fewer 8-value units so far; each
-  // column's outputs fill whole units (slot order, zero padded), and the K order interleaves
-  // the streams unit by unit: unit j of stream s is global unit 2 j + s.
+  // Fused contraction layout.  The columns are dealt to kFusedStreams streams (producer
+  // threads per point) in walk order, round robin (a stream's consecutive columns then lie
+  // kFusedStreams apart in |m| for a full mode set, one angle step each) unless that stream is
+  // more than two 8-value units ahead of the least loaded one, which then takes the column;
+  // each column's outputs fill whole units (slot order, zero padded), and the K order
+  // interleaves the streams unit by unit: unit j of stream s is global unit kFusedStreams j + s.
+  constexpr int NS = kFusedStreams;
   const size_t nc = p->cols.size();
   p->fused_col.assign(5 * nc, 0);
-  int32_t units[2] = {0, 0};
-  std::vector<int32_t> scol[2];
+  int32_t units[NS] = {};
+  std::vector<int32_t> scol[NS];
   std::vector<int32_t> col_first(nc, 0), col_stream(nc, 0);
   for (size_t c = 0; c < nc; ++c) {
     const Column& col = p->cols[c];
@@ -221,7 +224,10 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
     }
     if (kind < 0) kind = kFusedKindGeneric;
     const int32_t nvals = last - first;
-    const int st = units[1] < units[0] ? 1 : 0;
+    int least = 0;
+    for (int s2 = 1; s2 < NS; ++s2)
+      if (units[s2] < units[least]) least = s2;
+    const int st = units[c % NS] > units[least] + 2 ? least : (int)(c % NS);
     col_stream[c] = st;
     col_first[c] = units[st];
     p->fused_col[4 * c] = kind | (int32_t)(fa << 8) | (int32_t)(fb << 9);
@@ -231,19 +237,26 @@ zp_status build_plan_host(const int32_t* n, const int32_t* m, int64_t n_modes, z
     units[st] += (nvals + 7) / 8;
     scol[st].push_back((int32_t)c);
   }
-  for (int st = 0; st < 2; ++st)
-    for (size_t i = 0; i < scol[st].size(); ++i) p->fused_col[4 * nc + (st ? scol[0].size() : 0) + i] = scol[st][i];
-  p->fused_ncols[0] = (int32_t)scol[0].size();
-  p->fused_ncols[1] = (int32_t)scol[1].size();
-  // Units per stream: the larger count, rounded so that both streams fill whole 4-unit stages.
-  p->fused_units = std::max(units[0], units[1]);
-  p->fused_units += p->fused_units & 1;
-  p->fused_kperm.assign((size_t)p->fused_units * 2 * 8, -1);
+  size_t at = 4 * nc;
+  for (int st = 0; st < NS; ++st) {
+    for (size_t i = 0; i < scol[st].size(); ++i) p->fused_col[at + i] = scol[st][i];
+    at += scol[st].size();
+    p->fused_ncols[st] = (int32_t)scol[st].size();
+  }
+  // Global units G: the fewest, in whole 4-unit (32-position) stages, that give every stream
+  // its units (stream s owns the global units g < G with g = s mod NS: (G - s + NS - 1) / NS of
+  // them, so streams end at most one unit apart).
+  int32_t G = 0;
+  for (int st = 0; st < NS; ++st)
+    if (units[st] > 0) G = std::max(G, NS * (units[st] - 1) + st + 1);
+  G = (G + 3) / 4 * 4;
+  p->fused_units = G;
+  p->fused_kperm.assign((size_t)G * 8, -1);
   for (size_t c = 0; c < nc; ++c) {
     const Column& col = p->cols[c];
     const int32_t first = p->slot_ptr[col.slot_base];
     for (int32_t i = 0; i < p->fused_col[4 * c + 3]; ++i) {
-      const int32_t unit = 2 * (col_first[c] + i / 8) + col_stream[c];
+      const int32_t unit = NS * (col_first[c] + i / 8) + col_stream[c];
       p->fused_kperm[(size_t)unit * 8 + i % 8] = first + i;
     }
   }

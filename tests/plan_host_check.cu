@@ -31,5 +31,11 @@ int main() {
   for (int32_t v : plan.slot_idx) std::printf("%u\n", (unsigned)v);
   std::printf("split_step %zu\n", plan.split_step.size());
   for (uint32_t v : plan.split_step) std::printf("%u\n", v);
+  std::printf("fused %d %d %lld %d\n", zp::kFusedStreams, plan.fused_units, (long long)plan.fused_kpad, plan.fused_ep);
+  for (int s = 0; s < zp::kFusedStreams; ++s) std::printf("%d\n", plan.fused_ncols[s]);
+  std::printf("fused_col %zu\n", plan.fused_col.size());
+  for (int32_t v : plan.fused_col) std::printf("%d\n", v);
+  std::printf("fused_kperm %zu\n", plan.fused_kperm.size());
+  for (int32_t v : plan.fused_kperm) std::printf("%d\n", v);
   return 0;
 }

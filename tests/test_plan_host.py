@@ -46,6 +46,15 @@ def build(exe, ns, ms):
             plan[name] = [struct.unpack("<d", struct.pack("<Q", int(r, 16)))[0] for r in rows]
         else:
             plan[name] = [int(r) for r in rows]
+    head = next(it).split()
+    assert head[0] == "fused"
+    ns_, units, kpad, ep = map(int, head[1:])
+    plan["fused"] = {"streams": ns_, "units": units, "kpad": kpad, "ep": ep,
+                     "ncols": [int(next(it)) for _ in range(ns_)]}
+    for name in ("fused_col", "fused_kperm"):
+        head = next(it).split()
+        assert head[0] == name
+        plan[name] = [int(next(it)) for _ in range(int(head[1]))]
     return 0, plan
 
 
@@ -117,6 +126,62 @@ def test_plan_tables(driver):
                 flags = sum(((c >> 31) & 1) << i for i, c in enumerate(codes))
                 assert word == len(codes) | (flags << 8)
             assert plan["split_step"][2 * (row0 + K_HEADER + N) + 1] == trunc_bits(r[3])
+
+
+def check_fused_layout(plan):
+    """The fused kernel's contraction layout: columns dealt to the streams, each column's
+    outputs in whole 8-value units of its stream, unit j of stream s at global unit S j + s,
+    every output slot exactly once in the K order, padding elsewhere, whole 32-position stages."""
+    f, cols = plan["fused"], plan["cols"]
+    S, units, nc = f["streams"], f["units"], len(cols)
+    rec = [plan["fused_col"][4 * c:4 * c + 4] for c in range(nc)]
+    lists = plan["fused_col"][4 * nc:]
+    assert len(lists) == nc and sorted(lists) == list(range(nc))
+    at = 0
+    used = [0] * S
+    for s in range(S):
+        mine = lists[at:at + f["ncols"][s]]
+        at += f["ncols"][s]
+        for c in mine:  # walk order within the stream, units consecutive
+            assert rec[c][1] == s and rec[c][2] == used[s]
+            used[s] += -(-rec[c][3] // 8)
+    assert at == nc
+    G = units  # global units: stream s owns the g < G with g = s mod S
+    assert G % 4 == 0 and all(used[s] <= (G - s + S - 1) // S for s in range(S))
+    assert G < 4 or any(used[s] > (G - 4 - s + S - 1) // S for s in range(S))  # no whole stage to spare
+    assert f["kpad"] == len(plan["fused_kperm"]) == 8 * G and f["kpad"] % 32 == 0
+    # balance: round robin unless a stream runs more than two units ahead of the least loaded
+    biggest = max((-(-r[3] // 8) for r in rec), default=0)
+    assert max(used) - min(used) <= biggest + 2
+    kperm = plan["fused_kperm"]
+    want = {}
+    for c, (kind, s, first, nvals) in enumerate(rec):
+        am, n_steps, row0, sbase = cols[c]
+        slot0 = plan["slot_ptr"][sbase]
+        assert plan["slot_ptr"][sbase + n_steps] - slot0 == nvals
+        for i in range(nvals):
+            want[8 * (S * (first + i // 8) + s) + i % 8] = slot0 + i
+    assert {k: v for k, v in enumerate(kperm) if v >= 0} == want
+    assert sorted(want.values()) == list(range(len(plan["slot_idx"])))
+
+
+def test_fused_layout(driver):
+    for nmax in (0, 3, 10, 24, 32):
+        ns = [n for n in range(nmax + 1) for m in range(-n, n + 1, 2)]
+        ms = [m for n in range(nmax + 1) for m in range(-n, n + 1, 2)]
+        st, plan = build(driver, ns, ms)
+        assert st == 0
+        check_fused_layout(plan)
+        # a full mode set is dealt round robin: each stream's |m| advance by the stream count
+        S, cols = plan["fused"]["streams"], plan["cols"]
+        assert all(plan["fused_col"][4 * c + 1] == c % S for c in range(len(cols)))
+        assert [c[0] for c in cols] == list(range(nmax + 1))
+    # scrambled, duplicated and one-sided mode lists (irregular steps)
+    ns = [30, 4, 4, 9, 30, 0, 17, 4, 22, 12, 12, 12, 40, 1, 40] + [10] * 26
+    ms = [0, 2, -2, 9, -4, 0, 1, 2, 22, -4, 4, -4, 0, -1, 38] + [2, -2] * 13
+    st, plan = build(driver, ns, ms)
+    assert st == 0
+    check_fused_layout(plan)
 
 
 @pytest.mark.parametrize("n,m", [(3, 2), (-1, 1), (2, 3), (1001, 1)])
