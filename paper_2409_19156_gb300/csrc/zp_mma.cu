@@ -1298,6 +1298,45 @@ __global__ void recombine_kernel(RecombineArgs a) {
   }
 }
 
+// recombine_kernel for one K batch (only) and the common plane shapes, with the plane count, the
+// split of the Horner chains and the shift per plane fixed at compile time: the loops unroll
+// completely and every shift is a constant.  4 consecutive outputs per thread (16-byte loads of
+// each plane and of the column exponents, 16-byte stores); needs N % 4 == 0, an even ldc and
+// a 16-byte aligned C.
+template <int NPL, int SPLIT, int SH>
+__global__ void __launch_bounds__(256) recombine_planes_kernel(RecombineArgs a) {
+  constexpr int LS = SH * (NPL - SPLIT);
+  for (int64_t m = blockIdx.x; m < a.rows; m += gridDim.x) {
+    const int rx = a.rexp[m];
+    const bool row_bad = rx == kNonFiniteRow;
+    const int em = rx + a.e_base;
+    const int* trow = a.T + m * a.N;
+    double* crow = a.C + m * a.ldc;
+    for (int64_t n0 = (int64_t)threadIdx.x * 4; n0 < a.N; n0 += (int64_t)blockDim.x * 4) {
+      int4 v[NPL];
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) v[q] = __ldcs(reinterpret_cast<const int4*>(trow + q * a.diag_stride + n0));
+      const int4 ce = __ldg(reinterpret_cast<const int4*>(a.cexp + n0));
+      double out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        long long hi = 0, lo = 0;
+#pragma unroll
+        for (int q = 0; q < NPL; ++q) {
+          const int t = k == 0 ? v[q].x : (k == 1 ? v[q].y : (k == 2 ? v[q].z : v[q].w));
+          if (q < SPLIT) hi = horner(hi, SH, t);
+          else lo = horner(lo, SH, t);
+        }
+        const int ec = k == 0 ? ce.x : (k == 1 ? ce.y : (k == 2 ? ce.z : ce.w));
+        out[k] = (row_bad || ec == kNonFiniteRow) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                  : join_to_double(hi, lo, LS, em + ec);
+      }
+      __stcs(reinterpret_cast<double2*>(crow + n0), make_double2(out[0], out[1]));
+      __stcs(reinterpret_cast<double2*>(crow + n0 + 2), make_double2(out[2], out[3]));
+    }
+  }
+}
+
 // An emulated GEMM in progress: the B operand sliced once (all N rows), then A in slabs of
 // row tiles, each slab: row scales, slices, one GEMM launch per slice diagonal (all pairs of
 // the diagonal and all K batches), recombination into C.
@@ -1427,12 +1466,16 @@ struct EmuGemm {
       ra.k_batches = 1;
       recombine_kernel<kRecombineWidth, long long><<<rblocks, 256, 0, stream>>>(ra);
     } else {
-      // Constant Horner shifts for the slice widths in use (beta, or 2 beta for paired planes).
-      switch (ra.beta) {
-        case 12: recombine_kernel<kRecombineWidth, int, 12><<<rblocks, 256, 0, stream>>>(ra); break;
-        case 14: recombine_kernel<kRecombineWidth, int, 14><<<rblocks, 256, 0, stream>>>(ra); break;
-        case 10: recombine_kernel<kRecombineWidth, int, 10><<<rblocks, 256, 0, stream>>>(ra); break;
-        case 8: recombine_kernel<kRecombineWidth, int, 8><<<rblocks, 256, 0, stream>>>(ra); break;
+      // The paired plane shapes of the four slice widths (planes, chains' split, shift per
+      // plane) run fully unrolled; anything else takes the general kernel.
+      const bool vec = ra.k_batches == 1 && (N % 4) == 0 && (ldc % 2) == 0 && ((uintptr_t)Cout % 16) == 0 &&
+                       ((uintptr_t)cexp.ptr % 16) == 0;
+      const int shape = vec ? ra.ndiag * 10000 + ra.split * 100 + ra.beta : 0;
+      switch (shape) {
+        case 50312: recombine_planes_kernel<5, 3, 12><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 40314: recombine_planes_kernel<4, 3, 14><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 60410: recombine_planes_kernel<6, 4, 10><<<rblocks, 256, 0, stream>>>(ra); break;
+        case 70408: recombine_planes_kernel<7, 4, 8><<<rblocks, 256, 0, stream>>>(ra); break;
         default: recombine_kernel<kRecombineWidth, int><<<rblocks, 256, 0, stream>>>(ra); break;
       }
     }

@@ -50,6 +50,23 @@ def test_emulated_fp64_narrower_slices(nmax):
     assert (np.abs(F[rows] - want) <= tol).all()
 
 
+@pytest.mark.parametrize("nmax", [24, 32, 60, 100])
+def test_emulated_fp64_one_batch_plane_shapes(nmax):
+    """Outputs large enough for one K batch (>= 304 point tiles) with each slice width: the
+    paired planes (4, 5, 6 and 7 of them for beta = 7, 6, 5, 4) and the fully unrolled
+    recombination of each shape, against the DGEMM float64 path everywhere."""
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.sqrt_uniform_points(40_000, 71 + nmax)
+    C = inputs.scaled_normal_coeffs(ns, 20, 71 + nmax)
+    plan = zp.Plan(ns, ms)
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    F = zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan)
+    F64 = zp.series_eval(None, None, rt, tt, Ct, "fp64", plan=plan)
+    Z = zp.basis(None, None, rt, tt, 0, plan=plan)[0][0].abs()
+    bound = 2e-13 * (1.0 + Z.T @ Ct.abs())
+    assert bool(((F - F64).abs() <= bound).all())
+
+
 def test_emulated_fp64_series_n24_full_size():
     """The 325-mode, 50000-point polar grid, 256 sets: against the DGEMM float64 path everywhere
     and against the oracle on sampled rows."""
