@@ -931,8 +931,17 @@ def measure_batched(dev, steps: int = 3, n_instances: int = 512, point_scale: fl
     t_graph = _events_ms(stream, g.replay, steps)
     t_per = _events_ms(stream, b.forward_per_instance, 1)
     cfg_adj = b.tune("adjoint", reps=1)[0] if tune else b.config()
-    b.adjoint()
-    t_adj = _events_ms(stream, b.adjoint, 1)
+    b.adjoint("fp64")
+    t_adj = _events_ms(stream, lambda: b.adjoint("fp64"), 1)
+    adj64 = [rec["grad_coeffs"].clone() for rec in b.instances]
+    # The adjoint with the float64-accurate tensor-core contractions (per instance).
+    b.adjoint("fp64emu")
+    t_adj_emu = _events_ms(stream, lambda: b.adjoint("fp64emu"), 1)
+    out["fp64emu_adjoint_ms"] = t_adj_emu
+    out["fp64emu_adjoint_grad_coeffs_max_abs_diff_vs_fp64"] = max(
+        float((rec["grad_coeffs"] - a).abs().max()) for rec, a in zip(b.instances, adj64) if a.numel())
+    out["speedup_emulated_vs_fp64_adjoint"] = t_adj / t_adj_emu
+    del adj64
     out["fp64_forward_graph_ms"] = t_graph
     out["fp64_forward_per_instance_launches_ms"] = t_per
     out["fp64_adjoint_ms"] = t_adj

@@ -337,8 +337,15 @@ ZP_API zp_status zp_batch_destroy(zp_batch* batch);
 ZP_API zp_status zp_batch_forward(zp_batch* batch, zp_precision prec, void* stream);
 /* The same float64 forward as one launch per instance (comparison path). */
 ZP_API zp_status zp_batch_forward_per_instance(zp_batch* batch, zp_precision prec, void* stream);
-/* grad_r, grad_theta (one launch) and grad_coeffs (one launch), float64, deterministic. */
+/* grad_r, grad_theta (one launch) and grad_coeffs (one launch), float64 on the CUDA cores,
+ * deterministic (the same as zp_batch_adjoint_prec with ZP_PREC_FP64). */
 ZP_API zp_status zp_batch_adjoint(zp_batch* batch, void* stream);
+/* The adjoint with a chosen grad_coeffs contraction: ZP_PREC_FP64 as zp_batch_adjoint; or
+ * ZP_PREC_FP64_EMULATED: grad_r and grad_theta by the same persistent point kernel, and per
+ * instance grad_coeffs = Z G by the float64-accurate tensor-core GEMM of zp_series_adjoint_plan
+ * (Z walked into library scratch; several launches per instance, no host synchronisation,
+ * deterministic; that path's scale-relative error bound).  Other precisions: ZP_ERR_INVALID_ARG. */
+ZP_API zp_status zp_batch_adjoint_prec(zp_batch* batch, zp_precision prec, void* stream);
 /* Launch configuration: point-tile size (threads per CTA of the point kernel, multiple of 32),
  * persistent CTAs per SM, points per thread (1, 2, 4) and threads per CTA of the grad_coeffs
  * kernel.  cfg[4] receives the current values. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "zp_batch_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_dp]),
     "zp_batch_forward_per_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_dp]),
     "zp_batch_adjoint": (ctypes.c_int, [ctypes.c_void_p, c_dp]),
+    "zp_batch_adjoint_prec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_dp]),
     "zp_batch_set_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32]),
     "zp_batch_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),

@@ -337,8 +337,14 @@ class Batch:
         _lib.call("zp_batch_forward_per_instance", self.handle, 0,
                   _stream(torch.device("cuda", torch.cuda.current_device())))
 
-    def adjoint(self):
-        _lib.call("zp_batch_adjoint", self.handle, _stream(torch.device("cuda", torch.cuda.current_device())))
+    def adjoint(self, prec: str = "fp64emu"):
+        """grad_coeffs, grad_r, grad_theta for every instance: grad_r and grad_theta by the
+        persistent float64 point kernel; grad_coeffs per instance by the float64-accurate
+        tensor-core GEMM ("fp64emu") or by the persistent float64 column kernel ("fp64", one
+        launch)."""
+        code = {"fp64": 0, "fp64emu": 4}[prec]
+        _lib.call("zp_batch_adjoint_prec", self.handle, code,
+                  _stream(torch.device("cuda", torch.cuda.current_device())))
 
     def set_config(self, tile_points=128, ctas_per_sm=4, col_ppt=2, col_threads=128):
         _lib.call("zp_batch_set_config", self.handle, tile_points, ctas_per_sm, col_ppt, col_threads)

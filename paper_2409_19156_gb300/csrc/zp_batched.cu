@@ -538,9 +538,9 @@ zp_status build_fused(zp_batch* b) {
     d.mode_col = p->dev.mode_col;
     d.mode_N = p->dev.mode_N;
     d.fcols = p->dev.fused_col;
-  d.scols = (const int32_t*)(p->dev.fused_col + p->cols.size());
-  for (int st = 0; st < kFusedStreams; ++st) d.ncols_s[st] = p->fused_ncols[st];
-  d.units = p->fused_units;
+    d.scols = (const int32_t*)(p->dev.fused_col + p->cols.size());
+    for (int st = 0; st < kFusedStreams; ++st) d.ncols_s[st] = p->fused_ncols[st];
+    d.units = p->fused_units;
     d.ep_disc = p->fused_ep;
     d.kperm = p->dev.fused_kperm;
     d.Kp = in.n_modes > 0 ? p->fused_kpad : 0;
@@ -823,9 +823,11 @@ zp_status zp_batch_forward_per_instance(zp_batch* b, zp_precision prec, void* st
   return zp::entry_finish("zp_batch_forward_per_instance", stream, zp_batch_forward_per_instance_impl(b, prec, stream));
 }
 
-static zp_status zp_batch_adjoint_impl(zp_batch* b, void* stream) {
+static zp_status zp_batch_adjoint_impl(zp_batch* b, zp_precision prec, void* stream) {
   clear_error();
   if (!b) return set_error(ZP_ERR_INVALID_ARG, "batch is NULL");
+  if (prec != ZP_PREC_FP64 && prec != ZP_PREC_FP64_EMULATED)
+    return set_error(ZP_ERR_INVALID_ARG, "batched adjoint supports ZP_PREC_FP64 and ZP_PREC_FP64_EMULATED");
   cudaStream_t st = (cudaStream_t)stream;
   bool need_pt = false, need_c = false;
   for (size_t i = 0; i < b->inst.size(); ++i) {
@@ -849,13 +851,29 @@ static zp_status zp_batch_adjoint_impl(zp_batch* b, void* stream) {
   }
   if (b->n_sets == 0) return ZP_OK;
   if (need_pt && b->n_pitems) ZP_TRY(launch_points<ADJ>(b, st));
+  if (need_c && prec == ZP_PREC_FP64_EMULATED) {
+    // grad_C = Z G per instance by the float64-accurate tensor-core GEMM, Z walked into
+    // scratch (grad_r and grad_theta above: the point kernel forms H = C G^T on the fly).
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      const zp_instance& in = b->inst[i];
+      if (in.n_points == 0 || in.n_modes == 0 || !in.grad_coeffs) continue;
+      ZP_TRY(series_adjoint_fp64(b->plans[b->inst_plan[i]].get(), in.r, in.theta, in.n_points, in.coeffs, b->n_sets,
+                                 in.grad_out, in.grad_coeffs, nullptr, nullptr, st, HessOut(), true));
+    }
+    return ZP_OK;
+  }
   if (need_c && b->n_citems) ZP_TRY(launch_columns(b, st));
   return ZP_OK;
 }
 
 zp_status zp_batch_adjoint(zp_batch* b, void* stream) {
   zp::NvtxRange zp_range_("zp_batch_adjoint");
-  return zp::entry_finish("zp_batch_adjoint", stream, zp_batch_adjoint_impl(b, stream));
+  return zp::entry_finish("zp_batch_adjoint", stream, zp_batch_adjoint_impl(b, ZP_PREC_FP64, stream));
+}
+
+zp_status zp_batch_adjoint_prec(zp_batch* b, zp_precision prec, void* stream) {
+  zp::NvtxRange zp_range_("zp_batch_adjoint_prec");
+  return zp::entry_finish("zp_batch_adjoint_prec", stream, zp_batch_adjoint_impl(b, prec, stream));
 }
 
 zp_status zp_batch_set_config(zp_batch* b, int32_t tile_points, int32_t ctas_per_sm, int32_t col_ppt,
