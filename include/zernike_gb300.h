@@ -340,11 +340,14 @@ ZP_API zp_status zp_batch_forward_per_instance(zp_batch* batch, zp_precision pre
 /* grad_r, grad_theta (one launch) and grad_coeffs (one launch), float64 on the CUDA cores,
  * deterministic (the same as zp_batch_adjoint_prec with ZP_PREC_FP64). */
 ZP_API zp_status zp_batch_adjoint(zp_batch* batch, void* stream);
-/* The adjoint with a chosen grad_coeffs contraction: ZP_PREC_FP64 as zp_batch_adjoint; or
- * ZP_PREC_FP64_EMULATED: grad_r and grad_theta by the same persistent point kernel, and per
- * instance grad_coeffs = Z G by the float64-accurate tensor-core GEMM of zp_series_adjoint_plan
- * (Z walked into library scratch; several launches per instance, no host synchronisation,
- * deterministic; that path's scale-relative error bound).  Other precisions: ZP_ERR_INVALID_ARG. */
+/* The adjoint with a chosen contraction: ZP_PREC_FP64 as zp_batch_adjoint; or
+ * ZP_PREC_FP64_EMULATED (float64-accurate on the tensor cores, deterministic, no host
+ * synchronisation): grad_theta[p] = sum_s grad_out[p][s] (dZ/dtheta C)[p][s] and grad_r likewise
+ * with dZ/drho, each derivative series by the fused kernel of ZP_PREC_FP64_EMULATED's batched
+ * forward (one launch each; its row sums added onto the zeroed gradients) when n_sets <= 16 and
+ * every instance has at most 5041 modes, else by the float64 point kernel; and per instance
+ * grad_coeffs = Z G by the float64-accurate GEMM of zp_series_adjoint_plan (Z walked into
+ * library scratch).  Other precisions: ZP_ERR_INVALID_ARG. */
 ZP_API zp_status zp_batch_adjoint_prec(zp_batch* batch, zp_precision prec, void* stream);
 /* Launch configuration: point-tile size (threads per CTA of the point kernel, multiple of 32),
  * persistent CTAs per SM, points per thread (1, 2, 4) and threads per CTA of the grad_coeffs

@@ -418,6 +418,9 @@ struct zp_batch {
   bool fused_ok = false;
   void* fused_block = nullptr;
   zp::FusedInst* d_finst = nullptr;
+  // The adjoint's point gradients by the same kernel: [n] descriptors of the theta-derivative
+  // series (dot with grad_out into grad_theta), then [n] of the rho-derivative (into grad_r).
+  zp::FusedInst* d_fadj = nullptr;
   zp::FusedItem* d_fitems = nullptr;
   int32_t* d_fchunk = nullptr;
   int64_t n_fitems = 0, n_fchunks = 0;
@@ -563,23 +566,41 @@ zp_status build_fused(zp_batch* b) {
   for (auto& o : order)
     for (int64_t t = 0; t * 128 < b->inst[o.second].n_points; ++t) items.push_back(FusedItem{o.second, (int32_t)t});
   const size_t inst_b = align256(std::max<int64_t>(n, 1) * sizeof(FusedInst));
+  const size_t adj_b = align256(std::max<int64_t>(2 * n, 1) * sizeof(FusedInst));
   const size_t item_b = align256(std::max<size_t>(items.size(), 1) * sizeof(FusedItem));
   const size_t chunk_b = align256(std::max<int64_t>(kc_total, 1) * sizeof(int32_t));
   const size_t cexp_b = align256(std::max<int64_t>(n, 1) * kFusedMaxSets * sizeof(int));
   const size_t dig_b = (size_t)std::max<int64_t>(kc_total, 1) * kFusedBChunk;
-  cudaError_t e = cudaMalloc(&b->fused_block, inst_b + item_b + chunk_b + cexp_b + dig_b);
+  cudaError_t e = cudaMalloc(&b->fused_block, inst_b + adj_b + item_b + chunk_b + cexp_b + dig_b);
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fused batch)");
   char* base = (char*)b->fused_block;
-  int* cexp = (int*)(base + inst_b + item_b + chunk_b);
-  uint8_t* dig = (uint8_t*)(base + inst_b + item_b + chunk_b + cexp_b);
+  int* cexp = (int*)(base + inst_b + adj_b + item_b + chunk_b);
+  uint8_t* dig = (uint8_t*)(base + inst_b + adj_b + item_b + chunk_b + cexp_b);
   for (int64_t i = 0; i < n; ++i) {
     fi[i].cexp = cexp + i * kFusedMaxSets;
     fi[i].bdig = dig + (size_t)fi[i].kc_base * kFusedBChunk;
   }
+  // Adjoint descriptors: the same instances, the derivative series' row scales, and the row
+  // sums with grad_out written into grad_theta / grad_r instead of a series output.
+  std::vector<FusedInst> fa(2 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    const zp_instance& in = b->inst[i];
+    const zp_plan* p = b->plans[b->inst_plan[i]].get();
+    for (int k = 0; k < 2; ++k) {
+      FusedInst& d = fa[k * n + i];
+      d = fi[i];
+      d.out = nullptr;
+      d.gdot = in.grad_out;
+      d.dot_out = k == 0 ? in.grad_theta : in.grad_r;
+      d.ep_disc = fused_ep_for(p, k == 0 ? kFusedDTheta : kFusedDRho);
+    }
+  }
   b->d_finst = (FusedInst*)base;
-  b->d_fitems = (FusedItem*)(base + inst_b);
-  b->d_fchunk = (int32_t*)(base + inst_b + item_b);
+  b->d_fadj = (FusedInst*)(base + inst_b);
+  b->d_fitems = (FusedItem*)(base + inst_b + adj_b);
+  b->d_fchunk = (int32_t*)(base + inst_b + adj_b + item_b);
   e = cudaMemcpy(b->d_finst, fi.data(), n * sizeof(FusedInst), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpy(b->d_fadj, fa.data(), 2 * n * sizeof(FusedInst), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpy(b->d_fitems, items.data(), items.size() * sizeof(FusedItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && kc_total > 0)
@@ -850,7 +871,36 @@ static zp_status zp_batch_adjoint_impl(zp_batch* b, zp_precision prec, void* str
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
   }
   if (b->n_sets == 0) return ZP_OK;
-  if (need_pt && b->n_pitems) ZP_TRY(launch_points<ADJ>(b, st));
+  if (need_pt && prec == ZP_PREC_FP64_EMULATED && b->fused_ok) {
+    // grad_theta[p] = sum_s G[p][s] (dZ/dtheta C)[p][s] and grad_r likewise with dZ/drho: the
+    // fused tensor-core kernel for the two derivative series, each row sum formed in its drain
+    // and added onto the zeroed gradients.
+    bool need_t = false, need_r = false;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      const zp_instance& in = b->inst[i];
+      if (in.n_points == 0 || in.n_modes == 0) continue;
+      cudaError_t e = cudaSuccess;
+      if (in.grad_theta) e = cudaMemsetAsync(in.grad_theta, 0, in.n_points * 8, st), need_t = true;
+      if (e == cudaSuccess && in.grad_r) e = cudaMemsetAsync(in.grad_r, 0, in.n_points * 8, st), need_r = true;
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    }
+    FusedArgs a;
+    a.items = b->d_fitems;
+    a.n_items = b->n_fitems;
+    const int64_t n = (int64_t)b->inst.size();
+    bool digits = true;  // the coefficient digits once, for the first pass
+    if (need_t) {
+      a.insts = b->d_fadj;
+      ZP_TRY(fused_launch(a, n, b->d_fchunk, b->n_fchunks, st, kFusedDTheta, digits));
+      digits = false;
+    }
+    if (need_r) {
+      a.insts = b->d_fadj + n;
+      ZP_TRY(fused_launch(a, n, b->d_fchunk, b->n_fchunks, st, kFusedDRho, digits));
+    }
+  } else if (need_pt && b->n_pitems) {
+    ZP_TRY(launch_points<ADJ>(b, st));
+  }
   if (need_c && prec == ZP_PREC_FP64_EMULATED) {
     // grad_C = Z G per instance by the float64-accurate tensor-core GEMM, Z walked into
     // scratch (grad_r and grad_theta above: the point kernel forms H = C G^T on the fly).

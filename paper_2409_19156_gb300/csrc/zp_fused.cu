@@ -146,59 +146,59 @@ __device__ __forceinline__ void fail(volatile int* abort_flag) {
   atomicOr(&g_fused_error, 1u);
 }
 
+// Values the fused kernel contracts: VK_Z the basis Z (the forward series), VK_DTHETA its
+// theta-derivative (m R times the other angular factor, negated for cos), VK_DRHO its
+// rho-derivative (dR/drho times the angular factor, the recursion's derivative lane).  The
+// two derivative series give the adjoint's point gradients: grad_r = sum_s G (dZ/dr C).
+constexpr int VK_Z = kFusedZ, VK_DTHETA = kFusedDTheta, VK_DRHO = kFusedDRho;
+
 // The float64 walk of one point over every column of its plan (Sec. 2 recursion, rescaled as
-// in the plan's tables: Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2}, R = W0_N Q_N), calling
-// emit(Q_N cos/sin(m theta)) for every output slot in the plan's slot order: the values this
-// kernel digitises (the weight W0_N travels with the coefficients).
-template <typename Emit>
+// in the plan's tables: Q_N = (A_N rho^2 - B_N) Q_{N-1} - Q_{N-2}, R = W0_N Q_N; for VK_DRHO
+// also Q'_N = (A_N rho^2 - B_N) Q'_{N-1} + 2 A_N rho Q_{N-1} - Q'_{N-2}), calling emit(value)
+// for every output slot in the plan's slot order: Q_N cos/sin(m theta), Q_N times the
+// derivative of cos/sin(m theta), or Q'_N cos/sin(m theta) -- the values the kernel digitises
+// (the weight W0_N travels with the coefficients).  Used for the row scale of points off the
+// unit disc, so written for clarity: seeds from powers, angles from sincos.
+template <int VK, typename Emit>
 __device__ __forceinline__ void walk_point(const FusedInst& d, double rho, double th, Emit&& emit) {
   const double u = rho * rho;
-  double s1, c1;
-  sincos(th, &s1, &c1);
-  double cm = 1.0, sm = 0.0, pm = 1.0;
-  int m_prev = 0;
   for (int c = 0; c < d.n_cols; ++c) {
     const Column col = d.cols[c];
     const int m = col.m;
-    if (c > 0 && m == m_prev + 1) {
-      const double cn = fma(cm, c1, -sm * s1);
-      sm = fma(sm, c1, cm * s1);
-      cm = cn;
-      pm *= rho;
-    } else if (c == 0 || m != m_prev) {
-      cm = 1.0;
-      sm = 0.0;
-      if (m != 0) sincos((double)m * th, &sm, &cm);
-      pm = pow_uint(rho, m);
-    }
-    m_prev = m;
+    double cm = 1.0, sm = 0.0;
+    if (m != 0) sincos((double)m * th, &sm, &cm);
+    // Angular factors of a cos and of a sin output.
+    const double fc = VK == VK_DTHETA ? -(double)m * sm : cm;
+    const double fs = VK == VK_DTHETA ? (double)m * cm : sm;
     const double* h = d.table + (size_t)col.table_row * kRow;
     const uint2* st = d.steps + col.table_row + kHeaderRows;
     const int32_t* sp = d.slot_ptr + col.slot_base;
-    double T = pm, S = pm * fma(h[4], u, -h[8]);
+    // Seeds Q_{-1} = 0, Q_{-2} = -rho^m (and their rho-derivatives) with (A_0, B_0) = (0, 0),
+    // (A_1, B_1) = (m + 2, m + 1) from the column header.
+    double S = 0.0, T = -pow_uint(rho, m);
+    double Sd = 0.0, Td = m > 0 ? -(double)m * pow_uint(rho, m - 1) : 0.0;
     for (int N = 0; N < col.n_steps; ++N) {
       const double* row = h + (size_t)(kHeaderRows + N) * kRow;
-      double q;
-      if (N == 0) {
-        q = T;
-      } else if (N == 1) {
-        q = S;
-      } else {
-        const double g = fma(row[0], u, -row[1]);
-        q = fma(g, S, -T);
-        T = S;
-        S = q;
-      }
+      const double A = N >= 2 ? row[0] : (N == 1 ? h[4] : 0.0);
+      const double B = N >= 2 ? row[1] : (N == 1 ? h[8] : 0.0);
+      const double g = fma(A, u, -B);
+      const double qd = fma(g, Sd, fma(2.0 * A * rho, S, -Td));
+      const double q = fma(g, S, -T);
+      Td = Sd;
+      Sd = qd;
+      T = S;
+      S = q;
+      const double v = VK == VK_DRHO ? qd : q;
       const uint32_t info = st[N].x;
       uint32_t cnt = info & 0xffu, flags = info >> 8;
       if (cnt == 0) continue;
       if (cnt == kStepIrregular) {
         for (int s = sp[N]; s < sp[N + 1]; ++s) {
           const uint32_t code = (uint32_t)__ldg(d.slot_idx + s);
-          emit(q * ((code >> 31) ? sm : cm));
+          emit(v * ((code >> 31) ? fs : fc));
         }
       } else {
-        for (; cnt > 0; --cnt, flags >>= 1) emit(q * ((flags & 1u) ? sm : cm));
+        for (; cnt > 0; --cnt, flags >>= 1) emit(v * ((flags & 1u) ? fs : fc));
       }
     }
   }
@@ -241,6 +241,24 @@ __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint3
   }
   if (p >= d.P) return;
   const int e_base = ep - kBeta * (kDig + 1);
+  if (d.dot_out) {
+    // Row sum over this thread's 8 sets of G times the series; the point's two halves are added
+    // onto the zeroed output (two addends: the same float64 sum in either order).
+    const double* grow = d.gdot + p * d.S;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (h * 8 + i >= d.S) break;
+      const int ec = d.cexp[h * 8 + i];
+      const double v = (ep == kNonFiniteRow || ec == kNonFiniteRow)
+                           ? __longlong_as_double(0x7ff8000000000000ll)
+                           : join_to_double(hi[i], lo[i], kBeta * (kDig - kSplit), e_base + ec);
+      acc = fma(grow[h * 8 + i], v, acc);
+    }
+    atomicAdd(d.dot_out + p, acc);
+    return;
+  }
+  if (!d.out) return;
   double* orow = d.out + p * d.S;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -252,6 +270,7 @@ __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint3
   }
 }
 
+template <int VK>
 __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       if (!(rho >= 0.0 && rho <= 1.0 && isfinite(th))) {
         unsigned long long mx = 0;
         bool bad = false;
-        walk_point(d, rho, th, [&](double z) {
+        walk_point<VK>(d, rho, th, [&](double z) {
           const unsigned long long b = (unsigned long long)__double_as_longlong(z) & 0x7fffffffffffffffull;
           mx = b > mx ? b : mx;
           bad |= !isfinite(z);
@@ -416,6 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       // of 4 as two of 2).  The walk starts from the state of m = 0 (cos = 1, sin = 0, rho^0 = 1).
       const double c3 = fma(c2, c1, -s2 * s1), s3 = fma(s2, c1, c2 * s1), r3 = u * rho;
       double cm = 1.0, sm = 0.0, pm = 1.0;
+      double pm1 = 0.0;  // rho^(m-1) for the derivative lane's seed (VK_DRHO)
       int m_prev = 0;
       const int ncs = d.ncols_s[strm];
       int scol0 = 0;
@@ -429,41 +449,57 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           const double cn = fma(cm, c1, -sm * s1);
           sm = fma(sm, c1, cm * s1);
           cm = cn;
+          if constexpr (VK == VK_DRHO) pm1 = pm;
           pm *= rho;
         } else if (m == m_prev + 2) {
           const double cn = fma(cm, c2, -sm * s2);
           sm = fma(sm, c2, cm * s2);
           cm = cn;
+          if constexpr (VK == VK_DRHO) pm1 = pm * rho;
           pm *= u;
         } else if (m == m_prev + 3) {
           const double cn = fma(cm, c3, -sm * s3);
           sm = fma(sm, c3, cm * s3);
           cm = cn;
+          if constexpr (VK == VK_DRHO) pm1 = pm * u;
           pm *= r3;
         } else if (m != m_prev) {
           cm = 1.0;
           sm = 0.0;
           if (m != 0) sincos((double)m * th, &sm, &cm);
           pm = pow_uint(rho, m);
+          if constexpr (VK == VK_DRHO) pm1 = m > 0 ? pow_uint(rho, m - 1) : 0.0;
         }
         m_prev = m;
+        // Angular factors of a cos and of a sin output (their theta-derivatives for VK_DTHETA).
+        const double fcos = VK == VK_DTHETA ? -(double)m * sm : cm;
+        const double fsin = VK == VK_DTHETA ? (double)m * cm : sm;
         const double* h = d.table + (size_t)col.table_row * kRow;
         const int n_steps = col.n_steps;
         const int4 fc = d.fcols[c];
         const int kind = fc.x & 255;
-        const double fa = (fc.x >> 8) & 1 ? sm : cm, fb = (fc.x >> 9) & 1 ? sm : cm;
+        const double fa = (fc.x >> 8) & 1 ? fsin : fcos, fb = (fc.x >> 9) & 1 ? fsin : fcos;
         double S = 0.0, T = -pm;
-        // One recursion step N (>= n_steps: a padding step on the last row, its output unused).
+        // The derivative lane (VK_DRHO): Q'_{-1} = 0, Q'_{-2} = -m rho^(m-1).
+        double Sd = 0.0, Td = VK == VK_DRHO ? -(double)m * pm1 : 0.0;
+        // One recursion step N (>= n_steps: a padding step on the last row, its output unused):
+        // Q_N, or Q'_N for VK_DRHO.
         auto step = [&](int N) -> double {
           const int Nc = N < n_steps ? N : n_steps - 1;
           const double* rw = h + (size_t)(kHeaderRows + Nc) * kRow;
           const double A = N >= 2 ? rw[0] : (N == 1 ? h[4] : 0.0);
           const double B = N >= 2 ? rw[1] : (N == 1 ? h[8] : 0.0);
           const double g = fma(A, u, -B);
+          if constexpr (VK == VK_DRHO) {
+            const double A2 = N >= 2 ? rw[2] : (N == 1 ? 2.0 * h[4] : 0.0);  // 2 A_N
+            const double qd = fma(g, Sd, fma(A2 * rho, S, -Td));
+            Td = Sd;
+            Sd = qd;
+          }
           const double qv = fma(g, S, -T);
           T = S;
           S = qv;
-          return qv;
+          return VK == VK_DRHO ? Sd : qv;
         };
         if (kind == kFusedKindTwo) {
           // Two outputs per step: four steps fill one unit.
@@ -487,8 +523,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
               constexpr int i = decltype(ic)::value;
               const double q0 = step(N0 + 2 * i);
               const double q1 = step(N0 + 2 * i + 1);
-              // m = 0: the angular factor is 1 (no product)
-              const double z0 = m == 0 ? q0 : q0 * fa, z1 = m == 0 ? q1 : q1 * fa;
+              // m = 0: the angular factor is 1 (no product; the theta-derivative is 0)
+              const double z0 = m == 0 ? (VK == VK_DTHETA ? 0.0 : q0) : q0 * fa;
+              const double z1 = m == 0 ? (VK == VK_DTHETA ? 0.0 : q1) : q1 * fa;
               put_pair_const(ic, N0 + 2 * i < n_steps ? z0 : 0.0, N0 + 2 * i + 1 < n_steps ? z1 : 0.0);
             };
             two(std::integral_constant<int, 0>{});
@@ -536,9 +573,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             uint32_t cnt = info & 0xffu, flags = info >> 8;
             if (cnt == 0) continue;
             if (cnt == kStepIrregular) {
-              for (int sl = sp[N]; sl < sp[N + 1]; ++sl) emit(qv * (((uint32_t)__ldg(d.slot_idx + sl) >> 31) ? sm : cm));
+              for (int sl = sp[N]; sl < sp[N + 1]; ++sl) emit(qv * (((uint32_t)__ldg(d.slot_idx + sl) >> 31) ? fsin : fcos));
             } else {
-              for (; cnt > 0; --cnt, flags >>= 1) emit(qv * ((flags & 1u) ? sm : cm));
+              for (; cnt > 0; --cnt, flags >>= 1) emit(qv * ((flags & 1u) ? fsin : fcos));
             }
           }
           if (have) emit(0.0);
@@ -722,24 +759,46 @@ __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int
 
 }  // namespace
 
+int fused_ep_for(const zp_plan* plan, int vk) {
+  int m_max = 0, n_max = 0;
+  for (const Column& c : plan->cols) {
+    m_max = std::max(m_max, c.m);
+    n_max = std::max(n_max, c.m + 2 * (c.n_steps - 1));
+  }
+  const int64_t bound = vk == kFusedDTheta ? m_max : (vk == kFusedDRho ? (int64_t)n_max * n_max : 1);
+  int extra = 0;
+  while ((int64_t(1) << extra) < bound) ++extra;
+  return plan->fused_ep + extra;
+}
+
 zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int vk, bool coeff_digits) {
   if (a.n_items == 0) return ZP_OK;
+  if (vk != kFusedZ && vk != kFusedDTheta && vk != kFusedDRho) return set_error(ZP_ERR_INVALID_ARG, "fused value kind");
   static DeviceMemo<int> sms_memo;
   int sms = 0;
   ZP_TRY(sms_memo.get(&sms, [](int* x) -> zp_status {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(x, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_emu_kernel<VK_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_emu_kernel<VK_DTHETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_emu_kernel<VK_DRHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused kernel set-up");
   }));
-  fused_cexp_kernel<<<(unsigned)n_inst, 256, 0, stream>>>(a, n_inst);
-  const int64_t threads = n_chunks * FNS * (FBK / 8);
-  fused_coeff_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 8 * (int64_t)sms)), 256,
-                       0, stream>>>(a, chunk_inst, n_chunks);
+  if (coeff_digits) {
+    fused_cexp_kernel<<<(unsigned)n_inst, 256, 0, stream>>>(a, n_inst);
+    const int64_t threads = n_chunks * FNS * (FBK / 8);
+    fused_coeff_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 8 * (int64_t)sms)),
+                         256, 0, stream>>>(a, chunk_inst, n_chunks);
+  }
   const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, sms);
-  fused_emu_kernel<<<grid, kThreads, kSmem, stream>>>(a);
+  if (vk == kFusedDTheta) fused_emu_kernel<VK_DTHETA><<<grid, kThreads, kSmem, stream>>>(a);
+  else if (vk == kFusedDRho) fused_emu_kernel<VK_DRHO><<<grid, kThreads, kSmem, stream>>>(a);
+  else fused_emu_kernel<VK_Z><<<grid, kThreads, kSmem, stream>>>(a);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused series launch");
 }

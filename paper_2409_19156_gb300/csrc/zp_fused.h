@@ -59,7 +59,21 @@ struct FusedInst {
   uint8_t* bdig = nullptr;         // [KC][kFusedBChunk] coefficient digits (written per call)
   int* cexp = nullptr;             // [kFusedMaxSets] set scale exponents (written per call)
   double* out = nullptr;           // [P][S]
+  // Instead of out: dot_out[p] += sum_s gdot[p][s] F[p][s] (two atomic adds per point onto a
+  // zeroed array, one per half of the sets: the same sum in either order).
+  const double* gdot = nullptr;    // [P][S]
+  double* dot_out = nullptr;       // [P]
 };
+
+// Values a fused launch contracts with the coefficients: the basis Z (the series), its theta-
+// derivative or its rho-derivative (the adjoint's point gradients as row sums of G times those
+// series).
+constexpr int kFusedZ = 0, kFusedDTheta = 1, kFusedDRho = 2;
+
+// Row scale exponent of on-disc points for value kind vk: 2^e above every |value| of the plan on
+// the unit disc (|R| <= 1, |dR/dtheta| <= m_max, |dR/drho| <= n_max^2 by Markov's inequality, each
+// over the smallest weight W0_N).
+int fused_ep_for(const zp_plan* plan, int vk);
 
 // A 128-point tile of one instance.
 struct FusedItem {
@@ -77,10 +91,11 @@ struct FusedArgs {
 };
 
 // Coefficient scales and digits of every instance (n_inst instances, chunk_inst[g] = instance of
-// global chunk g, n_chunks chunks in total; chunk_inst NULL for the single-instance form), then the
-// fused kernel over all items: stream-ordered, no host synchronisation (capturable).
+// global chunk g, n_chunks chunks in total; chunk_inst NULL for the single-instance form; skipped
+// when coeff_digits is false: a previous launch on the stream made them), then the fused kernel
+// for value kind vk over all items: stream-ordered, no host synchronisation (capturable).
 zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int vk = kFusedZ, bool coeff_digits = true);
 
 // F = Z C for one plan with S <= kFusedMaxSets and plan->fused_kpad <= kFusedMaxModes (scratch
 // for the coefficient digits from the library's pool).

@@ -98,7 +98,7 @@ def test_batched_adjoint_matches_single_path_and_is_deterministic(S, prec):
     torch.cuda.synchronize()
     for f, rec in zip(first, b.instances):
         for a, k in zip(f, ("grad_coeffs", "grad_r", "grad_theta")):
-            assert torch.equal(a, rec[k]), k  # bitwise identical: no atomics
+            assert torch.equal(a, rec[k]), k  # bitwise identical (two-addend atomic sums are order-free)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64emu"])
@@ -113,6 +113,32 @@ def test_batched_adjoint_against_oracle_small(prec):
         assert np.max(np.abs(rec["grad_coeffs"].cpu().numpy() - np.array(wC))) < 1e-12
         assert np.max(np.abs(rec["grad_r"].cpu().numpy() - np.array(wr))) < 1e-11
         assert np.max(np.abs(rec["grad_theta"].cpu().numpy() - np.array(wt))) < 1e-11
+
+
+def test_batched_emulated_adjoint_off_disc_points():
+    """Points beyond the unit disc (r up to 1.4) take the fused kernel's per-point row scale for
+    the derivative series too: grad_r and grad_theta against the float64 CUDA-core form."""
+    S = 16
+    inst = make_instances([(20, 500), (9, 77), (0, 30)], S, seed=41)
+    rng = np.random.default_rng(5)
+    for d in inst:
+        r = rng.uniform(0.0, 1.4, len(d["_r"]))
+        d["_r"] = r
+        d["r"] = dev(r)
+    b = zp.Batch(inst, S)
+    b.adjoint("fp64")
+    torch.cuda.synchronize()
+    ref = [tuple(rec[k].clone() for k in ("grad_coeffs", "grad_r", "grad_theta")) for rec in b.instances]
+    b.adjoint("fp64emu")
+    torch.cuda.synchronize()
+    for f, rec in zip(ref, b.instances):
+        for want, k in zip(f, ("grad_coeffs", "grad_r", "grad_theta")):
+            if want.numel() == 0:
+                continue
+            got = rec[k]
+            assert bool(torch.isfinite(got).all())
+            scale = 1e-11 * (1.0 + float(want.abs().max()))
+            assert float((got - want).abs().max()) <= scale, k
 
 
 def test_batched_cuda_graph_and_tuner():
