@@ -219,7 +219,10 @@ ZP_API zp_status zp_series_adjoint_plan(const zp_plan* plan, const double* r, co
  * float64-accurate tensor-core GEMM of ZP_PREC_FP64_EMULATED, with the scale-relative error
  * bound stated there: about K 2^-54 times the largest operand magnitudes of the row and
  * column, K = n_points for grad_coeffs and n_sets for H).  grad_r and grad_theta are then
- * reduced in float64 as for ZP_PREC_FP64.  Other precisions: ZP_ERR_INVALID_ARG.
+ * reduced in float64 as for ZP_PREC_FP64 -- except for n_sets <= 16 (and at most 5041 padded
+ * modes), where they are the row sums grad_out[p] . (dZ/dtheta C)[p] and grad_out[p] . (dZ/drho
+ * C)[p] of the fused kernel's derivative series (no modes x points matrix H; deterministic).
+ * Other precisions: ZP_ERR_INVALID_ARG.
  */
 ZP_API zp_status zp_series_adjoint_plan_prec(const zp_plan* plan, const double* r, const double* theta,
                                              int64_t n_points, const double* coeffs, int64_t n_sets,

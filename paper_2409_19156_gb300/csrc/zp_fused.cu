@@ -803,13 +803,11 @@ zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused series launch");
 }
 
-zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
-                            int64_t S, double* out, cudaStream_t stream) {
-  const int64_t J = plan->n_modes;
-  if (S > kFusedMaxSets || plan->fused_kpad > kFusedMaxModes)
-    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 padded modes");
-  FusedArgs a;
-  FusedInst& d = a.single;
+namespace {
+// The single-instance descriptor of a plan's fused layout (value kind Z; no output set).
+FusedInst single_inst(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                      int64_t S) {
+  FusedInst d;
   d.cols = plan->dev.cols;
   d.table = plan->dev.table;
   d.steps = plan->dev.split_step;
@@ -827,12 +825,23 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.n_cols = (int32_t)plan->cols.size();
   d.KC = (int32_t)((plan->fused_kpad + FBK - 1) / FBK);
   d.kc_base = 0;
-  d.J = J;
+  d.J = plan->n_modes;
   d.P = P;
   d.S = S;
   d.r = r;
   d.theta = theta;
   d.coeffs = coeffs;
+  return d;
+}
+}  // namespace
+
+zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                            int64_t S, double* out, cudaStream_t stream) {
+  if (S > kFusedMaxSets || plan->fused_kpad > kFusedMaxModes)
+    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 padded modes");
+  FusedArgs a;
+  FusedInst& d = a.single;
+  d = single_inst(plan, r, theta, P, coeffs, S);
   d.out = out;
   ScratchBuffer buf;
   const size_t bbytes = (size_t)d.KC * kFusedBChunk;
@@ -841,6 +850,36 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.cexp = (int*)((uint8_t*)buf.ptr + bbytes);
   a.n_items = (P + FM - 1) / FM;
   return fused_launch(a, 1, nullptr, d.KC, stream);
+}
+
+zp_status fused_point_grads(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                            int64_t S, const double* G, double* grad_r, double* grad_theta, cudaStream_t stream) {
+  if (S > kFusedMaxSets || plan->fused_kpad > kFusedMaxModes)
+    return set_error(ZP_ERR_UNSUPPORTED, "fused series: at most 16 sets and 5041 padded modes");
+  if (P == 0 || (!grad_r && !grad_theta)) return ZP_OK;
+  FusedArgs a;
+  FusedInst& d = a.single;
+  d = single_inst(plan, r, theta, P, coeffs, S);
+  d.gdot = G;
+  ScratchBuffer buf;
+  const size_t bbytes = (size_t)d.KC * kFusedBChunk;
+  ZP_TRY(buf.alloc(bbytes + 256, stream));
+  d.bdig = (uint8_t*)buf.ptr;
+  d.cexp = (int*)((uint8_t*)buf.ptr + bbytes);
+  a.n_items = (P + FM - 1) / FM;
+  bool digits = true;  // the coefficient digits once, for the first pass
+  for (int k = 0; k < 2; ++k) {
+    double* g = k == 0 ? grad_theta : grad_r;
+    if (!g) continue;
+    const cudaError_t e = cudaMemsetAsync(g, 0, (size_t)P * sizeof(double), stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    const int vk = k == 0 ? kFusedDTheta : kFusedDRho;
+    d.dot_out = g;
+    d.ep_disc = fused_ep_for(plan, vk);
+    ZP_TRY(fused_launch(a, 1, nullptr, d.KC, stream, vk, digits));
+    digits = false;
+  }
+  return ZP_OK;
 }
 
 zp_status fused_error_word(unsigned int* value, bool reset) {

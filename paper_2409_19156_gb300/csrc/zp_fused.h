@@ -102,6 +102,13 @@ zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_
 zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
                             int64_t S, double* out, cudaStream_t stream);
 
+// grad_theta[p] = sum_s G[p][s] (dZ/dtheta C)[p][s] and grad_r[p] likewise with dZ/drho (either
+// may be NULL), by the fused kernel's derivative series: the adjoint's point gradients for
+// S <= kFusedMaxSets and plan->fused_kpad <= kFusedMaxModes, without the [modes x points]
+// matrix H = C G^T.
+zp_status fused_point_grads(const zp_plan* plan, const double* r, const double* theta, int64_t P, const double* coeffs,
+                            int64_t S, const double* G, double* grad_r, double* grad_theta, cudaStream_t stream);
+
 // Reads and optionally clears the fused kernel's wait-status word (non-zero: a bounded wait
 // gave up).
 zp_status fused_error_word(unsigned int* value, bool reset);

@@ -270,7 +270,12 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
                               const double* coeffs, int64_t S, const double* G, double* grad_coeffs, double* grad_r,
                               double* grad_theta, cudaStream_t stream, const HessOut& ho, bool emulated) {
   const int64_t J = plan->n_modes;
-  const bool need_h = grad_r || grad_theta || ho.any();
+  // Few sets, emulated, no Hessian: the point gradients come from the fused kernel's
+  // derivative series (no [modes x points] H).
+  const bool fused_pt = emulated && !ho.any() && (grad_r || grad_theta) && S <= kFusedMaxSets &&
+                        plan->fused_kpad <= kFusedMaxModes;
+  if (fused_pt) ZP_TRY(fused_point_grads(plan, r, theta, P, coeffs, S, G, grad_r, grad_theta, stream));
+  const bool need_h = !fused_pt && (grad_r || grad_theta || ho.any());
   ScratchBuffer z, hbuf;
   CublasLock cl;
   if (grad_coeffs) {

@@ -54,6 +54,9 @@ def test_hvp_matches_gradient_differences():
     fd_t = (gp[1] - gm[1]) / (2 * eps)
     assert float((fd_r - hv_r).abs().max()) < 1e-5 * (1 + float(hv_r.abs().max()))
     assert float((fd_t - hv_t).abs().max()) < 1e-5 * (1 + float(hv_t.abs().max()))
-    # the gradient part equals the adjoint's
+    # the gradient part equals the adjoint's to float64 accuracy (the adjoint's default takes
+    # the point gradients of at most 16 sets from the fused kernel's derivative series, the
+    # Hessian kernel from H = C G^T)
     _, gr, gt = zp.series_adjoint(None, None, rt, tt, C, G, plan=plan)
-    assert torch.equal(gr, hess[0]) and torch.equal(gt, hess[1])
+    for a, b in ((gr, hess[0]), (gt, hess[1])):
+        assert float((a - b).abs().max()) <= 1e-12 * (1 + float(b.abs().max()))

@@ -121,7 +121,8 @@ def scale_bound(K, A_rows, B_rows):
 @pytest.mark.parametrize("nmax,P,S", [(7, 90, 4), (3, 1500, 3)])
 def test_emulated_adjoint_against_oracle(nmax, P, S):
     """grad_C = Z G (contraction over the points; 1500 points with 10 modes cut K into many
-    batches) and grad_r, grad_theta through H = C G^T, all by the emulated contraction."""
+    batches) by the emulated contraction, grad_r and grad_theta (at most 16 sets) as row sums
+    of G times the fused kernel's derivative series."""
     ns, ms = inputs.full_zernike_modes(nmax)
     r, th = inputs.uniform_points(P, 22 + nmax)
     C = inputs.scaled_normal_coeffs(ns, S, 22)
@@ -134,6 +135,25 @@ def test_emulated_adjoint_against_oracle(nmax, P, S):
     scale = 1.0 + np.abs(G).sum(1) * np.abs(C).sum() * max(nmax, 1) ** 2
     assert (np.abs(gr.cpu().numpy() - np.array(wr)) <= 1e-12 * scale).all()
     assert (np.abs(gt.cpu().numpy() - np.array(wt)) <= 1e-12 * scale).all()
+
+
+@pytest.mark.parametrize("S", [1, 16, 17])
+def test_emulated_adjoint_point_gradients_off_disc(S):
+    """Points inside and beyond the unit disc (r up to 1.4), one to 17 sets (17: through H =
+    C G^T instead of the fused derivative series): grad_r and grad_theta against the float64
+    DGEMM form, relative to the size of the terms they sum."""
+    ns, ms = inputs.full_zernike_modes(15)
+    rng = np.random.default_rng(80 + S)
+    P = 700
+    r, th = rng.uniform(0.0, 1.4, P), rng.uniform(-np.pi, np.pi, P)
+    C = inputs.scaled_normal_coeffs(ns, S, 80 + S)
+    G = rng.standard_normal((P, S))
+    args = (ns, ms, dev(r), dev(th), dev(C), dev(G))
+    _, gr, gt = zp.series_adjoint(*args, prec="fp64emu")
+    _, wr, wt = zp.series_adjoint(*args, prec="fp64")
+    scale = 1.0 + torch.as_tensor(np.abs(G).sum(1) * np.abs(C).sum() * 15 ** 2 * r.max() ** 15, device=DEV)
+    assert bool(((gr - wr).abs() <= 1e-12 * scale).all())
+    assert bool(((gt - wt).abs() <= 1e-12 * scale).all())
 
 
 def test_emulated_adjoint_series_n24_full_size_against_fp64():
