@@ -751,6 +751,7 @@ def measure_fused_series(dev, peaks, steps: int = 5, n_points: int = 1_000_000) 
     fused kernel's float64 roofline (its walk issues fused_fp64_ops per point)."""
     import ctypes
 
+    import numpy as np
     import torch
 
     import paper_2409_19156_gb300 as zp
@@ -781,9 +782,32 @@ def measure_fused_series(dev, peaks, steps: int = 5, n_points: int = 1_000_000) 
     probe = (ctypes.c_double * 6)()
     _lib.check("zp_probe_fp64", lib.zp_probe_fp64(0, 20000, sp, probe))
     diff = float((out - out64).abs().max())
+    # The adjoint of the same series (grad_C, grad_r, grad_theta): the default path (grad_C by the
+    # emulated GEMM, the point gradients from the fused derivative series) against the float64
+    # basis + DGEMM form (H = C G^T through HBM).
+    G = torch.as_tensor(np.random.default_rng(cfg["seed"]).standard_normal((n_points, S)), device=dev)
+    gC = torch.empty((len(ns), S), dtype=torch.float64, device=dev)
+    gr = torch.empty(n_points, dtype=torch.float64, device=dev)
+    gt = torch.empty_like(gr)
+    res = [(gC.clone(), gr.clone(), gt.clone()) for _ in range(2)]
+
+    def adj(code, o):
+        _lib.check("zp_series_adjoint_plan_prec", lib.zp_series_adjoint_plan_prec(
+            plan.handle, rt.data_ptr(), tt.data_ptr(), n_points, Ct.data_ptr(), S, G.data_ptr(), o[0].data_ptr(),
+            o[1].data_ptr(), o[2].data_ptr(), code, sp))
+
+    adj(4, res[0])
+    t_adj_emu = _events_ms(stream, lambda: adj(4, res[0]), 3)
+    adj(0, res[1])
+    t_adj_64 = _events_ms(stream, lambda: adj(0, res[1]), 2)
+    adj_diff = [float((a - b).abs().max() / (1.0 + b.abs().max())) for a, b in zip(res[0], res[1])]
+    del G, res
     return {"workload": "mixed_n32 points, 16 sets", "modes": len(ns), "points": n_points, "sets": S,
             "fp64emu_fused_ms": t_fused, "fp64_basis_then_dgemm_ms": t_dgemm,
             "speedup_fused_vs_basis_then_dgemm": t_dgemm / t_fused,
+            "fp64emu_adjoint_ms": t_adj_emu, "fp64_dgemm_adjoint_ms": t_adj_64,
+            "speedup_emulated_vs_dgemm_adjoint": t_adj_64 / t_adj_emu,
+            "adjoint_rel_diff_vs_dgemm_gC_gr_gt": adj_diff,
             "max_abs_diff_vs_dgemm": diff, "max_abs_value": float(out64.abs().max()),
             "roofline": {"bound": "alu", "kernel": "fused_emu_kernel (includes the coefficient digit kernels)",
                          "fp64_ops": ops, "achieved_ops_per_s": ops / (t_fused * 1e-3),
