@@ -32,6 +32,7 @@
 // multiple of 8 positions (so a column's steps fill whole 16-byte operand units in unrolled
 // straight-line code), and the coefficient digits are prepared per call in that order
 // (fused_coeff_kernel).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -97,13 +98,52 @@ __device__ __forceinline__ void digits_of(long long X, uint32_t (&f)[kDig]) {
     f[t] = __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y, t)) - 8388624.0f);  // 2^23+16
 }
 
+// Digit t >= 1 of two biased words as one word of two bf16 (value 0 low): the unsigned 5-bit
+// fields f placed under the bfloat16 pattern of 128 (0x4300 | f is exactly 128 + f), then one
+// packed subtraction of 144 leaves the balanced digit f - 16 in each half (exact).
+template <int T>
+__device__ __forceinline__ uint32_t digit_pair_low(long long Y0, long long Y1) {
+  static_assert(T >= 1 && T < kDig, "unsigned digit fields");
+  constexpr int s = kBeta * (kDig - 1 - T);  // bit position of the field
+  uint32_t a, b;
+  if constexpr (s + kBeta <= 32) {
+    a = (uint32_t)Y0 >> s;
+    b = s >= 16 ? (uint32_t)Y1 >> (s - 16) : (uint32_t)Y1 << (16 - s);
+  } else {
+    a = (uint32_t)(Y0 >> s);
+    b = (uint32_t)(Y1 >> s) << 16;
+  }
+  const uint32_t w = (a & 0x1Fu) | (b & 0x1F0000u) | 0x43004300u;
+  __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&w);
+  v = __hsub2(v, __nv_bfloat162(__nv_bfloat16_raw{0x4310}, __nv_bfloat16_raw{0x4310}));  // 144
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Digit 0 (signed, at most 33 in magnitude) of two biased words, by the float32 magic sum.
+__device__ __forceinline__ uint32_t digit_pair_top(long long Y0, long long Y1) {
+  const uint32_t f0 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y0, 0)) - 12582912.0f);
+  const uint32_t f1 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y1, 0)) - 12582912.0f);
+  return __byte_perm(f0, f1, 0x7632);
+}
+
+// All 11 digits of two biased words Y = X + bias, joined per digit (value 0 low).
+__device__ __forceinline__ void digit_pair_biased(long long Y0, long long Y1, uint32_t (&w)[kDig]) {
+  w[0] = digit_pair_top(Y0, Y1);
+  w[1] = digit_pair_low<1>(Y0, Y1);
+  w[2] = digit_pair_low<2>(Y0, Y1);
+  w[3] = digit_pair_low<3>(Y0, Y1);
+  w[4] = digit_pair_low<4>(Y0, Y1);
+  w[5] = digit_pair_low<5>(Y0, Y1);
+  w[6] = digit_pair_low<6>(Y0, Y1);
+  w[7] = digit_pair_low<7>(Y0, Y1);
+  w[8] = digit_pair_low<8>(Y0, Y1);
+  w[9] = digit_pair_low<9>(Y0, Y1);
+  w[10] = digit_pair_low<10>(Y0, Y1);
+}
+
 // Two values' digits joined per digit into one 32-bit word of two bf16 (value 0 low).
 __device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t (&w)[kDig]) {
-  uint32_t f0[kDig], f1[kDig];
-  digits_of(X0, f0);
-  digits_of(X1, f1);
-#pragma unroll
-  for (int t = 0; t < kDig; ++t) w[t] = __byte_perm(f0[t], f1[t], 0x7632);
+  digit_pair_biased(X0 + kBias, X1 + kBias, w);
 }
 
 struct Barriers {
@@ -411,16 +451,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         constexpr int word = decltype(word_c)::value;
         const long long Y0 = (zero_row ? 0 : to_fixed_trunc(z0, shift)) + kBias;
         const long long Y1 = (zero_row ? 0 : to_fixed_trunc(z1, shift)) + kBias;
+        uint32_t pw[kDig];
+        digit_pair_biased(Y0, Y1, pw);
 #pragma unroll
-        for (int t = 0; t < kDig; ++t) {
-          const uint32_t f0 = t == 0 ? __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y0, 0)) - 12582912.0f)
-                                     : __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y0, t)) -
-                                                       8388624.0f);
-          const uint32_t f1 = t == 0 ? __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y1, 0)) - 12582912.0f)
-                                     : __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y1, t)) -
-                                                       8388624.0f);
-          w[t][word] = __byte_perm(f0, f1, 0x7632);
-        }
+        for (int t = 0; t < kDig; ++t) w[t][word] = pw[t];
       };
       // The walk of this stream's columns (Sec. 2 recursion in the plan's rescaled form, Algorithm
       // 1's column order within the stream).  The recursion runs uniformly from the seeds
