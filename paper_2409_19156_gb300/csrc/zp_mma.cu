@@ -12,12 +12,16 @@
 //      in the tensor core's swizzled K-major layout in a scratch buffer.
 //      The K order of the contraction is the plan's slot order (column by column), so a
 //      thread's outputs are consecutive in K; the coefficient rows are permuted to match.
-//  (B) split_gemm_kernel: persistent, warp-specialised tcgen05 GEMM.  Warp 0 streams A
-//      (points x K) and B (sets x K) chunks into a shared-memory ring with bulk copies and
-//      mbarrier transaction counts; warp 1 issues tcgen05.mma (M = 128 points, N = 256 sets,
-//      K = 16 per instruction) into one of two TMEM accumulators; warps 2-5 drain the other
-//      accumulator (tcgen05.ld) to float32 rows of F while the next tile accumulates.
-// The coefficients are split/permuted once per call by split_coeff_kernel.
+//  (B) split_gemm_kernel: persistent, warp-specialised tcgen05 GEMM on CTA pairs (clusters
+//      of two): in each CTA warp 0 streams its 128 points' A chunks and half of each B (sets x
+//      K) chunk into its own shared-memory ring with bulk copies and mbarrier transaction
+//      counts; warp 1 of the even CTA issues tcgen05.mma.cta_group::2 (M = 256 points across
+//      the pair, N = 256 sets, K = 16 per instruction) into one of two TMEM accumulators in
+//      each CTA; warps 2-5 of each CTA drain its other accumulator (tcgen05.ld) to float32
+//      rows of F while the next tile accumulates; warp 6 passes barrier signals between the
+//      pair.  A single-CTA form (M = 128) runs when pairs cannot.
+// The coefficients are split/permuted once per call by split_coeff_kernel.  The same GEMM with
+// integer-valued bfloat16 slices is the float64-emulating contraction (KIND_SLICE, below).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
