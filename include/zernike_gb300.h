@@ -314,7 +314,9 @@ ZP_API zp_status zp_series_fit_plan_prec(const zp_plan* plan, const double* r, c
  * [n_points] (float64, NULL = not computed).  All sets share one n_sets.
  * zp_batch_create validates every instance, builds one plan per distinct mode list, copies
  * tables and descriptors to the device (synchronously) and keeps the device pointers: the
- * arrays must stay allocated, and may change contents, between calls.
+ * arrays must stay allocated, and may change contents, between calls.  The passes of one batch
+ * share its scratch (work counters, coefficient digits): issue them on one stream, or order
+ * streams with events, never concurrently.
  */
 typedef struct {
   const int32_t* n;
