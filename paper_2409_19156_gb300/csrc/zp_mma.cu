@@ -415,9 +415,11 @@ struct GemmArgs {
   int dp = 0;
   int beta = 0;
   int s_slices = 0;
+  int nb = 128;  // paired: sets per tile = rows of a slice block (a multiple of 16; below 128 single CTAs only)
 };
 
-// Bytes of one 128-row slice block of the paired B layout.
+// Bytes of one 128-row slice block of the paired B layout (a narrow set tile of nb rows takes
+// nb * 128 bytes).
 constexpr uint32_t kSliceBlock = BM * Cfg<KIND_SLICE>::ROW;
 
 // Threads of the GEMM kernel: producer, MMA and 4 epilogue warps, plus, for a CTA pair, one
@@ -550,8 +552,9 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
             // B slices (dp - ts, dp + 1 - ts), or slice 0 alone for ts = dp + 1 (an N = 128
             // MMA); a pair's CTAs hold one slice each, or one half of slice 0's rows each.
             const bool both = ts <= a.dp;
-            const uint8_t* blk = a.B + (((size_t)nt * a.KC + kc) * a.s_slices + (both ? a.dp - ts : 0)) * kSliceBlock;
-            const uint32_t b_bytes = (both ? 2 * kSliceBlock : kSliceBlock) / CG;
+            const uint32_t blk_bytes = (uint32_t)a.nb * C::ROW;
+            const uint8_t* blk = a.B + (((size_t)nt * a.KC + kc) * a.s_slices + (both ? a.dp - ts : 0)) * blk_bytes;
+            const uint32_t b_bytes = (both ? 2 * blk_bytes : blk_bytes) / CG;
             ptx::mbar_arrive_expect_tx(&full[stage], C::A_CHUNK + b_bytes);
             ptx::bulk_g2s(sA, gA, C::A_CHUNK, &full[stage]);
             ptx::bulk_g2s(sB, blk + rank * b_bytes, b_bytes, &full[stage]);
@@ -579,7 +582,9 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
   } else if (warp == 1) {
     if (lane == 0 && leader) {
       constexpr uint32_t idesc = TF32 ? ptx::idesc_tf32_f32(BM * CG, BN) : ptx::idesc_bf16_f32(BM * CG, BN);
-      constexpr uint32_t idesc_half = ptx::idesc_bf16_f32(BM * CG, BN / 2);
+      // Paired slice tiles: N = 2 nb (both diagonals) or nb (the second alone).
+      const uint32_t idesc_pair = ptx::idesc_bf16_f32(BM * CG, KIND == KIND_SLICE && a.paired ? 2 * a.nb : BN);
+      const uint32_t idesc_half = ptx::idesc_bf16_f32(BM * CG, KIND == KIND_SLICE && a.paired ? a.nb : BN / 2);
       auto mma = [&](uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
         if constexpr (TF32) {
           if constexpr (PAIR) ptx::mma_tf32_pair(d, ad, bd, id, acc);
@@ -633,8 +638,9 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
               mma(d_tmem, ah, bl, idesc, 1u);
               mma(d_tmem, al, bh, idesc, 1u);
             } else {
-              mma(half ? d_tmem + BN / 2 : d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff),
-                  ptx::sw_kmajor_desc<C::ROW>(sB + koff), half ? idesc_half : idesc, first);
+              mma(half ? d_tmem + (uint32_t)a.nb : d_tmem, ptx::sw_kmajor_desc<C::ROW>(sA + koff),
+                  ptx::sw_kmajor_desc<C::ROW>(sB + koff),
+                  half ? idesc_half : (KIND == KIND_SLICE && a.paired ? idesc_pair : idesc), first);
             }
           }
           commit(&empty[stage]);
@@ -710,7 +716,7 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
       const int64_t p = (a.mt_base + mt_own) * BM + row;
       const bool store = mt_own < a.m_tiles && p < a.P;
       const bool paired = KIND == KIND_SLICE && a.paired;
-      const int tile_cols = paired ? BN / 2 : BN;
+      const int tile_cols = paired ? a.nb : BN;
       const int64_t col0 = (int64_t)nt * tile_cols;
       float* frow = a.F + (t / per_batch) * a.t_batch_stride + p * a.S;
       const bool vec = (a.S % 4) == 0;
@@ -719,8 +725,9 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
       for (int c0 = 0; c0 < tile_cols; c0 += 32) {
         uint32_t v[32];
         if (paired) {
-          // T_(dp+1) in columns 128-255, T_dp (none for dp = -1) in columns 0-127.
-          ptx::tmem_ld_32x32b_x32(tacc + BN / 2 + (uint32_t)c0, v);
+          // T_(dp+1) in columns nb .. 2 nb - 1, T_dp (none for dp = -1) in columns 0 .. nb - 1
+          // (a narrow tile reads past them into columns it does not store).
+          ptx::tmem_ld_32x32b_x32(tacc + (uint32_t)a.nb + (uint32_t)c0, v);
           ptx::tmem_ld_wait(v);
           if (a.dp >= 0) {
             uint32_t h[32];
@@ -745,7 +752,8 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
         }
         if (store) {
           const int64_t cbase = col0 + c0;
-          if (vec && cbase + 32 <= a.S) {
+          const int64_t cend = a.S < col0 + tile_cols ? a.S : col0 + tile_cols;  // this tile's columns only
+          if (vec && cbase + 32 <= cend) {
             float4* dst = reinterpret_cast<float4*>(frow + cbase);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -754,7 +762,7 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (cbase + i < a.S) frow[cbase + i] = __uint_as_float(v[i]);
+              if (cbase + i < cend) frow[cbase + i] = __uint_as_float(v[i]);
           }
         }
       }
@@ -885,7 +893,9 @@ template <int KIND>
 zp_status launch_gemm(const GemmArgs& ga, int64_t tiles, int NT, const GemmShape& g, cudaStream_t stream) {
   const int64_t kb = ga.k_batches > 0 ? ga.k_batches : 1;
   cudaError_t e;
-  if (g.pairs > 0 && tiles >= 2 && pairs_enabled()) {
+  // Narrow paired slice tiles (fewer than 128 sets) run on single CTAs: a pair splits B's rows.
+  const bool narrow = KIND == KIND_SLICE && ga.paired && ga.nb < BN / 2;
+  if (g.pairs > 0 && tiles >= 2 && !narrow && pairs_enabled()) {
     const int64_t groups = (tiles + 1) / 2 * NT * kb;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)(2 * std::min<int64_t>(groups, g.pairs)));
@@ -1118,11 +1128,12 @@ __device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, u
 // t * slice_stride.  Thread = (row, group of 8 consecutive K): rows fastest when an operand's
 // rows are contiguous (KFAST = false), K groups fastest when its K is (coalesced loads either
 // way).  Rows past `rows` and K past `K` are zero.
-template <int ROWS, bool KFAST>
+template <int ROWS_T, bool KFAST>
 __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
                                   const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride,
-                                  int64_t chunk_stride) {
+                                  int64_t chunk_stride, int rows_per_tile = 0) {
   constexpr int BK = Cfg<KIND_SLICE>::BK;
+  const int ROWS = ROWS_T > 0 ? ROWS_T : rows_per_tile;  // ROWS_T = 0: a multiple of 16 given at launch
   const int64_t rows_pad = tiles * ROWS;
   const int64_t groups = (int64_t)KC * (BK / 8);
   const int64_t total = rows_pad * groups;
@@ -1347,6 +1358,7 @@ __global__ void __launch_bounds__(256) recombine_planes_kernel(RecombineArgs a) 
 struct EmuGemm {
   EmuShape sh;
   int64_t N = 0, K = 0, NT = 0;
+  int nb = BN / 2;  // sets per tile of the paired layout
   int sms = 0;
   GemmShape gs;
   int64_t slab_tiles = 0;  // row tiles per slab
@@ -1378,14 +1390,20 @@ struct EmuGemm {
     recombine_blocks = (int64_t)std::max(per_sm, 1) * sms;
     if (!choose_emu_shape(K, MT * NT, sms, &sh))
       return set_error(ZP_ERR_UNSUPPORTED, "emulated float64 GEMM: contraction too long");
-    // Paired diagonals: set tiles of 128 (two diagonals share a tile's 256 accumulator columns).
-    if (sh.paired) NT = (N + BN / 2 - 1) / (BN / 2);
+    // Paired diagonals: set tiles of nb (two diagonals share a tile's 2 nb accumulator columns):
+    // 128, or for fewer sets the smallest multiple of 16 holding them all (a narrow tile: MMAs of
+    // N = 2 nb, so that few sets do not pay for 256-column MMAs).
+    if (sh.paired) {
+      nb = N >= BN / 2 ? BN / 2 : (int)((N + 15) / 16 * 16);
+      NT = (N + nb - 1) / nb;
+    }
     // Slab: int32 sums (k_batches x planes x rows x N x 4 B) within about 4 GB.
     const size_t t_tile = (size_t)sh.k_batches * sh.planes * BM * N * sizeof(int);
     slab_tiles = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / t_tile)));
     a_stride = slab_tiles * sh.KC * (int64_t)C::A_CHUNK;
-    b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;  // a paired B holds NT x KC x s blocks of 16 KB: the same bytes
-    ZP_TRY(bsl.alloc((size_t)sh.sp.s * b_stride / (sh.paired ? 2 : 1), stream));
+    b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;
+    // A paired B holds NT x KC x s blocks of nb rows.
+    ZP_TRY(bsl.alloc(sh.paired ? (size_t)NT * sh.KC * sh.sp.s * nb * C::ROW : (size_t)sh.sp.s * b_stride, stream));
     ZP_TRY(cexp.alloc((size_t)N * sizeof(int), stream));
     ZP_TRY(asl.alloc((size_t)sh.sp.s * a_stride, stream));
     ZP_TRY(rexp.alloc((size_t)slab_tiles * BM * sizeof(int), stream));
@@ -1396,14 +1414,14 @@ struct EmuGemm {
     ZP_TRY(scale_rows(B, N, K, (unsigned long long*)maxbits.ptr, (int*)cexp.ptr, stream));
     const bool kfast = B.sk == 1 && B.sr != 1;
     if (sh.paired) {
-      // Per (set tile, K chunk): slices 0..s-1 of 128 rows back to back.
-      const int64_t cs = (int64_t)sh.sp.s * kSliceBlock;
+      // Per (set tile, K chunk): slices 0..s-1 of nb rows back to back.
+      const int64_t blk = (int64_t)nb * C::ROW, cs = (int64_t)sh.sp.s * blk;
       if (kfast)
-        slice_rows_kernel<BN / 2, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
-                                                                 (uint8_t*)bsl.ptr, kSliceBlock, cs);
+        slice_rows_kernel<0, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                            (uint8_t*)bsl.ptr, blk, cs, nb);
       else
-        slice_rows_kernel<BN / 2, false><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
-                                                                  (uint8_t*)bsl.ptr, kSliceBlock, cs);
+        slice_rows_kernel<0, false><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
+                                                             (uint8_t*)bsl.ptr, blk, cs, nb);
     } else if (kfast) {
       slice_rows_kernel<BN, true><<<1024, 256, 0, stream>>>(B, N, NT, K, sh.KC, (const int*)cexp.ptr, sh.sp,
                                                            (uint8_t*)bsl.ptr, b_stride, C::B_CHUNK);
@@ -1438,6 +1456,7 @@ struct EmuGemm {
       if (sh.paired) {
         // Plane q: diagonals (2q - s % 2, 2q + 1 - s % 2), 0-based.
         ga.paired = 1;
+        ga.nb = nb;
         ga.dp = 2 * q - (sh.sp.s & 1);
         ga.beta = sh.sp.beta;
         ga.s_slices = sh.sp.s;
