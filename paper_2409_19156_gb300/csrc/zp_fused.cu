@@ -516,15 +516,19 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         double S = 0.0, T = -pm;
         // The derivative lane (VK_DRHO): Q'_{-1} = 0, Q'_{-2} = -m rho^(m-1).
         double Sd = 0.0, Td = VK == VK_DRHO ? -(double)m * pm1 : 0.0;
-        // One recursion step N (>= n_steps: a padding step on the last row, its output unused):
-        // Q_N, or Q'_N for VK_DRHO.
-        auto step = [&](int N) -> double {
-          const int Nc = N < n_steps ? N : n_steps - 1;
-          const double* rw = h + (size_t)(kHeaderRows + Nc) * kRow;
-          const double A = N >= 2 ? rw[0] : (N == 1 ? h[4] : 0.0);
+        // The recursion coefficient g_N = A_N rho^2 - B_N of step N < n_steps.
+        auto coef = [&](int N, double& A) -> double {
+          const double* rw = h + (size_t)(kHeaderRows + N) * kRow;
+          A = N >= 2 ? rw[0] : (N == 1 ? h[4] : 0.0);
           const double B = N >= 2 ? rw[1] : (N == 1 ? h[8] : 0.0);
-          const double g = fma(A, u, -B);
+          return fma(A, u, -B);
+        };
+        // One recursion step N < n_steps: Q_N, or Q'_N for VK_DRHO.
+        auto step = [&](int N) -> double {
+          double A;
+          const double g = coef(N, A);
           if constexpr (VK == VK_DRHO) {
+            const double* rw = h + (size_t)(kHeaderRows + N) * kRow;
             const double A2 = N >= 2 ? rw[2] : (N == 1 ? 2.0 * h[4] : 0.0);  // 2 A_N
             const double qd = fma(g, Sd, fma(A2 * rho, S, -Td));
             Td = Sd;
@@ -535,14 +539,36 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           S = qv;
           return VK == VK_DRHO ? Sd : qv;
         };
+        // The recursion is linear in its seeds: walked from the seeds times an angular factor f
+        // it gives Q_N f directly, one FMA per output instead of a product after the step (the
+        // derivative lane of VK_DRHO needs Q_N itself and keeps the products).  Steps past the
+        // column's end (the padding of its last unit) are not walked: a zero value's digits are
+        // zero words.
+        constexpr bool kScaled = VK != VK_DRHO;
         if (kind == kFusedKindTwo) {
           // Two outputs per step: four steps fill one unit.
+          double Sa = 0.0, Ta = -pm * fa, Sb = 0.0, Tb = -pm * fb;
           for (int N0 = 0; N0 < n_steps && ok; N0 += 4) {
             auto one = [&](auto ic) {
               constexpr int i = decltype(ic)::value;
-              const double qv = step(N0 + i);
-              const bool live = N0 + i < n_steps;
-              put_pair_const(ic, live ? qv * fa : 0.0, live ? qv * fb : 0.0);
+              if (i == 0 || N0 + i < n_steps) {
+                if constexpr (kScaled) {
+                  double A;
+                  const double g = coef(N0 + i, A);
+                  const double qa = fma(g, Sa, -Ta), qb = fma(g, Sb, -Tb);
+                  Ta = Sa;
+                  Sa = qa;
+                  Tb = Sb;
+                  Sb = qb;
+                  put_pair_const(ic, qa, qb);
+                } else {
+                  const double qv = step(N0 + i);
+                  put_pair_const(ic, qv * fa, qv * fb);
+                }
+              } else {
+#pragma unroll
+                for (int t = 0; t < kDig; ++t) w[t][i] = 0u;
+              }
             };
             one(std::integral_constant<int, 0>{});
             one(std::integral_constant<int, 1>{});
@@ -551,16 +577,32 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             ok = store_unit();
           }
         } else if (kind == kFusedKindOne) {
-          // One output per step: eight steps fill one unit.
+          // One output per step: eight steps fill one unit.  m = 0: the angular factor is 1 (its
+          // theta-derivative 0).
+          const double f1 = m == 0 ? (VK == VK_DTHETA ? 0.0 : 1.0) : fa;
+          double Sa = 0.0, Ta = -pm * f1;
+          auto out = [&](int N) -> double {
+            if constexpr (kScaled) {
+              double A;
+              const double qa = fma(coef(N, A), Sa, -Ta);
+              Ta = Sa;
+              Sa = qa;
+              return qa;
+            } else {
+              return step(N) * f1;
+            }
+          };
           for (int N0 = 0; N0 < n_steps && ok; N0 += 8) {
             auto two = [&](auto ic) {
               constexpr int i = decltype(ic)::value;
-              const double q0 = step(N0 + 2 * i);
-              const double q1 = step(N0 + 2 * i + 1);
-              // m = 0: the angular factor is 1 (no product; the theta-derivative is 0)
-              const double z0 = m == 0 ? (VK == VK_DTHETA ? 0.0 : q0) : q0 * fa;
-              const double z1 = m == 0 ? (VK == VK_DTHETA ? 0.0 : q1) : q1 * fa;
-              put_pair_const(ic, N0 + 2 * i < n_steps ? z0 : 0.0, N0 + 2 * i + 1 < n_steps ? z1 : 0.0);
+              if (i == 0 || N0 + 2 * i < n_steps) {
+                const double z0 = out(N0 + 2 * i);
+                const double z1 = N0 + 2 * i + 1 < n_steps ? out(N0 + 2 * i + 1) : 0.0;
+                put_pair_const(ic, z0, z1);
+              } else {
+#pragma unroll
+                for (int t = 0; t < kDig; ++t) w[t][i] = 0u;
+              }
             };
             two(std::integral_constant<int, 0>{});
             two(std::integral_constant<int, 1>{});
