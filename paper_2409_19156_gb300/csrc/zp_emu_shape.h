@@ -20,6 +20,25 @@ constexpr int kSliceOpts = 4;
 constexpr int kSliceBeta[kSliceOpts] = {7, 6, 5, 4};
 constexpr int kSliceS[kSliceOpts] = {8, 9, 11, 14};
 
+#if defined(__CUDACC__)
+#define ZP_SLICE_HD __host__ __device__
+#else
+#define ZP_SLICE_HD
+#endif
+
+// The balanced base-2^beta digits of a fixed-point X (s digits, the s - 1 low ones in
+// [-2^(beta-1), 2^(beta-1)), the top one what remains) read off the biased word
+// Y = X + slice_bias(beta, s): low digit p (least significant first) is Y's beta-bit field p minus
+// 2^(beta-1), the top digit Y >> (beta (s - 1)).
+ZP_SLICE_HD constexpr long long slice_bias(int beta, int s) {
+  long long b = 0;
+  for (int p = 0; p < s - 1; ++p) b += (1ll << (beta - 1)) << (beta * p);
+  return b;
+}
+ZP_SLICE_HD constexpr int slice_digit(long long y, int beta, int s, int p) {
+  return p == s - 1 ? (int)(y >> (beta * p)) : (int)((y >> (beta * p)) & ((1ll << beta) - 1)) - (1 << (beta - 1));
+}
+
 // Largest number of K chunks (kSliceBK values) one batch may hold with slice option o: with
 // |a_1| <= 2^beta and |a_t| <= 2^(beta-1) for t >= 2 (each later digit cuts a remainder of at
 // most 1/2), diagonal d sums K * (2 * 2^beta * 2^(beta-1) + (d-3) * 2^(2 beta - 2)) at most,

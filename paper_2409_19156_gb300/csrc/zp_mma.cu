@@ -406,7 +406,7 @@ struct GemmArgs {
   int64_t t_batch_stride = 0;
   // KIND_SLICE with paired diagonals (npairs unused): the tile is 128 points x 128 sets and
   // covers the diagonals dp and dp + 1 (0-based; dp = -1 leaves only diagonal 0).  B holds per
-  // (set tile, K chunk) all s_slices slices of 128 rows back to back (kSliceBlock bytes each),
+  // (set tile, K chunk) all s_slices slices of 128 rows back to back (128 rows x 128 bytes each),
   // so that one N = 256 MMA of A slice t against slices (dp - t, dp + 1 - t) adds into both
   // diagonals' accumulators (TMEM columns 0-127 and 128-255); A slice dp + 1 meets only B slice
   // 0 (an N = 128 MMA into columns 128-255).  The epilogue stores T_dp 2^beta + T_(dp+1) as one
@@ -417,10 +417,6 @@ struct GemmArgs {
   int s_slices = 0;
   int nb = 128;  // paired: sets per tile = rows of a slice block (a multiple of 16; below 128 single CTAs only)
 };
-
-// Bytes of one 128-row slice block of the paired B layout (a narrow set tile of nb rows takes
-// nb * 128 bytes).
-constexpr uint32_t kSliceBlock = BM * Cfg<KIND_SLICE>::ROW;
 
 // Threads of the GEMM kernel: producer, MMA and 4 epilogue warps, plus, for a CTA pair, one
 // warp whose thread passes barrier signals between the pair's two CTAs.
@@ -1092,34 +1088,46 @@ zp_status scale_rows(Operand X, int64_t rows, int64_t K, unsigned long long* bit
 }
 
 // Cuts 8 fixed-point values X[0..7] (beta * s fraction bits) into s balanced base-2^beta digits
-// and writes slice t's 16-byte unit of bf16 integers at `dst + t * slice_stride`.  Digits are
-// taken from the least significant end: a = X mod 2^beta moved into [-2^(beta-1), 2^(beta-1)),
-// X = (X - a) / 2^beta (exact); the most significant digit is what remains (|a_1| <= 2^beta).
-__device__ __forceinline__ void cut_slices(long long (&X)[8], int beta, int s, uint8_t* dst, int64_t slice_stride) {
-  const long long mask = (1ll << beta) - 1, half = 1ll << (beta - 1), full = 1ll << beta;
-  for (int t = s - 1; t >= 0; --t) {
+// and writes slice t's 16-byte unit of bf16 integers at `dst + t * slice_stride` (slice 0 the
+// most significant).  The digits below the top one lie in [-2^(beta-1), 2^(beta-1)); they are
+// the beta-bit fields f of the biased word Y = X + slice_bias(beta, s), minus 2^(beta-1), and the
+// top digit is what is left of Y above them (|a_1| <= 2^beta): the same digits as cutting
+// a = X mod 2^beta into that range and carrying.  A field (f < 128 for
+// beta <= 7) under the bfloat16 pattern 0x4300 is exactly 128 + f, so one packed subtraction of
+// 128 + 2^(beta-1) turns the fields of two values into their two digits (exact); the top digit
+// goes through float32 (exact below 2^22).
+__device__ __forceinline__ void cut_slices(const long long (&X)[8], int beta, int s, long long bias, uint8_t* dst,
+                                           int64_t slice_stride) {
+  const uint32_t mask = (1u << beta) - 1u;
+  const uint32_t mask2 = mask | (mask << 16);
+  const uint16_t sub_bits = (uint16_t)(0x4300u | (1u << (beta - 1)));  // bfloat16 128 + 2^(beta-1)
+  const __nv_bfloat162 sub(__nv_bfloat16_raw{sub_bits}, __nv_bfloat16_raw{sub_bits});
+  long long Y[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) Y[q] = X[q] + bias;
+  for (int p = 0; p < s - 1; ++p) {  // field p: slice s - 1 - p
     uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uint32_t h[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        long long& x = X[2 * i + k];
-        int a;
-        if (t > 0) {
-          const long long low = x & mask;
-          const long long d = low >= half ? low - full : low;
-          x = (x - d) >> beta;
-          a = (int)d;
-        } else {
-          a = (int)x;
-        }
-        h[k] = __float_as_uint(__int2float_rn(a)) >> 16;  // |a| <= 128: exact in bf16
-      }
-      w[i] = h[0] | (h[1] << 16);
+      const uint32_t f = (((uint32_t)Y[2 * i] & 0xffffu) | ((uint32_t)Y[2 * i + 1] << 16)) & mask2;
+      __nv_bfloat162 v;
+      const uint32_t pat = f | 0x43004300u;
+      v = *reinterpret_cast<const __nv_bfloat162*>(&pat);
+      v = __hsub2(v, sub);
+      w[i] = *reinterpret_cast<const uint32_t*>(&v);
+      Y[2 * i] >>= beta;
+      Y[2 * i + 1] >>= beta;
     }
-    *reinterpret_cast<uint4*>(dst + (size_t)t * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(dst + (size_t)(s - 1 - p) * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
   }
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t h0 = __float_as_uint(__int_as_float(0x4B400000 + (int)Y[2 * i]) - 12582912.0f);
+    const uint32_t h1 = __float_as_uint(__int_as_float(0x4B400000 + (int)Y[2 * i + 1]) - 12582912.0f);
+    w[i] = __byte_perm(h0, h1, 0x7632);
+  }
+  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Slices of an operand's rows in the tensor core's K-major swizzled chunks: tile
@@ -1137,6 +1145,7 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
   const int64_t rows_pad = tiles * ROWS;
   const int64_t groups = (int64_t)KC * (BK / 8);
   const int64_t total = rows_pad * groups;
+  const long long bias = slice_bias(sp.beta, sp.s);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = KFAST ? i / groups : i % rows_pad;
     const int64_t k0 = (KFAST ? i % groups : i / rows_pad) * 8;
@@ -1152,7 +1161,7 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     const int kc = (int)(k0 / BK);
     constexpr uint32_t ROW = Cfg<KIND_SLICE>::ROW;
     uint8_t* d = dst + ((size_t)tile * KC + kc) * chunk_stride + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
-    cut_slices(x, sp.beta, sp.s, d, slice_stride);
+    cut_slices(x, sp.beta, sp.s, bias, d, slice_stride);
   }
 }
 

@@ -97,3 +97,26 @@ def test_balanced_digit_bounds(beta, s):
         assert all(-half <= d < half for d in digits[:-1])
         assert abs(digits[-1]) <= full
         assert sum(d * 2 ** (beta * i) for i, d in enumerate(digits)) == round(x * 2 ** (beta * s))
+
+
+@pytest.mark.parametrize("beta,s", [(7, 8), (6, 9), (5, 11), (4, 14)])
+def test_biased_field_digits_match_the_carry_cut(driver, beta, s):
+    """The slice kernels read the digits off the biased word X + slice_bias(beta, s) (fields
+    minus 2^(beta-1), the top digit the rest); they must be exactly the digits of the carry cut
+    above, for values of either sign, at the fixed-point limits and at zero."""
+    rng = random.Random(beta * 1000 + s)
+    half, full, mask = 1 << (beta - 1), 1 << beta, (1 << beta) - 1
+    lim = 1 << (beta * s)
+    xs = [0, 1, -1, half, -half, half - 1, -half - 1, lim - 1, -(lim - 1), lim, -lim]
+    xs += [rng.randrange(-lim, lim + 1) for _ in range(2000)]
+    text = "".join(f"d {beta} {s} {x}\n" for x in xs)
+    out = subprocess.run([driver], input=text, capture_output=True, text=True, check=True).stdout.split("\n")
+    for x, line in zip(xs, out):
+        X, want = x, []
+        for _t in range(s - 1):
+            low = X & mask
+            d = low - full if low >= half else low
+            want.append(d)
+            X = (X - d) >> beta
+        want.append(X)
+        assert [int(v) for v in line.split()] == want[::-1], x
