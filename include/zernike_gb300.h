@@ -356,7 +356,7 @@ ZP_API zp_status zp_batch_adjoint(zp_batch* batch, void* stream);
 ZP_API zp_status zp_batch_adjoint_prec(zp_batch* batch, zp_precision prec, void* stream);
 /* Launch configuration: point-tile size (threads per CTA of the point kernel, multiple of 32),
  * persistent CTAs per SM, points per thread (1, 2, 4) and threads per CTA of the grad_coeffs
- * kernel.  cfg[4] receives the current values. */
+ * kernel (a new batch: 128, 8, 2, 128).  cfg[4] receives the current values. */
 ZP_API zp_status zp_batch_set_config(zp_batch* batch, int32_t tile_points, int32_t ctas_per_sm,
                                      int32_t col_ppt, int32_t col_threads);
 ZP_API zp_status zp_batch_get_config(const zp_batch* batch, int32_t* cfg);

@@ -346,7 +346,7 @@ class Batch:
         _lib.call("zp_batch_adjoint_prec", self.handle, code,
                   _stream(torch.device("cuda", torch.cuda.current_device())))
 
-    def set_config(self, tile_points=128, ctas_per_sm=4, col_ppt=2, col_threads=128):
+    def set_config(self, tile_points=128, ctas_per_sm=8, col_ppt=2, col_threads=128):
         _lib.call("zp_batch_set_config", self.handle, tile_points, ctas_per_sm, col_ppt, col_threads)
 
     def config(self) -> tuple:
