@@ -81,6 +81,8 @@ def parse_args():
     ap.add_argument("--fused-points", type=int, default=1_000_000)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched forward/adjoint on a reduced batch (profiling captures)")
+    ap.add_argument("--batched-adjoint-only", action="store_true",
+                    help="run only the batched float64-accurate adjoint (profiling captures)")
     ap.add_argument("--batched-instances", type=int, default=512)
     ap.add_argument("--batched-point-scale", type=float, default=1.0)
     ap.add_argument("--points", type=int, default=100_000,
@@ -1001,6 +1003,30 @@ def measure_batched(dev, steps: int = 3, n_instances: int = 512, point_scale: fl
     return out
 
 
+def measure_batched_adjoint(dev, steps: int = 2, n_instances: int = 512) -> dict:
+    """batched_512's float64-accurate adjoint alone (one warm-up call, then `steps` timed calls):
+    the two fused derivative-series passes and the per-instance grad_C."""
+    import torch
+
+    import paper_2409_19156_gb300 as zp
+    from paper_2409_19156_gb300 import inputs
+
+    cfg = inputs.WORKLOADS["batched_512"]
+    raw = inputs.batched_instances(n_instances, cfg["n_sets"], cfg["seed"])
+    S = cfg["n_sets"]
+    gen = torch.Generator(dev).manual_seed(5)
+    inst = [{"n": x.n, "m": x.m, "r": torch.as_tensor(x.r, device=dev), "theta": torch.as_tensor(x.theta, device=dev),
+             "coeffs": torch.as_tensor(x.coeffs, device=dev),
+             "grad_out": torch.randn((len(x.r), S), dtype=torch.float64, device=dev, generator=gen)} for x in raw]
+    b = zp.Batch(inst, S)
+    stream = torch.cuda.current_stream(dev)
+    b.adjoint("fp64emu")
+    t = _events_ms(stream, lambda: b.adjoint("fp64emu"), steps)
+    b.close()
+    return {"workload": "batched_512", "instances": len(raw), "points": sum(len(x.r) for x in raw), "sets": S,
+            "fp64emu_adjoint_ms": t}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args) -> None:
     """The oracle as it stands on the host cores: each step is a bounded sample of the same
@@ -1033,6 +1059,14 @@ def run_reference(args) -> None:
 
 def main():
     args = parse_args()
+    if args.batched_adjoint_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched_adjoint_only": measure_batched_adjoint(torch.device("cuda", 0), steps=args.steps,
+                                                                          n_instances=args.batched_instances)}),
+              flush=True)
+        return
     if args.batched_only:
         import torch
 

@@ -513,8 +513,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         const int4 fc = d.fcols[c];
         const int kind = fc.x & 255;
         const double fa = (fc.x >> 8) & 1 ? fsin : fcos, fb = (fc.x >> 9) & 1 ? fsin : fcos;
-        double S = 0.0, T = -pm;
-        // The derivative lane (VK_DRHO): Q'_{-1} = 0, Q'_{-2} = -m rho^(m-1).
+        // VK_DRHO walks the value lane times 2 rho (seed -2 rho^(m+1)): with u = rho^2,
+        // dQ_N/drho = 2 rho dQ_N/du and dQ_N/du = A_N Q_{N-1} + g_N dQ_{N-1}/du - dQ_{N-2}/du, so
+        // the derivative lane Q'_N = g_N Q'_{N-1} + A_N (2 rho Q_{N-1}) - Q'_{N-2} takes A_N from
+        // the table with no product by rho per step.  Its seeds: Q'_{-1} = 0, Q'_{-2} = -m rho^(m-1).
+        double S = 0.0, T = VK == VK_DRHO ? -pm * (2.0 * rho) : -pm;
         double Sd = 0.0, Td = VK == VK_DRHO ? -(double)m * pm1 : 0.0;
         // The recursion coefficient g_N = A_N rho^2 - B_N of step N < n_steps.
         auto coef = [&](int N, double& A) -> double {
@@ -523,14 +526,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
           const double B = N >= 2 ? rw[1] : (N == 1 ? h[8] : 0.0);
           return fma(A, u, -B);
         };
-        // One recursion step N < n_steps: Q_N, or Q'_N for VK_DRHO.
+        // One recursion step N < n_steps: Q_N, or Q'_N for VK_DRHO (S, T then hold 2 rho Q).
         auto step = [&](int N) -> double {
           double A;
           const double g = coef(N, A);
           if constexpr (VK == VK_DRHO) {
-            const double* rw = h + (size_t)(kHeaderRows + N) * kRow;
-            const double A2 = N >= 2 ? rw[2] : (N == 1 ? 2.0 * h[4] : 0.0);  // 2 A_N
-            const double qd = fma(g, Sd, fma(A2 * rho, S, -Td));
+            const double qd = fma(g, Sd, fma(A, S, -Td));
             Td = Sd;
             Sd = qd;
           }

@@ -1033,12 +1033,25 @@ __global__ void row_absmax_kernel(Operand X, int64_t rows, int64_t K, int64_t k_
   const int64_t k0 = (int64_t)blockIdx.y * k_per_block;
   const int64_t k1 = k0 + k_per_block < K ? k0 + k_per_block : K;
   unsigned long long mx = 0;
+  // |x| as bits; four loads in flight per thread before their maxima are taken.
+  auto mag = [&](int64_t row, int64_t k) {
+    return (unsigned long long)__double_as_longlong(X.x[row * X.sr + k * X.sk]) & 0x7fffffffffffffffull;
+  };
+  auto max4 = [](unsigned long long a, unsigned long long b, unsigned long long c, unsigned long long d) {
+    a = a > b ? a : b;
+    c = c > d ? c : d;
+    return a > c ? a : c;
+  };
   if constexpr (ROWS_FAST) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= rows) return;
-    for (int64_t k = k0; k < k1; ++k) {
-      const unsigned long long v =
-          (unsigned long long)__double_as_longlong(X.x[row * X.sr + k * X.sk]) & 0x7fffffffffffffffull;
+    int64_t k = k0;
+    for (; k + 3 < k1; k += 4) {
+      const unsigned long long v = max4(mag(row, k), mag(row, k + 1), mag(row, k + 2), mag(row, k + 3));
+      mx = v > mx ? v : mx;
+    }
+    for (; k < k1; ++k) {
+      const unsigned long long v = mag(row, k);
       mx = v > mx ? v : mx;
     }
     if (mx) atomicMax(bits + row, mx);
@@ -1046,9 +1059,13 @@ __global__ void row_absmax_kernel(Operand X, int64_t rows, int64_t K, int64_t k_
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (row >= rows) return;
-    for (int64_t k = k0 + lane; k < k1; k += 32) {
-      const unsigned long long v =
-          (unsigned long long)__double_as_longlong(X.x[row * X.sr + k * X.sk]) & 0x7fffffffffffffffull;
+    int64_t k = k0 + lane;
+    for (; k + 96 < k1; k += 128) {
+      const unsigned long long v = max4(mag(row, k), mag(row, k + 32), mag(row, k + 64), mag(row, k + 96));
+      mx = v > mx ? v : mx;
+    }
+    for (; k < k1; k += 32) {
+      const unsigned long long v = mag(row, k);
       mx = v > mx ? v : mx;
     }
     for (int off = 16; off > 0; off >>= 1) {
