@@ -785,6 +785,220 @@ __global__ void __launch_bounds__(gemm_threads<CG>(), 1) split_gemm_kernel(GemmA
   }
 }
 
+// ------------------------------------------------------------ stacked-diagonal slice products
+// For a narrow B (at most 16 sets, the adjoints' grad_C = Z G): one launch forms the sums of
+// every diagonal at once, so that A's slices cross HBM once instead of once per plane launch.
+// Per 32-value K chunk a stage holds A's s slices (128 rows x 64 bytes each, 64-byte swizzle)
+// and B's chunk as 2s - 1 blocks of 16 rows: s - 1 zero blocks, then slices 0 .. s-1.  The MMA
+// of A slice t against the s blocks that start at block s - 1 - t (N = 16 s) adds a_t b_(j-t)
+// into column block j for every j >= t (zeros below), so column block j accumulates diagonal
+// j (0-based) and one MMA per A slice and K step covers every slice pair of the kept diagonals.
+constexpr int kStkNB = 16;                          // sets per tile (rows of a B block)
+constexpr uint32_t kStkRow = 64;                    // bytes per operand row
+constexpr int kStkBK = (int)kStkRow / 2;            // K values per chunk
+constexpr int kStkMaxS = 11;                        // slices (two stages must fit)
+constexpr uint32_t kStkASlice = BM * kStkRow;       // 8 KB
+constexpr uint32_t kStkBBlock = kStkNB * kStkRow;   // 1 KB
+constexpr int kStkStages = 2;
+__host__ __device__ constexpr uint32_t stk_stage_bytes(int s) {
+  return (uint32_t)s * kStkASlice + (uint32_t)(2 * s - 1) * kStkBBlock;
+}
+constexpr uint32_t kStkSmem = kStkStages * stk_stage_bytes(kStkMaxS) + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(kStkSmem <= 232448, "shared memory per CTA");
+static_assert(kStkNB * kStkMaxS <= 256, "an accumulator fits half of the tensor memory");
+
+struct StackedArgs {
+  const uint8_t* A;  // [m_tiles][KC][s][kStkASlice]
+  const uint8_t* B;  // [KC][2s - 1][kStkBBlock]
+  int* T;            // diagonal d of K batch kb at T + kb * batch_stride + d * diag_stride, [rows][N]
+  int64_t rows, N;
+  int64_t m_tiles;
+  int KC, s, k_batches, kc_per_batch;
+  int64_t diag_stride, batch_stride;
+};
+
+// Persistent: warp 0 loads the stages (one thread, plain bulk copies), warp 1 issues the MMAs,
+// warps 2-5 store the diagonal sums of finished tiles as int32 (every sum is an integer below
+// 2^24, exact in float32).  Tile t = (K batch t / m_tiles, point tile t % m_tiles).
+__global__ void __launch_bounds__(192, 1) stacked_slice_gemm_kernel(StackedArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const int s = a.s;
+  const uint32_t a_bytes = (uint32_t)s * kStkASlice, b_bytes = (uint32_t)(2 * s - 1) * kStkBBlock;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStkStages * stk_stage_bytes(kStkMaxS));
+  uint64_t* empty = full + kStkStages;
+  uint64_t* tmem_full = empty + kStkStages;
+  uint64_t* tmem_empty = tmem_full + 2;
+  uint64_t* drain = tmem_empty + 2;
+  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_slot + 1);
+  volatile int* never = abort_flag + 1;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStkStages; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&tmem_full[i], 1);
+      ptx::mbar_init(&tmem_empty[i], 4);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    *never = 0;
+    ptx::fence_barrier_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_base_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_slot;
+
+  const int64_t total = a.m_tiles * a.k_batches;
+  auto k_range = [&](int64_t t, int& kc0, int& nkc) {
+    kc0 = (int)(t / a.m_tiles) * a.kc_per_batch;
+    nkc = (kc0 + a.kc_per_batch < a.KC ? kc0 + a.kc_per_batch : a.KC) - kc0;
+  };
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicOr(&g_split_error, 1u);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        const int64_t mt = t % a.m_tiles;
+        int kc0, nkc;
+        k_range(t, kc0, nkc);
+        bool ok = true;
+        for (int kc = kc0; kc < kc0 + nkc; ++kc) {
+          if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          uint8_t* sA = smem + stage * stage_bytes;
+          ptx::mbar_arrive_expect_tx(&full[stage], stage_bytes);
+          ptx::bulk_g2s(sA, a.A + ((size_t)mt * a.KC + kc) * a_bytes, a_bytes, &full[stage]);
+          ptx::bulk_g2s(sA + a_bytes, a.B + (size_t)kc * b_bytes, b_bytes, &full[stage]);
+          if (++stage == kStkStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16_f32(BM, kStkNB * s);
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t local = 0;
+      for (int64_t t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++local) {
+        const uint32_t acc = (uint32_t)(local & 1);
+        if (!ptx::mbar_wait(&tmem_empty[acc], (uint32_t)((local >> 1) & 1) ^ 1u, abort_flag)) {
+          fail();
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * 256u;
+        int kc0, nkc;
+        k_range(t, kc0, nkc);
+        bool ok = true;
+        for (int kk = 0; kk < nkc; ++kk) {
+          if (!ptx::mbar_wait(&full[stage], phase, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sA = ptx::smem_u32(smem + stage * stage_bytes);
+          const uint32_t sB = sA + a_bytes;
+          for (int ts = 0; ts < s; ++ts) {
+#pragma unroll
+            for (int ks = 0; ks < (int)kStkRow / 32; ++ks) {
+              const uint32_t first = (kk == 0 && ts == 0 && ks == 0) ? 0u : 1u;
+              ptx::mma_bf16(d_tmem, ptx::sw_kmajor_desc<kStkRow>(sA + (uint32_t)ts * kStkASlice + ks * 32u),
+                            ptx::sw_kmajor_desc<kStkRow>(sB + (uint32_t)(s - 1 - ts) * kStkBBlock + ks * 32u), idesc,
+                            first);
+            }
+          }
+          ptx::mma_commit(&empty[stage]);
+          if (++stage == kStkStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&tmem_full[acc]);
+      }
+      // Every MMA issued here completes before the CTA leaves.
+      ptx::mma_commit(drain);
+      if (!ptx::mbar_wait(drain, 0u, never)) atomicOr(&g_split_error, 1u);
+    }
+  } else {
+    // Epilogue: warp & 3 selects the TMEM lane quadrant it may access.
+    const uint32_t q = (uint32_t)(warp & 3);
+    const uint32_t row = q * 32 + lane;
+    const bool vec = a.N == kStkNB;
+    int64_t local = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+      const uint32_t acc = (uint32_t)(local & 1);
+      bool ok = true;
+      if (lane == 0) ok = ptx::mbar_wait(&tmem_full[acc], (uint32_t)((local >> 1) & 1), abort_flag);
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+        fail();
+        break;
+      }
+      ptx::tc_fence_after();
+      const int64_t p = (t % a.m_tiles) * BM + row;
+      const bool store = p < a.rows;
+      int* trow = a.T + (t / a.m_tiles) * a.batch_stride + p * a.N;
+      const uint32_t tacc = tmem_base + ((q * 32u) << 16) + acc * 256u;
+#pragma unroll 1
+      for (int d = 0; d < s; ++d) {
+        uint32_t v[8], w[8];
+        ptx::tmem_ld_32x32b_x8(tacc + (uint32_t)(d * kStkNB), v);
+        ptx::tmem_ld_wait(v);
+        ptx::tmem_ld_32x32b_x8(tacc + (uint32_t)(d * kStkNB + 8), w);
+        ptx::tmem_ld_wait(w);
+        if (store) {
+          int x[16];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            x[i] = __float2int_rn(__uint_as_float(v[i]));
+            x[8 + i] = __float2int_rn(__uint_as_float(w[i]));
+          }
+          int* dst = trow + d * a.diag_stride;
+          if (vec) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              __stcs(reinterpret_cast<int4*>(dst) + i, make_int4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]));
+          } else {
+            for (int i = 0; i < (int)a.N; ++i) dst[i] = x[i];
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&tmem_empty[acc]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 512);
+  }
+}
+
 // Optional per-phase timing: CUDA events recorded on the launching stream around every
 // launch, summed per phase after the stream is synchronised.
 struct PhaseTimer {
@@ -880,6 +1094,29 @@ zp_status gemm_shape(GemmShape* g) {
 inline bool pairs_enabled() {
   const char* v = std::getenv("ZP_GEMM_CTA_PAIRS");
   return !(v && v[0] == '0');
+}
+
+// The stacked-diagonal slice products for narrow B (ZP_EMU_STACKED=0 turns them off, for
+// comparison with the paired plane launches).
+inline bool stacked_enabled() {
+  const char* v = std::getenv("ZP_EMU_STACKED");
+  return !(v && v[0] == '0');
+}
+
+zp_status launch_stacked(const StackedArgs& sa, int sms, cudaStream_t stream) {
+  static DeviceMemo<int> attr;
+  int set = 0;
+  ZP_TRY(attr.get(&set, [](int* x) -> zp_status {
+    const cudaError_t e =
+        cudaFuncSetAttribute(stacked_slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStkSmem);
+    *x = 1;
+    return e == cudaSuccess ? ZP_OK : cuda_error(e, "cudaFuncSetAttribute");
+  }));
+  const int64_t total = sa.m_tiles * sa.k_batches;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(total, sms));
+  stacked_slice_gemm_kernel<<<grid, 192, kStkSmem, stream>>>(sa);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ZP_OK : cuda_error(e, "stacked_slice_gemm_kernel launch");
 }
 
 // Persistent launch over `tiles` point tiles x NT set tiles (x K batches): CTA pairs over
@@ -1147,17 +1384,17 @@ __device__ __forceinline__ void cut_slices(const long long (&X)[8], int beta, in
   *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Slices of an operand's rows in the tensor core's K-major swizzled chunks: tile
-// (row / ROWS) x K chunk kc at (tile * KC + kc) * chunk_stride bytes (ROWS * 128 for one slice
-// per chunk, s times that when the slices of a chunk lie back to back), slice t a further
-// t * slice_stride.  Thread = (row, group of 8 consecutive K): rows fastest when an operand's
+// Slices of an operand's rows in the tensor core's K-major swizzled chunks (rows of ROW bytes,
+// ROW / 2 K values): tile (row / ROWS) x K chunk kc at (tile * KC + kc) * chunk_stride bytes
+// (ROWS * ROW for one slice per chunk, s times that when the slices of a chunk lie back to
+// back), slice t a further t * slice_stride.  Thread = (row, group of 8 consecutive K): rows fastest when an operand's
 // rows are contiguous (KFAST = false), K groups fastest when its K is (coalesced loads either
 // way).  Rows past `rows` and K past `K` are zero.
-template <int ROWS_T, bool KFAST>
+template <int ROWS_T, bool KFAST, uint32_t ROW = Cfg<KIND_SLICE>::ROW>
 __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_t K, int KC,
                                   const int* __restrict__ expo, SliceParams sp, uint8_t* dst, int64_t slice_stride,
                                   int64_t chunk_stride, int rows_per_tile = 0) {
-  constexpr int BK = Cfg<KIND_SLICE>::BK;
+  constexpr int BK = (int)ROW / 2;
   const int ROWS = ROWS_T > 0 ? ROWS_T : rows_per_tile;  // ROWS_T = 0: a multiple of 16 given at launch
   const int64_t rows_pad = tiles * ROWS;
   const int64_t groups = (int64_t)KC * (BK / 8);
@@ -1176,7 +1413,6 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
     const int64_t tile = row / ROWS;
     const uint32_t r = (uint32_t)(row % ROWS);
     const int kc = (int)(k0 / BK);
-    constexpr uint32_t ROW = Cfg<KIND_SLICE>::ROW;
     uint8_t* d = dst + ((size_t)tile * KC + kc) * chunk_stride + ptx::sw_offset_b16<ROW>(r, (uint32_t)(k0 % BK));
     cut_slices(x, sp.beta, sp.s, bias, d, slice_stride);
   }
@@ -1392,6 +1628,11 @@ struct EmuGemm {
   ScratchBuffer accbuf;  // int64 batch sums (runs with many K batches)
   ScratchBuffer bsl, cexp, asl, rexp, tbuf, maxbits;
   int64_t a_stride = 0, b_stride = 0;
+  // Stacked-diagonal slice products (at most 16 sets, at most kStkMaxS slices): one launch per
+  // slab over 32-value K chunks (KCs of them, kcb_s per K batch, kb_s batches); s planes.
+  bool stacked = false;
+  int KCs = 0, kcb_s = 0, kb_s = 0;
+  int planes = 0;  // planes of sums written per K batch
 
   // Chooses the shape for M rows, slices B (B(n, k), n < N) and sizes the slab scratch.
   zp_status prepare(int64_t M, int64_t N_, int64_t K_, Operand B, cudaStream_t stream) {
@@ -1423,23 +1664,48 @@ struct EmuGemm {
       nb = N >= BN / 2 ? BN / 2 : (int)((N + 15) / 16 * 16);
       NT = (N + nb - 1) / nb;
     }
+    planes = sh.planes;
+    stacked = N <= kStkNB && sh.sp.s <= kStkMaxS && stacked_enabled();
+    if (stacked) {
+      NT = 1;
+      KCs = (int)((K + kStkBK - 1) / kStkBK);
+      kcb_s = 2 * sh.kc_per_batch;  // the same K values per batch as the 64-value chunks
+      kb_s = (KCs + kcb_s - 1) / kcb_s;
+      planes = sh.sp.s;
+    }
     // Slab: int32 sums (k_batches x planes x rows x N x 4 B) within about 4 GB.
-    const size_t t_tile = (size_t)sh.k_batches * sh.planes * BM * N * sizeof(int);
+    const size_t t_tile = (size_t)sh.k_batches * planes * BM * N * sizeof(int);
     slab_tiles = std::max<int64_t>(1, std::min<int64_t>(MT, (int64_t)((4ull << 30) / t_tile)));
     a_stride = slab_tiles * sh.KC * (int64_t)C::A_CHUNK;
     b_stride = NT * sh.KC * (int64_t)C::B_CHUNK;
-    // A paired B holds NT x KC x s blocks of nb rows.
-    ZP_TRY(bsl.alloc(sh.paired ? (size_t)NT * sh.KC * sh.sp.s * nb * C::ROW : (size_t)sh.sp.s * b_stride, stream));
+    // A paired B holds NT x KC x s blocks of nb rows; a stacked B KCs x (2s - 1) blocks of 16.
+    const size_t b_stk = (size_t)KCs * (2 * sh.sp.s - 1) * kStkBBlock;
+    ZP_TRY(bsl.alloc(stacked      ? b_stk
+                     : sh.paired ? (size_t)NT * sh.KC * sh.sp.s * nb * C::ROW
+                                 : (size_t)sh.sp.s * b_stride,
+                     stream));
     ZP_TRY(cexp.alloc((size_t)N * sizeof(int), stream));
-    ZP_TRY(asl.alloc((size_t)sh.sp.s * a_stride, stream));
+    ZP_TRY(asl.alloc(stacked ? (size_t)slab_tiles * KCs * sh.sp.s * kStkASlice : (size_t)sh.sp.s * a_stride, stream));
     ZP_TRY(rexp.alloc((size_t)slab_tiles * BM * sizeof(int), stream));
     ZP_TRY(tbuf.alloc((size_t)slab_tiles * t_tile, stream));
     if (sh.k_batches >= kPreReduceBatches)
-      ZP_TRY(accbuf.alloc((size_t)sh.planes * slab_tiles * BM * N * sizeof(long long), stream));
+      ZP_TRY(accbuf.alloc((size_t)planes * slab_tiles * BM * N * sizeof(long long), stream));
     ZP_TRY(maxbits.alloc((size_t)std::max<int64_t>(N, slab_tiles * BM) * sizeof(unsigned long long), stream));
     ZP_TRY(scale_rows(B, N, K, (unsigned long long*)maxbits.ptr, (int*)cexp.ptr, stream));
     const bool kfast = B.sk == 1 && B.sr != 1;
-    if (sh.paired) {
+    if (stacked) {
+      // Per 32-value K chunk: s - 1 zero blocks, then slices 0 .. s-1 of 16 rows.
+      cudaError_t e = cudaMemsetAsync(bsl.ptr, 0, b_stk, stream);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+      const int64_t cs = (int64_t)(2 * sh.sp.s - 1) * kStkBBlock;
+      uint8_t* b0 = (uint8_t*)bsl.ptr + (size_t)(sh.sp.s - 1) * kStkBBlock;
+      if (kfast)
+        slice_rows_kernel<kStkNB, true, kStkRow><<<1024, 256, 0, stream>>>(B, N, 1, K, KCs, (const int*)cexp.ptr,
+                                                                           sh.sp, b0, kStkBBlock, cs);
+      else
+        slice_rows_kernel<kStkNB, false, kStkRow><<<1024, 256, 0, stream>>>(B, N, 1, K, KCs, (const int*)cexp.ptr,
+                                                                            sh.sp, b0, kStkBBlock, cs);
+    } else if (sh.paired) {
       // Per (set tile, K chunk): slices 0..s-1 of nb rows back to back.
       const int64_t blk = (int64_t)nb * C::ROW, cs = (int64_t)sh.sp.s * blk;
       if (kfast)
@@ -1464,6 +1730,7 @@ struct EmuGemm {
     using C = Cfg<KIND_SLICE>;
     const int64_t tiles = (rows + BM - 1) / BM;
     ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
+    if (stacked) return run_slab_stacked(rows, tiles, A, Cout, ldc, stream);
     if (A.sk == 1 && A.sr != 1)
       slice_rows_kernel<BM, true><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
                                                            (uint8_t*)asl.ptr, a_stride, C::A_CHUNK);
@@ -1475,7 +1742,6 @@ struct EmuGemm {
     const int64_t trows = slab_tiles * BM;
     const int64_t diag_stride = trows * N, batch_stride = (int64_t)sh.planes * diag_stride;
     const int hsh = sh.paired ? 2 * sh.sp.beta : sh.sp.beta;
-    const int e_base = -sh.sp.beta * (sh.sp.s + 1);
     for (int q = 0; q < sh.planes; ++q) {
       GemmArgs ga{(const uint8_t*)asl.ptr, (const uint8_t*)bsl.ptr,
                   (float*)tbuf.ptr + (size_t)q * diag_stride, rows, N, 0, tiles, (int)NT, sh.KC};
@@ -1496,19 +1762,49 @@ struct EmuGemm {
       ga.t_batch_stride = batch_stride;
       ZP_TRY(launch_gemm<KIND_SLICE>(ga, tiles, (int)NT, gs, stream));
     }
-    RecombineArgs ra{(const int*)tbuf.ptr, nullptr, diag_stride, batch_stride, sh.k_batches, sh.planes,
-                     sh.plane_split, hsh, e_base,
+    return recombine(rows, Cout, ldc, sh.k_batches, sh.planes, sh.plane_split, hsh, stream);
+  }
+
+  // The stacked-diagonal form of run_slab: A's slices in 64-byte rows, all s diagonals of a tile
+  // by one launch, s planes of sums per K batch.
+  zp_status run_slab_stacked(int64_t rows, int64_t tiles, Operand A, double* Cout, int64_t ldc, cudaStream_t stream) {
+    const int sl = sh.sp.s;
+    const int64_t cs = (int64_t)sl * kStkASlice;
+    if (A.sk == 1 && A.sr != 1)
+      slice_rows_kernel<BM, true, kStkRow><<<2048, 256, 0, stream>>>(A, rows, tiles, K, KCs, (const int*)rexp.ptr,
+                                                                     sh.sp, (uint8_t*)asl.ptr, kStkASlice, cs);
+    else
+      slice_rows_kernel<BM, false, kStkRow><<<2048, 256, 0, stream>>>(A, rows, tiles, K, KCs, (const int*)rexp.ptr,
+                                                                      sh.sp, (uint8_t*)asl.ptr, kStkASlice, cs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "A slicing launch");
+    const int64_t diag_stride = slab_tiles * BM * N;
+    StackedArgs sa{(const uint8_t*)asl.ptr, (const uint8_t*)bsl.ptr, (int*)tbuf.ptr, rows, N, tiles,
+                   KCs, sl, kb_s, kcb_s, diag_stride, (int64_t)sl * diag_stride};
+    ZP_TRY(launch_stacked(sa, sms, stream));
+    return recombine(rows, Cout, ldc, kb_s, sl, sh.split, sh.sp.beta, stream);
+  }
+
+  // C rows [0, rows) from the int32 sums in tbuf: k_batches batches of ndiag planes (consecutive
+  // planes hsh bits apart), the first `split` planes in the first Horner chain.
+  zp_status recombine(int64_t rows, double* Cout, int64_t ldc, int k_batches, int ndiag, int split, int hsh,
+                      cudaStream_t stream) {
+    cudaError_t e = cudaSuccess;
+    const int64_t diag_stride = slab_tiles * BM * N, batch_stride = (int64_t)ndiag * diag_stride;
+    const int e_base = -sh.sp.beta * (sh.sp.s + 1);
+    RecombineArgs ra{(const int*)tbuf.ptr, nullptr, diag_stride, batch_stride, k_batches, ndiag,
+                     split, hsh, e_base,
                      (const int*)rexp.ptr, (const int*)cexp.ptr, rows, N, Cout, ldc};
     const unsigned rblocks = (unsigned)std::min<int64_t>(rows, recombine_blocks);
-    if (sh.k_batches >= kPreReduceBatches) {
+    if (k_batches >= kPreReduceBatches) {
       // Many K batches (a small output cut along a long K): the batches are first summed into
       // int64 planes by many threads, then recombined as one batch.
       if ((e = cudaMemsetAsync(accbuf.ptr, 0, (size_t)batch_stride * sizeof(long long), stream)) != cudaSuccess)
         return cuda_error(e, "cudaMemsetAsync");
       const int per = 8;
-      const int64_t work = batch_stride * ((sh.k_batches + per - 1) / per);
+      const int64_t work = batch_stride * ((k_batches + per - 1) / per);
       sum_batches_kernel<<<(unsigned)std::min<int64_t>((work + 255) / 256, 8 * (int64_t)sms), 256, 0, stream>>>(
-          (const int*)tbuf.ptr, batch_stride, sh.k_batches, per, (long long*)accbuf.ptr);
+          (const int*)tbuf.ptr, batch_stride, k_batches, per, (long long*)accbuf.ptr);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "sum_batches_kernel launch");
       ra.T = nullptr;
       ra.T64 = (const long long*)accbuf.ptr;

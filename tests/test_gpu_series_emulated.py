@@ -237,3 +237,41 @@ def test_emulated_non_finite_inputs_give_nan_rows_and_sets():
     want = np.array(oseries.series_eval(ns, ms, r[ok_rows], th[ok_rows], Cg.tolist()))
     tol = 1e-13 * (1.0 + abs_bound(ns, ms, r[ok_rows], th[ok_rows], Cg))
     assert (np.abs(F[good] - want) <= tol).all()
+
+
+@pytest.mark.parametrize("S", [1, 7, 16])
+def test_stacked_diagonals_match_plane_launches(S, monkeypatch):
+    """A narrow B (at most 16 sets) takes the stacked-diagonal slice products (one launch forms
+    every diagonal); ZP_EMU_STACKED=0 takes the launch per plane of paired diagonals.  Both form
+    the same exact integer sums, so grad_C over a long K (30000 points, many K batches) and a
+    forward whose K (5151 modes) is past the fused kernel's limit agree bitwise, and with the
+    DGEMM form to the float64 tolerance."""
+    ns, ms = inputs.full_zernike_modes(20)
+    rng = np.random.default_rng(90 + S)
+    P = 30000
+    r, th = np.sqrt(rng.uniform(0.0, 1.0, P)), rng.uniform(0.0, 2 * np.pi, P)
+    C = inputs.scaled_normal_coeffs(ns, S, 90 + S)
+    G = rng.standard_normal((P, S))
+    args = (ns, ms, dev(r), dev(th), dev(C), dev(G))
+    gc = zp.series_adjoint(*args, prec="fp64emu")[0]
+    monkeypatch.setenv("ZP_EMU_STACKED", "0")
+    gc_planes = zp.series_adjoint(*args, prec="fp64emu")[0]
+    monkeypatch.delenv("ZP_EMU_STACKED")
+    assert torch.equal(gc, gc_planes)
+    want = zp.series_adjoint(*args, prec="fp64")[0]
+    scale = 1.0 + torch.as_tensor(np.abs(G).sum(0), device=DEV)[None, :]
+    assert bool(((gc - want).abs() <= 1e-13 * scale).all())
+
+    ns2, ms2 = inputs.full_zernike_modes(100)
+    P2 = 600
+    r2, th2 = rng.uniform(0.0, 1.0, P2), rng.uniform(0.0, 2 * np.pi, P2)
+    C2 = inputs.scaled_normal_coeffs(ns2, S, 91 + S)
+    a2 = (ns2, ms2, dev(r2), dev(th2), dev(C2))
+    F = zp.series_eval(*a2, "fp64emu")
+    monkeypatch.setenv("ZP_EMU_STACKED", "0")
+    F_planes = zp.series_eval(*a2, "fp64emu")
+    monkeypatch.delenv("ZP_EMU_STACKED")
+    assert torch.equal(F, F_planes)
+    F64 = zp.series_eval(*a2, "fp64")
+    scale2 = 1.0 + torch.as_tensor(np.abs(C2).sum(0), device=DEV)[None, :]
+    assert bool(((F - F64).abs() <= 1e-13 * scale2).all())
