@@ -275,3 +275,24 @@ def test_stacked_diagonals_match_plane_launches(S, monkeypatch):
     F64 = zp.series_eval(*a2, "fp64")
     scale2 = 1.0 + torch.as_tensor(np.abs(C2).sum(0), device=DEV)[None, :]
     assert bool(((F - F64).abs() <= 1e-13 * scale2).all())
+
+
+def test_stacked_diagonals_widest_slices(monkeypatch):
+    """1.6 million points and two sets: grad_C's K is long enough that the slice width drops to
+    5 bits (11 slices, the widest stacked MMA, N = 176); stacked and plane launches agree
+    bitwise, and both with the DGEMM form to the float64 tolerance."""
+    ns, ms = inputs.full_zernike_modes(4)
+    rng = np.random.default_rng(97)
+    P, S = 1_600_000, 2
+    r, th = np.sqrt(rng.uniform(0.0, 1.0, P)), rng.uniform(0.0, 2 * np.pi, P)
+    C = inputs.scaled_normal_coeffs(ns, S, 97)
+    G = rng.standard_normal((P, S))
+    args = (ns, ms, dev(r), dev(th), dev(C), dev(G))
+    gc = zp.series_adjoint(*args, need=(True, False, False), prec="fp64emu")[0]
+    monkeypatch.setenv("ZP_EMU_STACKED", "0")
+    gc_planes = zp.series_adjoint(*args, need=(True, False, False), prec="fp64emu")[0]
+    monkeypatch.delenv("ZP_EMU_STACKED")
+    assert torch.equal(gc, gc_planes)
+    want = zp.series_adjoint(*args, need=(True, False, False), prec="fp64")[0]
+    scale = 1.0 + torch.as_tensor(np.abs(G).sum(0), device=DEV)[None, :]
+    assert bool(((gc - want).abs() <= 1e-13 * scale).all())
