@@ -1401,8 +1401,17 @@ __global__ void slice_rows_kernel(Operand X, int64_t rows, int64_t tiles, int64_
   const int64_t total = rows_pad * groups;
   const long long bias = slice_bias(sp.beta, sp.s);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = KFAST ? i / groups : i % rows_pad;
-    const int64_t k0 = (KFAST ? i % groups : i / rows_pad) * 8;
+    int64_t row, k0;
+    if constexpr (KFAST && ROW == 64) {
+      // Eight threads per (row pair, K chunk): rows 2j and 2j + 1 share a 128-byte line of the
+      // 64-byte layout, so each slice's stores fill whole lines.
+      const int64_t rest = i >> 3, sub = i & 7;
+      row = 2 * (rest / KC) + (sub >> 2);
+      k0 = (rest % KC) * BK + (sub & 3) * 8;
+    } else {
+      row = KFAST ? i / groups : i % rows_pad;
+      k0 = (KFAST ? i % groups : i / rows_pad) * 8;
+    }
     const bool valid = row < rows;
     const int ex = valid ? expo[row] : 0;
     const bool use = valid && ex != kNonFiniteRow;
