@@ -125,10 +125,12 @@ zp_status check_plan_device(const zp_plan* plan);
 
 // Kernel launchers (zp_walk.cu).
 // phase_ms: NULL, or [2] receiving the device time of the point preparation and of the walk
-// (events around each launch; the stream is synchronised).
+// (events around each launch; the stream is synchronised).  rowmax: NULL, or (a walk of Z:
+// theta given, max_deriv 0) [modes] words, zeroed by the caller, receiving each output row's
+// largest |value| high word << 32.
 zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points,
                       int max_deriv, double* out, double* out_dtheta, cudaStream_t stream,
-                      float* phase_ms = nullptr);
+                      float* phase_ms = nullptr, unsigned long long* rowmax = nullptr);
 zp_status launch_per_mode(const zp_plan* plan, const double* r, int64_t n_points, double* out,
                           cudaStream_t stream);
 

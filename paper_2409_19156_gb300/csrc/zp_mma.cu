@@ -1735,10 +1735,19 @@ struct EmuGemm {
   }
 
   // C rows [0, rows) (rows <= slab_tiles * BM) = A rows [0, rows) times B^T.
-  zp_status run_slab(int64_t rows, Operand A, double* Cout, int64_t ldc, cudaStream_t stream) {
+  // a_rowmax: NULL, or the rows' largest |value| high words << 32 (formed by the producer of
+  // A), which then replace the pass over A for the row scales.
+  zp_status run_slab(int64_t rows, Operand A, double* Cout, int64_t ldc, cudaStream_t stream,
+                     const unsigned long long* a_rowmax = nullptr) {
     using C = Cfg<KIND_SLICE>;
     const int64_t tiles = (rows + BM - 1) / BM;
-    ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
+    if (a_rowmax) {
+      row_exponent_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, stream>>>(a_rowmax, rows, (int*)rexp.ptr);
+      const cudaError_t e0 = cudaGetLastError();
+      if (e0 != cudaSuccess) return cuda_error(e0, "row_exponent_kernel launch");
+    } else {
+      ZP_TRY(scale_rows(A, rows, K, (unsigned long long*)maxbits.ptr, (int*)rexp.ptr, stream));
+    }
     if (stacked) return run_slab_stacked(rows, tiles, A, Cout, ldc, stream);
     if (A.sk == 1 && A.sr != 1)
       slice_rows_kernel<BM, true><<<2048, 256, 0, stream>>>(A, rows, tiles, K, sh.KC, (const int*)rexp.ptr, sh.sp,
@@ -1865,7 +1874,7 @@ zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const 
 
 zp_status emulated_gemm_fp64(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_sm, int64_t a_sk,
                              const double* B, int64_t b_sn, int64_t b_sk, double* C, int64_t ldc,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, const unsigned long long* a_rowmax) {
   if (M <= 0 || N <= 0) return ZP_OK;
   if (K <= 0) {
     for (int64_t m = 0; m < M; ++m) {
@@ -1879,7 +1888,8 @@ zp_status emulated_gemm_fp64(int64_t M, int64_t N, int64_t K, const double* A, i
   const int64_t slab_rows = g.slab_tiles * BM;
   for (int64_t m0 = 0; m0 < M; m0 += slab_rows) {
     const int64_t rows = std::min<int64_t>(slab_rows, M - m0);
-    ZP_TRY(g.run_slab(rows, Operand{A + m0 * a_sm, a_sm, a_sk}, C + m0 * ldc, ldc, stream));
+    ZP_TRY(g.run_slab(rows, Operand{A + m0 * a_sm, a_sm, a_sk}, C + m0 * ldc, ldc, stream,
+                      a_rowmax ? a_rowmax + m0 : nullptr));
   }
   return ZP_OK;
 }

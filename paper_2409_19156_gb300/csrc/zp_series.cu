@@ -280,11 +280,19 @@ zp_status series_adjoint_fp64(const zp_plan* plan, const double* r, const double
   CublasLock cl;
   if (grad_coeffs) {
     ZP_TRY(z.alloc((size_t)J * P * sizeof(double), stream));
-    ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream));
     if (emulated) {
-      // grad_C[j][s] = sum_p Z[j][p] G[p][s]: A(j, p) = Z[j * P + p], B(s, p) = G[p * S + s].
-      ZP_TRY(emulated_gemm_fp64(J, S, P, (const double*)z.ptr, P, 1, G, 1, S, grad_coeffs, S, stream));
+      // grad_C[j][s] = sum_p Z[j][p] G[p][s]: A(j, p) = Z[j * P + p], B(s, p) = G[p * S + s];
+      // the walk also forms Z's row maxima for A's row scales.
+      ScratchBuffer zmax;
+      ZP_TRY(zmax.alloc((size_t)J * sizeof(unsigned long long), stream));
+      const cudaError_t e = cudaMemsetAsync(zmax.ptr, 0, (size_t)J * sizeof(unsigned long long), stream);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+      ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream, nullptr,
+                         (unsigned long long*)zmax.ptr));
+      ZP_TRY(emulated_gemm_fp64(J, S, P, (const double*)z.ptr, P, 1, G, 1, S, grad_coeffs, S, stream,
+                                (const unsigned long long*)zmax.ptr));
     } else {
+      ZP_TRY(launch_walk(plan, r, theta, P, 0, (double*)z.ptr, nullptr, stream));
       ZP_TRY(get_cublas(cl, stream));
       // grad_C row-major [J][S] = column-major S x J = G^T (S x P) * Z^T (P x J):
       //   G row-major [P][S] is column-major S x P; Z row-major [J][P] is column-major P x J.

@@ -73,10 +73,12 @@ zp_status series_eval_emulated_fp64(const zp_plan* plan, const double* r, const 
 // Float64-accurate GEMM on the tensor cores by the same slicing:
 //   C[m * ldc + n] = sum_k A[m * a_sm + k * a_sk] * B[n * b_sn + k * b_sk],  m < M, n < N.
 // Error bound: about K 2^-54 max_k |A(m, k)| max_k |B(n, k)| per element.  Scratch is
-// allocated stream-ordered on `stream`.
+// allocated stream-ordered on `stream`.  a_rowmax: NULL, or per row m of A the high word of
+// max_k |A(m, k)| shifted left by 32 (as the walk's rowmax output gives it), used for A's row
+// scales instead of a pass over A.
 zp_status emulated_gemm_fp64(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_sm, int64_t a_sk,
                              const double* B, int64_t b_sn, int64_t b_sk, double* C, int64_t ldc,
-                             cudaStream_t stream);
+                             cudaStream_t stream, const unsigned long long* a_rowmax = nullptr);
 
 // Caller-provided scratch for the split path: `b` holds the split coefficient tiles,
 // `a` the split basis of as many point tiles as fit (at least one).

@@ -53,6 +53,10 @@ struct WalkArgs {
   const double* cs = nullptr;
   const double* sn = nullptr;
   int pw_max = 0;
+  // Optional (NULL: none; walks of Z at k = 0 only): per output row j, the largest high word
+  // of |value| over all points, atomically maxed into rowmax[j] << 32 (zeroed by the caller):
+  // what the float64-accurate GEMM needs for its power-of-two row scales.
+  unsigned long long* rowmax = nullptr;
 };
 
 // Point preparation: rho^j for j = 0..pw_max and (theta given) cos / sin(j theta) for
@@ -193,6 +197,15 @@ __global__ void __launch_bounds__(TPB) walk_kernel(WalkArgs a) {
     }
   }
 
+  // Row maximum of output row j (walks of Z at k = 0): the warp's live lanes reduce the high
+  // words of |v| and one of them maxes the result into rowmax[j].
+  auto note_max = [&](int64_t j, double v0, double v1) {
+    uint32_t h = (uint32_t)__double2hiint(v0) & 0x7fffffffu;
+    if (PPT == 2 && two) h = max(h, (uint32_t)__double2hiint(v1) & 0x7fffffffu);
+    const unsigned mask = __activemask();
+    const uint32_t mx = __reduce_max_sync(mask, h);
+    if ((int)(threadIdx.x & 31u) == __ffs((int)mask) - 1) atomicMax(a.rowmax + j, (unsigned long long)mx << 32);
+  };
   auto store_step = [&](int N, const double (&V)[PPT][KMAX + 1]) {
     const int s_begin = sptr[N], s_end = sptr[N + 1];
     if (s_begin == s_end) return;
@@ -225,6 +238,8 @@ __global__ void __launch_bounds__(TPB) walk_kernel(WalkArgs a) {
             const bool is_sin = (code >> 31) != 0;
             store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, is_sin ? rs[0] : rc[0], is_sin ? rs[PPT - 1] : rc[PPT - 1], two,
                        VEC);
+            if constexpr (KMAX == 0)
+              if (a.rowmax) note_max(j, is_sin ? rs[0] : rc[0], is_sin ? rs[PPT - 1] : rc[PPT - 1]);
           }
         }
         if (a.out_dtheta) {
@@ -255,9 +270,12 @@ __global__ void __launch_bounds__(TPB) walk_kernel(WalkArgs a) {
 #pragma unroll
         for (int i = 0; i < PPT; ++i) f[i] = is_sin ? sn[i] : cs[i];
 #pragma unroll
-        for (int k = 0; k <= KMAX; ++k)
-          store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, fma(R[0][k], f[0], zero), fma(R[PPT - 1][k], f[PPT - 1], zero),
-                     two, VEC);
+        for (int k = 0; k <= KMAX; ++k) {
+          const double v0 = fma(R[0][k], f[0], zero), v1 = fma(R[PPT - 1][k], f[PPT - 1], zero);
+          store_pts<PPT>(a.out + ((int64_t)k * a.J + j) * a.P, p0, v0, v1, two, VEC);
+          if constexpr (KMAX == 0)
+            if (a.rowmax) note_max(j, v0, v1);
+        }
         if (a.out_dtheta) {
           const double md = (double)m;
           double dt[PPT];
@@ -388,8 +406,11 @@ struct WalkTimer {
 }  // namespace
 
 zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta, int64_t n_points, int max_deriv,
-                      double* out, double* out_dtheta, cudaStream_t stream, float* phase_ms) {
+                      double* out, double* out_dtheta, cudaStream_t stream, float* phase_ms,
+                      unsigned long long* rowmax) {
   if (phase_ms) phase_ms[0] = phase_ms[1] = 0.0f;
+  if (rowmax && (max_deriv != 0 || theta == nullptr))
+    return set_error(ZP_ERR_INVALID_ARG, "row maxima are formed for walks of Z at k = 0 only");
   if (n_points == 0 || plan->n_modes == 0) return ZP_OK;
   WalkTimer timer(phase_ms, stream);
   WalkArgs a;
@@ -403,6 +424,7 @@ zp_status launch_walk(const zp_plan* plan, const double* r, const double* theta,
   a.J = plan->n_modes;
   a.out = out;
   a.out_dtheta = out_dtheta;
+  a.rowmax = rowmax;
   // Short launches (fewer than eight 128-thread blocks per SM) take 32-thread blocks of one
   // point per thread: more, shorter warps over more SMs.
   int dev = 0, sms = 152;

@@ -149,11 +149,17 @@ def test_emulated_adjoint_point_gradients_off_disc(S):
     C = inputs.scaled_normal_coeffs(ns, S, 80 + S)
     G = rng.standard_normal((P, S))
     args = (ns, ms, dev(r), dev(th), dev(C), dev(G))
-    _, gr, gt = zp.series_adjoint(*args, prec="fp64emu")
-    _, wr, wt = zp.series_adjoint(*args, prec="fp64")
+    gc, gr, gt = zp.series_adjoint(*args, prec="fp64emu")
+    wc, wr, wt = zp.series_adjoint(*args, prec="fp64")
     scale = 1.0 + torch.as_tensor(np.abs(G).sum(1) * np.abs(C).sum() * 15 ** 2 * r.max() ** 15, device=DEV)
     assert bool(((gr - wr).abs() <= 1e-12 * scale).all())
     assert bool(((gt - wt).abs() <= 1e-12 * scale).all())
+    # grad_C = Z G with Z's row scales from the walk's row maxima (|Z| up to about 1.4^15 here):
+    # within K 2^-54 max_p |Z_j(p)| sum_p |G[p][s]| of the DGEMM form.
+    Z = zp.basis(ns, ms, dev(r), dev(th))[0][0]
+    zmax = Z.abs().max(dim=1).values[:, None]
+    gsum = torch.as_tensor(np.abs(G).sum(0), device=DEV)[None, :]
+    assert bool(((gc - wc).abs() <= 1e-13 * (1.0 + zmax * gsum)).all())
 
 
 def test_emulated_adjoint_series_n24_full_size_against_fp64():
