@@ -426,6 +426,7 @@ struct zp_batch {
   zp::FusedItem* d_fitems = nullptr;
   int32_t* d_fchunk = nullptr;
   int64_t n_fitems = 0, n_fchunks = 0;
+  int fused_ndig = zp::kFusedDigits;  // digits per value of the fused launches (the longest instance's)
 };
 
 namespace zp {
@@ -524,8 +525,12 @@ zp_status launch_columns(const zp_batch* b, cudaStream_t st) {
 // Descriptors, items and buffers of the fused forward (see zp_batch::fused_ok).
 zp_status build_fused(zp_batch* b) {
   if (b->n_sets > kFusedMaxSets || b->n_sets == 0) return ZP_OK;
-  for (size_t i = 0; i < b->inst.size(); ++i)
+  int64_t kpad_max = 0;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
     if (b->plans[b->inst_plan[i]]->fused_kpad > kFusedMaxModes) return ZP_OK;
+    if (b->inst[i].n_modes > 0) kpad_max = std::max(kpad_max, b->plans[b->inst_plan[i]]->fused_kpad);
+  }
+  b->fused_ndig = fused_digits_for(kpad_max);
   const int64_t n = (int64_t)b->inst.size();
   std::vector<FusedInst> fi(n);
   std::vector<int32_t> chunk_inst;
@@ -623,6 +628,7 @@ zp_status batch_forward(zp_batch* b, zp_precision prec, cudaStream_t st) {
     a.insts = b->d_finst;
     a.items = b->d_fitems;
     a.n_items = b->n_fitems;
+    a.ndig = b->fused_ndig;
     if (b->n_fitems == 0) return ZP_OK;
     return fused_launch(a, (int64_t)b->inst.size(), b->d_fchunk, b->n_fchunks, st);
   }
@@ -889,6 +895,7 @@ static zp_status zp_batch_adjoint_impl(zp_batch* b, zp_precision prec, void* str
     FusedArgs a;
     a.items = b->d_fitems;
     a.n_items = b->n_fitems;
+    a.ndig = b->fused_ndig;
     const int64_t n = (int64_t)b->inst.size();
     bool digits = true;  // the coefficient digits once, for the first pass
     if (need_t) {

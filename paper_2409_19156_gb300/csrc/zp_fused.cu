@@ -6,26 +6,27 @@
 //
 // contracted by error-free slicing (Ozaki et al., a published scheme, written here from its
 // definition): every Z_j(p) is scaled by 2^-e_p (e_p = 1 for 0 <= r <= 1, where |Z| <= 1;
-// else from a first pass over the point's modes), truncated to a fixed-point integer with 55
-// fraction bits and cut into 11 balanced base-32 digits a_1..a_11 (integers of at most 6 bits,
-// exact in bfloat16); the coefficients are rounded to the same fixed point and cut the same way
-// per set (b_1..b_11, scale 2^-e_s).
-// Then Z C = 2^(e_p + e_s) sum_d T_d 2^(-5 d) with T_d = sum_{t+u=d} sum_j a_t b_u, kept for
-// d <= 12 (the dropped pairs weigh below 2^-60 of the scales).
+// else from a first pass over the point's modes), truncated to a fixed-point integer and cut
+// into D balanced base-2^beta digits a_1..a_D (integers of at most beta + 1 bits, exact in
+// bfloat16): D = 11 digits of 5 bits (55 fraction bits) for contractions of up to 5041
+// positions, D = 9 of 6 bits (54 bits) for up to 1489; the coefficients are rounded to the same
+// fixed point and cut the same way per set (b_1..b_D, scale 2^-e_s).
+// Then Z C = 2^(e_p + e_s) sum_d T_d 2^(-beta d) with T_d = sum_{t+u=d} sum_j a_t b_u, kept for
+// d <= D + 1 (the dropped pairs weigh below about 2^-(beta D) of the scales).
 //
 // One persistent CTA per SM works through 128-point tiles:
 //  - warps 0-11 (three threads per point, each walking one of three streams of |m| columns:
 //    more independent float64 chains per scheduler than two streams give) run the float64
 //    recursion of Sec. 2 (Algorithm 1's column order within a stream, cos/sin(m theta) by
-//    angle addition between consecutive columns), form each value, cut it into its 11 digits
-//    on the integer pipe and write them into 11 digit tiles in shared memory (the tensor
+//    angle addition between consecutive columns), form each value, cut it into its D digits
+//    on the integer pipe and write them into D digit tiles in shared memory (the tensor
 //    core's 64-byte swizzled K-major layout, 32 K values per stage, two stages, the streams'
 //    8-value units interleaved along K);
-//  - warp 12 issues the tcgen05 MMAs: per K step and A digit t, one MMA of N = 176 against the
-//    coefficient digit tile shifted by t blocks of 16 rows (zero blocks in front), so that
+//  - warp 12 issues the tcgen05 MMAs: per K step and A digit t, one MMA of N = 16 D against
+//    the coefficient digit tile shifted by t blocks of 16 rows (zero blocks in front), so that
 //    every MMA adds a_t b_u into the TMEM columns of diagonal t + u for all u at once; every
-//    diagonal sum is an integer below 2^24 (at most 5041 modes), hence exact in float32;
-//  - the warps of streams 0 and 1, after producing a tile, take the previous tile's 11 x 16
+//    diagonal sum is an integer below 2^24 (the position limits above), hence exact in float32;
+//  - the warps of streams 0 and 1, after producing a tile, take the previous tile's D x 16
 //    diagonal sums out of TMEM, recombine them exactly in integers (two Horner chains joined
 //    into 128 bits) and round once to float64.
 // The K order of the contraction is the plan's slot order with every column padded to a
@@ -50,20 +51,13 @@
 namespace zp {
 namespace {
 
-constexpr int kBeta = kFusedBeta;   // digit width (bits)
-constexpr int kDig = kFusedDigits;  // digits per value
 constexpr int FM = 128;             // points per tile (TMEM lanes)
 constexpr int FBK = 32;             // K values per stage (64-byte bf16 rows)
 constexpr int FNS = kFusedMaxSets;  // sets per digit block (rows of a B block, TMEM columns)
 constexpr uint32_t kRowBytes = 64;
 constexpr uint32_t kASlice = FM * kRowBytes;                 // one digit tile of A: 8 KB
-constexpr uint32_t kABytes = kDig * kASlice;                 // 88 KB
 constexpr uint32_t kBBlock = FNS * kRowBytes;                // one digit block of B: 1 KB
-constexpr uint32_t kBPadBytes = (2 * kDig - 1) * kBBlock;    // 10 zero blocks + 11 digit blocks
-constexpr uint32_t kBCopyOffset = (kDig - 1) * kBBlock;
-constexpr uint32_t kStageBytes = kABytes + kBPadBytes;       // 109.5 KB
 constexpr int kStages = 2;
-constexpr int kAccCols = kDig * FNS;                         // 176 TMEM columns per tile
 constexpr int kAccStride = 256;                              // two accumulators in 512 columns
 // Warps 0 .. 4 kStreams - 1 produce (warp w: point rows 32 (w % 4) .. + 31, stream w / 4); the
 // warps of streams 0 and 1 also drain the accumulator of the previous tile (warp w: its rows,
@@ -72,14 +66,31 @@ constexpr int kStreams = kFusedStreams;
 constexpr int kProducerWarps = 4 * kStreams, kMmaWarp = kProducerWarps;
 constexpr int kDrainWarps = 8;
 constexpr int kThreads = 32 * (kProducerWarps + 1);  // 416
-constexpr int kSplit = 5;  // diagonals d = 2..6 in the first Horner chain, 7..12 in the second
 constexpr uint32_t kAux = 2048;
-constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + kAux;
-static_assert(kBPadBytes % 1024 == 0 && kABytes % 1024 == 0, "1024-byte aligned operand tiles");
-static_assert(kSmem <= 232448, "shared memory per CTA");
-static_assert(kAccCols <= kAccStride, "accumulator fits its TMEM half");
 
-constexpr long long kBias = fused_bias();
+// The digit shape of a launch: NDIG digits of Beta bits per value (11 x 5 for contractions of
+// up to 5041 positions, 9 x 6 for up to 1489).  A stage holds NDIG digit tiles of A and
+// 2 NDIG - 1 blocks of B (NDIG - 1 zero blocks, then the coefficient digits); the accumulator
+// holds NDIG diagonal blocks of 16 sets; the drain's first Horner chain takes Split diagonals.
+template <int NDIG>
+struct FK {
+  static constexpr int Beta = fused_beta(NDIG);
+  static constexpr uint32_t ABytes = NDIG * kASlice;
+  static constexpr uint32_t BPadBytes = (2 * NDIG - 1) * kBBlock;
+  static constexpr uint32_t BCopyOffset = (NDIG - 1) * kBBlock;
+  static constexpr uint32_t BCopyBytes = NDIG * kBBlock;
+  static constexpr uint32_t StageBytes = ABytes + BPadBytes;
+  static constexpr int AccCols = NDIG * FNS;
+  static constexpr int Split = NDIG == kFusedDigits ? 5 : 4;
+  static constexpr long long Bias = fused_bias<NDIG>();
+  static constexpr uint32_t Smem = kStages * StageBytes + 1024 + kAux;
+  static_assert(BPadBytes % 1024 == 0 && ABytes % 1024 == 0, "1024-byte aligned operand tiles");
+  static_assert(Smem <= 232448, "shared memory per CTA");
+  static_assert(AccCols <= kAccStride, "accumulator fits its TMEM half");
+  static_assert(BCopyBytes <= kFusedBChunk, "a chunk's digit blocks fit its stride");
+  // Both Horner chains stay within int64: diagonal sums below 2^24, Beta bits per step.
+  static_assert(24 + Beta * (Split - 1) + 1 <= 63 && 24 + Beta * (NDIG - Split - 1) + 1 <= 63, "Horner chains");
+};
 
 __device__ unsigned int g_fused_error = 0;  // set when a bounded wait gives up
 
@@ -87,63 +98,59 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-// bf16 bit patterns (in the high half of a float's bits) of the 11 digits of fixed-point X,
-// most significant first: word[t] holds digit a_{t+1} of the value.  Balanced digits come from
-// the biased word's bit fields; a small integer d is exact as float(2^23 + d) - 2^23.
-__device__ __forceinline__ void digits_of(long long X, uint32_t (&f)[kDig]) {
-  const long long Y = X + kBias;
-  f[0] = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y, 0)) - 12582912.0f);
-#pragma unroll
-  for (int t = 1; t < kDig; ++t)
-    f[t] = __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)fused_digit_field(Y, t)) - 8388624.0f);  // 2^23+16
-}
-
-// Digit t >= 1 of two biased words as one word of two bf16 (value 0 low): the unsigned 5-bit
-// fields f placed under the bfloat16 pattern of 128 (0x4300 | f is exactly 128 + f), then one
-// packed subtraction of 144 leaves the balanced digit f - 16 in each half (exact).
-template <int T>
+// Digit t >= 1 of two biased words as one word of two bf16 (value 0 low): the unsigned Beta-bit
+// fields f placed under the bfloat16 pattern of 128 (0x4300 | f is exactly 128 + f for f < 128),
+// then one packed subtraction of 128 + 2^(Beta-1) leaves the balanced digit f - 2^(Beta-1) in
+// each half (exact).
+template <int NDIG, int T>
 __device__ __forceinline__ uint32_t digit_pair_low(long long Y0, long long Y1) {
-  static_assert(T >= 1 && T < kDig, "unsigned digit fields");
-  constexpr int s = kBeta * (kDig - 1 - T);  // bit position of the field
+  constexpr int B = FK<NDIG>::Beta;
+  static_assert(T >= 1 && T < NDIG, "unsigned digit fields");
+  constexpr int s = B * (NDIG - 1 - T);  // bit position of the field
+  constexpr uint32_t mask = (1u << B) - 1u;
   uint32_t a, b;
-  if constexpr (s + kBeta <= 32) {
+  if constexpr (s + B <= 32) {
     a = (uint32_t)Y0 >> s;
     b = s >= 16 ? (uint32_t)Y1 >> (s - 16) : (uint32_t)Y1 << (16 - s);
   } else {
     a = (uint32_t)(Y0 >> s);
     b = (uint32_t)(Y1 >> s) << 16;
   }
-  const uint32_t w = (a & 0x1Fu) | (b & 0x1F0000u) | 0x43004300u;
+  const uint32_t w = (a & mask) | (b & (mask << 16)) | 0x43004300u;
   __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&w);
-  v = __hsub2(v, __nv_bfloat162(__nv_bfloat16_raw{0x4310}, __nv_bfloat16_raw{0x4310}));  // 144
+  constexpr unsigned short sub = (unsigned short)(0x4300u | (1u << (B - 1)));  // 128 + 2^(B-1)
+  v = __hsub2(v, __nv_bfloat162(__nv_bfloat16_raw{sub}, __nv_bfloat16_raw{sub}));
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// Digit 0 (signed, at most 33 in magnitude) of two biased words, by the float32 magic sum.
+// Digit 0 (signed, at most 2^Beta + 1 in magnitude) of two biased words, by the float32 magic
+// sum.
+template <int NDIG>
 __device__ __forceinline__ uint32_t digit_pair_top(long long Y0, long long Y1) {
-  const uint32_t f0 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y0, 0)) - 12582912.0f);
-  const uint32_t f1 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field(Y1, 0)) - 12582912.0f);
+  const uint32_t f0 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field<NDIG>(Y0, 0)) - 12582912.0f);
+  const uint32_t f1 = __float_as_uint(__int_as_float(0x4B400000 + fused_digit_field<NDIG>(Y1, 0)) - 12582912.0f);
   return __byte_perm(f0, f1, 0x7632);
 }
 
-// All 11 digits of two biased words Y = X + bias, joined per digit (value 0 low).
-__device__ __forceinline__ void digit_pair_biased(long long Y0, long long Y1, uint32_t (&w)[kDig]) {
-  w[0] = digit_pair_top(Y0, Y1);
-  w[1] = digit_pair_low<1>(Y0, Y1);
-  w[2] = digit_pair_low<2>(Y0, Y1);
-  w[3] = digit_pair_low<3>(Y0, Y1);
-  w[4] = digit_pair_low<4>(Y0, Y1);
-  w[5] = digit_pair_low<5>(Y0, Y1);
-  w[6] = digit_pair_low<6>(Y0, Y1);
-  w[7] = digit_pair_low<7>(Y0, Y1);
-  w[8] = digit_pair_low<8>(Y0, Y1);
-  w[9] = digit_pair_low<9>(Y0, Y1);
-  w[10] = digit_pair_low<10>(Y0, Y1);
+template <int NDIG, int T = 1>
+__device__ __forceinline__ void digit_pair_lows(long long Y0, long long Y1, uint32_t (&w)[NDIG]) {
+  if constexpr (T < NDIG) {
+    w[T] = digit_pair_low<NDIG, T>(Y0, Y1);
+    digit_pair_lows<NDIG, T + 1>(Y0, Y1, w);
+  }
+}
+
+// All NDIG digits of two biased words Y = X + bias, joined per digit (value 0 low).
+template <int NDIG>
+__device__ __forceinline__ void digit_pair_biased(long long Y0, long long Y1, uint32_t (&w)[NDIG]) {
+  w[0] = digit_pair_top<NDIG>(Y0, Y1);
+  digit_pair_lows<NDIG>(Y0, Y1, w);
 }
 
 // Two values' digits joined per digit into one 32-bit word of two bf16 (value 0 low).
-__device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t (&w)[kDig]) {
-  digit_pair_biased(X0 + kBias, X1 + kBias, w);
+template <int NDIG>
+__device__ __forceinline__ void digit_pair(long long X0, long long X1, uint32_t (&w)[NDIG]) {
+  digit_pair_biased<NDIG>(X0 + FK<NDIG>::Bias, X1 + FK<NDIG>::Bias, w);
 }
 
 struct Barriers {
@@ -260,27 +267,29 @@ __device__ __forceinline__ const FusedInst& inst_of(const FusedArgs& a, int inst
   return a.insts ? a.insts[inst] : a.single;
 }
 
-// Drains accumulator `acc` of a finished tile for this thread's row and 8 sets (h): 11 diagonal
+// Drains accumulator `acc` of a finished tile for this thread's row and 8 sets (h): NDIG diagonal
 // sums per output out of TMEM, recombined exactly (two Horner chains joined into 128 bits) and
 // rounded once to float64.
+template <int NDIG>
 __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint32_t tmem_base, uint32_t acc, uint32_t q,
                                            uint32_t row, int h, int ep) {
+  using K = FK<NDIG>;
   const int64_t p = p0 + row;
   long long hi[8] = {}, lo[8] = {};
 #pragma unroll
-  for (int db = 0; db < kDig; ++db) {
+  for (int db = 0; db < NDIG; ++db) {
     uint32_t v[8];
     ptx::tmem_ld_32x32b_x8(tmem_base + ((q * 32u) << 16) + acc * kAccStride + (uint32_t)(db * FNS + h * 8), v);
     ptx::tmem_ld_wait(v);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const long long tv = (long long)__float2int_rn(__uint_as_float(v[i]));
-      if (db < kSplit) hi[i] = horner(hi[i], kBeta, tv);
-      else lo[i] = horner(lo[i], kBeta, tv);
+      if (db < K::Split) hi[i] = horner(hi[i], K::Beta, tv);
+      else lo[i] = horner(lo[i], K::Beta, tv);
     }
   }
   if (p >= d.P) return;
-  const int e_base = ep - kBeta * (kDig + 1);
+  const int e_base = ep - K::Beta * (NDIG + 1);
   if (d.dot_out) {
     // Row sum over this thread's 8 sets of G times the series; the point's two halves are added
     // onto the zeroed output (two addends: the same float64 sum in either order).
@@ -292,7 +301,7 @@ __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint3
       const int ec = d.cexp[h * 8 + i];
       const double v = (ep == kNonFiniteRow || ec == kNonFiniteRow)
                            ? __longlong_as_double(0x7ff8000000000000ll)
-                           : join_to_double(hi[i], lo[i], kBeta * (kDig - kSplit), e_base + ec);
+                           : join_to_double(hi[i], lo[i], K::Beta * (NDIG - K::Split), e_base + ec);
       acc = fma(grow[h * 8 + i], v, acc);
     }
     atomicAdd(d.dot_out + p, acc);
@@ -306,15 +315,16 @@ __device__ __forceinline__ void drain_tile(const FusedInst& d, int64_t p0, uint3
     const int ec = d.cexp[h * 8 + i];
     orow[h * 8 + i] = (ep == kNonFiniteRow || ec == kNonFiniteRow)
                           ? __longlong_as_double(0x7ff8000000000000ll)
-                          : join_to_double(hi[i], lo[i], kBeta * (kDig - kSplit), e_base + ec);
+                          : join_to_double(hi[i], lo[i], K::Beta * (NDIG - K::Split), e_base + ec);
   }
 }
 
-template <int VK>
+template <int VK, int NDIG>
 __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
+  using K = FK<NDIG>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  Barriers* bar = reinterpret_cast<Barriers*>(smem + kStages * kStageBytes);
+  Barriers* bar = reinterpret_cast<Barriers*>(smem + kStages * K::StageBytes);
   volatile int* abort_flag = &bar->abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -333,9 +343,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
     ptx::fence_barrier_init();
   }
   // The zero blocks in front of each stage's coefficient digits (never overwritten).
-  for (uint32_t i = threadIdx.x; i < kStages * kBCopyOffset / 16; i += kThreads) {
-    const uint32_t st = i / (kBCopyOffset / 16), o = i % (kBCopyOffset / 16);
-    reinterpret_cast<uint4*>(smem + st * kStageBytes + kABytes)[o] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = threadIdx.x; i < kStages * K::BCopyOffset / 16; i += kThreads) {
+    const uint32_t st = i / (K::BCopyOffset / 16), o = i % (K::BCopyOffset / 16);
+    reinterpret_cast<uint4*>(smem + st * K::StageBytes + K::ABytes)[o] = make_uint4(0u, 0u, 0u, 0u);
   }
   ptx::fence_proxy_async_smem();
   if (warp == kMmaWarp) {
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       const uint32_t pacc = (uint32_t)((local - 1) & 1), puse = (uint32_t)(((local - 1) >> 1) & 1);
       if (!warp_wait(&bar->tfull[pacc], puse, abort_flag, lane)) return false;
       ptx::tc_fence_after();
-      drain_tile(inst_of(a, prev_inst), prev_p0, tmem_base, pacc, q, row, strm, prev_ep);
+      drain_tile<NDIG>(inst_of(a, prev_inst), prev_p0, tmem_base, pacc, q, row, strm, prev_ep);
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&bar->tempty[pacc]);
@@ -395,11 +405,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         ep = bad ? kNonFiniteRow : scale_exponent(mx);
       }
       const bool zero_row = ep == kNonFiniteRow;
-      const int shift = kBeta * kDig - (zero_row ? 0 : ep);
+      const int shift = K::Beta * NDIG - (zero_row ? 0 : ep);
 
       int unit = 0;  // this stream's next unit; its global unit is kStreams unit + strm
-      uint32_t w[kDig][4];
-      uint8_t* sA = smem + stage * kStageBytes;
+      uint32_t w[NDIG][4];
+      uint8_t* sA = smem + stage * K::StageBytes;
       // This stream's next unit in shared memory (its byte offset within digit tile 0), opening
       // the stage at the stream's first unit in it (slot below kStreams: the stream's previous
       // unit lies in the stage before): waiting for the stage to be free, stream 0 starting its
@@ -409,11 +419,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         const int slot = g & 3;                 // unit slot within the stage (0..3)
         if (slot < kStreams) {
           if (!warp_wait(&bar->empty[stage], sphase ^ 1u, abort_flag, lane)) return -1;
-          sA = smem + stage * kStageBytes;
+          sA = smem + stage * K::StageBytes;
           if (warp == 0 && lane == 0) {
             const int kc = g >> 2;
-            ptx::mbar_arrive_expect_tx(&bar->bfull[stage], kFusedBChunk);
-            ptx::bulk_g2s(sA + kABytes + kBCopyOffset, d.bdig + (size_t)kc * kFusedBChunk, kFusedBChunk,
+            ptx::mbar_arrive_expect_tx(&bar->bfull[stage], K::BCopyBytes);
+            ptx::bulk_g2s(sA + K::ABytes + K::BCopyOffset, d.bdig + (size_t)kc * kFusedBChunk, K::BCopyBytes,
                           &bar->bfull[stage]);
             if (stage == 0) ++b_issued0;
             else ++b_issued1;
@@ -440,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
         const int off = open_unit();
         if (off < 0) return false;
 #pragma unroll
-        for (int t = 0; t < kDig; ++t)
+        for (int t = 0; t < NDIG; ++t)
           *reinterpret_cast<uint4*>(sA + t * kASlice + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
         finish_unit();
         return true;
@@ -449,12 +459,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       // the two values' bf16 patterns joined into one 32-bit word.
       auto put_pair_const = [&](auto word_c, double z0, double z1) {
         constexpr int word = decltype(word_c)::value;
-        const long long Y0 = (zero_row ? 0 : to_fixed_trunc(z0, shift)) + kBias;
-        const long long Y1 = (zero_row ? 0 : to_fixed_trunc(z1, shift)) + kBias;
-        uint32_t pw[kDig];
-        digit_pair_biased(Y0, Y1, pw);
+        const long long Y0 = (zero_row ? 0 : to_fixed_trunc(z0, shift)) + K::Bias;
+        const long long Y1 = (zero_row ? 0 : to_fixed_trunc(z1, shift)) + K::Bias;
+        uint32_t pw[NDIG];
+        digit_pair_biased<NDIG>(Y0, Y1, pw);
 #pragma unroll
-        for (int t = 0; t < kDig; ++t) w[t][word] = pw[t];
+        for (int t = 0; t < NDIG; ++t) w[t][word] = pw[t];
       };
       // The walk of this stream's columns (Sec. 2 recursion in the plan's rescaled form, Algorithm
       // 1's column order within the stream).  The recursion runs uniformly from the seeds
@@ -568,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
                 }
               } else {
 #pragma unroll
-                for (int t = 0; t < kDig; ++t) w[t][i] = 0u;
+                for (int t = 0; t < NDIG; ++t) w[t][i] = 0u;
               }
             };
             one(std::integral_constant<int, 0>{});
@@ -602,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
                 put_pair_const(ic, z0, z1);
               } else {
 #pragma unroll
-                for (int t = 0; t < kDig; ++t) w[t][i] = 0u;
+                for (int t = 0; t < NDIG; ++t) w[t][i] = 0u;
               }
             };
             two(std::integral_constant<int, 0>{});
@@ -634,10 +644,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
                 return;
               }
             }
-            uint32_t pw[kDig];
-            digit_pair(zero_row ? 0 : to_fixed_trunc(pending, shift), zero_row ? 0 : to_fixed_trunc(z, shift), pw);
+            uint32_t pw[NDIG];
+            digit_pair<NDIG>(zero_row ? 0 : to_fixed_trunc(pending, shift), zero_row ? 0 : to_fixed_trunc(z, shift), pw);
 #pragma unroll
-            for (int t = 0; t < kDig; ++t) *reinterpret_cast<uint32_t*>(sA + t * kASlice + off + kin * 2) = pw[t];
+            for (int t = 0; t < NDIG; ++t) *reinterpret_cast<uint32_t*>(sA + t * kASlice + off + kin * 2) = pw[t];
             kin += 2;
             if (kin == 8) {
               kin = 0;
@@ -661,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
       }
       // Zero units up to the tile's unit count (the same for every stream, whole stages).
 #pragma unroll
-      for (int t = 0; t < kDig; ++t) w[t][0] = w[t][1] = w[t][2] = w[t][3] = 0u;
+      for (int t = 0; t < NDIG; ++t) w[t][0] = w[t][1] = w[t][2] = w[t][3] = 0u;
       const int my_units = (d.units - strm + kStreams - 1) / kStreams;
       while (ok && unit < my_units) ok = store_unit();
       // Drain the previous tile's accumulator now that this one is on its way.
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(FM, kAccCols);
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(FM, K::AccCols);
       int stage = 0;
       uint32_t phase = 0;
       int64_t local = 0;
@@ -710,16 +720,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_emu_kernel(FusedArgs a) {
             break;
           }
           ptx::tc_fence_after();
-          const uint32_t sA = ptx::smem_u32(smem + stage * kStageBytes);
-          const uint32_t sB = sA + kABytes;
+          const uint32_t sA = ptx::smem_u32(smem + stage * K::StageBytes);
+          const uint32_t sB = sA + K::ABytes;
 #pragma unroll
           for (int ks = 0; ks < FBK / 16; ++ks) {
 #pragma unroll
-            for (int t = 0; t < kDig; ++t) {
+            for (int t = 0; t < NDIG; ++t) {
               // A digit t+1 times the coefficient digits shifted down by t blocks: block
               // (t+1) + u - 2 of the accumulator (diagonal t+1+u) receives a_{t+1} b_u.
               const uint64_t adesc = ptx::sw_kmajor_desc<kRowBytes>(sA + t * kASlice + ks * 32);
-              const uint64_t bdesc = ptx::sw_kmajor_desc<kRowBytes>(sB + (kDig - 1 - t) * kBBlock + ks * 32);
+              const uint64_t bdesc = ptx::sw_kmajor_desc<kRowBytes>(sB + (NDIG - 1 - t) * kBBlock + ks * 32);
               ptx::mma_bf16(d_tmem, adesc, bdesc, idesc, (kc == 0 && ks == 0 && t == 0) ? 0u : 1u);
             }
           }
@@ -795,8 +805,10 @@ __global__ void __launch_bounds__(256) fused_cexp_kernel(FusedArgs a, int64_t n_
 
 // Coefficient digits in the fused layout's K order (the plan's slot order, each column padded to
 // a multiple of 8 positions): thread = (chunk, set, group of 8 positions); the
-// 8 values' 11 digits are written as one 16-byte unit into each digit block's row for the set.
+// 8 values' NDIG digits are written as one 16-byte unit into each digit block's row for the set.
+template <int NDIG>
 __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int32_t* chunk_inst, int64_t n_chunks) {
+  using K = FK<NDIG>;
   const int64_t total = n_chunks * FNS * (FBK / 8);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t g = i / (FNS * (FBK / 8));
@@ -815,20 +827,20 @@ __global__ void __launch_bounds__(256) fused_coeff_kernel(FusedArgs a, const int
       const int32_t slot = (use && k < d.Kp) ? __ldg(d.kperm + k) : -1;
       if (slot >= 0) {
         const int64_t j = (int64_t)((uint32_t)__ldg(d.slot_idx + slot) & 0x7fffffffu);
-        X[e] = to_fixed(mode_weight(d, j) * d.coeffs[j * d.S + s], kBeta * kDig - ec);
+        X[e] = to_fixed(mode_weight(d, j) * d.coeffs[j * d.S + s], K::Beta * NDIG - ec);
       }
     }
-    uint32_t w[kDig][4];
+    uint32_t w[NDIG][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      uint32_t pw[kDig];
-      digit_pair(X[2 * e], X[2 * e + 1], pw);
+      uint32_t pw[NDIG];
+      digit_pair<NDIG>(X[2 * e], X[2 * e + 1], pw);
 #pragma unroll
-      for (int t = 0; t < kDig; ++t) w[t][e] = pw[t];
+      for (int t = 0; t < NDIG; ++t) w[t][e] = pw[t];
     }
     uint8_t* chunk = d.bdig + (size_t)kc * kFusedBChunk;
 #pragma unroll
-    for (int t = 0; t < kDig; ++t)
+    for (int t = 0; t < NDIG; ++t)
       *reinterpret_cast<uint4*>(chunk + ptx::sw_offset_b16<kRowBytes>((uint32_t)(t * FNS + s), (uint32_t)(q * 8))) =
           make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
   }
@@ -848,34 +860,54 @@ int fused_ep_for(const zp_plan* plan, int vk) {
   return plan->fused_ep + extra;
 }
 
+namespace {
+template <int NDIG>
+cudaError_t fused_set_smem() {
+  constexpr int smem = (int)FK<NDIG>::Smem;
+  cudaError_t e = cudaFuncSetAttribute(fused_emu_kernel<VK_Z, NDIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_emu_kernel<VK_DTHETA, NDIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_emu_kernel<VK_DRHO, NDIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+template <int NDIG>
+void fused_launch_ndig(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks, int sms,
+                       cudaStream_t stream, int vk, bool coeff_digits) {
+  constexpr uint32_t smem = FK<NDIG>::Smem;
+  if (coeff_digits) {
+    fused_cexp_kernel<<<(unsigned)n_inst, 256, 0, stream>>>(a, n_inst);
+    const int64_t threads = n_chunks * FNS * (FBK / 8);
+    fused_coeff_kernel<NDIG><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 8 * (int64_t)sms)),
+                               256, 0, stream>>>(a, chunk_inst, n_chunks);
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, sms);
+  if (vk == kFusedDTheta) fused_emu_kernel<VK_DTHETA, NDIG><<<grid, kThreads, smem, stream>>>(a);
+  else if (vk == kFusedDRho) fused_emu_kernel<VK_DRHO, NDIG><<<grid, kThreads, smem, stream>>>(a);
+  else fused_emu_kernel<VK_Z, NDIG><<<grid, kThreads, smem, stream>>>(a);
+}
+}  // namespace
+
 zp_status fused_launch(const FusedArgs& a, int64_t n_inst, const int32_t* chunk_inst, int64_t n_chunks,
                        cudaStream_t stream, int vk, bool coeff_digits) {
   if (a.n_items == 0) return ZP_OK;
   if (vk != kFusedZ && vk != kFusedDTheta && vk != kFusedDRho) return set_error(ZP_ERR_INVALID_ARG, "fused value kind");
+  if (a.ndig != kFusedDigits && a.ndig != kFusedDigitsShort) return set_error(ZP_ERR_INVALID_ARG, "fused digit count");
   static DeviceMemo<int> sms_memo;
   int sms = 0;
   ZP_TRY(sms_memo.get(&sms, [](int* x) -> zp_status {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(x, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_emu_kernel<VK_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_emu_kernel<VK_DTHETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_emu_kernel<VK_DRHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess) e = fused_set_smem<kFusedDigits>();
+    if (e == cudaSuccess) e = fused_set_smem<kFusedDigitsShort>();
     return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused kernel set-up");
   }));
-  if (coeff_digits) {
-    fused_cexp_kernel<<<(unsigned)n_inst, 256, 0, stream>>>(a, n_inst);
-    const int64_t threads = n_chunks * FNS * (FBK / 8);
-    fused_coeff_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 8 * (int64_t)sms)),
-                         256, 0, stream>>>(a, chunk_inst, n_chunks);
-  }
-  const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, sms);
-  if (vk == kFusedDTheta) fused_emu_kernel<VK_DTHETA><<<grid, kThreads, kSmem, stream>>>(a);
-  else if (vk == kFusedDRho) fused_emu_kernel<VK_DRHO><<<grid, kThreads, kSmem, stream>>>(a);
-  else fused_emu_kernel<VK_Z><<<grid, kThreads, kSmem, stream>>>(a);
+  if (a.ndig == kFusedDigitsShort)
+    fused_launch_ndig<kFusedDigitsShort>(a, n_inst, chunk_inst, n_chunks, sms, stream, vk, coeff_digits);
+  else
+    fused_launch_ndig<kFusedDigits>(a, n_inst, chunk_inst, n_chunks, sms, stream, vk, coeff_digits);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ZP_OK : cuda_error(e, "fused series launch");
 }
@@ -926,6 +958,7 @@ zp_status fused_series_eval(const zp_plan* plan, const double* r, const double* 
   d.bdig = (uint8_t*)buf.ptr;
   d.cexp = (int*)((uint8_t*)buf.ptr + bbytes);
   a.n_items = (P + FM - 1) / FM;
+  a.ndig = fused_digits_for(plan->fused_kpad);
   return fused_launch(a, 1, nullptr, d.KC, stream);
 }
 
@@ -944,6 +977,7 @@ zp_status fused_point_grads(const zp_plan* plan, const double* r, const double* 
   d.bdig = (uint8_t*)buf.ptr;
   d.cexp = (int*)((uint8_t*)buf.ptr + bbytes);
   a.n_items = (P + FM - 1) / FM;
+  a.ndig = fused_digits_for(plan->fused_kpad);
   bool digits = true;  // the coefficient digits once, for the first pass
   for (int k = 0; k < 2; ++k) {
     double* g = k == 0 ? grad_theta : grad_r;

@@ -8,29 +8,43 @@
 
 namespace zp {
 
-constexpr int kFusedBeta = 5;       // bits per digit
+constexpr int kFusedBeta = 5;       // bits per digit (the long-contraction shape)
 constexpr int kFusedDigits = 11;    // digits per value: 55 fraction bits
 constexpr int kFusedMaxSets = 16;   // coefficient sets per launch
 // Longest contraction (K positions of the fused layout, padding included) whose diagonal sums
 // stay exact integers in float32: K * 2^(2 beta) * (1 + (digits - 2) / 4) < 2^24.
 constexpr int64_t kFusedMaxModes = 5041;
-// Bytes of one 32-mode chunk of coefficient digits: 11 digit blocks of 16 sets x 64 bytes, each
-// row the tensor core's 64-byte swizzled K-major layout.
+// Short contractions take 9 digits of 6 bits (54 fraction bits): K * 2^12 * (1 + 7 / 4) < 2^24
+// for K <= 1489, and two digits fewer to cut, multiply and recombine per value.
+constexpr int kFusedDigitsShort = 9;
+constexpr int64_t kFusedMaxModesShort = 1489;
+// Digits per value for a launch whose longest contraction has `kpad` positions.
+inline int fused_digits_for(int64_t kpad) { return kpad <= kFusedMaxModesShort ? kFusedDigitsShort : kFusedDigits; }
+// Bits per digit of the NDIG-digit shape.
+__host__ __device__ constexpr int fused_beta(int ndig) { return ndig == kFusedDigitsShort ? 6 : kFusedBeta; }
+// Bytes between consecutive 32-mode chunks of coefficient digits: room for 11 digit blocks of 16
+// sets x 64 bytes (each row the tensor core's 64-byte swizzled K-major layout); the 9-digit shape
+// uses the first 9 blocks of each chunk.
 constexpr uint32_t kFusedBChunk = (uint32_t)kFusedDigits * kFusedMaxSets * 64u;
 
-// Balanced base-32 digits of a fixed-point value X (|X| < 2^55), most significant first:
-// Y = X + fused_bias() holds, for the 10 low positions, the unsigned fields f_t = d_t + 16 of
-// the balanced digits d_t in [-16, 16); the most significant digit is Y >> 50 itself (at most
-// 33 in magnitude), so that X = sum_t d_t 2^(5 (10 - t)) with d_0 the top digit.
+// Balanced base-2^beta digits of a fixed-point value X (|X| < 2^(beta NDIG)), most significant
+// first: Y = X + fused_bias<NDIG>() holds, for the NDIG - 1 low positions, the unsigned fields
+// f_t = d_t + 2^(beta-1) of the balanced digits d_t in [-2^(beta-1), 2^(beta-1)); the most
+// significant digit is Y >> (beta (NDIG - 1)) itself (at most 2^beta + 1 in magnitude), so that
+// X = sum_t d_t 2^(beta (NDIG - 1 - t)) with d_0 the top digit.
+template <int NDIG = kFusedDigits>
 __host__ __device__ constexpr long long fused_bias() {
+  constexpr int beta = fused_beta(NDIG);
   long long b = 0;
-  for (int t = 0; t < kFusedDigits - 1; ++t) b += (long long)(1 << (kFusedBeta - 1)) << (kFusedBeta * t);
+  for (int t = 0; t < NDIG - 1; ++t) b += (long long)(1 << (beta - 1)) << (beta * t);
   return b;
 }
 // Digit t of the biased word Y: t = 0 the signed top digit, else the unsigned field.
+template <int NDIG = kFusedDigits>
 __host__ __device__ inline int fused_digit_field(long long Y, int t) {
-  return t == 0 ? (int)(Y >> (kFusedBeta * (kFusedDigits - 1)))
-                : (int)((unsigned long long)(Y >> (kFusedBeta * (kFusedDigits - 1 - t))) & 31u);
+  constexpr int beta = fused_beta(NDIG);
+  return t == 0 ? (int)(Y >> (beta * (NDIG - 1)))
+                : (int)((unsigned long long)(Y >> (beta * (NDIG - 1 - t))) & ((1u << beta) - 1u));
 }
 
 // One series instance of the fused kernel (device pointers).
@@ -87,6 +101,7 @@ struct FusedArgs {
   const FusedInst* insts = nullptr;
   const FusedItem* items = nullptr;
   int64_t n_items = 0;
+  int ndig = kFusedDigits;  // digits per value: fused_digits_for(the largest instance's Kp)
   FusedInst single;
 };
 

@@ -78,3 +78,33 @@ def test_digits_against_exact_arithmetic(driver):
         assert sum(d << (beta * (s - 1 - t)) for t, d in enumerate(got)) == x
         assert all(-(1 << (beta - 1)) <= d < (1 << (beta - 1)) for d in got[1:])
         assert abs(got[0]) <= (1 << beta) + 1
+
+
+def test_short_shape_bounds_and_digits(driver):
+    """The 9-digit shape (6-bit digits) for contractions of at most 1489 positions: at least 54
+    fraction bits, diagonal sums below 2^24 up to the limit and not one position beyond, Horner
+    chains (4 and 5 diagonals) within int64, the shape chosen exactly up to the limit, and its
+    digits against exact arithmetic."""
+    beta, s, max_modes, bias, at_limit, past_limit = (int(v) for v in run(driver, "c9\n")[0].split())
+    assert (beta, s) == (6, 9) and beta * s >= 54
+    assert bias == sum((1 << (beta - 1)) << (beta * t) for t in range(s - 1))
+    # the last kept diagonal (t + u = s + 1) holds two pairs with a top digit (|a_1| <= 2^beta)
+    # and s - 2 pairs of lower digits (< 2^(beta-1) in magnitude)
+    per_k = 2 * (1 << beta) * (1 << (beta - 1)) + (s - 2) * (1 << (beta - 1)) ** 2
+    assert max_modes * per_k < 1 << 24 <= (max_modes + 1) * per_k
+    assert (at_limit, past_limit) == (9, 11)
+    split = 4
+    hi = sum((1 << 24) << (beta * (split - 1 - i)) for i in range(split))
+    lo = sum((1 << 24) << (beta * (s - split - 1 - i)) for i in range(s - split))
+    assert hi < 1 << 63 and lo < 1 << 63
+    rng = random.Random(12)
+    lim = 1 << (beta * s)
+    xs = [0, 1, -1, 31, 32, -32, -33, lim - 1, -(lim - 1), lim, -lim, 98765432109876]
+    xs += [rng.randrange(-lim, lim + 1) for _ in range(3000)]
+    out = run(driver, "".join(f"d9 {x}\n" for x in xs))
+    for x, line in zip(xs, out):
+        got = [int(v) for v in line.split()]
+        assert got == balanced_digits(x, beta, s), x
+        assert sum(d << (beta * (s - 1 - t)) for t, d in enumerate(got)) == x
+        assert all(-(1 << (beta - 1)) <= d < (1 << (beta - 1)) for d in got[1:])
+        assert abs(got[0]) <= (1 << beta) + 1

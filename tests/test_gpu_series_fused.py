@@ -222,3 +222,32 @@ def test_batched_512_fused_full_size_sampled():
     want = np.array(oseries.series_eval(x.n, x.m, x.r[rows], x.theta[rows], x.coeffs.tolist()))
     tol = 1e-13 * (1.0 + abs_bound(x.n, x.m, x.r[rows], x.theta[rows], x.coeffs))
     assert (np.abs(b.instances[17]["out"][rows].cpu().numpy() - want) <= tol).all()
+
+
+@pytest.mark.parametrize("nmax", [49, 50])
+def test_fused_on_both_sides_of_the_short_digit_shape(nmax):
+    """n <= 49 (1472 padded positions) takes 9 digits of 6 bits, n <= 50 (1504) 11 digits of 5
+    bits: both against the DGEMM baseline within the float64 bound, forward and the adjoint's
+    fused point gradients, with coefficients that fill the digit range."""
+    ns, ms = inputs.full_zernike_modes(nmax)
+    r, th = inputs.sqrt_uniform_points(2000, 60 + nmax)
+    r[:3] = [1.0, 0.999, 0.0]
+    C = np.random.default_rng(nmax).standard_normal((len(ns), 16))
+    rt, tt, Ct = dev(r), dev(th), dev(C)
+    plan = zp.Plan(ns, ms)
+    F = zp.series_eval(None, None, rt, tt, Ct, "fp64emu", plan=plan)
+    Fd = zp.series_eval(None, None, rt, tt, Ct, "fp64", plan=plan)
+    check_waits()
+    Z = zp.basis(None, None, rt, tt, 0, plan=plan)[0][0].abs()
+    bound = 1e-13 * (1.0 + Z.T @ Ct.abs())
+    assert bool(((F - Fd).abs() <= bound).all())
+    G = dev(np.random.default_rng(nmax + 1).standard_normal((len(r), 16)))
+    _, gr, gt = zp.series_adjoint(None, None, rt, tt, Ct, G, need=(False, True, True), plan=plan, prec="fp64emu")
+    _, wr, wt = zp.series_adjoint(None, None, rt, tt, Ct, G, need=(False, True, True), plan=plan, prec="fp64")
+    check_waits()
+    # |dZ_j/drho| <= n_j^2 (Markov) and |dZ_j/dtheta| <= |m_j| <= n_j on the disc: per point,
+    # sum_s |G[p][s]| sum_j n_j^2 |C[j][s]| bounds the terms either gradient sums
+    w = dev((np.asarray(ns, dtype=np.float64) ** 2)[:, None] * np.abs(C)).sum(0)
+    scale = 1.0 + G.abs() @ w
+    assert bool(((gr - wr).abs() <= 1e-13 * scale).all())
+    assert bool(((gt - wt).abs() <= 1e-13 * scale).all())

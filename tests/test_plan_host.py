@@ -184,6 +184,20 @@ def test_fused_layout(driver):
     check_fused_layout(plan)
 
 
+def test_fused_padded_lengths_around_the_short_digit_shape(driver):
+    """The fused kernel cuts values into 9 digits of 6 bits when the padded contraction has at
+    most 1489 positions, else 11 of 5 bits: the full sets n <= 49 (1275 modes, 1472 positions)
+    and n <= 50 (1326 modes, 1504 positions) fall on either side, which the GPU tests rely on."""
+    kp = {}
+    for nmax in (49, 50):
+        ns = [n for n in range(nmax + 1) for m in range(-n, n + 1, 2)]
+        ms = [m for n in range(nmax + 1) for m in range(-n, n + 1, 2)]
+        st, plan = build(driver, ns, ms)
+        assert st == 0
+        kp[nmax] = plan["fused"]["kpad"]
+    assert kp[49] <= 1489 < kp[50]
+
+
 @pytest.mark.parametrize("n,m", [(3, 2), (-1, 1), (2, 3), (1001, 1)])
 def test_plan_rejects_invalid_modes(driver, n, m):
     st, _ = build(driver, [4, n], [0, m])
