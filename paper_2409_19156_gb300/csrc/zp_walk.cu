@@ -294,11 +294,13 @@ __global__ void __launch_bounds__(TPB) walk_kernel(WalkArgs a) {
   store_step(0, T);
   if (col.n_steps < 2) return;
   store_step(1, S);
-  // Derivative walks take eight steps per iteration: the independent float64 chains of the
-  // unrolled steps overlap their latencies (radial n <= 100, k <= 3, one million points:
-  // 6.58 ms with one step, 6.48 with two, 6.34 with four, 6.29 with eight; no spills).  The
-  // value-only walk keeps one step: unrolled by two or four it measured 8 % slower.
-#pragma unroll(KMAX >= 1 ? 8 : 1)
+  // Derivative walks of the 128-thread form take eight steps per iteration: the independent
+  // float64 chains of the unrolled steps overlap their latencies (radial n <= 100, k <= 3,
+  // 100000 points: 6.58 ms with one step, 6.48 with two, 6.34 with four, 6.29 with eight; no
+  // spills).  The value-only walk keeps one step (unrolled by two or four it measured 8 %
+  // slower), and so do the short launches' 32-thread blocks (latency-bound; unrolling them only
+  // adds compile time).
+#pragma unroll((KMAX >= 1 && TPB == kThreads) ? 8 : 1)
   for (int N = 2; N < col.n_steps; ++N) {
     const double* row = tab + (size_t)(kHeaderRows + N) * kRow;
     const double A = row[0], B = row[1], A2 = row[2], zero = row[7];
