@@ -173,7 +173,13 @@ ZP_API zp_status zp_radial_per_mode(const zp_plan* plan, const double* r, int64_
  * from the library's scratch pool, see zp_release_scratch, and released to it before return)
  * and contracts with cuBLAS DGEMM.  The split forms run the float64 recursion into
  * tensor-core operand tiles in scratch (slabs of whole waves of point tiles) and contract them
- * with tcgen05 MMAs and float32 accumulation.
+ * with tcgen05 MMAs and float32 accumulation.  ZP_PREC_FP64_EMULATED with n_sets <= 16 and at
+ * most 5041 padded modes builds the basis inside the tensor-core kernel (no basis in memory):
+ * each value Q_N cos/sin(m theta) is scaled by one power of two per point (on the unit disc
+ * the plan's bound on |Z| over its smallest recursion weight; off the disc the point's own
+ * largest value) and cut into 11 digits of 5 bits, or 9 of 6 bits when the padded modes are
+ * at most 1489 (54 or 55 fraction bits: the error bound above with that power of two in place
+ * of max_j |Z[j][p]|).
  */
 ZP_API zp_status zp_series_eval(const int32_t* n, const int32_t* m, int64_t n_modes,
                          const double* r, const double* theta, int64_t n_points,
